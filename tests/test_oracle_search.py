@@ -137,6 +137,13 @@ def test_extension_drop_equal_to_x_continues():
     rq = "GATTACAGAT" + "AAAAAA" + m30
     rs = "GATTACAGAT" + "TTTTTT" + m30
     assert _ext_case("", "", core, rq, rs, p) == (0, 32, 0, 32)
+    # the same on the left end (flanks read right to left from the core)
+    lq = m30 + "AAAAA" + "GATTACAGAT"
+    ls = m30 + "TTTTT" + "GATTACAGAT"
+    assert _ext_case(lq, ls, core, "", "", p) == (0, 45 + 22, 0, 45 + 22)
+    lq = m30 + "AAAAAA" + "GATTACAGAT"
+    ls = m30 + "TTTTTT" + "GATTACAGAT"
+    assert _ext_case(lq, ls, core, "", "", p) == (36, 36 + 32, 36, 36 + 32)
 
 
 def test_extension_first_best_and_left_side():
@@ -168,6 +175,10 @@ def test_overlap_merge_hand_cases():
     assert m([(0, 0, 10, 0, 10), (0, 5, 15, 50, 60)]) == [(0, 0, 10, 0, 10), (0, 5, 15, 50, 60)]
     # half-open ranges that only touch do not intersect
     assert m([(0, 0, 10, 0, 10), (0, 10, 20, 10, 20)]) == [(0, 0, 10, 0, 10), (0, 10, 20, 10, 20)]
+    # query ranges only touch while bank ranges overlap -> still two boxes (both must intersect)
+    assert m([(0, 0, 10, 0, 10), (0, 10, 20, 5, 15)]) == [(0, 0, 10, 0, 10), (0, 10, 20, 5, 15)]
+    # bank ranges only touch while query ranges overlap -> two boxes
+    assert m([(0, 0, 10, 0, 10), (0, 5, 15, 10, 20)]) == [(0, 0, 10, 0, 10), (0, 5, 15, 10, 20)]
     # different bank sequences never merge
     assert m([(1, 0, 10, 0, 10), (0, 0, 10, 0, 10)]) == [(0, 0, 10, 0, 10), (1, 0, 10, 0, 10)]
     # a third HSP that meets only the union of the first two still joins it
@@ -247,6 +258,13 @@ def test_sw_hand_cases():
     t = s[:100] + s[101:]
     assert oracle.banded_sw(s, t, (0, 200, 0, 199), wide)[0] == 192
     assert oracle.banded_sw(t, s, (0, 199, 0, 200), wide)[0] == 192
+    # a 3-base deletion in either sequence: 197 matches and one gap of 3: 197 - (5 + 3*2) = 186
+    t3 = s[:100] + s[103:]
+    assert oracle.banded_sw(s, t3, (0, 200, 0, 197), wide)[0] == 186
+    assert oracle.banded_sw(t3, s, (0, 197, 0, 200), wide)[0] == 186
+    # the DP window reaches w rows and columns beyond the HSP: an HSP given as [50, 150) on an
+    # identical pair yields the alignment [34, 166) with w = 16
+    assert oracle.banded_sw(s, s, (50, 150, 50, 150), P) == (132, 34, 166, 34, 166)
     # equal-score alignments: the one ending at the smallest query end, then smallest bank end
     assert oracle.banded_sw("ACG", "ACGTTTTTACG", (0, 3, 0, 11), wide) == (3, 0, 3, 0, 3)
 
