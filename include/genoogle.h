@@ -1,0 +1,207 @@
+/*
+ * genoogle.h - C ABI of the GB300 (sm_103a) implementation of the Genoogle
+ * search path: indexed search of DNA queries against a sequence bank
+ * (F. F. Albrecht, "Genoogle: an indexed and parallelized search engine for
+ * similar DNA sequences", arXiv 1507.02987).
+ *
+ * Conventions
+ *  - All functions return gn_status; GN_OK is 0.  On failure gn_last_error()
+ *    returns a message for the calling thread (valid until its next call).
+ *  - Handles (gn_index, gn_results, gn_server) are opaque and owned by the
+ *    library; free them with the matching gn_*_free / gn_serve_stop.
+ *  - Inputs are copied (host inputs) or only read (device inputs) during the
+ *    call; the caller keeps ownership of every pointer it passes.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    work of a call is ordered on that stream; the call returns after the
+ *    stream has finished the call's work unless stated otherwise.
+ *  - Positions are 0-based; ranges are half-open [start, end).
+ *  - Bases are ASCII.  A, C, G, T (and U, read as T) in either case are bases;
+ *    anything else (N, IUPAC codes) is a non-base: windows holding one are
+ *    neither indexed nor looked up, and it scores as a mismatch against
+ *    everything in extension and alignment.
+ *  - Limits: bank < 2^32 bases in total; query length < 65,536 bases; at most
+ *    65,536 queries per gn_search call; k in 1..16; stride >= 1.
+ */
+#ifndef GENOOGLE_H
+#define GENOOGLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GN_OK = 0,
+    GN_EINVAL = 1,    /* invalid argument (k, stride, lengths, null pointers, ...) */
+    GN_ENOMEM = 2,    /* device or host allocation failed */
+    GN_ECUDA = 3,     /* a CUDA call or a kernel-side check failed */
+    GN_ETIMEOUT = 4,  /* a bounded wait ran out (serving poll, device waits) */
+    GN_EBUSY = 5,     /* the server is stopping or its queue is full */
+    GN_ETOOBIG = 6,   /* the request exceeds a documented limit or the memory budget */
+    GN_EINTERNAL = 7  /* broken internal invariant (a bug) */
+} gn_status;
+
+typedef enum { GN_MEM_HOST = 0, GN_MEM_DEVICE = 1 } gn_memory;
+
+/* A sequence bank: sequence s is bases[seq_start[s] .. seq_start[s+1]).
+ * seq_start (n_seqs + 1 entries, non-decreasing) is always host memory;
+ * bases lives where bases_mem says. */
+typedef struct {
+    uint32_t n_seqs;
+    const uint64_t *seq_start;
+    const char *bases;
+    gn_memory bases_mem;
+} gn_bank;
+
+/* Queries back to back: query i is bases[start[i] .. start[i+1]).  start is host
+ * memory; bases lives where bases_mem says. */
+typedef struct {
+    uint32_t n;
+    const uint64_t *start;
+    const char *bases;
+    gn_memory bases_mem;
+} gn_queries;
+
+/* Scores (the paper states none; defaults +1, -3, -5, -2).  A gap of length g
+ * scores gap_open + g * gap_extend.  lambda and K are the Karlin-Altschul
+ * parameters used for the e-value and the bit ("normalized") score. */
+typedef struct {
+    int32_t match, mismatch, gap_open, gap_extend;
+    double lambda, K;
+} gn_scoring;
+
+/* Run-time parameters ("Methods" section: maximum distance between index
+ * entries of one HSP, minimum HSP length, drop-off of the extension; "Searching
+ * process": maximum quantity of alignments; band of the modified
+ * Smith-Waterman). */
+typedef struct {
+    uint32_t max_hit_distance; /* D: largest query-offset gap between hits of one HSP; 0 = 3 * stride */
+    uint32_t min_hsp_len;      /* HSPs shorter than this are dropped; 0 = 2 * k */
+    int32_t xdrop;             /* extension stops once the score is more than xdrop below its best */
+    uint32_t max_alignments;   /* per query, longest HSPs first; 0 = all */
+    uint32_t band_w;           /* band half-width w of the alignment */
+    double max_evalue;         /* report alignments with e-value <= this (INFINITY = all) */
+    uint32_t flags;            /* GN_FLAG_* */
+} gn_params;
+
+#define GN_FLAG_KEEP_STAGES 1u  /* keep every phase's output in the results (tests, debugging) */
+#define GN_FLAG_KEEP_HITS 2u    /* also keep the sorted hit list (small inputs only) */
+
+/* One reported alignment. */
+typedef struct {
+    uint32_t query;     /* index of the query in the call */
+    uint32_t seq;       /* bank sequence id */
+    uint32_t q_start, q_end;
+    uint32_t db_start, db_end;
+    int32_t score;
+    uint32_t rank;      /* 0 = best alignment of this query */
+    double evalue;
+    double bits;
+} gn_hit;
+
+/* An HSP (stage outputs): query and bank ranges, length = min of the two spans. */
+typedef struct {
+    uint32_t query, seq, q_start, q_end, db_start, db_end, len;
+} gn_hsp;
+
+typedef struct gn_index gn_index;
+typedef struct gn_results gn_results;
+typedef struct gn_server gn_server;
+
+/* Defaults: scoring +1/-3/-5/-2 with lambda = 1.3740631, K = 0.711; params
+ * D = 0 (3 * stride), min_hsp_len = 0 (2k), xdrop = 20, max_alignments = 100,
+ * band_w = 16, max_evalue = INFINITY, flags = 0.  Either pointer may be NULL. */
+gn_status gn_default_params(gn_scoring *scoring, gn_params *params);
+
+/* Builds the inverted index on the device ("Inverted Indexes" section):
+ * 2-bit packing of the bank, non-overlapping windows at offsets 0, stride,
+ * 2*stride, ... of every sequence (a partial tail is dropped; windows never
+ * cross sequences), a histogram over the 4^k buckets, an exclusive scan of it
+ * and a stable scatter that keeps each bucket's occurrences in ascending
+ * (sequence, position) order.  The packed bank and the index stay resident in
+ * device memory until gn_index_free.  k in 1..16, stride >= 1.
+ * Errors: GN_EINVAL (bad k/stride/bank), GN_ETOOBIG (bank >= 2^32 bases),
+ * GN_ENOMEM, GN_ECUDA. */
+gn_status gn_index_build(const gn_bank *db, int k, int stride, void *cuda_stream, gn_index **out);
+void gn_index_free(gn_index *index);
+
+typedef struct {
+    int32_t k, stride;
+    uint32_t n_seqs;
+    uint64_t n_bases;
+    uint64_t n_postings;
+    uint64_t device_bytes; /* device memory held by the index (packed bank + index) */
+} gn_index_info;
+gn_status gn_index_get_info(const gn_index *index, gn_index_info *info);
+
+/* Copies the index to host memory: bucket_start (4^k + 1 entries) and, for each
+ * occurrence, its sequence id and position (n_postings entries each).  Any
+ * pointer may be NULL to skip it.  Intended for tests. */
+gn_status gn_index_export(const gn_index *index, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos);
+
+/* Searches every query against the index ("Searching process", seven phases):
+ * rolling k-mer codes of every query offset; lookup of each code's
+ * occurrences (hits); grouping of the hits by (sequence, diagonal) with a radix
+ * sort and merging of hits at most D query offsets apart into HSPs of length >=
+ * min_hsp_len; X-drop ungapped extension of both HSP ends; merging of
+ * overlapped HSPs; selection of the longest max_alignments HSPs per query;
+ * banded affine-gap Smith-Waterman of each selected HSP; ranking by score with
+ * e-value and bit score.  Queries are independent: results do not depend on
+ * how queries are grouped into calls.  Results are host memory owned by the
+ * library (gn_results_free).  Errors: GN_EINVAL, GN_ETOOBIG (a query >= 65,536
+ * bases or > 65,536 queries), GN_ENOMEM, GN_ECUDA. */
+gn_status gn_search(const gn_index *index, const gn_queries *queries, const gn_scoring *scoring,
+                    const gn_params *params, void *cuda_stream, gn_results **out);
+void gn_results_free(gn_results *results);
+
+/* Ranked alignments of one query (rank order).  *hits stays valid until
+ * gn_results_free. */
+gn_status gn_results_get(const gn_results *results, uint32_t query, const gn_hit **hits, uint32_t *n);
+gn_status gn_results_count(const gn_results *results, uint32_t *n_queries, uint64_t *n_hits);
+
+/* Phase outputs kept with GN_FLAG_KEEP_STAGES (GN_EINVAL otherwise).
+ * Stage ids: GN_STAGE_HSP (HSPs from merged hits), GN_STAGE_EXT (after
+ * extension), GN_STAGE_MERGED (after merging overlapped HSPs),
+ * GN_STAGE_SELECTED (after selection) - gn_hsp records of all queries, in no
+ * particular order; GN_STAGE_ALIGNED - gn_hit records (score and ranges of each
+ * selected HSP's alignment, rank and e-value unset); GN_STAGE_HITS (with
+ * GN_FLAG_KEEP_HITS) - uint32 triples (query offset, sequence id, position) of
+ * every hit, query by query.  GN_STAGE_HIT_COUNTS - uint64 hit count per query. */
+typedef enum {
+    GN_STAGE_HSP = 0, GN_STAGE_EXT = 1, GN_STAGE_MERGED = 2, GN_STAGE_SELECTED = 3,
+    GN_STAGE_ALIGNED = 4, GN_STAGE_HITS = 5, GN_STAGE_HIT_COUNTS = 6
+} gn_stage;
+gn_status gn_results_stage(const gn_results *results, gn_stage stage, const void **data, uint64_t *n);
+
+/* Per-phase device time of the last gn_search on this index handle, in
+ * milliseconds (CUDA events); names[i] is a static string.  Returns the
+ * number of phases written (<= cap). */
+int gn_last_phase_times(const gn_index *index, const char **names, float *ms, int cap);
+
+/* ----------------------------------------------------------- serving ---
+ * Request loop with continuous batching (the paper's web-services interface,
+ * "Implementation" section, as a resident-index service).  A server thread
+ * admits submitted queries while their footprint (hit buffer + alignment
+ * bytes) fits mem_budget, launches them as a micro-batch on one of its streams
+ * while earlier micro-batches still run, and makes each result available to
+ * gn_serve_poll.  Each query's result is identical to a gn_search of that query
+ * alone. */
+gn_status gn_serve_start(const gn_index *index, const gn_scoring *scoring, const gn_params *params,
+                         uint64_t mem_budget, gn_server **out);
+/* Thread-safe; copies the query.  GN_ETOOBIG if the query alone exceeds the budget. */
+gn_status gn_serve_submit(gn_server *server, const char *bases, uint32_t len, uint64_t *ticket);
+/* Waits up to timeout_ms; GN_ETIMEOUT if not done yet.  On GN_OK *out holds a
+ * one-query result owned by the caller (gn_results_free). */
+gn_status gn_serve_poll(gn_server *server, uint64_t ticket, uint32_t timeout_ms, gn_results **out);
+/* Finishes admitted work, rejects new submissions, joins the server thread, frees the server. */
+gn_status gn_serve_stop(gn_server *server);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *gn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENOOGLE_H */

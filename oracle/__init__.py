@@ -113,6 +113,8 @@ def _load():
             lib.or_evalue.argtypes = [i32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Params)]
             lib.or_bits.restype = ctypes.c_double
             lib.or_bits.argtypes = [i32, ctypes.POINTER(_Params)]
+            lib.or_rank.restype = u32
+            lib.or_rank.argtypes = [vp, u32, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Params), vp]
             lib.or_sizeof_result.restype = ctypes.c_size_t
             assert lib.or_sizeof_result() == ctypes.sizeof(_Result)
             _lib = lib
@@ -289,6 +291,18 @@ def merge_overlaps(hsps):
     out = np.zeros(max(len(hsps), 1), dtype=HSP_DTYPE)
     n = lib.or_merge_overlaps(arr.ctypes.data, len(hsps), out.ctypes.data)
     return [tuple(int(x) for x in r)[:5] for r in out[:n]]
+
+
+def rank(alns, m: float, n_bank: float, params: Params):
+    """Phase 7 on a list of (seq, qs, qe, ds, de, score); returns (seq, qs, qe, ds, de, score, rank)."""
+    lib = _load()
+    arr = np.zeros(max(len(alns), 1), dtype=ALN_DTYPE)
+    for i, (seq, qs, qe, ds, de, sc) in enumerate(alns):
+        arr[i]["seq"], arr[i]["qs"], arr[i]["qe"], arr[i]["ds"], arr[i]["de"], arr[i]["score"] = seq, qs, qe, ds, de, sc
+    out = np.zeros(max(len(alns), 1), dtype=ALN_DTYPE)
+    cp = params._c()
+    n = lib.or_rank(arr.ctypes.data, len(alns), float(m), float(n_bank), ctypes.byref(cp), out.ctypes.data)
+    return [tuple(int(r[f]) for f in ("seq", "qs", "qe", "ds", "de", "score", "rank")) for r in out[:n]]
 
 
 def evalue(score: int, m: float, n: float, params: Params) -> float:

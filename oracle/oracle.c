@@ -411,6 +411,36 @@ static int cmp_score(const void *a, const void *b) {
     return 0;
 }
 
+/* "Searching process", phase 7: alignments sorted by score (ties: sequence,
+ * query start, bank start, query end, bank end), alignments with the same
+ * sequence and ranges as an earlier one removed (the earlier, better one is
+ * kept), e-value and bit score attached, e-value cut applied, ranks numbered
+ * from 0.  Writes to out (capacity n); returns the count. */
+uint32_t or_rank(const or_aln *in, uint32_t n, double m, double n_bank, const or_params *p, or_aln *out) {
+    or_aln *all = (or_aln *)malloc(sizeof(or_aln) * (n ? n : 1));
+    uint32_t na = 0;
+    for (uint32_t i = 0; i < n; ++i)
+        if (in[i].score > 0) all[na++] = in[i];
+    qsort(all, na, sizeof(or_aln), cmp_score);
+    uint32_t nr = 0;
+    for (uint32_t i = 0; i < na; ++i) {
+        int dup = 0;
+        for (uint32_t j = 0; j < i && !dup; ++j) {
+            const or_aln *a = &all[j], *b = &all[i];
+            dup = a->seq == b->seq && a->qs == b->qs && a->qe == b->qe && a->ds == b->ds && a->de == b->de;
+        }
+        if (dup) continue;
+        or_aln a = all[i];
+        a.evalue = or_evalue(a.score, m, n_bank, p);
+        a.bits = or_bits(a.score, p);
+        if (!(a.evalue <= p->max_evalue)) continue;
+        a.rank = nr;
+        out[nr++] = a;
+    }
+    free(all);
+    return nr;
+}
+
 /* ------------------------------------------------------------ search --- */
 /* One query through the seven phases of "Searching process". */
 int or_search_one(const or_index *ix, const uint8_t *q, uint32_t m, const or_params *p, or_result *r) {
@@ -449,26 +479,8 @@ int or_search_one(const or_index *ix, const uint8_t *q, uint32_t m, const or_par
     }
     r->n_aln = r->n_sel;
     /* phase 7: best score first, exact duplicates removed, statistics */
-    or_aln *all = (or_aln *)malloc(sizeof(or_aln) * (r->n_aln ? r->n_aln : 1));
-    uint32_t na = 0;
-    for (uint32_t i = 0; i < r->n_aln; ++i)
-        if (r->aln[i].score > 0) all[na++] = r->aln[i];
-    qsort(all, na, sizeof(or_aln), cmp_score);
-    double n_bank = (double)ix->seq_start[ix->n_seqs];
-    uint32_t nr = 0;
-    for (uint32_t i = 0; i < na; ++i) {
-        if (nr > 0) {
-            const or_aln *a = &all[nr - 1], *b = &all[i];
-            if (a->seq == b->seq && a->qs == b->qs && a->qe == b->qe && a->ds == b->ds && a->de == b->de) continue;
-        }
-        or_aln a = all[i];
-        a.evalue = or_evalue(a.score, (double)m, n_bank, p);
-        a.bits = or_bits(a.score, p);
-        if (!(a.evalue <= p->max_evalue)) continue;
-        all[nr++] = a;
-    }
-    for (uint32_t i = 0; i < nr; ++i) all[i].rank = i;
-    r->ranked = all; r->n_ranked = nr;
+    r->ranked = (or_aln *)malloc(sizeof(or_aln) * (r->n_aln ? r->n_aln : 1));
+    r->n_ranked = or_rank(r->aln, r->n_aln, (double)m, (double)ix->seq_start[ix->n_seqs], p, r->ranked);
     return 0;
 }
 

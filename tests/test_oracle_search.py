@@ -325,6 +325,20 @@ def test_evalue_and_bits_identities():
     assert oracle.bits(0, P) == pytest.approx(-math.log2(P.K))
 
 
+def test_rank_order_and_duplicates():
+    """Score descending, ties by (seq, q_start, db_start, q_end, db_end); a record with the same
+    sequence and ranges as an earlier (better) one is dropped even when others sort between them;
+    non-positive scores are dropped; the e-value cut applies after de-duplication."""
+    alns = [(2, 0, 10, 0, 10, 5), (1, 0, 10, 0, 10, 9), (1, 0, 10, 0, 10, 5), (1, 0, 10, 0, 11, 5),
+            (0, 3, 9, 3, 9, 7), (0, 2, 9, 3, 9, 7), (3, 0, 5, 0, 5, 0), (1, 0, 10, 0, 10, 9)]
+    got = oracle.rank(alns, 100, 1000, P)
+    assert got == [(1, 0, 10, 0, 10, 9, 0), (0, 2, 9, 3, 9, 7, 1), (0, 3, 9, 3, 9, 7, 2),
+                   (1, 0, 10, 0, 11, 5, 3), (2, 0, 10, 0, 10, 5, 4)]
+    cut = oracle.evalue(7, 100, 1000, P)
+    got = oracle.rank(alns, 100, 1000, oracle.Params(max_evalue=cut))
+    assert [g[5] for g in got] == [9, 7, 7]
+
+
 # ------------------------------------------------------------ end to end --
 @pytest.fixture(scope="module")
 def tiny():
