@@ -28,6 +28,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define GN_API __attribute__((visibility("default")))
+#else
+#define GN_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -113,7 +119,7 @@ typedef struct gn_server gn_server;
 /* Defaults: scoring +1/-3/-5/-2 with lambda = 1.3740631, K = 0.711; params
  * D = 0 (3 * stride), min_hsp_len = 0 (2k), xdrop = 20, max_alignments = 100,
  * band_w = 16, max_evalue = INFINITY, flags = 0.  Either pointer may be NULL. */
-gn_status gn_default_params(gn_scoring *scoring, gn_params *params);
+GN_API gn_status gn_default_params(gn_scoring *scoring, gn_params *params);
 
 /* Builds the inverted index on the device ("Inverted Indexes" section):
  * 2-bit packing of the bank, non-overlapping windows at offsets 0, stride,
@@ -124,8 +130,8 @@ gn_status gn_default_params(gn_scoring *scoring, gn_params *params);
  * device memory until gn_index_free.  k in 1..16, stride >= 1.
  * Errors: GN_EINVAL (bad k/stride/bank), GN_ETOOBIG (bank >= 2^32 bases),
  * GN_ENOMEM, GN_ECUDA. */
-gn_status gn_index_build(const gn_bank *db, int k, int stride, void *cuda_stream, gn_index **out);
-void gn_index_free(gn_index *index);
+GN_API gn_status gn_index_build(const gn_bank *db, int k, int stride, void *cuda_stream, gn_index **out);
+GN_API void gn_index_free(gn_index *index);
 
 typedef struct {
     int32_t k, stride;
@@ -134,12 +140,12 @@ typedef struct {
     uint64_t n_postings;
     uint64_t device_bytes; /* device memory held by the index (packed bank + index) */
 } gn_index_info;
-gn_status gn_index_get_info(const gn_index *index, gn_index_info *info);
+GN_API gn_status gn_index_get_info(const gn_index *index, gn_index_info *info);
 
 /* Copies the index to host memory: bucket_start (4^k + 1 entries) and, for each
  * occurrence, its sequence id and position (n_postings entries each).  Any
  * pointer may be NULL to skip it.  Intended for tests. */
-gn_status gn_index_export(const gn_index *index, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos);
+GN_API gn_status gn_index_export(const gn_index *index, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos);
 
 /* Searches every query against the index ("Searching process", seven phases):
  * rolling k-mer codes of every query offset; lookup of each code's
@@ -152,14 +158,14 @@ gn_status gn_index_export(const gn_index *index, uint64_t *bucket_start, uint32_
  * how queries are grouped into calls.  Results are host memory owned by the
  * library (gn_results_free).  Errors: GN_EINVAL, GN_ETOOBIG (a query >= 65,536
  * bases or > 65,536 queries), GN_ENOMEM, GN_ECUDA. */
-gn_status gn_search(const gn_index *index, const gn_queries *queries, const gn_scoring *scoring,
+GN_API gn_status gn_search(const gn_index *index, const gn_queries *queries, const gn_scoring *scoring,
                     const gn_params *params, void *cuda_stream, gn_results **out);
-void gn_results_free(gn_results *results);
+GN_API void gn_results_free(gn_results *results);
 
 /* Ranked alignments of one query (rank order).  *hits stays valid until
  * gn_results_free. */
-gn_status gn_results_get(const gn_results *results, uint32_t query, const gn_hit **hits, uint32_t *n);
-gn_status gn_results_count(const gn_results *results, uint32_t *n_queries, uint64_t *n_hits);
+GN_API gn_status gn_results_get(const gn_results *results, uint32_t query, const gn_hit **hits, uint32_t *n);
+GN_API gn_status gn_results_count(const gn_results *results, uint32_t *n_queries, uint64_t *n_hits);
 
 /* Phase outputs kept with GN_FLAG_KEEP_STAGES (GN_EINVAL otherwise).
  * Stage ids: GN_STAGE_HSP (HSPs from merged hits), GN_STAGE_EXT (after
@@ -167,18 +173,19 @@ gn_status gn_results_count(const gn_results *results, uint32_t *n_queries, uint6
  * GN_STAGE_SELECTED (after selection) - gn_hsp records of all queries, in no
  * particular order; GN_STAGE_ALIGNED - gn_hit records (score and ranges of each
  * selected HSP's alignment, rank and e-value unset); GN_STAGE_HITS (with
- * GN_FLAG_KEEP_HITS) - uint32 triples (query offset, sequence id, position) of
- * every hit, query by query.  GN_STAGE_HIT_COUNTS - uint64 hit count per query. */
+ * GN_FLAG_KEEP_HITS) - uint32 quadruples (query, query offset, sequence id,
+ * position) of every hit, in no particular order; GN_STAGE_HIT_COUNTS - uint64
+ * hit count per query. */
 typedef enum {
     GN_STAGE_HSP = 0, GN_STAGE_EXT = 1, GN_STAGE_MERGED = 2, GN_STAGE_SELECTED = 3,
     GN_STAGE_ALIGNED = 4, GN_STAGE_HITS = 5, GN_STAGE_HIT_COUNTS = 6
 } gn_stage;
-gn_status gn_results_stage(const gn_results *results, gn_stage stage, const void **data, uint64_t *n);
+GN_API gn_status gn_results_stage(const gn_results *results, gn_stage stage, const void **data, uint64_t *n);
 
 /* Per-phase device time of the last gn_search on this index handle, in
  * milliseconds (CUDA events); names[i] is a static string.  Returns the
  * number of phases written (<= cap). */
-int gn_last_phase_times(const gn_index *index, const char **names, float *ms, int cap);
+GN_API int gn_last_phase_times(const gn_index *index, const char **names, float *ms, int cap);
 
 /* ----------------------------------------------------------- serving ---
  * Request loop with continuous batching (the paper's web-services interface,
@@ -188,18 +195,18 @@ int gn_last_phase_times(const gn_index *index, const char **names, float *ms, in
  * while earlier micro-batches still run, and makes each result available to
  * gn_serve_poll.  Each query's result is identical to a gn_search of that query
  * alone. */
-gn_status gn_serve_start(const gn_index *index, const gn_scoring *scoring, const gn_params *params,
+GN_API gn_status gn_serve_start(const gn_index *index, const gn_scoring *scoring, const gn_params *params,
                          uint64_t mem_budget, gn_server **out);
 /* Thread-safe; copies the query.  GN_ETOOBIG if the query alone exceeds the budget. */
-gn_status gn_serve_submit(gn_server *server, const char *bases, uint32_t len, uint64_t *ticket);
+GN_API gn_status gn_serve_submit(gn_server *server, const char *bases, uint32_t len, uint64_t *ticket);
 /* Waits up to timeout_ms; GN_ETIMEOUT if not done yet.  On GN_OK *out holds a
  * one-query result owned by the caller (gn_results_free). */
-gn_status gn_serve_poll(gn_server *server, uint64_t ticket, uint32_t timeout_ms, gn_results **out);
+GN_API gn_status gn_serve_poll(gn_server *server, uint64_t ticket, uint32_t timeout_ms, gn_results **out);
 /* Finishes admitted work, rejects new submissions, joins the server thread, frees the server. */
-gn_status gn_serve_stop(gn_server *server);
+GN_API gn_status gn_serve_stop(gn_server *server);
 
 /* Message of the last failing call on this thread ("" if none). */
-const char *gn_last_error(void);
+GN_API const char *gn_last_error(void);
 
 #ifdef __cplusplus
 }

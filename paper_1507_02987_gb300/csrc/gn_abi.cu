@@ -1,0 +1,393 @@
+// gn_abi.cu - the extern "C" boundary: argument checking, error reporting,
+// handle ownership, and the serving loop (continuous batching).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
+#include "gn_internal.cuh"
+
+namespace gn {
+static thread_local std::string g_last_error;
+
+void set_error(gn_status st, const std::string &msg) {
+    (void)st;
+    g_last_error = msg;
+}
+
+template <class F>
+static gn_status guarded(F &&f) {
+    try {
+        f();
+        g_last_error.clear();
+        return GN_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return GN_ENOMEM;
+    } catch (const std::exception &e) {
+        g_last_error = e.what();
+        return GN_EINTERNAL;
+    }
+}
+
+static void resolve(const gn_index *ix, const gn_scoring *sc, const gn_params *pp, SearchOptions &o) {
+    gn_default_params(&o.sc, &o.p);
+    if (sc) o.sc = *sc;
+    if (pp) o.p = *pp;
+    if (o.p.max_hit_distance == 0) o.p.max_hit_distance = 3u * (uint32_t)ix->t;
+    if (o.p.min_hsp_len == 0) o.p.min_hsp_len = 2u * (uint32_t)ix->k;
+    GN_REQUIRE(o.p.xdrop >= 0, GN_EINVAL, "xdrop must be >= 0");
+    GN_REQUIRE(o.p.band_w <= 16384, GN_EINVAL, "band_w must be <= 16384");
+    GN_REQUIRE(o.p.max_hit_distance < 65536, GN_EINVAL, "max_hit_distance must be < 65536");
+    GN_REQUIRE(o.sc.gap_extend <= 0 && o.sc.gap_open <= 0, GN_EINVAL, "gap scores must be <= 0");
+    GN_REQUIRE(o.sc.match > 0 && o.sc.mismatch < 0, GN_EINVAL, "match must be > 0 and mismatch < 0");
+    GN_REQUIRE(o.sc.K > 0 && o.sc.lambda > 0, GN_EINVAL, "lambda and K must be > 0");
+}
+
+static void check_queries(const gn_queries *q) {
+    GN_REQUIRE(q && q->start, GN_EINVAL, "queries and queries.start are required");
+    GN_REQUIRE(q->n <= MAX_QUERIES, GN_ETOOBIG, "at most 65,536 queries per call");
+    GN_REQUIRE(q->start[0] == 0, GN_EINVAL, "queries.start[0] must be 0");
+    for (uint32_t i = 0; i < q->n; ++i) {
+        GN_REQUIRE(q->start[i + 1] >= q->start[i], GN_EINVAL, "queries.start must be non-decreasing");
+        GN_REQUIRE(q->start[i + 1] - q->start[i] <= MAX_QUERY_LEN, GN_ETOOBIG, "a query holds 65,536 bases or more");
+    }
+    GN_REQUIRE(q->start[q->n] == 0 || q->bases, GN_EINVAL, "queries.bases is required");
+}
+
+// ------------------------------------------------------------ serving --
+struct Request {
+    uint64_t ticket;
+    std::string bases;
+    uint64_t footprint;
+};
+
+}  // namespace gn
+
+struct gn_server {
+    const gn_index *ix = nullptr;
+    gn::SearchOptions opt;
+    uint64_t budget = 0;
+    uint64_t in_use = 0;
+    bool stopping = false;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<gn::Request> queue;
+    std::map<uint64_t, gn_results *> done;
+    std::map<uint64_t, std::string> failed;
+    uint64_t next_ticket = 1;
+    std::vector<std::thread> workers;
+    int device = 0;
+};
+
+namespace gn {
+static uint64_t footprint_of(const gn_index *ix, const SearchOptions &o, uint64_t len) {
+    // expected hits (mean list length, with a margin for skewed lists) x 16 bytes of keys, plus the
+    // alignment strips of the selected HSPs and per-offset arrays
+    double mean_list = (double)ix->n_postings / (double)(1ull << (2 * ix->k));
+    double hits = (double)len * std::max(1.0, mean_list) * 4.0;
+    double sw = (double)std::max<uint32_t>(o.p.max_alignments ? o.p.max_alignments : 1000, 1) *
+                (2.0 * o.p.band_w + 2.0) * 16.0;
+    return (uint64_t)(hits * 16.0 + sw + (double)len * 32.0) + (1u << 20);
+}
+
+static void serve_worker(gn_server *sv) {
+    cudaSetDevice(sv->device);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+    uint8_t *dbuf = nullptr;
+    size_t dcap = 0;
+    for (;;) {
+        std::vector<Request> batch;
+        uint64_t taken = 0;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] {
+                return (sv->stopping && sv->queue.empty()) ||
+                       (!sv->queue.empty() && sv->in_use + sv->queue.front().footprint <= sv->budget);
+            });
+            if (sv->queue.empty()) break;
+            // admit arrivals in order while they fit the memory budget (continuous batching)
+            while (!sv->queue.empty() && batch.size() < MAX_QUERIES &&
+                   sv->in_use + taken + sv->queue.front().footprint <= sv->budget) {
+                taken += sv->queue.front().footprint;
+                batch.push_back(std::move(sv->queue.front()));
+                sv->queue.pop_front();
+            }
+            sv->in_use += taken;
+        }
+        std::vector<uint64_t> qstart(batch.size() + 1, 0);
+        for (size_t i = 0; i < batch.size(); ++i) qstart[i + 1] = qstart[i] + batch[i].bases.size();
+        std::string err;
+        gn_results all;
+        gn_status st = guarded([&] {
+            uint64_t M = qstart.back();
+            if (M > dcap) {
+                if (dbuf) cudaFree(dbuf);
+                dbuf = nullptr;
+                dcap = std::max<uint64_t>(M, 1 << 20);
+                GN_CUDA(cudaMalloc(&dbuf, dcap));
+            }
+            std::string host;
+            host.reserve(M);
+            for (auto &r : batch) host += r.bases;
+            if (M) GN_CUDA(cudaMemcpyAsync(dbuf, host.data(), M, cudaMemcpyHostToDevice, s));
+            search(const_cast<gn_index *>(sv->ix), dbuf, qstart, sv->opt, s, &all);
+        });
+        if (st != GN_OK) err = g_last_error;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (size_t i = 0; i < batch.size(); ++i) {
+                if (st != GN_OK) {
+                    sv->failed[batch[i].ticket] = err;
+                    continue;
+                }
+                gn_results *r = new gn_results();
+                r->n_queries = 1;
+                r->qoff = {0, all.qoff[i + 1] - all.qoff[i]};
+                r->hits.assign(all.hits.begin() + all.qoff[i], all.hits.begin() + all.qoff[i + 1]);
+                for (auto &h : r->hits) h.query = 0;
+                sv->done[batch[i].ticket] = r;
+            }
+            sv->in_use -= taken;
+        }
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+    if (dbuf) cudaFree(dbuf);
+    cudaStreamDestroy(s);
+}
+}  // namespace gn
+
+using namespace gn;
+
+extern "C" {
+
+gn_status gn_default_params(gn_scoring *sc, gn_params *p) {
+    if (sc) {
+        sc->match = 1;
+        sc->mismatch = -3;
+        sc->gap_open = -5;
+        sc->gap_extend = -2;
+        sc->lambda = 1.3740631;
+        sc->K = 0.711;
+    }
+    if (p) {
+        p->max_hit_distance = 0;
+        p->min_hsp_len = 0;
+        p->xdrop = 20;
+        p->max_alignments = 100;
+        p->band_w = 16;
+        p->max_evalue = INFINITY;
+        p->flags = 0;
+    }
+    return GN_OK;
+}
+
+gn_status gn_index_build(const gn_bank *db, int k, int stride, void *cuda_stream, gn_index **out) {
+    if (!out) { g_last_error = "out is required"; return GN_EINVAL; }
+    *out = nullptr;
+    gn_index *ix = new (std::nothrow) gn_index();
+    if (!ix) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
+    gn_status st = guarded([&] { index_build(db, k, stride, (cudaStream_t)cuda_stream, ix); });
+    if (st != GN_OK) {
+        std::string msg = g_last_error;
+        index_free(ix);
+        delete ix;
+        g_last_error = msg;
+        return st;
+    }
+    *out = ix;
+    return GN_OK;
+}
+
+void gn_index_free(gn_index *ix) {
+    if (!ix) return;
+    index_free(ix);
+    delete ix;
+}
+
+gn_status gn_index_get_info(const gn_index *ix, gn_index_info *info) {
+    if (!ix || !info) { g_last_error = "index and info are required"; return GN_EINVAL; }
+    info->k = ix->k;
+    info->stride = ix->t;
+    info->n_seqs = ix->n_seqs;
+    info->n_bases = ix->n_bases;
+    info->n_postings = ix->n_postings;
+    info->device_bytes = ix->device_bytes;
+    return GN_OK;
+}
+
+gn_status gn_index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos) {
+    if (!ix) { g_last_error = "index is required"; return GN_EINVAL; }
+    return guarded([&] { index_export(ix, bucket_start, post_seq, post_pos); });
+}
+
+gn_status gn_search(const gn_index *ix, const gn_queries *q, const gn_scoring *sc, const gn_params *p,
+                    void *cuda_stream, gn_results **out) {
+    if (!out) { g_last_error = "out is required"; return GN_EINVAL; }
+    *out = nullptr;
+    if (!ix) { g_last_error = "index is required"; return GN_EINVAL; }
+    gn_results *res = new (std::nothrow) gn_results();
+    if (!res) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
+    gn_status st = guarded([&] {
+        check_queries(q);
+        SearchOptions o;
+        resolve(ix, sc, p, o);
+        int dev = 0;
+        GN_CUDA(cudaGetDevice(&dev));
+        GN_REQUIRE(dev == ix->device, GN_EINVAL, "the current device is not the index's device");
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        std::vector<uint64_t> qstart(q->start, q->start + q->n + 1);
+        const uint64_t M = qstart[q->n];
+        const uint8_t *qd = reinterpret_cast<const uint8_t *>(q->bases);
+        DeviceArena arena(s);
+        if (q->bases_mem == GN_MEM_HOST && M > 0) {
+            uint8_t *tmp = arena.alloc_n<uint8_t>(M);
+            GN_CUDA(cudaMemcpyAsync(tmp, q->bases, M, cudaMemcpyHostToDevice, s));
+            qd = tmp;
+        }
+        search(const_cast<gn_index *>(ix), qd, qstart, o, s, res);
+        arena.release();
+    });
+    if (st != GN_OK) {
+        delete res;
+        return st;
+    }
+    *out = res;
+    return GN_OK;
+}
+
+void gn_results_free(gn_results *r) { delete r; }
+
+gn_status gn_results_get(const gn_results *r, uint32_t query, const gn_hit **hits, uint32_t *n) {
+    if (!r || !hits || !n) { g_last_error = "results, hits and n are required"; return GN_EINVAL; }
+    if (query >= r->n_queries) { g_last_error = "query index out of range"; return GN_EINVAL; }
+    *n = (uint32_t)(r->qoff[query + 1] - r->qoff[query]);
+    *hits = *n ? r->hits.data() + r->qoff[query] : nullptr;
+    return GN_OK;
+}
+
+gn_status gn_results_count(const gn_results *r, uint32_t *nq, uint64_t *nh) {
+    if (!r) { g_last_error = "results are required"; return GN_EINVAL; }
+    if (nq) *nq = r->n_queries;
+    if (nh) *nh = r->hits.size();
+    return GN_OK;
+}
+
+gn_status gn_results_stage(const gn_results *r, gn_stage stage, const void **data, uint64_t *n) {
+    if (!r || !data || !n) { g_last_error = "results, data and n are required"; return GN_EINVAL; }
+    if (!r->has_stages && stage != GN_STAGE_HITS) { g_last_error = "search ran without GN_FLAG_KEEP_STAGES"; return GN_EINVAL; }
+    switch (stage) {
+    case GN_STAGE_HSP: *data = r->st_hsp.data(); *n = r->st_hsp.size(); break;
+    case GN_STAGE_EXT: *data = r->st_ext.data(); *n = r->st_ext.size(); break;
+    case GN_STAGE_MERGED: *data = r->st_merged.data(); *n = r->st_merged.size(); break;
+    case GN_STAGE_SELECTED: *data = r->st_sel.data(); *n = r->st_sel.size(); break;
+    case GN_STAGE_ALIGNED: *data = r->st_aln.data(); *n = r->st_aln.size(); break;
+    case GN_STAGE_HITS: *data = r->st_hits.data(); *n = r->st_hits.size() / 4; break;
+    case GN_STAGE_HIT_COUNTS: *data = r->st_hit_counts.data(); *n = r->st_hit_counts.size(); break;
+    default: g_last_error = "unknown stage"; return GN_EINVAL;
+    }
+    return GN_OK;
+}
+
+int gn_last_phase_times(const gn_index *ix, const char **names, float *ms, int cap) {
+    if (!ix) return 0;
+    std::lock_guard<std::mutex> lk(const_cast<gn_index *>(ix)->phase_mu);
+    int n = 0;
+    for (auto &ph : ix->last_phases) {
+        if (n >= cap) break;
+        if (names) names[n] = ph.first;
+        if (ms) ms[n] = ph.second;
+        ++n;
+    }
+    return n;
+}
+
+gn_status gn_serve_start(const gn_index *ix, const gn_scoring *sc, const gn_params *p, uint64_t mem_budget,
+                         gn_server **out) {
+    if (!out || !ix) { g_last_error = "index and out are required"; return GN_EINVAL; }
+    *out = nullptr;
+    gn_server *sv = new (std::nothrow) gn_server();
+    if (!sv) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
+    gn_status st = guarded([&] {
+        resolve(ix, sc, p, sv->opt);
+        sv->opt.p.flags &= ~(GN_FLAG_KEEP_STAGES | GN_FLAG_KEEP_HITS);
+        sv->ix = ix;
+        sv->budget = mem_budget;
+        sv->device = ix->device;
+        for (int w = 0; w < 3; ++w) sv->workers.emplace_back(serve_worker, sv);
+    });
+    if (st != GN_OK) { delete sv; return st; }
+    *out = sv;
+    return GN_OK;
+}
+
+gn_status gn_serve_submit(gn_server *sv, const char *bases, uint32_t len, uint64_t *ticket) {
+    if (!sv || !ticket || (len && !bases)) { g_last_error = "server, bases and ticket are required"; return GN_EINVAL; }
+    if (len > MAX_QUERY_LEN) { g_last_error = "a query holds 65,536 bases or more"; return GN_ETOOBIG; }
+    uint64_t fp = footprint_of(sv->ix, sv->opt, len);
+    if (fp > sv->budget) { g_last_error = "the query alone exceeds the server's memory budget"; return GN_ETOOBIG; }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stopping) { g_last_error = "server is stopping"; return GN_EBUSY; }
+        Request r;
+        r.ticket = sv->next_ticket++;
+        r.bases.assign(bases ? bases : "", len);
+        r.footprint = fp;
+        *ticket = r.ticket;
+        sv->queue.push_back(std::move(r));
+    }
+    sv->cv_work.notify_one();
+    g_last_error.clear();
+    return GN_OK;
+}
+
+gn_status gn_serve_poll(gn_server *sv, uint64_t ticket, uint32_t timeout_ms, gn_results **out) {
+    if (!sv || !out) { g_last_error = "server and out are required"; return GN_EINVAL; }
+    *out = nullptr;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto ready = [&] { return sv->done.count(ticket) || sv->failed.count(ticket); };
+    if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+        g_last_error = "not done yet";
+        return GN_ETIMEOUT;
+    }
+    auto f = sv->failed.find(ticket);
+    if (f != sv->failed.end()) {
+        g_last_error = f->second;
+        sv->failed.erase(f);
+        return GN_ECUDA;
+    }
+    auto it = sv->done.find(ticket);
+    *out = it->second;
+    sv->done.erase(it);
+    g_last_error.clear();
+    return GN_OK;
+}
+
+gn_status gn_serve_stop(gn_server *sv) {
+    if (!sv) return GN_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stopping = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto &t : sv->workers) t.join();
+    for (auto &kv : sv->done) delete kv.second;
+    delete sv;
+    return GN_OK;
+}
+
+const char *gn_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

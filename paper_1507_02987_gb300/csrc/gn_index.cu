@@ -1,0 +1,186 @@
+// gn_index.cu - device construction of the inverted index ("Inverted Indexes"
+// section of the paper): the bank is packed to 2 bits per base, cut into
+// non-overlapping windows at offsets 0, t, 2t, ... of every sequence, and each
+// window's occurrence is filed under its k-mer code.  Buckets are a CSR
+// structure: off[c] .. off[c+1] index the occurrences of code c, in ascending
+// (sequence, position) order, stored as the window's global base offset.
+#include <algorithm>
+
+#include "gn_internal.cuh"
+
+namespace gn {
+
+// windows per sequence: len >= k ? (len - k) / t + 1 : 0
+__global__ void k_window_counts(const uint64_t *__restrict__ seq_start, uint32_t n_seqs, int k, int t,
+                                uint32_t *__restrict__ wcnt) {
+    uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_seqs) return;
+    uint64_t L = seq_start[s + 1] - seq_start[s];
+    wcnt[s] = L >= (uint64_t)k ? (uint32_t)((L - k) / t + 1) : 0u;
+}
+
+constexpr int WIN_J = 8;  // windows per lane per warp chunk
+
+// Pass 1 (flags = true): validity flag of every window + bucket histogram.
+// Pass 2 (flags = false): key (code << 32 | global offset) of every valid window at its compacted slot.
+template <bool FLAGS>
+__global__ void k_bank_windows(const uint64_t *__restrict__ seq_start, const uint64_t *__restrict__ woff,
+                               uint32_t n_seqs, uint64_t W, const uint32_t *__restrict__ pk,
+                               const uint32_t *__restrict__ nb, int k, int t, uint32_t *__restrict__ flags,
+                               uint32_t *__restrict__ hist, const uint64_t *__restrict__ slot,
+                               uint64_t *__restrict__ keys) {
+    const int lane = threadIdx.x & 31;
+    uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint64_t w0 = warp * 32 * WIN_J;
+    if (w0 >= W) return;
+    uint32_t s = 0;
+    if (lane == 0) s = dev_upper_index(woff, n_seqs + 1, w0);
+    s = __shfl_sync(0xffffffffu, s, 0);
+#pragma unroll
+    for (int it = 0; it < WIN_J; ++it) {
+        uint64_t w = w0 + (uint64_t)it * 32 + lane;
+        if (w >= W) break;
+        while (woff[s + 1] <= w) ++s;
+        uint64_t g = seq_start[s] + (w - woff[s]) * (uint64_t)t;
+        bool bad = dev_has_nonbase(nb, g, k);
+        uint32_t code = dev_kmer(pk, g, k);
+        if (FLAGS) {
+            flags[w] = bad ? 0u : 1u;
+            if (!bad) atomicAdd(&hist[code], 1u);
+        } else if (!bad) {
+            keys[slot[w]] = ((uint64_t)code << 32) | g;
+        }
+    }
+}
+
+__global__ void k_low_words(const uint64_t *__restrict__ keys, uint64_t n, uint32_t *__restrict__ out) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint32_t)keys[i];
+}
+
+void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) {
+    GN_REQUIRE(db && db->seq_start, GN_EINVAL, "bank and bank.seq_start are required");
+    GN_REQUIRE(k >= 1 && k <= 16, GN_EINVAL, "k must be in 1..16");
+    GN_REQUIRE(t >= 1, GN_EINVAL, "stride must be >= 1");
+    const uint32_t ns = db->n_seqs;
+    const uint64_t n = db->seq_start[ns] - db->seq_start[0];
+    GN_REQUIRE(db->seq_start[0] == 0, GN_EINVAL, "bank.seq_start[0] must be 0");
+    GN_REQUIRE(n < (1ull << 32), GN_ETOOBIG, "bank must hold fewer than 2^32 bases");
+    GN_REQUIRE(n == 0 || db->bases, GN_EINVAL, "bank.bases is required");
+    uint64_t maxlen = 0;
+    for (uint32_t i = 0; i < ns; ++i) {
+        GN_REQUIRE(db->seq_start[i + 1] >= db->seq_start[i], GN_EINVAL, "bank.seq_start must be non-decreasing");
+        maxlen = std::max<uint64_t>(maxlen, db->seq_start[i + 1] - db->seq_start[i]);
+    }
+    GN_CUDA(cudaGetDevice(&ix->device));
+    configure_mempool(ix->device);
+    ix->k = k;
+    ix->t = t;
+    ix->n_seqs = ns;
+    ix->n_bases = n;
+    ix->max_seq_len = (uint32_t)maxlen;
+    ix->seq_start_h.assign(db->seq_start, db->seq_start + ns + 1);
+
+    const uint64_t nbk = 1ull << (2 * k);
+    uint64_t bytes = 0;
+    GN_CUDA(cudaMalloc(&ix->seq_start_d, sizeof(uint64_t) * (ns + 1)));
+    bytes += sizeof(uint64_t) * (ns + 1);
+    GN_CUDA(cudaMalloc(&ix->bank.pk, 4 * Packed::pk_words(n)));
+    GN_CUDA(cudaMalloc(&ix->bank.nb, 4 * Packed::nb_words(n)));
+    bytes += 4 * (Packed::pk_words(n) + Packed::nb_words(n));
+    GN_CUDA(cudaMalloc(&ix->off_d, sizeof(uint64_t) * (nbk + 1)));
+    bytes += sizeof(uint64_t) * (nbk + 1);
+    GN_CUDA(cudaMemcpyAsync(ix->seq_start_d, ix->seq_start_h.data(), sizeof(uint64_t) * (ns + 1),
+                            cudaMemcpyHostToDevice, s));
+
+    DeviceArena arena(s);
+    // K1: 2-bit packing of the bank
+    const uint8_t *bases_d = reinterpret_cast<const uint8_t *>(db->bases);
+    if (db->bases_mem == GN_MEM_HOST && n > 0) {
+        uint8_t *tmp = arena.alloc_n<uint8_t>(n);
+        GN_CUDA(cudaMemcpyAsync(tmp, db->bases, n, cudaMemcpyHostToDevice, s));
+        bases_d = tmp;
+    }
+    pack_bases(bases_d, n, ix->bank, s);
+
+    // windows per sequence and their exclusive scan
+    uint32_t *wcnt = arena.alloc_n<uint32_t>(ns);
+    uint64_t *woff = arena.alloc_n<uint64_t>(ns + 1);
+    if (ns) {
+        k_window_counts<<<(ns + 255) / 256, 256, 0, s>>>(ix->seq_start_d, ns, k, t, wcnt);
+        GN_CHECK_LAUNCH();
+    }
+    void *scan_scr = arena.alloc(std::max(scan_scratch_bytes(ns), scan_scratch_bytes(nbk)));
+    exclusive_scan_u32(wcnt, woff, ns, scan_scr, s);
+    uint64_t W = 0;
+    GN_CUDA(cudaMemcpyAsync(&W, woff + ns, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    GN_CUDA(cudaStreamSynchronize(s));
+
+    // K2: window validity + bucket histogram
+    uint32_t *hist = arena.alloc_n<uint32_t>(nbk);
+    GN_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nbk, s));
+    uint32_t *flags = arena.alloc_n<uint32_t>(W);
+    uint64_t *slot = arena.alloc_n<uint64_t>(W + 1);
+    uint64_t warps = (W + 32 * WIN_J - 1) / (32 * WIN_J);
+    unsigned grid = (unsigned)std::max<uint64_t>(1, (warps * 32 + 255) / 256);
+    if (W) {
+        k_bank_windows<true><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
+                                                  flags, hist, nullptr, nullptr);
+        GN_CHECK_LAUNCH();
+    }
+    // K3: bucket starts = exclusive scan of the histogram
+    exclusive_scan_u32(hist, ix->off_d, nbk, scan_scr, s);
+    void *scan_scr2 = arena.alloc(scan_scratch_bytes(W));
+    exclusive_scan_u32(flags, slot, W, scan_scr2, s);
+    uint64_t P = 0;
+    GN_CUDA(cudaMemcpyAsync(&P, ix->off_d + nbk, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    GN_CUDA(cudaStreamSynchronize(s));
+    ix->n_postings = P;
+
+    // K4: stable scatter = stable radix sort of (code, global offset) keys by code
+    uint64_t *keys = arena.alloc_n<uint64_t>(P);
+    uint64_t *keys_alt = arena.alloc_n<uint64_t>(P);
+    if (W) {
+        k_bank_windows<false><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
+                                                   nullptr, nullptr, slot, keys);
+        GN_CHECK_LAUNCH();
+    }
+    void *rs = arena.alloc(radix_scratch_bytes(P));
+    bool flipped = radix_sort(keys, keys_alt, nullptr, nullptr, P, 32, 32 + 2 * k, rs, s);
+    GN_CUDA(cudaMalloc(&ix->post_d, sizeof(uint32_t) * (P ? P : 1)));
+    bytes += sizeof(uint32_t) * P;
+    if (P) {
+        k_low_words<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(flipped ? keys_alt : keys, P, ix->post_d);
+        GN_CHECK_LAUNCH();
+    }
+    arena.release();
+    GN_CUDA(cudaStreamSynchronize(s));
+    ix->device_bytes = bytes;
+}
+
+void index_free(gn_index *ix) {
+    if (!ix) return;
+    cudaFree(ix->seq_start_d);
+    cudaFree(ix->bank.pk);
+    cudaFree(ix->bank.nb);
+    cudaFree(ix->off_d);
+    cudaFree(ix->post_d);
+}
+
+void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos) {
+    const uint64_t nbk = 1ull << (2 * ix->k);
+    if (bucket_start) GN_CUDA(cudaMemcpy(bucket_start, ix->off_d, sizeof(uint64_t) * (nbk + 1), cudaMemcpyDeviceToHost));
+    if (!post_seq && !post_pos) return;
+    std::vector<uint32_t> g(ix->n_postings);
+    if (ix->n_postings)
+        GN_CUDA(cudaMemcpy(g.data(), ix->post_d, sizeof(uint32_t) * ix->n_postings, cudaMemcpyDeviceToHost));
+    // decode global offsets to (sequence, position) for the caller
+    const std::vector<uint64_t> &st = ix->seq_start_h;
+    for (uint64_t i = 0; i < ix->n_postings; ++i) {
+        uint32_t sidx = (uint32_t)(std::upper_bound(st.begin(), st.end(), (uint64_t)g[i]) - st.begin()) - 1;
+        if (post_seq) post_seq[i] = sidx;
+        if (post_pos) post_pos[i] = (uint32_t)(g[i] - st[sidx]);
+    }
+}
+
+}  // namespace gn

@@ -1,0 +1,199 @@
+// gn_internal.cuh - internal declarations shared by the CUDA translation units of
+// the Genoogle search path (device data layout, primitives, error plumbing).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "genoogle.h"
+
+namespace gn {
+
+// ------------------------------------------------------------------ errors --
+struct Error {
+    gn_status status;
+    std::string msg;
+};
+
+void set_error(gn_status st, const std::string &msg);
+
+#define GN_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t _e = (call);                                                               \
+        if (_e != cudaSuccess) {                                                               \
+            throw ::gn::Error{_e == cudaErrorMemoryAllocation ? GN_ENOMEM : GN_ECUDA,          \
+                              std::string(#call) + ": " + cudaGetErrorString(_e)};             \
+        }                                                                                      \
+    } while (0)
+
+#define GN_CHECK_LAUNCH() GN_CUDA(cudaGetLastError())
+
+#define GN_REQUIRE(cond, st, msg)                 \
+    do {                                          \
+        if (!(cond)) throw ::gn::Error{(st), (msg)}; \
+    } while (0)
+
+// Device-side status word bits (kernels record a failed check and skip the access).
+enum : uint32_t {
+    DEV_ERR_BAND_TOO_WIDE = 1u,   // alignment band wider than the start encoding allows
+    DEV_ERR_CAPACITY = 2u,        // an output buffer was too small (caller retries with more room)
+    DEV_ERR_BOUNDS = 4u,          // an index fell outside its buffer
+};
+
+// ------------------------------------------------------------- constants --
+constexpr uint32_t QBIAS = 65536;          // > any query offset: diagonal key = gpos - qpos + QBIAS > 0
+constexpr uint32_t MAX_QUERY_LEN = 65535;
+constexpr uint32_t MAX_QUERIES = 65536;
+
+// --------------------------------------------------------- device memory --
+// Stream-ordered allocations from the device's default memory pool.
+class DeviceArena {
+public:
+    explicit DeviceArena(cudaStream_t s) : stream_(s) {}
+    ~DeviceArena() { release(); }
+    void *alloc(size_t bytes);
+    template <class T> T *alloc_n(size_t n) { return static_cast<T *>(alloc(sizeof(T) * (n ? n : 1))); }
+    void release();
+    cudaStream_t stream() const { return stream_; }
+
+private:
+    cudaStream_t stream_;
+    std::vector<void *> ptrs_;
+};
+
+void configure_mempool(int device);
+
+// ------------------------------------------------------------ packed DNA --
+// 16 bases per uint32 word, first base in the two most significant bits;
+// a parallel bitmap marks non-bases (bit g & 31 of word g >> 5).  One extra
+// zero word is kept at the end of both arrays so windows can read word w + 1.
+struct Packed {
+    uint32_t *pk = nullptr;
+    uint32_t *nb = nullptr;
+    uint64_t n = 0;
+    static uint64_t pk_words(uint64_t n) { return (n + 15) / 16 + 2; }
+    static uint64_t nb_words(uint64_t n) { return (n + 31) / 32 + 2; }
+};
+
+void pack_bases(const uint8_t *ascii_dev, uint64_t n, Packed &out, cudaStream_t s);
+
+// --------------------------------------------------------------- scans --
+// out[i] = sum(in[0..i)), out[n] = total; out has n + 1 entries.
+size_t scan_scratch_bytes(uint64_t n);
+void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scratch, cudaStream_t s);
+
+// ----------------------------------------------------------- radix sort --
+// Stable LSD radix sort of 64-bit keys (optionally carrying 32-bit values) on
+// key bits [bit_lo, bit_hi).  Ping-pongs between the two buffers; returns true
+// when the sorted data ended in the *_alt buffers.
+size_t radix_scratch_bytes(uint64_t n);
+bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
+                int bit_hi, void *scratch, cudaStream_t s);
+
+// Sort of fixed-size records made of uint32 words by a list of fields (first =
+// most significant).  Produces the permutation perm (record ids in order).
+struct SortField {
+    int word;   // word index inside the record
+    int bits;   // significant bits of the field
+    bool desc;  // descending order
+};
+void sort_records(const uint32_t *recs, int rec_words, uint32_t n, const std::vector<SortField> &fields,
+                  uint32_t *perm_out, DeviceArena &arena, cudaStream_t s);
+
+// Gathers records by a permutation: out[i] = in[perm[i]].
+void gather_records(const uint32_t *in, int rec_words, const uint32_t *perm, uint32_t n, uint32_t *out,
+                    cudaStream_t s);
+
+int bits_for(uint64_t max_value);  // bits needed to hold values in [0, max_value]
+
+int num_sms();
+
+// Compacts records whose flag is non-zero, keeping their order; returns the count
+// (synchronizes the stream to read it).
+uint32_t compact_records(const uint32_t *in, int rec_words, const uint32_t *flags, uint32_t n, uint32_t *out,
+                         DeviceArena &arena, cudaStream_t s);
+
+// ------------------------------------------------------- device helpers --
+__device__ __forceinline__ uint32_t dev_kmer(const uint32_t *__restrict__ pk, uint64_t g, int k) {
+    uint64_t w = g >> 4;
+    int off = (int)(g & 15);
+    uint64_t v = ((uint64_t)pk[w] << 32) | (uint64_t)pk[w + 1];
+    v <<= 2 * off;
+    return (uint32_t)(v >> (64 - 2 * k));
+}
+
+__device__ __forceinline__ bool dev_has_nonbase(const uint32_t *__restrict__ nb, uint64_t g, int k) {
+    uint64_t w = g >> 5;
+    int off = (int)(g & 31);
+    uint64_t v = ((uint64_t)nb[w + 1] << 32) | (uint64_t)nb[w];
+    v >>= off;
+    return (v & ((1ull << k) - 1ull)) != 0ull;
+}
+
+// 2-bit code of base g, or 4 for a non-base
+__device__ __forceinline__ uint32_t dev_base(const uint32_t *__restrict__ pk, const uint32_t *__restrict__ nb,
+                                             uint64_t g) {
+    uint32_t bad = (nb[g >> 5] >> (g & 31)) & 1u;
+    uint32_t c = (pk[g >> 4] >> (30 - 2 * (int)(g & 15))) & 3u;
+    return bad ? 4u : c;
+}
+
+// last index s in [0, n) with a[s] <= x (a non-decreasing, a[0] <= x)
+__device__ __forceinline__ uint32_t dev_upper_index(const uint64_t *__restrict__ a, uint32_t n, uint64_t x) {
+    uint32_t lo = 0, hi = n;  // invariant: a[lo] <= x, a[hi] > x (hi == n: past the end)
+    while (hi - lo > 1) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (a[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace gn
+
+// --------------------------------------------------------------- handles --
+struct gn_index {
+    int k = 0, t = 0;
+    int device = 0;
+    uint32_t n_seqs = 0;
+    uint64_t n_bases = 0;
+    uint64_t n_postings = 0;
+    uint32_t max_seq_len = 0;
+    std::vector<uint64_t> seq_start_h;
+    uint64_t *seq_start_d = nullptr;  // n_seqs + 1
+    gn::Packed bank;                  // packed bank + non-base bitmap
+    uint64_t *off_d = nullptr;        // 4^k + 1 bucket starts
+    uint32_t *post_d = nullptr;       // occurrences: global base offset of the window
+    uint64_t device_bytes = 0;
+    // per-phase device times of the most recent search through this handle
+    std::vector<std::pair<const char *, float>> last_phases;
+    std::mutex phase_mu;
+};
+
+struct gn_results {
+    uint32_t n_queries = 0;
+    std::vector<uint64_t> qoff;  // n_queries + 1
+    std::vector<gn_hit> hits;
+    bool has_stages = false;
+    std::vector<gn_hsp> st_hsp, st_ext, st_merged, st_sel;
+    std::vector<gn_hit> st_aln;
+    std::vector<uint32_t> st_hits;     // quadruples (query, qpos, seq, pos)
+    std::vector<uint64_t> st_hit_counts;
+};
+
+namespace gn {
+void index_build(const gn_bank *db, int k, int stride, cudaStream_t s, gn_index *ix);
+void index_free(gn_index *ix);
+void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos);
+
+struct SearchOptions {
+    gn_scoring sc;
+    gn_params p;      // resolved (no zero defaults left)
+};
+// Device-resident query set: bases (ASCII) on the device, starts on the host.
+void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart, const SearchOptions &o,
+            cudaStream_t s, gn_results *res);
+}  // namespace gn

@@ -1,0 +1,497 @@
+// gn_prims.cu - device primitives of the search path: 2-bit packing, exclusive
+// scans, a stable LSD radix sort and record sorting built on it.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "gn_internal.cuh"
+
+namespace gn {
+
+// ------------------------------------------------------------- helpers --
+int bits_for(uint64_t max_value) {
+    int b = 0;
+    while (b < 64 && (max_value >> b) != 0) ++b;
+    return b;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+void configure_mempool(int device) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    GN_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t thr = UINT64_MAX;  // keep freed blocks in the pool: repeated searches reuse them
+    GN_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    done[device] = true;
+}
+
+void *DeviceArena::alloc(size_t bytes) {
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 1, stream_);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{GN_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                   cudaGetErrorString(e)};
+    }
+    ptrs_.push_back(p);
+    return p;
+}
+
+void DeviceArena::release() {
+    for (void *p : ptrs_) cudaFreeAsync(p, stream_);
+    ptrs_.clear();
+}
+
+// --------------------------------------------------------------- packing --
+__device__ __forceinline__ uint32_t base_bits(uint32_t b, uint32_t &bad) {
+    uint32_t c = b & 0xDFu;  // upper case for letters; other bytes stay non-bases
+    uint32_t code = (c == 'C') ? 1u : (c == 'G') ? 2u : (c == 'T' || c == 'U') ? 3u : 0u;
+    bad = (c == 'A' || c == 'C' || c == 'G' || c == 'T' || c == 'U') ? 0u : 1u;
+    return code;
+}
+
+// One thread packs 32 bases: two code words and one non-base word.
+__global__ void k_pack(const uint8_t *__restrict__ ascii, uint64_t n, uint32_t *__restrict__ pk,
+                       uint32_t *__restrict__ nb, int aligned16) {
+    uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t g0 = t * 32;
+    if (g0 >= n) return;
+    uint8_t buf[32];
+    if (aligned16 && g0 + 32 <= n) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(ascii + g0);
+        uint4 a = __ldg(src), b = __ldg(src + 1);
+        memcpy(buf, &a, 16);
+        memcpy(buf + 16, &b, 16);
+    } else {
+        for (int i = 0; i < 32; ++i) buf[i] = (g0 + i < n) ? ascii[g0 + i] : (uint8_t)'N';
+    }
+    uint32_t w0 = 0, w1 = 0, bw = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        uint32_t bad;
+        uint32_t c = base_bits(buf[i], bad);
+        if (i < 16) w0 |= c << (30 - 2 * i);
+        else w1 |= c << (30 - 2 * (i - 16));
+        bw |= bad << i;
+    }
+    pk[2 * t] = w0;
+    pk[2 * t + 1] = w1;
+    nb[t] = bw;
+}
+
+void pack_bases(const uint8_t *ascii_dev, uint64_t n, Packed &out, cudaStream_t s) {
+    out.n = n;
+    GN_CUDA(cudaMemsetAsync(out.pk, 0, Packed::pk_words(n) * 4, s));
+    GN_CUDA(cudaMemsetAsync(out.nb, 0xFF, Packed::nb_words(n) * 4, s));
+    if (n == 0) return;
+    uint64_t threads = (n + 31) / 32;
+    int aligned = ((uintptr_t)ascii_dev % 16) == 0;
+    k_pack<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ascii_dev, n, out.pk, out.nb, aligned);
+    GN_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------------- scans --
+constexpr int SC_THREADS = 256;
+constexpr int SC_ITEMS = 16;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over the block; returns the block total in *total.
+template <class T, int THREADS>
+__device__ __forceinline__ T block_excl_scan(T v, T *warp_sums, T *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T x = (lane < THREADS / 32) ? warp_sums[lane] : T(0);
+        T xi = warp_incl_scan(x);
+        if (lane < THREADS / 32) warp_sums[lane] = xi - x;
+        if (lane == THREADS / 32 - 1) *total = xi;
+    }
+    __syncthreads();
+    T r = inc - v + warp_sums[w];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t *__restrict__ in, uint64_t n, uint64_t *__restrict__ sums) {
+    __shared__ uint64_t ws[SC_THREADS / 32];
+    __shared__ uint64_t tot;
+    uint64_t base = (uint64_t)blockIdx.x * SC_TILE;
+    uint64_t s = 0;
+#pragma unroll 4
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    block_excl_scan<uint64_t, SC_THREADS>(s, ws, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of nb 64-bit block sums in place; total to *total_out.
+__global__ void k_scan_sums(uint64_t *sums, uint64_t nb, uint64_t *total_out) {
+    constexpr int T = 1024;
+    __shared__ uint64_t ws[T / 32];
+    __shared__ uint64_t tot;
+    uint64_t per = (nb + T - 1) / T;
+    uint64_t b = threadIdx.x * per, e = min(nb, b + per);
+    uint64_t s = 0;
+    for (uint64_t i = b; i < e; ++i) s += sums[i];
+    uint64_t off = block_excl_scan<uint64_t, T>(s, ws, &tot);
+    for (uint64_t i = b; i < e; ++i) {
+        uint64_t v = sums[i];
+        sums[i] = off;
+        off += v;
+    }
+    if (threadIdx.x == 0) *total_out = tot;
+}
+
+__global__ void k_scan_down(const uint32_t *__restrict__ in, uint64_t n, const uint64_t *__restrict__ sums,
+                            uint64_t *__restrict__ out) {
+    __shared__ uint64_t tile[SC_TILE];
+    __shared__ uint64_t ws[SC_THREADS / 32];
+    __shared__ uint64_t tot;
+    uint64_t base = (uint64_t)blockIdx.x * SC_TILE;
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        int li = j * SC_THREADS + threadIdx.x;
+        uint64_t i = base + li;
+        tile[li] = (i < n) ? in[i] : 0;
+    }
+    __syncthreads();
+    uint64_t loc[SC_ITEMS];
+    uint64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        loc[j] = s;
+        s += tile[threadIdx.x * SC_ITEMS + j];
+    }
+    uint64_t off = block_excl_scan<uint64_t, SC_THREADS>(s, ws, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) tile[threadIdx.x * SC_ITEMS + j] = loc[j] + off;
+    __syncthreads();
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        int li = j * SC_THREADS + threadIdx.x;
+        uint64_t i = base + li;
+        if (i < n) out[i] = tile[li];
+    }
+}
+
+size_t scan_scratch_bytes(uint64_t n) { return sizeof(uint64_t) * ((n + SC_TILE - 1) / SC_TILE + 1); }
+
+void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scratch, cudaStream_t s) {
+    uint64_t nb = (n + SC_TILE - 1) / SC_TILE;
+    if (nb == 0) {
+        GN_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), s));
+        return;
+    }
+    uint64_t *sums = static_cast<uint64_t *>(scratch);
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums);
+    GN_CHECK_LAUNCH();
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, out + n);
+    GN_CHECK_LAUNCH();
+    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums, out);
+    GN_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------------ radix sort --
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_MAX_GRID_PER_SM = 8;
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint64_t *__restrict__ keys, uint64_t n,
+                                                           uint64_t chunk, int shift, uint32_t mask,
+                                                           uint32_t *__restrict__ counts) {
+    __shared__ uint32_t h[RS_WARPS][256];
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5;
+    uint64_t beg = (uint64_t)blockIdx.x * chunk, end = min(n, beg + chunk);
+    uint64_t i = beg + threadIdx.x;
+    for (; i + 3 * RS_THREADS < end; i += 4 * RS_THREADS) {
+        uint64_t k0 = keys[i], k1 = keys[i + RS_THREADS], k2 = keys[i + 2 * RS_THREADS], k3 = keys[i + 3 * RS_THREADS];
+        atomicAdd(&h[w][(uint32_t)(k0 >> shift) & mask], 1u);
+        atomicAdd(&h[w][(uint32_t)(k1 >> shift) & mask], 1u);
+        atomicAdd(&h[w][(uint32_t)(k2 >> shift) & mask], 1u);
+        atomicAdd(&h[w][(uint32_t)(k3 >> shift) & mask], 1u);
+    }
+    for (; i < end; i += RS_THREADS) atomicAdd(&h[w][(uint32_t)(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int ww = 0; ww < RS_WARPS; ++ww) s += h[ww][d];
+        counts[(uint64_t)d * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+struct RsSmem {
+    uint32_t wcnt[RS_WARPS][256];
+    uint32_t tcnt[256];
+    uint32_t tbase[256];
+    unsigned long long run[256];
+    uint32_t ws[RS_WARPS];
+    uint32_t tot;
+};
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t *__restrict__ kin,
+                                                             const uint32_t *__restrict__ vin,
+                                                             uint64_t *__restrict__ kout,
+                                                             uint32_t *__restrict__ vout, uint64_t n,
+                                                             uint64_t chunk, int shift, uint32_t mask,
+                                                             const uint64_t *__restrict__ offs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RsSmem &S = *reinterpret_cast<RsSmem *>(smem_raw);
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw + ((sizeof(RsSmem) + 15) / 16) * 16);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_TILE);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    if (tid < 256) S.run[tid] = offs[(uint64_t)tid * gridDim.x + blockIdx.x];
+    uint64_t beg = (uint64_t)blockIdx.x * chunk, end = min(n, beg + chunk);
+
+    for (uint64_t tb = beg; tb < end; tb += RS_TILE) {
+        const uint32_t tn = (uint32_t)min((uint64_t)RS_TILE, end - tb);
+        for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&S.wcnt[0][0])[i] = 0;
+        __syncthreads();
+        uint64_t k[RS_ITEMS];
+        uint32_t v[RS_ITEMS];
+        uint32_t dg[RS_ITEMS];
+        uint32_t rk[RS_ITEMS];
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            uint32_t li = warp * (RS_ITEMS * 32) + it * 32 + lane;
+            bool ok = li < tn;
+            k[it] = ok ? kin[tb + li] : 0ull;
+            if (VALS) v[it] = ok ? vin[tb + li] : 0u;
+            dg[it] = ok ? ((uint32_t)(k[it] >> shift) & mask) : 256u;
+        }
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            uint32_t d = dg[it];
+            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            uint32_t before = (d < 256u) ? S.wcnt[warp][d] : 0u;
+            __syncwarp();
+            rk[it] = before + __popc(peers & lt_mask);
+            if (d < 256u && (peers & lt_mask) == 0u) S.wcnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = tid;  // RS_THREADS == 256 digits
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) {
+                uint32_t c = S.wcnt[w][d];
+                S.wcnt[w][d] = s;
+                s += c;
+            }
+            S.tcnt[d] = s;
+            uint32_t b = block_excl_scan<uint32_t, RS_THREADS>(s, S.ws, &S.tot);
+            S.tbase[d] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < RS_ITEMS; ++it) {
+            uint32_t d = dg[it];
+            if (d < 256u) {
+                uint32_t pos = S.tbase[d] + S.wcnt[warp][d] + rk[it];
+                sk[pos] = k[it];
+                if (VALS) sv[pos] = v[it];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < tn; i += RS_THREADS) {
+            uint64_t key = sk[i];
+            uint32_t d = (uint32_t)(key >> shift) & mask;
+            uint64_t dst = S.run[d] + (i - S.tbase[d]);
+            kout[dst] = key;
+            if (VALS) vout[dst] = sv[i];
+        }
+        __syncthreads();
+        S.run[tid] += S.tcnt[tid];
+        __syncthreads();
+    }
+}
+
+static size_t rs_smem_bytes() {
+    return ((sizeof(RsSmem) + 15) / 16) * 16 + (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t));
+}
+
+struct RsGeom {
+    int grid;
+    uint64_t chunk;
+};
+
+static RsGeom rs_geometry(uint64_t n) {
+    static int occ = 0;
+    if (!occ) {
+        size_t smem = rs_smem_bytes();
+        cudaFuncSetAttribute(k_rs_downsweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_rs_downsweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_rs_downsweep<true>, RS_THREADS, smem);
+        occ = std::max(1, std::min(o, RS_MAX_GRID_PER_SM));
+    }
+    uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    uint64_t g = std::min<uint64_t>((uint64_t)num_sms() * occ, std::max<uint64_t>(tiles, 1));
+    uint64_t tiles_per = (tiles + g - 1) / g;
+    if (tiles_per == 0) tiles_per = 1;
+    RsGeom geo;
+    geo.chunk = tiles_per * RS_TILE;
+    geo.grid = (int)std::max<uint64_t>(1, (n + geo.chunk - 1) / geo.chunk);
+    return geo;
+}
+
+size_t radix_scratch_bytes(uint64_t n) {
+    (void)n;
+    size_t g = (size_t)num_sms() * RS_MAX_GRID_PER_SM;
+    size_t cnt = 256 * g;
+    return cnt * sizeof(uint32_t) + (cnt + 1) * sizeof(uint64_t) + scan_scratch_bytes(cnt) + 256;
+}
+
+bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
+                int bit_hi, void *scratch, cudaStream_t s) {
+    if (n <= 1 || bit_hi <= bit_lo) return false;
+    RsGeom geo = rs_geometry(n);
+    size_t cnt = (size_t)256 * geo.grid;
+    uint32_t *counts = static_cast<uint32_t *>(scratch);
+    uint64_t *offs = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(counts + cnt) + 15) & ~(uintptr_t)15);
+    void *scan_scratch = reinterpret_cast<void *>(
+        (reinterpret_cast<uintptr_t>(offs + cnt + 1) + 15) & ~(uintptr_t)15);
+    const size_t smem = rs_smem_bytes();
+    bool flip = false;
+    for (int shift = bit_lo; shift < bit_hi; shift += 8) {
+        int nbits = std::min(8, bit_hi - shift);
+        uint32_t mask = (1u << nbits) - 1u;
+        const uint64_t *kin = flip ? keys_alt : keys;
+        uint64_t *kout = flip ? keys : keys_alt;
+        const uint32_t *vin = flip ? vals_alt : vals;
+        uint32_t *vout = flip ? vals : vals_alt;
+        k_rs_upsweep<<<geo.grid, RS_THREADS, 0, s>>>(kin, n, geo.chunk, shift, mask, counts);
+        GN_CHECK_LAUNCH();
+        exclusive_scan_u32(counts, offs, cnt, scan_scratch, s);
+        if (vals) {
+            k_rs_downsweep<true><<<geo.grid, RS_THREADS, smem, s>>>(kin, vin, kout, vout, n, geo.chunk, shift,
+                                                                    mask, offs);
+        } else {
+            k_rs_downsweep<false><<<geo.grid, RS_THREADS, smem, s>>>(kin, nullptr, kout, nullptr, n, geo.chunk,
+                                                                     shift, mask, offs);
+        }
+        GN_CHECK_LAUNCH();
+        flip = !flip;
+    }
+    return flip;
+}
+
+// --------------------------------------------------------- record sort --
+struct KeyFields {
+    int n;
+    int word[4];
+    int shift[4];
+    uint32_t mask[4];
+    int desc[4];
+};
+
+__global__ void k_iota(uint32_t *p, uint32_t n) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = i;
+}
+
+__global__ void k_make_keys(const uint32_t *__restrict__ recs, int rec_words, const uint32_t *__restrict__ perm,
+                            uint32_t n, KeyFields f, uint64_t *__restrict__ keys) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t *r = recs + (uint64_t)perm[i] * rec_words;
+    uint64_t k = 0;
+    for (int j = 0; j < f.n; ++j) {
+        uint32_t v = r[f.word[j]];
+        if (f.desc[j]) v = ~v;
+        k |= (uint64_t)(v & f.mask[j]) << f.shift[j];
+    }
+    keys[i] = k;
+}
+
+void sort_records(const uint32_t *recs, int rec_words, uint32_t n, const std::vector<SortField> &fields,
+                  uint32_t *perm_out, DeviceArena &arena, cudaStream_t s) {
+    if (n == 0) return;
+    unsigned grid = (n + 255) / 256;
+    uint32_t *perm = perm_out;
+    uint32_t *perm_alt = arena.alloc_n<uint32_t>(n);
+    uint64_t *keys = arena.alloc_n<uint64_t>(n);
+    uint64_t *keys_alt = arena.alloc_n<uint64_t>(n);
+    void *scratch = arena.alloc(radix_scratch_bytes(n));
+    k_iota<<<grid, 256, 0, s>>>(perm, n);
+    GN_CHECK_LAUNCH();
+    // group fields into <= 64-bit keys, least significant group first
+    int fi = (int)fields.size() - 1;
+    while (fi >= 0) {
+        KeyFields kf;
+        kf.n = 0;
+        int used = 0;
+        while (fi >= 0 && kf.n < 4 && used + fields[fi].bits <= 64) {
+            const SortField &sf = fields[fi];
+            kf.word[kf.n] = sf.word;
+            kf.shift[kf.n] = used;
+            kf.mask[kf.n] = sf.bits >= 32 ? 0xFFFFFFFFu : ((1u << sf.bits) - 1u);
+            kf.desc[kf.n] = sf.desc ? 1 : 0;
+            used += sf.bits;
+            ++kf.n;
+            --fi;
+        }
+        if (kf.n == 0) throw Error{GN_EINTERNAL, "sort field wider than 64 bits"};
+        if (used == 0) continue;
+        k_make_keys<<<grid, 256, 0, s>>>(recs, rec_words, perm, n, kf, keys);
+        GN_CHECK_LAUNCH();
+        bool flipped = radix_sort(keys, keys_alt, perm, perm_alt, n, 0, used, scratch, s);
+        if (flipped) std::swap(perm, perm_alt);
+    }
+    if (perm != perm_out) GN_CUDA(cudaMemcpyAsync(perm_out, perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+}
+
+__global__ void k_gather_records(const uint32_t *__restrict__ in, int W, const uint32_t *__restrict__ perm,
+                                 uint32_t n, uint32_t *__restrict__ out) {
+    uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)n * W) return;
+    uint32_t i = (uint32_t)(t / W), w = (uint32_t)(t % W);
+    out[t] = in[(uint64_t)perm[i] * W + w];
+}
+
+void gather_records(const uint32_t *in, int rec_words, const uint32_t *perm, uint32_t n, uint32_t *out,
+                    cudaStream_t s) {
+    if (n == 0) return;
+    uint64_t tot = (uint64_t)n * rec_words;
+    k_gather_records<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(in, rec_words, perm, n, out);
+    GN_CHECK_LAUNCH();
+}
+
+}  // namespace gn

@@ -1,0 +1,807 @@
+// gn_search.cu - the search phases of the paper ("Searching process" section) on
+// the device, for a batch of independent queries:
+//   a5  input processing: rolling k-mer code of every query offset
+//   a6  index lookup: gather of every occurrence of every code (hits)
+//   a7  grouping: radix sort of hits by (diagonal key, query, query offset)
+//   a8  merging of hits at most D apart on one (sequence, diagonal) into HSPs
+//   a9  X-drop ungapped extension of both HSP ends
+//   a10 merging of overlapped HSPs (single sweep per query and sequence)
+//   a11 selection of the longest HSPs per query
+//   a12 banded affine-gap Smith-Waterman of each selected HSP
+//   a13 ranking by score, duplicate removal, e-value and bit score
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "gn_internal.cuh"
+
+namespace gn {
+
+// HSP record (7 words, same layout as gn_hsp)
+struct DevHsp {
+    uint32_t qi, seq, qs, qe, ds, de, len;
+};
+static_assert(sizeof(DevHsp) == 28, "DevHsp layout");
+constexpr int HSP_WORDS = 7;
+enum { W_QI = 0, W_SEQ = 1, W_QS = 2, W_QE = 3, W_DS = 4, W_DE = 5, W_LEN = 6 };
+
+// alignment record (8 words)
+struct DevAln {
+    uint32_t qi, seq, qs, qe, ds, de;
+    int32_t score;
+    uint32_t pad;
+};
+static_assert(sizeof(DevAln) == 32, "DevAln layout");
+constexpr int ALN_WORDS = 8;
+enum { A_QI = 0, A_SEQ = 1, A_QS = 2, A_QE = 3, A_DS = 4, A_DE = 5, A_SCORE = 6 };
+
+// ------------------------------------------------------ a5: query codes --
+// Per global query offset x: query id and offset (qinfo = qi << 16 | qpos),
+// k-mer code and the length of its occurrence list (0 for no window).
+__global__ void k_query_codes(const uint64_t *__restrict__ qstart, uint32_t nq, uint64_t M,
+                              const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb, int k,
+                              const uint64_t *__restrict__ off, uint32_t *__restrict__ codes,
+                              uint32_t *__restrict__ qinfo, uint32_t *__restrict__ cnt) {
+    uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= M) return;
+    uint32_t qi = dev_upper_index(qstart, nq + 1, x);
+    uint64_t qpos = x - qstart[qi];
+    uint64_t m = qstart[qi + 1] - qstart[qi];
+    uint32_t c = 0, n = 0;
+    if (qpos + (uint64_t)k <= m && !dev_has_nonbase(qnb, x, k)) {
+        c = dev_kmer(qpk, x, k);
+        n = (uint32_t)(off[c + 1] - off[c]);
+    }
+    codes[x] = c;
+    qinfo[x] = (qi << 16) | (uint32_t)qpos;
+    cnt[x] = n;
+}
+
+__global__ void k_gather_u64(const uint64_t *__restrict__ src, const uint64_t *__restrict__ idx, uint32_t n,
+                             uint64_t *__restrict__ out) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = src[idx[i]];
+}
+
+// ------------------------------------------------------- a6: seed gather --
+// A warp takes 32 consecutive query offsets; their occurrence lists are
+// copied one after another by the whole warp (coalesced reads of the list,
+// coalesced writes of the hit keys).
+// key = (gpos - qpos + QBIAS) << (16 + qbits) | (qi - qa) << 16 | qpos
+__global__ void __launch_bounds__(256) k_seed_gather(const uint32_t *__restrict__ codes,
+                                                     const uint32_t *__restrict__ qinfo,
+                                                     const uint64_t *__restrict__ hoff, uint64_t xa, uint64_t xb,
+                                                     uint64_t ha, const uint64_t *__restrict__ off,
+                                                     const uint32_t *__restrict__ post, uint32_t qa, int qbits,
+                                                     uint64_t *__restrict__ keys) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (uint64_t x0 = xa + warp * 32; x0 < xb; x0 += nwarps * 32) {
+        uint64_t x = x0 + lane;
+        uint32_t my_cnt = 0;
+        uint64_t my_src = 0, my_dst = 0, my_pref = 0;
+        uint32_t my_qpos = 0;
+        if (x < xb) {
+            my_cnt = (uint32_t)(hoff[x + 1] - hoff[x]);
+            if (my_cnt) {
+                uint32_t qinf = qinfo[x];
+                my_src = off[codes[x]];
+                my_dst = hoff[x] - ha;
+                my_qpos = qinf & 0xFFFFu;
+                my_pref = ((uint64_t)((qinf >> 16) - qa) << 16) | my_qpos;
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
+        while (todo) {
+            int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
+            uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
+            uint64_t dp = __shfl_sync(0xffffffffu, my_dst, src);
+            uint64_t pref = __shfl_sync(0xffffffffu, my_pref, src);
+            uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
+            for (uint32_t j = lane; j < cnt; j += 32) {
+                uint64_t g = post[sp + j];
+                uint64_t gkey = g + QBIAS - qpos;
+                keys[dp + j] = (gkey << (16 + qbits)) | pref;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------ a8: hit merging --
+struct HitKey {
+    uint64_t gkey;  // gpos - qpos + QBIAS
+    uint32_t ql, qpos;
+};
+
+__device__ __forceinline__ HitKey dec_key(uint64_t key, int qbits) {
+    HitKey h;
+    h.qpos = (uint32_t)(key & 0xFFFFu);
+    h.ql = (uint32_t)((key >> 16) & ((1ull << qbits) - 1ull));
+    h.gkey = key >> (16 + qbits);
+    return h;
+}
+
+// b directly follows a in one chain: same diagonal key and query, query gap <= D, same bank sequence
+__device__ __forceinline__ bool dev_linked(uint64_t a, uint64_t b, int qbits, uint32_t D,
+                                           const uint64_t *__restrict__ seq_start, uint32_t n_seqs) {
+    if ((a >> 16) != (b >> 16)) return false;
+    uint32_t qa = (uint32_t)(a & 0xFFFFu), qb = (uint32_t)(b & 0xFFFFu);
+    if (qb - qa > D) return false;
+    uint64_t gk = b >> (16 + qbits);
+    uint64_t ga = gk - QBIAS + qa, gb = gk - QBIAS + qb;
+    return dev_upper_index(seq_start, n_seqs + 1, ga) == dev_upper_index(seq_start, n_seqs + 1, gb);
+}
+
+__global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int qbits, uint32_t qa, int k,
+                            uint32_t D, uint32_t min_len, const uint64_t *__restrict__ seq_start, uint32_t n_seqs,
+                            DevHsp *__restrict__ out, uint32_t *__restrict__ count, uint32_t cap,
+                            uint32_t *__restrict__ status) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint64_t key = keys[i];
+        if (i > 0 && dev_linked(keys[i - 1], key, qbits, D, seq_start, n_seqs)) continue;
+        uint64_t j = i, kj = key;
+        while (j + 1 < n) {
+            uint64_t kn = keys[j + 1];
+            if (!dev_linked(kj, kn, qbits, D, seq_start, n_seqs)) break;
+            kj = kn;
+            ++j;
+        }
+        HitKey a = dec_key(key, qbits), b = dec_key(kj, qbits);
+        uint32_t qs = a.qpos, qe = b.qpos + (uint32_t)k;
+        uint32_t len = qe - qs;
+        if (len < min_len) continue;
+        uint64_t gpos = a.gkey - QBIAS + a.qpos;
+        uint32_t sq = dev_upper_index(seq_start, n_seqs + 1, gpos);
+        uint32_t ds = (uint32_t)(gpos - seq_start[sq]);
+        uint32_t slot = atomicAdd(count, 1u);
+        if (slot < cap) {
+            DevHsp h;
+            h.qi = qa + a.ql; h.seq = sq; h.qs = qs; h.qe = qe; h.ds = ds; h.de = ds + len; h.len = len;
+            out[slot] = h;
+        } else {
+            atomicOr(status, DEV_ERR_CAPACITY);
+        }
+    }
+}
+
+// quadruples (query, qpos, seq, pos) of sorted hits (tests)
+__global__ void k_decode_hits(const uint64_t *__restrict__ keys, uint64_t n, int qbits, uint32_t qa,
+                              const uint64_t *__restrict__ seq_start, uint32_t n_seqs, uint32_t *__restrict__ out) {
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    HitKey h = dec_key(keys[i], qbits);
+    uint64_t gpos = h.gkey - QBIAS + h.qpos;
+    uint32_t sq = dev_upper_index(seq_start, n_seqs + 1, gpos);
+    out[4 * i + 0] = qa + h.ql;
+    out[4 * i + 1] = h.qpos;
+    out[4 * i + 2] = sq;
+    out[4 * i + 3] = (uint32_t)(gpos - seq_start[sq]);
+}
+
+// --------------------------------------------------- a9: X-drop extension --
+__device__ __forceinline__ int32_t dev_pair(uint32_t a, uint32_t b, int32_t match, int32_t mismatch) {
+    return (a < 4u && a == b) ? match : mismatch;
+}
+
+__global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__restrict__ qpk,
+                        const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
+                        const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                        const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch, int32_t X) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    DevHsp r = h[i];
+    const uint64_t qb = qstart[r.qi], sb = seq_start[r.seq];
+    const uint32_t m = (uint32_t)(qstart[r.qi + 1] - qb), L = (uint32_t)(seq_start[r.seq + 1] - sb);
+    int32_t score = 0, best = 0;
+    uint32_t ext = 0;
+    for (uint32_t e = 1; e <= r.qs && e <= r.ds; ++e) {
+        score += dev_pair(dev_base(qpk, qnb, qb + r.qs - e), dev_base(bpk, bnb, sb + r.ds - e), match, mismatch);
+        if (score > best) { best = score; ext = e; }
+        else if (best - score > X) break;
+    }
+    r.qs -= ext;
+    r.ds -= ext;
+    score = 0; best = 0; ext = 0;
+    for (uint32_t e = 1; r.qe + e - 1 < m && r.de + e - 1 < L; ++e) {
+        score += dev_pair(dev_base(qpk, qnb, qb + r.qe + e - 1), dev_base(bpk, bnb, sb + r.de + e - 1), match,
+                          mismatch);
+        if (score > best) { best = score; ext = e; }
+        else if (best - score > X) break;
+    }
+    r.qe += ext;
+    r.de += ext;
+    r.len = min(r.qe - r.qs, r.de - r.ds);
+    h[i] = r;
+}
+
+// -------------------------------------------------- a10: overlap merging --
+// Records sorted by (qi, seq, qs, ds, qe, de).  The first record of each
+// (qi, seq) run sweeps the run: each record joins the current box when both its
+// query and bank ranges intersect the box, otherwise it starts a new box.  Box
+// i is written at the index of its first record; flag marks box heads.
+__global__ void k_overlap_sweep(const DevHsp *__restrict__ in, uint32_t n, DevHsp *__restrict__ out,
+                                uint32_t *__restrict__ flag) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // only the head of a (qi, seq) run writes, for every record of the run
+    if (i > 0 && in[i - 1].qi == in[i].qi && in[i - 1].seq == in[i].seq) return;
+    uint32_t j = i;
+    while (j < n) {
+        DevHsp box = in[j];
+        uint32_t head = j;
+        ++j;
+        while (j < n && in[j].qi == box.qi && in[j].seq == box.seq) {
+            DevHsp h = in[j];
+            bool q_meet = h.qs < box.qe && box.qs < h.qe;
+            bool d_meet = h.ds < box.de && box.ds < h.de;
+            if (!(q_meet && d_meet)) break;
+            box.qs = min(box.qs, h.qs);
+            box.qe = max(box.qe, h.qe);
+            box.ds = min(box.ds, h.ds);
+            box.de = max(box.de, h.de);
+            flag[j] = 0;
+            ++j;
+        }
+        box.len = min(box.qe - box.qs, box.de - box.ds);
+        out[head] = box;
+        flag[head] = 1;
+        if (j >= n || in[j].qi != in[i].qi || in[j].seq != in[i].seq) break;
+    }
+}
+
+// ----------------------------------------------------- a11: selection --
+__global__ void k_first_of_query(const uint32_t *__restrict__ recs, int W, uint32_t n, uint32_t *__restrict__ first) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t q = recs[(uint64_t)i * W];
+    if (i == 0 || recs[(uint64_t)(i - 1) * W] != q) first[q] = i;
+}
+
+__global__ void k_select_flags(const DevHsp *__restrict__ h, uint32_t n, const uint32_t *__restrict__ first,
+                               uint32_t N, uint32_t *__restrict__ flag) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = (N == 0 || i - first[h[i].qi] < N) ? 1u : 0u;
+}
+
+// -------------------------------------------- a12: banded Smith-Waterman --
+// One warp per selected HSP.  Lanes own band offsets b (diagonal j - i = dlo + b);
+// rows i of the DP window are processed in order, each row in chunks of 32
+// offsets.  The previous row (H, E and their start cells) lives in a per-HSP
+// scratch strip of B entries.  Horizontal gaps (F) inside a row are resolved
+// by a warp max-scan of X(b') = H0(b') + go + ge - ge*b' (H0 = the cell's best
+// over 0, diagonal and vertical gap), since F(b) = max_{b'<b} X(b') + ge*(b-1)
+// reproduces the sequential recurrence, including its "open wins ties" choice
+// when the scan keeps the later of equal values.
+struct SwCell {
+    int32_t H, E;
+    uint32_t SH, SE;  // start cells: (row - I0) << 16 | band offset
+};
+
+constexpr int32_t SW_NEG = -(1 << 29);
+constexpr int32_t SW_XNEG = -(1 << 30);
+
+__device__ __forceinline__ void scan_pair_max(int32_t &v, uint32_t &s, int lane) {
+    // inclusive scan, later lane wins ties
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t ov = __shfl_up_sync(0xffffffffu, v, o);
+        uint32_t os = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o && ov > v) { v = ov; s = os; }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ sel, uint32_t n,
+                                                   const uint64_t *__restrict__ strip_off, SwCell *__restrict__ strips,
+                                                   const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
+                                                   const uint64_t *__restrict__ qstart,
+                                                   const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                                                   const uint64_t *__restrict__ seq_start, int32_t match,
+                                                   int32_t mismatch, int32_t go, int32_t ge, int32_t w,
+                                                   uint32_t *__restrict__ next_task, DevAln *__restrict__ out,
+                                                   uint32_t *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t task = 0;
+        if (lane == 0) task = atomicAdd(next_task, 1u);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if (task >= n) return;
+        const DevHsp h = sel[task];
+        const uint64_t qb = qstart[h.qi], sb = seq_start[h.seq];
+        const int64_t m = (int64_t)(qstart[h.qi + 1] - qb), L = (int64_t)(seq_start[h.seq + 1] - sb);
+        const int64_t d_s = (int64_t)h.ds - h.qs, d_e = (int64_t)h.de - h.qe;
+        const int64_t dlo = min(d_s, d_e) - w, dhi = max(d_s, d_e) + w;
+        const int64_t I0 = max((int64_t)0, (int64_t)h.qs - w), I1 = min(m, (int64_t)h.qe + w);
+        const int64_t J0 = max((int64_t)0, (int64_t)h.ds - w), J1 = min(L, (int64_t)h.de + w);
+        const int64_t B = dhi - dlo + 1;
+        DevAln res;
+        res.qi = h.qi; res.seq = h.seq; res.qs = res.qe = res.ds = res.de = 0; res.score = 0; res.pad = 0;
+        if (B > 65535 || I1 - I0 > 65535) {
+            if (lane == 0) { atomicOr(status, DEV_ERR_BAND_TOO_WIDE); out[task] = res; }
+            continue;
+        }
+        SwCell *row = strips + strip_off[task];
+        int32_t best = 0;
+        int64_t bi = INT64_MAX, bj = INT64_MAX;
+        uint32_t bs = 0;
+        const int32_t goe = go + ge;
+        for (int64_t i = I0; i < I1; ++i) {
+            const int64_t blo = max((int64_t)0, J0 - i - dlo), bhi = min(B - 1, J1 - 1 - i - dlo);
+            if (blo > bhi) continue;
+            const bool prow = i - 1 >= I0;
+            const int64_t pblo = max((int64_t)0, J0 - (i - 1) - dlo), pbhi = min(B - 1, J1 - 1 - (i - 1) - dlo);
+            const uint32_t qc = dev_base(qpk, qnb, qb + (uint64_t)i);
+            int32_t carry_v = SW_XNEG;
+            uint32_t carry_s = 0;
+            for (int64_t c0 = blo; c0 <= bhi; c0 += 32) {
+                const int64_t b = c0 + lane;
+                const bool act = b <= bhi;
+                SwCell pd{0, SW_NEG, 0, 0}, pu{0, SW_NEG, 0, 0};
+                const bool ok_d = act && prow && b >= pblo && b <= pbhi;
+                const bool ok_u = act && prow && b + 1 >= pblo && b + 1 <= pbhi;
+                if (ok_d) pd = row[b];
+                if (ok_u) pu = row[b + 1];
+                __syncwarp();
+                int32_t E = SW_NEG;
+                uint32_t SE = 0;
+                if (ok_u) {
+                    int32_t eo = pu.H + goe, ee = pu.E + ge;
+                    if (eo >= ee) { E = eo; SE = pu.SH; } else { E = ee; SE = pu.SE; }
+                }
+                const int32_t Hd = ok_d ? pd.H : 0;
+                const uint32_t SD = (Hd > 0) ? pd.SH : ((uint32_t)(i - I0) << 16) | (uint32_t)b;
+                const int64_t j = i + dlo + b;
+                int32_t sigma = mismatch;
+                if (act) sigma = dev_pair(qc, dev_base(bpk, bnb, sb + (uint64_t)j), match, mismatch);
+                const int32_t Dg = Hd + sigma;
+                int32_t cand;
+                uint32_t Sc;
+                if (Dg >= E) { cand = Dg; Sc = SD; } else { cand = E; Sc = SE; }
+                const int32_t H0 = cand > 0 ? cand : 0;
+                // F by max-scan with carry from earlier chunks of this row
+                int32_t xv = act ? H0 + goe - ge * (int32_t)b : SW_XNEG;
+                uint32_t xs = Sc;
+                scan_pair_max(xv, xs, lane);
+                int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1);
+                uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1);
+                // the carry (earlier chunks) wins only when strictly larger
+                if (lane == 0) { ev = carry_v; es = carry_s; }
+                else if (carry_v > ev) { ev = carry_v; es = carry_s; }
+                int32_t last_v = __shfl_sync(0xffffffffu, xv, 31);
+                uint32_t last_s = __shfl_sync(0xffffffffu, xs, 31);
+                if (last_v >= carry_v) { carry_v = last_v; carry_s = last_s; }
+                int32_t F = (ev > SW_XNEG) ? ev + ge * (int32_t)(b - 1) : SW_NEG;
+                uint32_t SF = es;
+                int32_t H;
+                uint32_t SH;
+                if (H0 >= F) { H = H0; SH = Sc; } else { H = F; SH = SF; }
+                if (act) {
+                    SwCell c;
+                    c.H = H; c.E = E; c.SH = SH; c.SE = SE;
+                    row[b] = c;
+                    if (H > best) { best = H; bi = i; bj = j; bs = SH; }
+                }
+                __syncwarp();
+            }
+        }
+        // reduce: highest score, then smallest i, then smallest j
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            int32_t ob = __shfl_down_sync(0xffffffffu, best, o);
+            int64_t oi = __shfl_down_sync(0xffffffffu, bi, o);
+            int64_t oj = __shfl_down_sync(0xffffffffu, bj, o);
+            uint32_t os = __shfl_down_sync(0xffffffffu, bs, o);
+            if (ob > best || (ob == best && (oi < bi || (oi == bi && oj < bj)))) {
+                best = ob; bi = oi; bj = oj; bs = os;
+            }
+        }
+        if (lane == 0) {
+            if (best > 0) {
+                int64_t i0 = I0 + (int64_t)(bs >> 16);
+                int64_t j0 = i0 + dlo + (int64_t)(bs & 0xFFFFu);
+                res.qs = (uint32_t)i0; res.qe = (uint32_t)(bi + 1);
+                res.ds = (uint32_t)j0; res.de = (uint32_t)(bj + 1);
+                res.score = best;
+            }
+            out[task] = res;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_band_width(const DevHsp *__restrict__ h, uint32_t n, int32_t w, uint32_t *__restrict__ B) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t d_s = (int64_t)h[i].ds - h[i].qs, d_e = (int64_t)h[i].de - h[i].qe;
+    int64_t b = (max(d_s, d_e) + w) - (min(d_s, d_e) - w) + 1;
+    B[i] = (uint32_t)min(b + 1, (int64_t)65537);  // +1: the strip is read at b + 1
+}
+
+// ------------------------------------------------------ a13: ranking --
+__global__ void k_dup_flags(const DevAln *__restrict__ a, uint32_t n, uint32_t *__restrict__ flag) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const DevAln x = a[i];
+    bool keep = x.score > 0;
+    if (keep && i > 0) {
+        const DevAln y = a[i - 1];
+        if (y.qi == x.qi && y.seq == x.seq && y.qs == x.qs && y.qe == x.qe && y.ds == x.ds && y.de == x.de)
+            keep = false;
+    }
+    flag[i] = keep ? 1u : 0u;
+}
+
+__global__ void k_finalize(const DevAln *__restrict__ a, uint32_t n, const uint32_t *__restrict__ first,
+                           const uint64_t *__restrict__ qstart, double n_bank, double lambda, double K,
+                           double max_e, gn_hit *__restrict__ out, uint32_t *__restrict__ flag) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const DevAln x = a[i];
+    double m = (double)(qstart[x.qi + 1] - qstart[x.qi]);
+    gn_hit h;
+    h.query = x.qi; h.seq = x.seq; h.q_start = x.qs; h.q_end = x.qe; h.db_start = x.ds; h.db_end = x.de;
+    h.score = x.score;
+    h.rank = i - first[x.qi];
+    h.evalue = K * m * n_bank * exp(-lambda * (double)x.score);
+    h.bits = (lambda * (double)x.score - log(K)) / log(2.0);
+    out[i] = h;
+    flag[i] = (h.evalue <= max_e) ? 1u : 0u;
+}
+
+// ------------------------------------------------------------ compaction --
+__global__ void k_scatter_flagged(const uint32_t *__restrict__ in, int W, const uint32_t *__restrict__ flags,
+                                  const uint64_t *__restrict__ pos, uint32_t n, uint32_t *__restrict__ out) {
+    uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint64_t)n * W) return;
+    uint32_t i = (uint32_t)(t / W), w = (uint32_t)(t % W);
+    if (flags[i]) out[pos[i] * W + w] = in[t];
+}
+
+uint32_t compact_records(const uint32_t *in, int W, const uint32_t *flags, uint32_t n, uint32_t *out,
+                         DeviceArena &arena, cudaStream_t s) {
+    if (n == 0) return 0;
+    uint64_t *pos = arena.alloc_n<uint64_t>(n + 1);
+    void *scr = arena.alloc(scan_scratch_bytes(n));
+    exclusive_scan_u32(flags, pos, n, scr, s);
+    uint64_t tot = (uint64_t)n * W;
+    k_scatter_flagged<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(in, W, flags, pos, n, out);
+    GN_CHECK_LAUNCH();
+    uint64_t cnt = 0;
+    GN_CUDA(cudaMemcpyAsync(&cnt, pos + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    GN_CUDA(cudaStreamSynchronize(s));
+    return (uint32_t)cnt;
+}
+
+// ---------------------------------------------------------------- driver --
+namespace {
+struct PhaseTimer {
+    cudaStream_t s;
+    std::vector<std::pair<const char *, cudaEvent_t>> marks;
+    explicit PhaseTimer(cudaStream_t st) : s(st) {}
+    void mark(const char *name) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, s);
+        marks.emplace_back(name, e);
+    }
+    void finish(std::vector<std::pair<const char *, float>> &out) {
+        out.clear();
+        for (size_t i = 1; i < marks.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second);
+            out.emplace_back(marks[i].first, ms);
+        }
+    }
+    ~PhaseTimer() {
+        for (auto &m : marks) cudaEventDestroy(m.second);
+    }
+};
+
+template <class T>
+std::vector<T> to_host(const T *d, size_t n, cudaStream_t s) {
+    std::vector<T> h(n);
+    if (n) {
+        GN_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+        GN_CUDA(cudaStreamSynchronize(s));
+    }
+    return h;
+}
+
+unsigned blocks_for(uint64_t n, unsigned t = 256) { return (unsigned)std::max<uint64_t>(1, (n + t - 1) / t); }
+}  // namespace
+
+void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart_h, const SearchOptions &o,
+            cudaStream_t s, gn_results *res) {
+    const uint32_t nq = (uint32_t)(qstart_h.size() - 1);
+    const uint64_t M = qstart_h[nq];
+    const int k = ix->k;
+    const gn_params &p = o.p;
+    const gn_scoring &sc = o.sc;
+    const bool keep = (p.flags & GN_FLAG_KEEP_STAGES) != 0;
+    const bool keep_hits = (p.flags & GN_FLAG_KEEP_HITS) != 0;
+    res->n_queries = nq;
+    res->has_stages = keep;
+    PhaseTimer timer(s);
+    timer.mark("start");
+    DeviceArena arena(s);
+
+    // a5: pack queries, code every offset, list lengths
+    Packed qp;
+    qp.pk = arena.alloc_n<uint32_t>(Packed::pk_words(M));
+    qp.nb = arena.alloc_n<uint32_t>(Packed::nb_words(M));
+    pack_bases(qbases_dev, M, qp, s);
+    uint64_t *qstart_d = arena.alloc_n<uint64_t>(nq + 1);
+    GN_CUDA(cudaMemcpyAsync(qstart_d, qstart_h.data(), sizeof(uint64_t) * (nq + 1), cudaMemcpyHostToDevice, s));
+    uint32_t *codes = arena.alloc_n<uint32_t>(M);
+    uint32_t *qinfo = arena.alloc_n<uint32_t>(M);
+    uint32_t *cnt = arena.alloc_n<uint32_t>(M);
+    uint64_t *hoff = arena.alloc_n<uint64_t>(M + 1);
+    if (M) {
+        k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, k, ix->off_d, codes, qinfo, cnt);
+        GN_CHECK_LAUNCH();
+    }
+    {
+        void *scr = arena.alloc(scan_scratch_bytes(M));
+        exclusive_scan_u32(cnt, hoff, M, scr, s);
+    }
+    // hit offsets at query boundaries -> per-query hit counts (chunk plan)
+    uint64_t *hq_d = arena.alloc_n<uint64_t>(nq + 1);
+    k_gather_u64<<<blocks_for(nq + 1), 256, 0, s>>>(hoff, qstart_d, nq + 1, hq_d);
+    GN_CHECK_LAUNCH();
+    std::vector<uint64_t> hq = to_host(hq_d, nq + 1, s);
+    timer.mark("query_codes");
+    if (keep) {
+        res->st_hit_counts.resize(nq);
+        for (uint32_t i = 0; i < nq; ++i) res->st_hit_counts[i] = hq[i + 1] - hq[i];
+    }
+
+    // a6-a8 per chunk of queries whose hits fit the budget
+    size_t free_b = 0, total_b = 0;
+    GN_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t hit_budget = std::max<uint64_t>(1ull << 20, (uint64_t)(free_b * 0.55) / 16);
+    if (const char *e = getenv("GN_MAX_CHUNK_HITS")) {  // smaller chunks (exercises the multi-chunk path)
+        uint64_t v = strtoull(e, nullptr, 10);
+        if (v) hit_budget = v;
+    }
+    const uint64_t gbits_max = (uint64_t)bits_for(ix->n_bases + QBIAS);
+    const uint32_t max_chunk_q = (uint32_t)std::min<uint64_t>(MAX_QUERIES, 1ull << std::min<uint64_t>(48 - gbits_max, 31));
+
+    uint32_t hsp_cap = 1u << 16;
+    DevHsp *hsp = arena.alloc_n<DevHsp>(hsp_cap);
+    uint32_t n_hsp = 0;
+    uint32_t *counter = arena.alloc_n<uint32_t>(4);
+    uint32_t *status = arena.alloc_n<uint32_t>(1);
+    GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
+    std::vector<uint32_t> hits_q;
+
+    uint32_t qa = 0;
+    while (qa < nq) {
+        uint32_t qb = qa + 1;
+        while (qb < nq && qb - qa < max_chunk_q && hq[qb + 1] - hq[qa] <= hit_budget) ++qb;
+        const uint64_t xa = qstart_h[qa], xb = qstart_h[qb];
+        const uint64_t ha = hq[qa], Hc = hq[qb] - hq[qa];
+        if (Hc > 0) {
+            const int qbits = bits_for(qb - qa - 1);
+            const int gbits = (int)gbits_max;
+            DeviceArena carena(s);
+            uint64_t *keys = carena.alloc_n<uint64_t>(Hc);
+            uint64_t *keys_alt = carena.alloc_n<uint64_t>(Hc);
+            void *rs = carena.alloc(radix_scratch_bytes(Hc));
+            uint64_t gwarps = std::min<uint64_t>((xb - xa + 31) / 32, (uint64_t)num_sms() * 64);
+            k_seed_gather<<<blocks_for(gwarps * 32), 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ha, ix->off_d, ix->post_d,
+                                                                  qa, qbits, keys);
+            GN_CHECK_LAUNCH();
+            timer.mark("seed_gather");
+            bool fl = radix_sort(keys, keys_alt, nullptr, nullptr, Hc, 16 + qbits, 16 + qbits + gbits, rs, s);
+            uint64_t *sorted = fl ? keys_alt : keys;
+            timer.mark("hit_sort");
+            if (keep_hits) {
+                uint32_t *quad = carena.alloc_n<uint32_t>(4 * Hc);
+                k_decode_hits<<<blocks_for(Hc), 256, 0, s>>>(sorted, Hc, qbits, qa, ix->seq_start_d, ix->n_seqs, quad);
+                GN_CHECK_LAUNCH();
+                std::vector<uint32_t> hh = to_host(quad, 4 * Hc, s);
+                hits_q.insert(hits_q.end(), hh.begin(), hh.end());
+            }
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
+                uint64_t threads = std::min<uint64_t>(Hc, (uint64_t)num_sms() * 2048);
+                k_hit_merge<<<blocks_for(threads), 256, 0, s>>>(sorted, Hc, qbits, qa, k, p.max_hit_distance,
+                                                                p.min_hsp_len, ix->seq_start_d, ix->n_seqs,
+                                                                hsp + n_hsp, counter, hsp_cap - n_hsp, status);
+                GN_CHECK_LAUNCH();
+                uint32_t got = 0;
+                GN_CUDA(cudaMemcpyAsync(&got, counter, 4, cudaMemcpyDeviceToHost, s));
+                GN_CUDA(cudaStreamSynchronize(s));
+                if (n_hsp + (uint64_t)got <= hsp_cap) {
+                    n_hsp += got;
+                    break;
+                }
+                // grow the HSP buffer and redo this chunk's merge
+                uint64_t need = (uint64_t)n_hsp + got;
+                GN_REQUIRE(need < (1ull << 32), GN_ETOOBIG, "more than 2^32 HSPs in one call");
+                uint32_t ncap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(need + need / 4, 2ull * hsp_cap));
+                DevHsp *nh = arena.alloc_n<DevHsp>(ncap);
+                if (n_hsp) GN_CUDA(cudaMemcpyAsync(nh, hsp, sizeof(DevHsp) * n_hsp, cudaMemcpyDeviceToDevice, s));
+                hsp = nh;
+                hsp_cap = ncap;
+                GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
+            }
+            timer.mark("hit_merge");
+        }
+        qa = qb;
+    }
+    if (keep_hits) res->st_hits.swap(hits_q);
+    if (keep) {
+        std::vector<DevHsp> v = to_host(hsp, n_hsp, s);
+        res->st_hsp.resize(n_hsp);
+        if (n_hsp) memcpy(res->st_hsp.data(), v.data(), sizeof(DevHsp) * n_hsp);
+    }
+
+    // a9: extension
+    if (n_hsp) {
+        k_xdrop<<<blocks_for(n_hsp, 128), 128, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d, ix->bank.pk, ix->bank.nb,
+                                                       ix->seq_start_d, sc.match, sc.mismatch, p.xdrop);
+        GN_CHECK_LAUNCH();
+    }
+    timer.mark("xdrop_extend");
+    if (keep) {
+        std::vector<DevHsp> v = to_host(hsp, n_hsp, s);
+        res->st_ext.resize(n_hsp);
+        if (n_hsp) memcpy(res->st_ext.data(), v.data(), sizeof(DevHsp) * n_hsp);
+    }
+
+    const int qib = bits_for(nq ? nq - 1 : 0);
+    const int seqb = bits_for(ix->n_seqs ? ix->n_seqs - 1 : 0);
+    const int posb = bits_for(ix->max_seq_len);
+    const int qposb = 16;
+
+    // a10: merge overlapped HSPs
+    uint32_t n_mg = 0;
+    DevHsp *merged = arena.alloc_n<DevHsp>(n_hsp);
+    if (n_hsp) {
+        uint32_t *perm = arena.alloc_n<uint32_t>(n_hsp);
+        sort_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, n_hsp,
+                     {{W_QI, qib, false}, {W_SEQ, seqb, false}, {W_QS, qposb, false}, {W_DS, posb, false},
+                      {W_QE, qposb + 1, false}, {W_DE, posb + 1, false}},
+                     perm, arena, s);
+        DevHsp *srt = arena.alloc_n<DevHsp>(n_hsp);
+        gather_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, perm, n_hsp,
+                       reinterpret_cast<uint32_t *>(srt), s);
+        DevHsp *boxes = arena.alloc_n<DevHsp>(n_hsp);
+        uint32_t *flag = arena.alloc_n<uint32_t>(n_hsp);
+        k_overlap_sweep<<<blocks_for(n_hsp), 256, 0, s>>>(srt, n_hsp, boxes, flag);
+        GN_CHECK_LAUNCH();
+        n_mg = compact_records(reinterpret_cast<const uint32_t *>(boxes), HSP_WORDS, flag, n_hsp,
+                               reinterpret_cast<uint32_t *>(merged), arena, s);
+    }
+    timer.mark("overlap_merge");
+    if (keep) {
+        std::vector<DevHsp> v = to_host(merged, n_mg, s);
+        res->st_merged.resize(n_mg);
+        if (n_mg) memcpy(res->st_merged.data(), v.data(), sizeof(DevHsp) * n_mg);
+    }
+
+    // a11: longest first, at most max_alignments per query
+    uint32_t n_sel = 0;
+    DevHsp *sel = arena.alloc_n<DevHsp>(n_mg);
+    uint32_t *first = arena.alloc_n<uint32_t>(nq);
+    if (n_mg) {
+        uint32_t *perm = arena.alloc_n<uint32_t>(n_mg);
+        sort_records(reinterpret_cast<const uint32_t *>(merged), HSP_WORDS, n_mg,
+                     {{W_QI, qib, false}, {W_LEN, qposb + 1, true}, {W_SEQ, seqb, false}, {W_QS, qposb, false},
+                      {W_DS, posb, false}, {W_QE, qposb + 1, false}, {W_DE, posb + 1, false}},
+                     perm, arena, s);
+        DevHsp *srt = arena.alloc_n<DevHsp>(n_mg);
+        gather_records(reinterpret_cast<const uint32_t *>(merged), HSP_WORDS, perm, n_mg,
+                       reinterpret_cast<uint32_t *>(srt), s);
+        k_first_of_query<<<blocks_for(n_mg), 256, 0, s>>>(reinterpret_cast<const uint32_t *>(srt), HSP_WORDS, n_mg, first);
+        GN_CHECK_LAUNCH();
+        uint32_t *flag = arena.alloc_n<uint32_t>(n_mg);
+        k_select_flags<<<blocks_for(n_mg), 256, 0, s>>>(srt, n_mg, first, p.max_alignments, flag);
+        GN_CHECK_LAUNCH();
+        n_sel = compact_records(reinterpret_cast<const uint32_t *>(srt), HSP_WORDS, flag, n_mg,
+                                reinterpret_cast<uint32_t *>(sel), arena, s);
+    }
+    timer.mark("select");
+    if (keep) {
+        std::vector<DevHsp> v = to_host(sel, n_sel, s);
+        res->st_sel.resize(n_sel);
+        if (n_sel) memcpy(res->st_sel.data(), v.data(), sizeof(DevHsp) * n_sel);
+    }
+
+    // a12: banded Smith-Waterman
+    DevAln *aln = arena.alloc_n<DevAln>(n_sel);
+    if (n_sel) {
+        uint32_t *B = arena.alloc_n<uint32_t>(n_sel);
+        uint64_t *soff = arena.alloc_n<uint64_t>(n_sel + 1);
+        k_band_width<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, B);
+        GN_CHECK_LAUNCH();
+        void *scr = arena.alloc(scan_scratch_bytes(n_sel));
+        exclusive_scan_u32(B, soff, n_sel, scr, s);
+        uint64_t cells = 0;
+        GN_CUDA(cudaMemcpyAsync(&cells, soff + n_sel, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        GN_CUDA(cudaStreamSynchronize(s));
+        SwCell *strips = arena.alloc_n<SwCell>(cells);
+        GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
+        unsigned warps = (unsigned)std::min<uint64_t>(n_sel, (uint64_t)num_sms() * 32);
+        k_banded_sw<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
+                                                            ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
+                                                            sc.mismatch, sc.gap_open, sc.gap_extend,
+                                                            (int32_t)p.band_w, counter, aln, status);
+        GN_CHECK_LAUNCH();
+    }
+    timer.mark("banded_sw");
+    if (keep) {
+        std::vector<DevAln> v = to_host(aln, n_sel, s);
+        res->st_aln.resize(n_sel);
+        for (uint32_t i = 0; i < n_sel; ++i) {
+            gn_hit &h = res->st_aln[i];
+            h.query = v[i].qi; h.seq = v[i].seq; h.q_start = v[i].qs; h.q_end = v[i].qe;
+            h.db_start = v[i].ds; h.db_end = v[i].de; h.score = v[i].score; h.rank = 0; h.evalue = 0; h.bits = 0;
+        }
+    }
+
+    // a13: duplicates (same query, sequence and ranges: keep the best score), rank by score, statistics
+    uint32_t n_out = 0;
+    gn_hit *fin = arena.alloc_n<gn_hit>(n_sel);
+    if (n_sel) {
+        const int scb = std::min(31, bits_for((uint64_t)65535 * (uint64_t)std::max(1, sc.match)));
+        uint32_t *perm = arena.alloc_n<uint32_t>(n_sel);
+        sort_records(reinterpret_cast<const uint32_t *>(aln), ALN_WORDS, n_sel,
+                     {{A_QI, qib, false}, {A_SEQ, seqb, false}, {A_QS, qposb, false}, {A_QE, qposb + 1, false},
+                      {A_DS, posb, false}, {A_DE, posb + 1, false}, {A_SCORE, scb, true}},
+                     perm, arena, s);
+        DevAln *srt = arena.alloc_n<DevAln>(n_sel);
+        gather_records(reinterpret_cast<const uint32_t *>(aln), ALN_WORDS, perm, n_sel, reinterpret_cast<uint32_t *>(srt), s);
+        uint32_t *flag = arena.alloc_n<uint32_t>(n_sel);
+        k_dup_flags<<<blocks_for(n_sel), 256, 0, s>>>(srt, n_sel, flag);
+        GN_CHECK_LAUNCH();
+        DevAln *uniq = arena.alloc_n<DevAln>(n_sel);
+        uint32_t nu = compact_records(reinterpret_cast<const uint32_t *>(srt), ALN_WORDS, flag, n_sel,
+                                      reinterpret_cast<uint32_t *>(uniq), arena, s);
+        if (nu) {
+            uint32_t *perm2 = arena.alloc_n<uint32_t>(nu);
+            sort_records(reinterpret_cast<const uint32_t *>(uniq), ALN_WORDS, nu,
+                         {{A_QI, qib, false}, {A_SCORE, scb, true}, {A_SEQ, seqb, false}, {A_QS, qposb, false},
+                          {A_DS, posb, false}, {A_QE, qposb + 1, false}, {A_DE, posb + 1, false}},
+                         perm2, arena, s);
+            DevAln *ranked = arena.alloc_n<DevAln>(nu);
+            gather_records(reinterpret_cast<const uint32_t *>(uniq), ALN_WORDS, perm2, nu,
+                           reinterpret_cast<uint32_t *>(ranked), s);
+            k_first_of_query<<<blocks_for(nu), 256, 0, s>>>(reinterpret_cast<const uint32_t *>(ranked), ALN_WORDS, nu, first);
+            GN_CHECK_LAUNCH();
+            gn_hit *hits = arena.alloc_n<gn_hit>(nu);
+            uint32_t *f2 = arena.alloc_n<uint32_t>(nu);
+            k_finalize<<<blocks_for(nu), 256, 0, s>>>(ranked, nu, first, qstart_d, (double)ix->n_bases, sc.lambda, sc.K,
+                                                      p.max_evalue, hits, f2);
+            GN_CHECK_LAUNCH();
+            static_assert(sizeof(gn_hit) % 4 == 0, "gn_hit words");
+            n_out = compact_records(reinterpret_cast<const uint32_t *>(hits), (int)(sizeof(gn_hit) / 4), f2, nu,
+                                    reinterpret_cast<uint32_t *>(fin), arena, s);
+        }
+    }
+    timer.mark("rank");
+    uint32_t st = 0;
+    GN_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
+    res->hits = to_host(fin, n_out, s);
+    GN_REQUIRE((st & (DEV_ERR_BAND_TOO_WIDE | DEV_ERR_BOUNDS)) == 0, GN_ETOOBIG,
+               "an alignment band or window exceeded 65,535 cells in one dimension");
+    res->qoff.assign(nq + 1, 0);
+    for (uint32_t i = 0; i < n_out; ++i) res->qoff[res->hits[i].query + 1]++;
+    for (uint32_t i = 0; i < nq; ++i) res->qoff[i + 1] += res->qoff[i];
+    timer.mark("output");
+    GN_CUDA(cudaStreamSynchronize(s));
+    {
+        std::lock_guard<std::mutex> lk(ix->phase_mu);
+        timer.finish(ix->last_phases);
+    }
+    arena.release();
+}
+
+}  // namespace gn

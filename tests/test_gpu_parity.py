@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, phase by phase.
+
+Integer outputs (index, hits, HSPs, alignments, scores, ranks) must be identical;
+e-values and bit scores agree to 1e-9 relative (both are fp64: exp and log of the
+device and of the host C library may differ in the last bit)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = (("seq", "seq"), ("q_start", "qs"), ("q_end", "qe"), ("db_start", "ds"), ("db_end", "de"),
+          ("score", "score"), ("rank", "rank"))
+
+
+@pytest.fixture(scope="module")
+def gn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1507_02987_gb300 import _build
+    _build.build()
+    import paper_1507_02987_gb300 as g
+    g.load()
+    return g
+
+
+def assert_ranked_equal(got, exp, ctx=""):
+    assert len(got) == len(exp), f"{ctx}: {len(got)} vs {len(exp)} alignments"
+    for fg, fe in FIELDS:
+        a, b = got[fg].astype(np.int64), exp[fe].astype(np.int64)
+        assert np.array_equal(a, b), f"{ctx}: field {fg} differs at {np.nonzero(a != b)[0][:5]}"
+    for f in ("evalue", "bits"):
+        a, b = got[f], exp[f]
+        tiny = (np.abs(a) < 1e-300) & (np.abs(b) < 1e-300)
+        ok = tiny | np.isclose(a, b, rtol=1e-9, atol=0)
+        assert ok.all(), f"{ctx}: {f} differs"
+
+
+def by_query(arr, qi):
+    return arr[arr["query"] == qi]
+
+
+def hsp_tuples_gpu(arr):
+    return [tuple(int(r[f]) for f in ("seq", "q_start", "q_end", "db_start", "db_end", "len")) for r in arr]
+
+
+def hsp_tuples_or(arr):
+    return [tuple(int(r[f]) for f in ("seq", "qs", "qe", "ds", "de", "len")) for r in arr]
+
+
+def aln_tuples_gpu(arr):
+    return [tuple(int(r[f]) for f in ("seq", "q_start", "q_end", "db_start", "db_end", "score")) for r in arr]
+
+
+def aln_tuples_or(arr):
+    return [tuple(int(r[f]) for f in ("seq", "qs", "qe", "ds", "de", "score")) for r in arr]
+
+
+def check_stages(g, res, ref, n, ctx):
+    hsp = res.stage(g.GN_STAGE_HSP)
+    ext = res.stage(g.GN_STAGE_EXT)
+    merged = res.stage(g.GN_STAGE_MERGED)
+    sel = res.stage(g.GN_STAGE_SELECTED)
+    aln = res.stage(g.GN_STAGE_ALIGNED)
+    counts = res.stage(g.GN_STAGE_HIT_COUNTS)
+    assert len(hsp) == len(ext)
+    for i in range(n):
+        r = ref[i]
+        c = f"{ctx} query {i}"
+        assert int(counts[i]) == r.n_hits, c
+        h_mask = hsp["query"] == i
+        assert sorted(hsp_tuples_gpu(hsp[h_mask])) == sorted(hsp_tuples_or(r.hsp)), c + " HSPs"
+        pairs_gpu = sorted(zip(hsp_tuples_gpu(hsp[h_mask]), hsp_tuples_gpu(ext[h_mask])))
+        pairs_or = sorted(zip(hsp_tuples_or(r.hsp), hsp_tuples_or(r.ext)))
+        assert pairs_gpu == pairs_or, c + " extension"
+        assert hsp_tuples_gpu(by_query(merged, i)) == hsp_tuples_or(r.merged), c + " overlap merge"
+        assert hsp_tuples_gpu(by_query(sel, i)) == hsp_tuples_or(r.sel), c + " selection"
+        assert aln_tuples_gpu(by_query(aln, i)) == aln_tuples_or(r.aln), c + " alignment"
+        assert_ranked_equal(res.query(i), r.ranked, c + " ranking")
+
+
+# ---------------------------------------------------------------- index --
+@pytest.mark.parametrize("k,t", [(11, 11), (11, 1), (5, 3), (8, 8), (16, 16)])
+def test_index_bitexact_tiny(gn, k, t):
+    bank = synth.make_bank("tiny", n_seqs=400 if k < 16 else 1000)
+    ix = gn.Index.from_bank(bank, k=k, stride=t)
+    got = ix.export() if k <= 12 else None
+    ref = oracle.Index(bank, k=k, stride=t)
+    assert ix.info().n_postings == ref.n_postings
+    if got is not None:
+        bs, ps, pp = ref.buckets()
+        assert np.array_equal(got[0], bs)
+        assert np.array_equal(got[1], ps) and np.array_equal(got[2], pp)
+
+
+def test_index_bitexact_odd_bank(gn):
+    rng = np.random.default_rng(5)
+    seqs = []
+    for i in range(300):
+        L = int(rng.integers(0, 90))
+        s = bytearray(rng.choice(list(b"ACGT"), size=L).astype(np.uint8).tobytes())
+        if L and i % 4 == 0:
+            s[int(rng.integers(L))] = ord("N")
+        if L and i % 5 == 0:
+            s[int(rng.integers(L))] = ord(rng.choice(list("acgtuU")))
+        seqs.append(bytes(s))
+    bank = synth.bank_from_strings(seqs)
+    for k, t in ((4, 2), (7, 1), (3, 3)):
+        ix = gn.Index.from_bank(bank, k=k, stride=t)
+        bs, ps, pp = ix.export()
+        r = oracle.Index(bank, k=k, stride=t).buckets()
+        assert np.array_equal(bs, r[0]) and np.array_equal(ps, r[1]) and np.array_equal(pp, r[2])
+
+
+# --------------------------------------------------------------- search --
+@pytest.fixture(scope="module")
+def tiny(gn):
+    bank = synth.make_bank("tiny")
+    qs = synth.make_queries("tiny", bank)
+    return bank, qs, gn.Index.from_bank(bank), oracle.Index(bank)
+
+
+def test_search_stages_tiny(gn, tiny):
+    bank, qs, ix, ox = tiny
+    flags = gn.GN_FLAG_KEEP_STAGES | gn.GN_FLAG_KEEP_HITS
+    res = gn.search(ix, qs.start, qs.bases, params=gn.make_params(flags=flags))
+    ref = ox.search(qs, oracle.Params(keep_hits=True))
+    hits = res.stage(gn.GN_STAGE_HITS)
+    for i in range(qs.n):
+        got = sorted((int(h["qpos"]), int(h["seq"]), int(h["pos"])) for h in hits[hits["query"] == i])
+        exp = sorted((int(h["qpos"]), int(h["seq"]), int(h["pos"])) for h in ref[i].hits)
+        assert got == exp, f"hits of query {i}"
+    check_stages(gn, res, ref, qs.n, "tiny")
+
+
+@pytest.fixture(scope="module")
+def mid_small(gn):
+    bank = synth.make_bank("mid", n_seqs=20000)
+    q1 = synth.make_queries("mid", bank, n=60)
+    q2 = synth.make_queries("batched", bank, n=60)
+    qs = synth.queries_from_strings([q1.query(i) for i in range(q1.n)] + [q2.query(i) for i in range(q2.n)])
+    return bank, qs, gn.Index.from_bank(bank), oracle.Index(bank)
+
+
+def test_search_stages_mid_small(gn, mid_small):
+    bank, qs, ix, ox = mid_small
+    res = gn.search(ix, qs.start, qs.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
+    ref = ox.search(qs, oracle.Params(), threads=os.cpu_count() or 1)
+    check_stages(gn, res, ref, qs.n, "mid")
+    assert sum(len(r.ranked) for r in ref) > 100
+
+
+def test_batched_equals_plain(gn, mid_small):
+    bank, qs, ix, ox = mid_small
+    allq = gn.search(ix, qs.start, qs.bases)
+    for i in range(0, qs.n, 7):
+        one = synth.queries_from_strings([qs.query(i)])
+        r1 = gn.search(ix, one.start, one.bases).query(0)
+        ra = allq.query(i)
+        assert np.array_equal(r1[[f for f, _ in FIELDS]], ra[[f for f, _ in FIELDS]]), i
+
+
+def test_chunked_equals_unchunked(gn, mid_small, monkeypatch):
+    bank, qs, ix, ox = mid_small
+    whole = gn.search(ix, qs.start, qs.bases).all()
+    monkeypatch.setenv("GN_MAX_CHUNK_HITS", "20000")
+    parts = gn.search(ix, qs.start, qs.bases).all()
+    for a, b in zip(whole, parts):
+        assert np.array_equal(a, b)
+
+
+def test_device_queries_equal_host_queries(gn, mid_small):
+    import torch
+    bank, qs, ix, ox = mid_small
+    a = gn.search(ix, qs.start, qs.bases).all()
+    b = gn.search(ix, qs.start, torch.from_numpy(qs.bases).cuda()).all()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("kw", [dict(max_alignments=0), dict(max_alignments=1), dict(band_w=0),
+                                dict(band_w=64), dict(xdrop=5), dict(max_hit_distance=11, min_hsp_len=33)])
+def test_parameters_mid_small(gn, mid_small, kw):
+    bank, qs, ix, ox = mid_small
+    sub = qs.subset(range(0, qs.n, 3))
+    res = gn.search(ix, sub.start, sub.bases, params=gn.make_params(**kw))
+    okw = {("max_alignments" if k == "max_alignments" else k): v for k, v in kw.items()}
+    ref = ox.search(sub, oracle.Params(**okw), threads=os.cpu_count() or 1)
+    for i in range(sub.n):
+        assert_ranked_equal(res.query(i), ref[i].ranked, f"{kw} query {i}")
+
+
+def test_edge_queries(gn, tiny):
+    bank, qs, ix, ox = tiny
+    empty = synth.queries_from_strings([])
+    r = gn.search(ix, empty.start, empty.bases)
+    assert r.n_queries == 0
+    src = bank.seq(17)
+    cases = [b"", b"ACG", b"N" * 50, src[:300], src[:150] + b"NNNN" + src[154:400], src[:300].lower(),
+             b"ACGTACGTACG"]
+    q = synth.queries_from_strings(cases)
+    res = gn.search(ix, q.start, q.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
+    ref = ox.search(q, oracle.Params())
+    check_stages(gn, res, ref, q.n, "edge")
+    assert len(res.query(3)) >= 1 and int(res.query(3)[0]["seq"]) == 17
+
+
+def test_too_long_query_rejected(gn, tiny):
+    bank, qs, ix, ox = tiny
+    q = synth.queries_from_strings([b"A" * 70000])
+    with pytest.raises(gn.GnError) as e:
+        gn.search(ix, q.start, q.bases)
+    assert e.value.status == gn.GN_ETOOBIG
