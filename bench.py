@@ -1,0 +1,436 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the Genoogle search path on GB300.
+
+Metric: query kbp/s (query bases searched per second, in thousands) against the
+~4 Gbp synthetic bank, index resident in device memory.  One step = one
+gn_search call over the whole query set of the workload (2,000 queries of
+200-20,000 bp for the default `large` workload), i.e. every phase of the
+search: query codes, seed gather, hit sort, hit merge, X-drop extension,
+overlap merge, selection, banded Smith-Waterman, ranking.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs as N independent replicas under torchrun (one bank, index and query
+set per rank; no data exchange), reported as weak scaling.  `--impl reference`
+times the CPU oracle (the plain C implementation used as the correctness
+reference) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "query kbp/s vs 4 Gbp bank (batched/served vs plain, same GPU); p50/p99 latency"
+UNIT = "kbp/s"
+
+# Algorithmic bytes per work item of each kernel (HBM-bound kernels), see the design notes:
+#   sort downsweep: read + write one 8-byte key; upsweep: read the key
+#   seed gather: read one 4-byte occurrence, write one 8-byte hit key
+#   hit merge: read one 8-byte hit key
+BYTES_PER_UNIT = {
+    "hit_sort_downsweep": 16.0,
+    "hit_sort_upsweep": 8.0,
+    "k_seed_gather": 12.0,
+    "k_hit_merge": 8.0,
+    "record_sort_downsweep": 24.0,
+    "record_sort_upsweep": 8.0,
+    "k_query_codes": 17.0,
+}
+ALU_KERNELS = {"k_banded_sw"}  # units = DP cells
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="large", choices=["tiny", "mid", "batched", "large"])
+    ap.add_argument("--stride", type=int, default=11)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-queries", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle time of the CPU baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------- plumbing --
+class Dist:
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group(backend="gloo")  # host-side barrier and timing reduction only
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "", 1).isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1507_02987_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per work item of `kernel` from the committed ncu summary, if it is current."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except Exception:
+        return None
+    if t.get("csrc_digest") != csrc_digest():
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    return k.get("dram_bytes_per_unit") if k else None
+
+
+def workload(name: str, stride: int, rank: int):
+    import dataclasses
+
+    import numpy as np
+    import synth
+    import torch
+
+    pinned = lambda n: torch.empty(int(n), dtype=torch.uint8, pin_memory=True).numpy()
+    bank = synth.make_bank(name, alloc=pinned if torch.cuda.is_available() else None)
+    spec = synth.QUERIES[name]
+    if rank:
+        spec = dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
+    queries = synth.make_queries(spec, bank)
+    desc = {
+        "tiny": "tiny bank (1,000 uniform sequences, ~1.25 Mbp), 10 mutated-copy queries",
+        "mid": "mid bank (200,000 log-normal sequences, ~400 Mbp, GC 0.35-0.65, 20% repeats), 1,000 homolog queries 80-10,000 bp",
+        "batched": "mid bank (~400 Mbp), 10,000 queries 50-5,000 bp, half planted homologs",
+        "large": "large bank (2.5 M log-normal sequences, ~4.0 Gbp, GC 0.35-0.65, 20% repeats), 2,000 queries 200-20,000 bp, half planted homologs",
+    }[name]
+    return bank, queries, f"{desc}; k=11, stride {stride}; one gn_search over all queries per step"
+
+
+def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0):
+    """Times the oracle on growing samples of the query set until one takes >= target_s/2; returns
+    (kbp/s, seconds, sample description, sample indices, results)."""
+    import oracle
+    ox = oracle.Index(bank, k=11, stride=stride)
+    n = min(queries.n, 16)
+    order = list(range(0, queries.n, max(1, queries.n // 997)))
+    while True:
+        idx = order[:n] if n <= len(order) else list(range(min(n, queries.n)))
+        sub = queries.subset(idx)
+        t0 = time.perf_counter()
+        res = ox.search(sub, oracle.Params(stride=stride), threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 2 or n >= queries.n:
+            bases = int(sub.start[-1])
+            return bases / 1e3 / dt, dt, (f"{len(idx)} of {queries.n} queries (evenly spaced), {bases} bases, "
+                                          f"all {threads} host threads, index resident"), idx, res, ox
+        n = min(queries.n, max(n + 1, int(n * min(8.0, max(2.0, target_s / max(dt, 1e-3))))))
+
+
+# ----------------------------------------------------------------- arms --
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return 0
+    bank, queries, desc = workload(args.workload, args.stride, 0)
+    import oracle
+    threads = os.cpu_count() or 1
+    ox = oracle.Index(bank, k=11, stride=args.stride)
+    # size one step to about cpu_seconds / 3 of oracle time
+    per_step = 8
+    while True:
+        sub = queries.subset(range(per_step))
+        t0 = time.perf_counter()
+        ox.search(sub, oracle.Params(stride=args.stride), threads=threads)
+        dt = time.perf_counter() - t0
+        if dt > args.cpu_seconds / 6 or per_step >= queries.n:
+            break
+        per_step = min(queries.n, per_step * 2)
+    times, bases = [], 0
+    for step in range(args.warmup + args.steps):
+        lo = (step * per_step) % queries.n
+        idx = [(lo + i) % queries.n for i in range(per_step)]
+        sub = queries.subset(idx)
+        t0 = time.perf_counter()
+        ox.search(sub, oracle.Params(stride=args.stride), threads=threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            bases += int(sub.start[-1])
+    total = sum(times)
+    value = bases / 1e3 / total
+    sample = f"{per_step} queries per step (consecutive, wrapping), all {threads} host threads, index resident"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": desc, "stride": args.stride},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, dist):
+    import numpy as np
+    import torch
+
+    import paper_1507_02987_gb300 as gn
+
+    dev = dist.local if torch.cuda.device_count() > dist.local else 0
+    torch.cuda.set_device(dev)
+    gn.load()
+    log = lambda *a: print(f"[rank {dist.rank}]", *a, file=sys.stderr, flush=True)
+
+    t = time.perf_counter()
+    bank, queries, desc = workload(args.workload, args.stride, dist.rank)
+    log(f"workload generated in {time.perf_counter() - t:.1f}s: {bank.n_seqs} seqs, {bank.n_bases} bases, "
+        f"{queries.n} queries, {int(queries.start[-1])} query bases")
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = gn.Index(bank.seq_start, bank.bases, k=11, stride=args.stride, stream=sh)
+    torch.cuda.synchronize()
+    t_index = time.perf_counter() - t0
+    info = ix.info()
+    log(f"index built in {t_index:.2f}s: {info.n_postings} postings, {info.device_bytes / 2**30:.2f} GiB")
+
+    qd = torch.from_numpy(queries.bases).to(f"cuda:{dev}")
+    qh = torch.empty(len(queries.bases), dtype=torch.uint8, pin_memory=True)
+    qh.numpy()[:] = queries.bases
+    qstart = queries.start
+    M = int(qstart[-1])
+    flags_t = gn.GN_FLAG_TIME_KERNELS
+
+    for _ in range(args.warmup):
+        gn.search(ix, qstart, qd, stream=sh).close()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident queries, per-kernel events on the launching stream
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    time.sleep(0.4)
+    launches0 = gn.gn_kernel_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern = {}
+    phases = {}
+    n_hits = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        r = gn.search(ix, qstart, qd, params=gn.make_params(flags=flags_t), stream=sh)
+        n_hits = r.n_queries and gn.gn_results_count(r.handle)[1]
+        for name, (ms, la, un) in ix.kernel_times().items():
+            a = kern.setdefault(name, [0.0, 0, 0])
+            a[0] += ms; a[1] += la; a[2] += un
+        for name, ms in ix.phase_times().items():
+            phases[name] = phases.get(name, 0.0) + ms
+        r.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    launches = gn.gn_kernel_launch_count() - launches0
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms_step = dist.max(ms_local)
+    bases_all = dist.sum(float(M))
+    value = bases_all / 1e3 / (ms_step / 1e3)
+
+    # ---- end to end through the public call with pinned host queries and host results
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        r = gn.search(ix, qstart, qh, stream=sh)
+        nq, nh = gn.gn_results_count(r.handle)
+        d2h = nh * gn.HIT_DTYPE.itemsize
+        r.close()
+    torch.cuda.synchronize()
+    e2e_s = dist.max((time.perf_counter() - t0) / args.steps)
+    e2e = {"value": bases_all / 1e3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": M + 8 * (queries.n + 1),
+           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
+
+    # ---- plain per-query path on a sample (one gn_search per query), same GPU
+    plain = None
+    if args.plain_queries > 0:
+        idx = list(range(0, queries.n, max(1, queries.n // args.plain_queries)))[:args.plain_queries]
+        sub = queries.subset(idx)
+        subs = [(np.array([0, int(sub.start[i + 1] - sub.start[i])], dtype=np.uint64),
+                 torch.from_numpy(sub.bases[int(sub.start[i]):int(sub.start[i + 1])]).to(f"cuda:{dev}"))
+                for i in range(sub.n)]
+        for st, b in subs[:3]:
+            gn.search(ix, st, b, stream=sh).close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for st, b in subs:
+            gn.search(ix, st, b, stream=sh).close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        batched_sub = gn.search(ix, sub.start, torch.from_numpy(sub.bases).to(f"cuda:{dev}"), stream=sh)
+        batched_sub.close()
+        plain = {"value": int(sub.start[-1]) / 1e3 / dt, "unit": UNIT,
+                 "sample": f"{sub.n} evenly spaced queries, one gn_search call per query"}
+
+    # ---- roofline of the dominant kernel
+    peaks = measured_peaks()
+    dom = max(kern.items(), key=lambda kv: kv[1][0]) if kern else None
+    roof = None
+    if dom:
+        name, (ms, la, un) = dom
+        if name in ALU_KERNELS:
+            roof = {"kernel": name, "bound": "alu", "achieved": un / (ms / 1e3) / 1e9, "unit": "Gcell/s",
+                    "peak": None, "frac": None, "traffic": None}
+        else:
+            bpu = BYTES_PER_UNIT.get(name)
+            achieved = (un * bpu) / (ms / 1e3) / 1e9 if bpu else None
+            peak = peaks.get("hbm_gbs")
+            tpu = ncu_traffic(name)
+            roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                    "peak_source": "measured" if peak else None, "unit": "GB/s",
+                    "frac": (achieved / peak) if (achieved and peak) else None,
+                    "traffic": (tpu * un / la) if tpu else None,
+                    "algorithmic_bytes_per_launch": (un * bpu / la) if bpu else None,
+                    "avg_launch_ms": ms / la, "launches": la}
+    kernels_out = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                       "units_per_step": v[2] / args.steps} for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
+
+    # ---- CPU oracle baseline on a bounded sample (rank 0, N = 1), with a parity check of that sample
+    cpu = None
+    parity = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        kbps, dt, sample, idx, ref, _ = oracle_run(bank, queries, args.stride, threads, args.cpu_seconds)
+        cpu = {"value": kbps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample, "seconds": dt}
+        full = gn.search(ix, qstart, qd, stream=sh)
+        mism = 0
+        for j, qi in enumerate(idx):
+            got = full.query(qi)
+            exp = ref[j].ranked
+            same = len(got) == len(exp) and all(
+                np.array_equal(got[a].astype(np.int64), exp[b].astype(np.int64))
+                for a, b in (("seq", "seq"), ("q_start", "qs"), ("q_end", "qe"), ("db_start", "ds"),
+                             ("db_end", "de"), ("score", "score"), ("rank", "rank")))
+            same = same and np.allclose(got["evalue"], exp["evalue"], rtol=1e-9, atol=1e-300)
+            mism += 0 if same else 1
+        full.close()
+        parity = {"queries_compared": len(idx), "mismatches": mism}
+
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": desc, "bank_bases": bank.n_bases, "bank_seqs": bank.n_seqs,
+                           "n_queries": queries.n, "query_bases_per_rank": M, "k": 11, "stride": args.stride,
+                           "hits_per_step": kern.get("k_seed_gather", [0, 0, 0])[2] / max(1, args.steps),
+                           "parallelism": f"replicas x{dist.world}",
+                           "l2": "inputs larger than L2 (postings and hit keys are GBs per step); no flush"},
+                "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+                "gpu_launches_per_step": launches / max(1, args.steps), "roofline": roof,
+                "cpu_baseline": cpu, "plain_per_query": plain, "oracle_parity_on_sample": parity,
+                "index_build": {"seconds": t_index, "bank_gbp_per_s": bank.n_bases / 1e9 / t_index,
+                                "postings": info.n_postings, "device_gib": info.device_bytes / 2**30,
+                                "includes": "host-to-device copy of the bank + pack + windows + scan + sort"},
+                "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
+                "kernels": kernels_out, "alignments_per_step": n_hits}
+        print(json.dumps(line), flush=True)
+    ix.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, dist)
+        return run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -94,6 +94,7 @@ typedef struct {
 
 #define GN_FLAG_KEEP_STAGES 1u  /* keep every phase's output in the results (tests, debugging) */
 #define GN_FLAG_KEEP_HITS 2u    /* also keep the sorted hit list (small inputs only) */
+#define GN_FLAG_TIME_KERNELS 4u /* bracket every kernel launch with CUDA events (gn_last_kernel_times) */
 
 /* One reported alignment. */
 typedef struct {
@@ -186,6 +187,17 @@ GN_API gn_status gn_results_stage(const gn_results *results, gn_stage stage, con
  * milliseconds (CUDA events); names[i] is a static string.  Returns the
  * number of phases written (<= cap). */
 GN_API int gn_last_phase_times(const gn_index *index, const char **names, float *ms, int cap);
+
+/* Per-kernel device time of the last gn_search on this index handle that ran
+ * with GN_FLAG_TIME_KERNELS: for each kernel name, the summed duration of its
+ * launches (CUDA events on the launching stream), the number of launches and
+ * the summed work items (keys, hits, HSPs or DP cells, per kernel).  Returns
+ * the number of kernels written (<= cap). */
+GN_API int gn_last_kernel_times(const gn_index *index, const char **names, double *ms, uint32_t *launches,
+                                uint64_t *units, int cap);
+
+/* Number of kernels this library has launched in the process so far. */
+GN_API uint64_t gn_kernel_launch_count(void);
 
 /* ----------------------------------------------------------- serving ---
  * Request loop with continuous batching (the paper's web-services interface,

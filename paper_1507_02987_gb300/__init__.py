@@ -24,7 +24,7 @@ __all__ = ["GnError", "load", "Index", "search", "HIT_DTYPE", "HSP_DTYPE"]
 
 GN_OK, GN_EINVAL, GN_ENOMEM, GN_ECUDA, GN_ETIMEOUT, GN_EBUSY, GN_ETOOBIG, GN_EINTERNAL = range(8)
 GN_MEM_HOST, GN_MEM_DEVICE = 0, 1
-GN_FLAG_KEEP_STAGES, GN_FLAG_KEEP_HITS = 1, 2
+GN_FLAG_KEEP_STAGES, GN_FLAG_KEEP_HITS, GN_FLAG_TIME_KERNELS = 1, 2, 4
 GN_STAGE_HSP, GN_STAGE_EXT, GN_STAGE_MERGED, GN_STAGE_SELECTED, GN_STAGE_ALIGNED, GN_STAGE_HITS, \
     GN_STAGE_HIT_COUNTS = range(7)
 STATUS_NAMES = {0: "GN_OK", 1: "GN_EINVAL", 2: "GN_ENOMEM", 3: "GN_ECUDA", 4: "GN_ETIMEOUT", 5: "GN_EBUSY",
@@ -100,6 +100,10 @@ def load():
             "gn_results_stage": (st, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(u64)]),
             "gn_last_phase_times": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_char_p),
                                                    ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+            "gn_last_kernel_times": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_char_p),
+                                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32),
+                                                    ctypes.POINTER(u64), ctypes.c_int]),
+            "gn_kernel_launch_count": (u64, []),
             "gn_serve_start": (st, [vp, ctypes.POINTER(gn_scoring), ctypes.POINTER(gn_params), u64,
                                     ctypes.POINTER(vp)]),
             "gn_serve_submit": (st, [vp, ctypes.c_char_p, u32, ctypes.POINTER(u64)]),
@@ -191,6 +195,20 @@ def gn_last_phase_times(h: int) -> dict:
         key = names[i].decode()
         out[key] = out.get(key, 0.0) + ms[i]
     return out
+
+
+def gn_last_kernel_times(h: int) -> dict:
+    """{kernel name: (total ms, launches, work items)} of the last search run with GN_FLAG_TIME_KERNELS."""
+    names = (ctypes.c_char_p * 128)()
+    ms = (ctypes.c_double * 128)()
+    la = (ctypes.c_uint32 * 128)()
+    un = (ctypes.c_uint64 * 128)()
+    n = load().gn_last_kernel_times(ctypes.c_void_p(h), names, ms, la, un, 128)
+    return {names[i].decode(): (ms[i], la[i], un[i]) for i in range(n)}
+
+
+def gn_kernel_launch_count() -> int:
+    return int(load().gn_kernel_launch_count())
 
 
 def gn_serve_start(h: int, scoring: gn_scoring, params: gn_params, mem_budget: int) -> int:
@@ -288,6 +306,9 @@ class Index:
 
     def phase_times(self) -> dict:
         return gn_last_phase_times(self.handle)
+
+    def kernel_times(self) -> dict:
+        return gn_last_kernel_times(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

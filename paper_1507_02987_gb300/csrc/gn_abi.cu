@@ -314,6 +314,24 @@ int gn_last_phase_times(const gn_index *ix, const char **names, float *ms, int c
     return n;
 }
 
+int gn_last_kernel_times(const gn_index *ix, const char **names, double *ms, uint32_t *launches, uint64_t *units,
+                         int cap) {
+    if (!ix) return 0;
+    std::lock_guard<std::mutex> lk(const_cast<gn_index *>(ix)->phase_mu);
+    int n = 0;
+    for (auto &k : ix->last_kernels) {
+        if (n >= cap) break;
+        if (names) names[n] = k.name;
+        if (ms) ms[n] = k.ms;
+        if (launches) launches[n] = k.launches;
+        if (units) units[n] = k.units;
+        ++n;
+    }
+    return n;
+}
+
+uint64_t gn_kernel_launch_count(void) { return (uint64_t)launch_count(); }
+
 gn_status gn_serve_start(const gn_index *ix, const gn_scoring *sc, const gn_params *p, uint64_t mem_budget,
                          gn_server **out) {
     if (!out || !ix) { g_last_error = "index and out are required"; return GN_EINVAL; }

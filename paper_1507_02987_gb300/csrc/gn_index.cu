@@ -107,8 +107,8 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     uint32_t *wcnt = arena.alloc_n<uint32_t>(ns);
     uint64_t *woff = arena.alloc_n<uint64_t>(ns + 1);
     if (ns) {
-        k_window_counts<<<(ns + 255) / 256, 256, 0, s>>>(ix->seq_start_d, ns, k, t, wcnt);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_window_counts", ns, s,
+                  k_window_counts<<<(ns + 255) / 256, 256, 0, s>>>(ix->seq_start_d, ns, k, t, wcnt));
     }
     void *scan_scr = arena.alloc(std::max(scan_scratch_bytes(ns), scan_scratch_bytes(nbk)));
     exclusive_scan_u32(wcnt, woff, ns, scan_scr, s);
@@ -124,9 +124,9 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     uint64_t warps = (W + 32 * WIN_J - 1) / (32 * WIN_J);
     unsigned grid = (unsigned)std::max<uint64_t>(1, (warps * 32 + 255) / 256);
     if (W) {
-        k_bank_windows<true><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
-                                                  flags, hist, nullptr, nullptr);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_bank_windows_flags", W, s,
+                  k_bank_windows<true><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
+                                                  flags, hist, nullptr, nullptr));
     }
     // K3: bucket starts = exclusive scan of the histogram
     exclusive_scan_u32(hist, ix->off_d, nbk, scan_scr, s);
@@ -141,17 +141,17 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     uint64_t *keys = arena.alloc_n<uint64_t>(P);
     uint64_t *keys_alt = arena.alloc_n<uint64_t>(P);
     if (W) {
-        k_bank_windows<false><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
-                                                   nullptr, nullptr, slot, keys);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_bank_windows_keys", W, s,
+                  k_bank_windows<false><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
+                                                   nullptr, nullptr, slot, keys));
     }
     void *rs = arena.alloc(radix_scratch_bytes(P));
-    bool flipped = radix_sort(keys, keys_alt, nullptr, nullptr, P, 32, 32 + 2 * k, rs, s);
+    bool flipped = radix_sort(keys, keys_alt, nullptr, nullptr, P, 32, 32 + 2 * k, rs, s, TAG_INDEX_SORT);
     GN_CUDA(cudaMalloc(&ix->post_d, sizeof(uint32_t) * (P ? P : 1)));
     bytes += sizeof(uint32_t) * P;
     if (P) {
-        k_low_words<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(flipped ? keys_alt : keys, P, ix->post_d);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_low_words", P, s,
+                  k_low_words<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(flipped ? keys_alt : keys, P, ix->post_d));
     }
     arena.release();
     GN_CUDA(cudaStreamSynchronize(s));

@@ -32,6 +32,43 @@ void set_error(gn_status st, const std::string &msg);
 
 #define GN_CHECK_LAUNCH() GN_CUDA(cudaGetLastError())
 
+// ------------------------------------------------------ kernel timing --
+// When a search runs with GN_FLAG_TIME_KERNELS, every launch made through
+// GN_LAUNCH is bracketed by CUDA events on its stream; `units` is the number
+// of work items the launch processed (keys, hits, HSPs, cells...).
+struct KernelRecord {
+    const char *name;
+    cudaEvent_t a, b;
+    uint64_t units;
+};
+struct KernelTimer {
+    std::vector<KernelRecord> recs;
+    ~KernelTimer() {
+        for (auto &r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+    }
+};
+extern thread_local KernelTimer *g_ktimer;
+void count_launch();
+
+#define GN_LAUNCH(name, units, stream, ...)                                        \
+    do {                                                                           \
+        ::gn::KernelTimer *_kt = ::gn::g_ktimer;                                   \
+        cudaEvent_t _ea = nullptr, _eb = nullptr;                                  \
+        if (_kt && cudaEventCreate(&_ea) == cudaSuccess) cudaEventRecord(_ea, stream); \
+        __VA_ARGS__;                                                               \
+        GN_CHECK_LAUNCH();                                                         \
+        ::gn::count_launch();                                                      \
+        if (_ea && cudaEventCreate(&_eb) == cudaSuccess) {                         \
+            cudaEventRecord(_eb, stream);                                          \
+            _kt->recs.push_back({(name), _ea, _eb, (uint64_t)(units)});            \
+        } else if (_ea) {                                                          \
+            cudaEventDestroy(_ea);                                                 \
+        }                                                                          \
+    } while (0)
+
 #define GN_REQUIRE(cond, st, msg)                 \
     do {                                          \
         if (!(cond)) throw ::gn::Error{(st), (msg)}; \
@@ -91,8 +128,13 @@ void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scr
 // key bits [bit_lo, bit_hi).  Ping-pongs between the two buffers; returns true
 // when the sorted data ended in the *_alt buffers.
 size_t radix_scratch_bytes(uint64_t n);
+struct RadixTag {
+    const char *up, *down;  // kernel-timer names of the two passes
+};
+extern const RadixTag TAG_HIT_SORT, TAG_INDEX_SORT, TAG_RECORD_SORT;
 bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
-                int bit_hi, void *scratch, cudaStream_t s);
+                int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag);
+unsigned long long launch_count();
 
 // Sort of fixed-size records made of uint32 words by a list of fields (first =
 // most significant).  Produces the permutation perm (record ids in order).
@@ -170,6 +212,13 @@ struct gn_index {
     uint64_t device_bytes = 0;
     // per-phase device times of the most recent search through this handle
     std::vector<std::pair<const char *, float>> last_phases;
+    struct KernelStat {
+        const char *name;
+        double ms;
+        uint32_t launches;
+        uint64_t units;
+    };
+    std::vector<KernelStat> last_kernels;
     std::mutex phase_mu;
 };
 

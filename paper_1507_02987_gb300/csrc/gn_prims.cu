@@ -1,6 +1,7 @@
 // gn_prims.cu - device primitives of the search path: 2-bit packing, exclusive
 // scans, a stable LSD radix sort and record sorting built on it.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -101,8 +102,8 @@ void pack_bases(const uint8_t *ascii_dev, uint64_t n, Packed &out, cudaStream_t 
     if (n == 0) return;
     uint64_t threads = (n + 31) / 32;
     int aligned = ((uintptr_t)ascii_dev % 16) == 0;
-    k_pack<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ascii_dev, n, out.pk, out.nb, aligned);
-    GN_CHECK_LAUNCH();
+    GN_LAUNCH("k_pack", n, s,
+              k_pack<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ascii_dev, n, out.pk, out.nb, aligned));
 }
 
 // ----------------------------------------------------------------- scans --
@@ -211,12 +212,12 @@ void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scr
         return;
     }
     uint64_t *sums = static_cast<uint64_t *>(scratch);
-    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums);
-    GN_CHECK_LAUNCH();
-    k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, out + n);
-    GN_CHECK_LAUNCH();
-    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums, out);
-    GN_CHECK_LAUNCH();
+    GN_LAUNCH("k_scan_reduce", n, s,
+              k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums));
+    GN_LAUNCH("k_scan_sums", nb, s,
+              k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, out + n));
+    GN_LAUNCH("k_scan_down", n, s,
+              k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums, out));
 }
 
 // ------------------------------------------------------------ radix sort --
@@ -378,8 +379,17 @@ size_t radix_scratch_bytes(uint64_t n) {
     return cnt * sizeof(uint32_t) + (cnt + 1) * sizeof(uint64_t) + scan_scratch_bytes(cnt) + 256;
 }
 
+const RadixTag TAG_HIT_SORT{"hit_sort_upsweep", "hit_sort_downsweep"};
+const RadixTag TAG_INDEX_SORT{"index_sort_upsweep", "index_sort_downsweep"};
+const RadixTag TAG_RECORD_SORT{"record_sort_upsweep", "record_sort_downsweep"};
+
+thread_local KernelTimer *g_ktimer = nullptr;
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
-                int bit_hi, void *scratch, cudaStream_t s) {
+                int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag) {
     if (n <= 1 || bit_hi <= bit_lo) return false;
     RsGeom geo = rs_geometry(n);
     size_t cnt = (size_t)256 * geo.grid;
@@ -397,17 +407,18 @@ bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *va
         uint64_t *kout = flip ? keys : keys_alt;
         const uint32_t *vin = flip ? vals_alt : vals;
         uint32_t *vout = flip ? vals : vals_alt;
-        k_rs_upsweep<<<geo.grid, RS_THREADS, 0, s>>>(kin, n, geo.chunk, shift, mask, counts);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH(tag.up, n, s,
+                  k_rs_upsweep<<<geo.grid, RS_THREADS, 0, s>>>(kin, n, geo.chunk, shift, mask, counts));
         exclusive_scan_u32(counts, offs, cnt, scan_scratch, s);
         if (vals) {
-            k_rs_downsweep<true><<<geo.grid, RS_THREADS, smem, s>>>(kin, vin, kout, vout, n, geo.chunk, shift,
-                                                                    mask, offs);
+            GN_LAUNCH(tag.down, n, s,
+                      k_rs_downsweep<true><<<geo.grid, RS_THREADS, smem, s>>>(kin, vin, kout, vout, n, geo.chunk,
+                                                                              shift, mask, offs));
         } else {
-            k_rs_downsweep<false><<<geo.grid, RS_THREADS, smem, s>>>(kin, nullptr, kout, nullptr, n, geo.chunk,
-                                                                     shift, mask, offs);
+            GN_LAUNCH(tag.down, n, s,
+                      k_rs_downsweep<false><<<geo.grid, RS_THREADS, smem, s>>>(kin, nullptr, kout, nullptr, n,
+                                                                               geo.chunk, shift, mask, offs));
         }
-        GN_CHECK_LAUNCH();
         flip = !flip;
     }
     return flip;
@@ -450,8 +461,7 @@ void sort_records(const uint32_t *recs, int rec_words, uint32_t n, const std::ve
     uint64_t *keys = arena.alloc_n<uint64_t>(n);
     uint64_t *keys_alt = arena.alloc_n<uint64_t>(n);
     void *scratch = arena.alloc(radix_scratch_bytes(n));
-    k_iota<<<grid, 256, 0, s>>>(perm, n);
-    GN_CHECK_LAUNCH();
+    GN_LAUNCH("k_iota", n, s, k_iota<<<grid, 256, 0, s>>>(perm, n));
     // group fields into <= 64-bit keys, least significant group first
     int fi = (int)fields.size() - 1;
     while (fi >= 0) {
@@ -470,9 +480,9 @@ void sort_records(const uint32_t *recs, int rec_words, uint32_t n, const std::ve
         }
         if (kf.n == 0) throw Error{GN_EINTERNAL, "sort field wider than 64 bits"};
         if (used == 0) continue;
-        k_make_keys<<<grid, 256, 0, s>>>(recs, rec_words, perm, n, kf, keys);
-        GN_CHECK_LAUNCH();
-        bool flipped = radix_sort(keys, keys_alt, perm, perm_alt, n, 0, used, scratch, s);
+        GN_LAUNCH("k_make_keys", n, s,
+                  k_make_keys<<<grid, 256, 0, s>>>(recs, rec_words, perm, n, kf, keys));
+        bool flipped = radix_sort(keys, keys_alt, perm, perm_alt, n, 0, used, scratch, s, TAG_RECORD_SORT);
         if (flipped) std::swap(perm, perm_alt);
     }
     if (perm != perm_out) GN_CUDA(cudaMemcpyAsync(perm_out, perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
@@ -490,8 +500,8 @@ void gather_records(const uint32_t *in, int rec_words, const uint32_t *perm, uin
                     cudaStream_t s) {
     if (n == 0) return;
     uint64_t tot = (uint64_t)n * rec_words;
-    k_gather_records<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(in, rec_words, perm, n, out);
-    GN_CHECK_LAUNCH();
+    GN_LAUNCH("k_gather_records", n, s,
+              k_gather_records<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(in, rec_words, perm, n, out));
 }
 
 }  // namespace gn

@@ -470,8 +470,8 @@ uint32_t compact_records(const uint32_t *in, int W, const uint32_t *flags, uint3
     void *scr = arena.alloc(scan_scratch_bytes(n));
     exclusive_scan_u32(flags, pos, n, scr, s);
     uint64_t tot = (uint64_t)n * W;
-    k_scatter_flagged<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(in, W, flags, pos, n, out);
-    GN_CHECK_LAUNCH();
+    GN_LAUNCH("k_scatter_flagged", n, s,
+              k_scatter_flagged<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(in, W, flags, pos, n, out));
     uint64_t cnt = 0;
     GN_CUDA(cudaMemcpyAsync(&cnt, pos + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     GN_CUDA(cudaStreamSynchronize(s));
@@ -529,6 +529,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     res->has_stages = keep;
     PhaseTimer timer(s);
     timer.mark("start");
+    KernelTimer ktimer;
+    struct TimerScope {
+        KernelTimer *prev;
+        explicit TimerScope(KernelTimer *t) : prev(g_ktimer) { g_ktimer = t; }
+        ~TimerScope() { g_ktimer = prev; }
+    };
+    TimerScope tscope((p.flags & GN_FLAG_TIME_KERNELS) ? &ktimer : nullptr);
     DeviceArena arena(s);
 
     // a5: pack queries, code every offset, list lengths
@@ -543,8 +550,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     uint32_t *cnt = arena.alloc_n<uint32_t>(M);
     uint64_t *hoff = arena.alloc_n<uint64_t>(M + 1);
     if (M) {
-        k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, k, ix->off_d, codes, qinfo, cnt);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_query_codes", M, s,
+                  k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, k, ix->off_d, codes, qinfo, cnt));
     }
     {
         void *scr = arena.alloc(scan_scratch_bytes(M));
@@ -552,8 +559,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     }
     // hit offsets at query boundaries -> per-query hit counts (chunk plan)
     uint64_t *hq_d = arena.alloc_n<uint64_t>(nq + 1);
-    k_gather_u64<<<blocks_for(nq + 1), 256, 0, s>>>(hoff, qstart_d, nq + 1, hq_d);
-    GN_CHECK_LAUNCH();
+    GN_LAUNCH("k_gather_u64", nq + 1, s,
+              k_gather_u64<<<blocks_for(nq + 1), 256, 0, s>>>(hoff, qstart_d, nq + 1, hq_d));
     std::vector<uint64_t> hq = to_host(hq_d, nq + 1, s);
     timer.mark("query_codes");
     if (keep) {
@@ -594,27 +601,28 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
             uint64_t *keys_alt = carena.alloc_n<uint64_t>(Hc);
             void *rs = carena.alloc(radix_scratch_bytes(Hc));
             uint64_t gwarps = std::min<uint64_t>((xb - xa + 31) / 32, (uint64_t)num_sms() * 64);
-            k_seed_gather<<<blocks_for(gwarps * 32), 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ha, ix->off_d, ix->post_d,
-                                                                  qa, qbits, keys);
-            GN_CHECK_LAUNCH();
+            GN_LAUNCH("k_seed_gather", Hc, s,
+                      k_seed_gather<<<blocks_for(gwarps * 32), 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ha, ix->off_d, ix->post_d,
+                                                                  qa, qbits, keys));
             timer.mark("seed_gather");
-            bool fl = radix_sort(keys, keys_alt, nullptr, nullptr, Hc, 16 + qbits, 16 + qbits + gbits, rs, s);
+            bool fl = radix_sort(keys, keys_alt, nullptr, nullptr, Hc, 16 + qbits, 16 + qbits + gbits, rs, s,
+                                 TAG_HIT_SORT);
             uint64_t *sorted = fl ? keys_alt : keys;
             timer.mark("hit_sort");
             if (keep_hits) {
                 uint32_t *quad = carena.alloc_n<uint32_t>(4 * Hc);
-                k_decode_hits<<<blocks_for(Hc), 256, 0, s>>>(sorted, Hc, qbits, qa, ix->seq_start_d, ix->n_seqs, quad);
-                GN_CHECK_LAUNCH();
+                GN_LAUNCH("k_decode_hits", Hc, s,
+                          k_decode_hits<<<blocks_for(Hc), 256, 0, s>>>(sorted, Hc, qbits, qa, ix->seq_start_d, ix->n_seqs, quad));
                 std::vector<uint32_t> hh = to_host(quad, 4 * Hc, s);
                 hits_q.insert(hits_q.end(), hh.begin(), hh.end());
             }
             for (int attempt = 0; attempt < 2; ++attempt) {
                 GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
                 uint64_t threads = std::min<uint64_t>(Hc, (uint64_t)num_sms() * 2048);
-                k_hit_merge<<<blocks_for(threads), 256, 0, s>>>(sorted, Hc, qbits, qa, k, p.max_hit_distance,
+                GN_LAUNCH("k_hit_merge", Hc, s,
+                          k_hit_merge<<<blocks_for(threads), 256, 0, s>>>(sorted, Hc, qbits, qa, k, p.max_hit_distance,
                                                                 p.min_hsp_len, ix->seq_start_d, ix->n_seqs,
-                                                                hsp + n_hsp, counter, hsp_cap - n_hsp, status);
-                GN_CHECK_LAUNCH();
+                                                                hsp + n_hsp, counter, hsp_cap - n_hsp, status));
                 uint32_t got = 0;
                 GN_CUDA(cudaMemcpyAsync(&got, counter, 4, cudaMemcpyDeviceToHost, s));
                 GN_CUDA(cudaStreamSynchronize(s));
@@ -645,9 +653,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
 
     // a9: extension
     if (n_hsp) {
-        k_xdrop<<<blocks_for(n_hsp, 128), 128, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d, ix->bank.pk, ix->bank.nb,
-                                                       ix->seq_start_d, sc.match, sc.mismatch, p.xdrop);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_xdrop", n_hsp, s,
+                  k_xdrop<<<blocks_for(n_hsp, 128), 128, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d, ix->bank.pk, ix->bank.nb,
+                                                       ix->seq_start_d, sc.match, sc.mismatch, p.xdrop));
     }
     timer.mark("xdrop_extend");
     if (keep) {
@@ -675,8 +683,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                        reinterpret_cast<uint32_t *>(srt), s);
         DevHsp *boxes = arena.alloc_n<DevHsp>(n_hsp);
         uint32_t *flag = arena.alloc_n<uint32_t>(n_hsp);
-        k_overlap_sweep<<<blocks_for(n_hsp), 256, 0, s>>>(srt, n_hsp, boxes, flag);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_overlap_sweep", n_hsp, s,
+                  k_overlap_sweep<<<blocks_for(n_hsp), 256, 0, s>>>(srt, n_hsp, boxes, flag));
         n_mg = compact_records(reinterpret_cast<const uint32_t *>(boxes), HSP_WORDS, flag, n_hsp,
                                reinterpret_cast<uint32_t *>(merged), arena, s);
     }
@@ -700,11 +708,11 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         DevHsp *srt = arena.alloc_n<DevHsp>(n_mg);
         gather_records(reinterpret_cast<const uint32_t *>(merged), HSP_WORDS, perm, n_mg,
                        reinterpret_cast<uint32_t *>(srt), s);
-        k_first_of_query<<<blocks_for(n_mg), 256, 0, s>>>(reinterpret_cast<const uint32_t *>(srt), HSP_WORDS, n_mg, first);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_first_of_query", 0, s,
+                  k_first_of_query<<<blocks_for(n_mg), 256, 0, s>>>(reinterpret_cast<const uint32_t *>(srt), HSP_WORDS, n_mg, first));
         uint32_t *flag = arena.alloc_n<uint32_t>(n_mg);
-        k_select_flags<<<blocks_for(n_mg), 256, 0, s>>>(srt, n_mg, first, p.max_alignments, flag);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_select_flags", n_mg, s,
+                  k_select_flags<<<blocks_for(n_mg), 256, 0, s>>>(srt, n_mg, first, p.max_alignments, flag));
         n_sel = compact_records(reinterpret_cast<const uint32_t *>(srt), HSP_WORDS, flag, n_mg,
                                 reinterpret_cast<uint32_t *>(sel), arena, s);
     }
@@ -720,8 +728,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     if (n_sel) {
         uint32_t *B = arena.alloc_n<uint32_t>(n_sel);
         uint64_t *soff = arena.alloc_n<uint64_t>(n_sel + 1);
-        k_band_width<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, B);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_band_width", n_sel, s,
+                  k_band_width<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, B));
         void *scr = arena.alloc(scan_scratch_bytes(n_sel));
         exclusive_scan_u32(B, soff, n_sel, scr, s);
         uint64_t cells = 0;
@@ -730,11 +738,11 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         SwCell *strips = arena.alloc_n<SwCell>(cells);
         GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
         unsigned warps = (unsigned)std::min<uint64_t>(n_sel, (uint64_t)num_sms() * 32);
-        k_banded_sw<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
+        GN_LAUNCH("k_banded_sw", cells, s,
+                  k_banded_sw<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
                                                             ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
                                                             sc.mismatch, sc.gap_open, sc.gap_extend,
-                                                            (int32_t)p.band_w, counter, aln, status);
-        GN_CHECK_LAUNCH();
+                                                            (int32_t)p.band_w, counter, aln, status));
     }
     timer.mark("banded_sw");
     if (keep) {
@@ -760,8 +768,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         DevAln *srt = arena.alloc_n<DevAln>(n_sel);
         gather_records(reinterpret_cast<const uint32_t *>(aln), ALN_WORDS, perm, n_sel, reinterpret_cast<uint32_t *>(srt), s);
         uint32_t *flag = arena.alloc_n<uint32_t>(n_sel);
-        k_dup_flags<<<blocks_for(n_sel), 256, 0, s>>>(srt, n_sel, flag);
-        GN_CHECK_LAUNCH();
+        GN_LAUNCH("k_dup_flags", n_sel, s,
+                  k_dup_flags<<<blocks_for(n_sel), 256, 0, s>>>(srt, n_sel, flag));
         DevAln *uniq = arena.alloc_n<DevAln>(n_sel);
         uint32_t nu = compact_records(reinterpret_cast<const uint32_t *>(srt), ALN_WORDS, flag, n_sel,
                                       reinterpret_cast<uint32_t *>(uniq), arena, s);
@@ -774,13 +782,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
             DevAln *ranked = arena.alloc_n<DevAln>(nu);
             gather_records(reinterpret_cast<const uint32_t *>(uniq), ALN_WORDS, perm2, nu,
                            reinterpret_cast<uint32_t *>(ranked), s);
-            k_first_of_query<<<blocks_for(nu), 256, 0, s>>>(reinterpret_cast<const uint32_t *>(ranked), ALN_WORDS, nu, first);
-            GN_CHECK_LAUNCH();
+            GN_LAUNCH("k_first_of_query", 0, s,
+                      k_first_of_query<<<blocks_for(nu), 256, 0, s>>>(reinterpret_cast<const uint32_t *>(ranked), ALN_WORDS, nu, first));
             gn_hit *hits = arena.alloc_n<gn_hit>(nu);
             uint32_t *f2 = arena.alloc_n<uint32_t>(nu);
-            k_finalize<<<blocks_for(nu), 256, 0, s>>>(ranked, nu, first, qstart_d, (double)ix->n_bases, sc.lambda, sc.K,
-                                                      p.max_evalue, hits, f2);
-            GN_CHECK_LAUNCH();
+            GN_LAUNCH("k_finalize", nu, s,
+                      k_finalize<<<blocks_for(nu), 256, 0, s>>>(ranked, nu, first, qstart_d, (double)ix->n_bases, sc.lambda, sc.K,
+                                                      p.max_evalue, hits, f2));
             static_assert(sizeof(gn_hit) % 4 == 0, "gn_hit words");
             n_out = compact_records(reinterpret_cast<const uint32_t *>(hits), (int)(sizeof(gn_hit) / 4), f2, nu,
                                     reinterpret_cast<uint32_t *>(fin), arena, s);
@@ -800,7 +808,22 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     {
         std::lock_guard<std::mutex> lk(ix->phase_mu);
         timer.finish(ix->last_phases);
+        ix->last_kernels.clear();
+        for (auto &r : ktimer.recs) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, r.a, r.b);
+            auto it = std::find_if(ix->last_kernels.begin(), ix->last_kernels.end(),
+                                   [&](const gn_index::KernelStat &k) { return strcmp(k.name, r.name) == 0; });
+            if (it == ix->last_kernels.end()) {
+                ix->last_kernels.push_back({r.name, 0.0, 0u, 0ull});
+                it = ix->last_kernels.end() - 1;
+            }
+            it->ms += ms;
+            it->launches += 1;
+            it->units += r.units;
+        }
     }
+
     arena.release();
 }
 
