@@ -217,6 +217,36 @@ GN_API gn_status gn_serve_poll(gn_server *server, uint64_t ticket, uint32_t time
 /* Finishes admitted work, rejects new submissions, joins the server thread, frees the server. */
 GN_API gn_status gn_serve_stop(gn_server *server);
 
+/* ------------------------------------------- allocation-free alignment ---
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory on their path - code whose device memory is
+ * owned by another allocator that must stay the only one, code running near a
+ * hard memory limit that cannot risk an allocation failure mid-job, or loops
+ * that cannot afford an allocation call.  It aligns caller-given HSPs exactly
+ * as the alignment phase of gn_search does (same band, recurrence, tie-breaks
+ * and output as its GN_STAGE_ALIGNED records: query, seq, ranges and score;
+ * rank, evalue and bits are 0) and allocates nothing: its scratch (one row
+ * strip per warp for 512 warps, bands of at most 1,024 diagonals; about 8 MiB)
+ * is a static array in the library's device image, which every GPU that loads
+ * the library holds until the process exits.
+ *   query_bases  device memory, ASCII, queries back to back
+ *   query_start  device memory, n_queries + 1 offsets into query_bases
+ *   hsps, out    device memory, n_hsps records each (caller-owned); out[i]
+ *                is the alignment of hsps[i]; db ranges are positions in
+ *                bank sequence hsps[i].seq of the index
+ *   band_w       band half-width w (2*w + 1 <= 1024)
+ * The first call on a device looks up the scratch array's address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and clears its counters first:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * not be issued.  The call returns after the stream has finished.  Errors:
+ * GN_ETOOBIG if band_w is too large or an HSP's band spans more than 1,024
+ * diagonals (that HSP's record is written with score 0), GN_EINVAL for a
+ * missing pointer or an HSP naming a query or sequence that does not exist. */
+GN_API gn_status gn_align_hsps_static(const gn_index *index, const char *query_bases, const uint64_t *query_start,
+                                      uint32_t n_queries, const gn_hsp *hsps, uint32_t n_hsps,
+                                      const gn_scoring *scoring, uint32_t band_w, gn_hit *out, void *cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 GN_API const char *gn_last_error(void);
 

@@ -109,6 +109,7 @@ def load():
             "gn_serve_submit": (st, [vp, ctypes.c_char_p, u32, ctypes.POINTER(u64)]),
             "gn_serve_poll": (st, [vp, u64, u32, ctypes.POINTER(vp)]),
             "gn_serve_stop": (st, [vp]),
+            "gn_align_hsps_static": (st, [vp, vp, vp, u32, vp, u32, ctypes.POINTER(gn_scoring), u32, vp, vp]),
             "gn_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -236,6 +237,15 @@ def gn_serve_poll(s: int, ticket: int, timeout_ms: int):
 
 def gn_serve_stop(s: int):
     _check(load().gn_serve_stop(ctypes.c_void_p(s)))
+
+
+def gn_align_hsps_static(h: int, query_bases_dev: int, query_start_dev: int, n_queries: int, hsps_dev: int,
+                         n_hsps: int, scoring: gn_scoring, band_w: int, out_dev: int, stream: int = 0):
+    """Allocation-free alignment of caller-given HSPs; every pointer is a device address."""
+    _check(load().gn_align_hsps_static(ctypes.c_void_p(h), ctypes.c_void_p(query_bases_dev),
+                                       ctypes.c_void_p(query_start_dev), n_queries, ctypes.c_void_p(hsps_dev),
+                                       n_hsps, ctypes.byref(scoring), band_w, ctypes.c_void_p(out_dev),
+                                       ctypes.c_void_p(stream)))
 
 
 def gn_last_error() -> str:

@@ -406,6 +406,15 @@ gn_status gn_serve_stop(gn_server *sv) {
     return GN_OK;
 }
 
+gn_status gn_align_hsps_static(const gn_index *ix, const char *query_bases, const uint64_t *query_start,
+                               uint32_t n_queries, const gn_hsp *hsps, uint32_t n_hsps, const gn_scoring *scoring,
+                               uint32_t band_w, gn_hit *out, void *cuda_stream) {
+    return guarded([&] {
+        align_hsps_static(ix, query_bases, query_start, n_queries, hsps, n_hsps, scoring, band_w, out,
+                          (cudaStream_t)cuda_stream);
+    });
+}
+
 const char *gn_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

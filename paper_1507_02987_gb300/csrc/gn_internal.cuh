@@ -245,4 +245,7 @@ struct SearchOptions {
 // Device-resident query set: bases (ASCII) on the device, starts on the host.
 void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart, const SearchOptions &o,
             cudaStream_t s, gn_results *res);
+void align_hsps_static(const gn_index *ix, const char *qbases, const uint64_t *qstart, uint32_t n_queries,
+                       const gn_hsp *hsps, uint32_t n, const gn_scoring *sc, uint32_t band_w, gn_hit *out,
+                       cudaStream_t s);
 }  // namespace gn
