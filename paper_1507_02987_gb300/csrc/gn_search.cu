@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "gn_internal.cuh"
 
@@ -167,6 +168,216 @@ __global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int q
         } else {
             atomicOr(status, DEV_ERR_CAPACITY);
         }
+    }
+}
+
+
+// ------------------------------------------ a6-a8: bucketed hit grouping --
+// Hits of query i are partitioned into 2^b_i buckets by the high bits of their
+// diagonal key G' = gpos - qpos + QBIAS (bucket = bbase[i] + (G' >> bshift[i])).
+// Every (query, diagonal) lies in one bucket, so each bucket is grouped on its
+// own in shared memory.  A diagonal holding a single hit cannot form an HSP when
+// min_hsp_len > k, so a hash count per diagonal drops those before the (small)
+// sort by (G', qpos) that the chaining needs.
+// Bucket entry: G' << 16 | qpos.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_bucket_hits(const uint32_t *__restrict__ codes,
+                                                     const uint32_t *__restrict__ qinfo,
+                                                     const uint64_t *__restrict__ hoff, uint64_t xa, uint64_t xb,
+                                                     const uint64_t *__restrict__ off,
+                                                     const uint32_t *__restrict__ post, uint32_t qa,
+                                                     const uint32_t *__restrict__ bbase,
+                                                     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcnt,
+                                                     const uint64_t *__restrict__ boff,
+                                                     uint64_t *__restrict__ bkeys) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (uint64_t x0 = xa + warp * 32; x0 < xb; x0 += nwarps * 32) {
+        uint64_t x = x0 + lane;
+        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
+        uint64_t my_src = 0;
+        if (x < xb) {
+            my_cnt = (uint32_t)(hoff[x + 1] - hoff[x]);
+            if (my_cnt) {
+                uint32_t qinf = qinfo[x];
+                my_src = off[codes[x]];
+                my_qpos = qinf & 0xFFFFu;
+                my_ql = (qinf >> 16) - qa;
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
+        while (todo) {
+            int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
+            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
+            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
+            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
+            const uint32_t base = bbase[ql], sh = bshift[ql];
+            for (uint32_t j = lane; j < cnt; j += 32) {
+                const uint64_t gk = (uint64_t)post[sp + j] + QBIAS - qpos;
+                const uint32_t b = base + (uint32_t)(gk >> sh);
+                if (!SCATTER) {
+                    atomicAdd(&bcnt[b], 1u);
+                } else {
+                    const uint32_t slot = atomicAdd(&bcnt[b], 1u);
+                    bkeys[boff[b] + slot] = (gk << 16) | qpos;
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_bucket_overflow(const uint64_t *__restrict__ boff, uint32_t NB, uint32_t cap,
+                                  unsigned long long *__restrict__ total) {
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= NB) return;
+    uint64_t n = boff[b + 1] - boff[b];
+    if (n > cap) atomicAdd(total, (unsigned long long)n);
+}
+
+// bucket entries a, b (a first): consecutive hits of one chain?
+__device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D, const uint64_t *__restrict__ seq_start,
+                                             uint32_t n_seqs) {
+    if ((a >> 16) != (b >> 16)) return false;
+    const uint32_t qa = (uint32_t)(a & 0xFFFFu), qb = (uint32_t)(b & 0xFFFFu);
+    if (qb - qa > D) return false;
+    const uint64_t gk = b >> 16;
+    return dev_upper_index(seq_start, n_seqs + 1, gk - QBIAS + qa) ==
+           dev_upper_index(seq_start, n_seqs + 1, gk - QBIAS + qb);
+}
+
+constexpr uint32_t BG_EMPTY = 0xFFFFFFFFu;
+
+// last index i in [0, n) with a[i] <= x (a non-decreasing 32-bit array, a[0] <= x)
+__device__ __forceinline__ uint32_t dev_upper_index32(const uint32_t *__restrict__ a, uint32_t n, uint32_t x) {
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (a[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_bucket_group(
+    const uint64_t *__restrict__ bkeys, const uint64_t *__restrict__ boff, uint32_t NB,
+    const uint32_t *__restrict__ bbase, const uint32_t *__restrict__ bshift, uint32_t nqc, uint32_t qa, int qbits,
+    int k, uint32_t D, uint32_t min_len, int singles, uint32_t cap, const uint64_t *__restrict__ seq_start,
+    uint32_t n_seqs, DevHsp *__restrict__ out, uint32_t *__restrict__ count, uint32_t out_cap,
+    uint64_t *__restrict__ ovf, unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char bg_smem[];
+    uint64_t *skeys = reinterpret_cast<uint64_t *>(bg_smem);
+    uint64_t *cand = skeys + cap;
+    uint32_t *tkey = reinterpret_cast<uint32_t *>(cand + cap);
+    uint32_t *tcnt = tkey + 2 * cap;
+    __shared__ uint32_t nc_s;
+    __shared__ unsigned long long ovf_pos;
+    const int tid = threadIdx.x;
+    const int nth = blockDim.x;
+    for (uint32_t b = blockIdx.x; b < NB; b += gridDim.x) {
+        const uint64_t beg = boff[b];
+        const uint32_t n = (uint32_t)(boff[b + 1] - beg);
+        if (n == 0 || (n == 1 && !singles)) continue;
+        const uint32_t ql = dev_upper_index32(bbase, nqc + 1, b);
+        const uint32_t sh = bshift[ql];
+        const uint64_t glo = (uint64_t)(b - bbase[ql]) << sh;
+        if (n > cap) {
+            // too large for shared memory: hand the bucket to the global sort path, in its key format
+            if (tid == 0) ovf_pos = atomicAdd(ovf_count, (unsigned long long)n);
+            __syncthreads();
+            const unsigned long long p0 = ovf_pos;
+            for (uint32_t i = tid; i < n; i += nth) {
+                const uint64_t e = bkeys[beg + i];
+                ovf[p0 + i] = ((e >> 16) << (16 + qbits)) | ((uint64_t)ql << 16) | (e & 0xFFFFu);
+            }
+            __syncthreads();
+            continue;
+        }
+        uint32_t ts = 2;
+        while (ts < 2 * n) ts <<= 1;
+        const int tbits = 31 - __clz(ts);
+        for (uint32_t i = tid; i < ts; i += nth) { tkey[i] = BG_EMPTY; tcnt[i] = 0; }
+        if (tid == 0) nc_s = 0;
+        for (uint32_t i = tid; i < n; i += nth) skeys[i] = bkeys[beg + i];
+        __syncthreads();
+        // count hits per diagonal (open addressing; the table is at most half full)
+        if (!singles) {
+            for (uint32_t i = tid; i < n; i += nth) {
+                const uint32_t rel = (uint32_t)((skeys[i] >> 16) - glo);
+                uint32_t h = (rel * 2654435761u) >> (32 - tbits);
+                for (uint32_t probe = 0; probe < ts; ++probe) {
+                    const uint32_t old = atomicCAS(&tkey[h], BG_EMPTY, rel);
+                    if (old == BG_EMPTY || old == rel) { atomicAdd(&tcnt[h], 1u); break; }
+                    h = (h + 1) & (ts - 1);
+                }
+            }
+            __syncthreads();
+        }
+        // candidates: hits whose diagonal holds at least two hits (all hits when single hits can be HSPs)
+        for (uint32_t i = tid; i < n; i += nth) {
+            bool keep = singles;
+            if (!keep) {
+                const uint32_t rel = (uint32_t)((skeys[i] >> 16) - glo);
+                uint32_t h = (rel * 2654435761u) >> (32 - tbits);
+                for (uint32_t probe = 0; probe < ts; ++probe) {
+                    const uint32_t kk = tkey[h];
+                    if (kk == rel) { keep = tcnt[h] >= 2u; break; }
+                    if (kk == BG_EMPTY) break;
+                    h = (h + 1) & (ts - 1);
+                }
+            }
+            if (keep) cand[atomicAdd(&nc_s, 1u)] = skeys[i];
+        }
+        __syncthreads();
+        const uint32_t nc = nc_s;
+        if (nc == 0) { __syncthreads(); continue; }
+        // bitonic sort of the candidates by (G', qpos)
+        uint32_t P = 1;
+        while (P < nc) P <<= 1;
+        for (uint32_t i = nc + tid; i < P; i += nth) cand[i] = ~0ull;
+        __syncthreads();
+        for (uint32_t k2 = 2; k2 <= P; k2 <<= 1) {
+            for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = tid; i < P; i += nth) {
+                    const uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint64_t a = cand[i], c = cand[ixj];
+                        const bool up = (i & k2) == 0;
+                        if ((a > c) == up) { cand[i] = c; cand[ixj] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // chains: each chain start walks to its end
+        for (uint32_t i = tid; i < nc; i += nth) {
+            const uint64_t key = cand[i];
+            if (i > 0 && dev_linked_b(cand[i - 1], key, D, seq_start, n_seqs)) continue;
+            uint32_t j = i;
+            uint64_t kj = key;
+            while (j + 1 < nc) {
+                const uint64_t kn = cand[j + 1];
+                if (!dev_linked_b(kj, kn, D, seq_start, n_seqs)) break;
+                kj = kn;
+                ++j;
+            }
+            const uint32_t qs = (uint32_t)(key & 0xFFFFu), qe = (uint32_t)(kj & 0xFFFFu) + (uint32_t)k;
+            const uint32_t len = qe - qs;
+            if (len < min_len) continue;
+            const uint64_t gpos = (key >> 16) - QBIAS + qs;
+            const uint32_t sq = dev_upper_index(seq_start, n_seqs + 1, gpos);
+            const uint32_t ds = (uint32_t)(gpos - seq_start[sq]);
+            const uint32_t slot = atomicAdd(count, 1u);
+            if (slot < out_cap) {
+                DevHsp hh;
+                hh.qi = qa + ql; hh.seq = sq; hh.qs = qs; hh.qe = qe; hh.ds = ds; hh.de = ds + len; hh.len = len;
+                out[slot] = hh;
+            } else {
+                atomicOr(status, DEV_ERR_CAPACITY);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -596,49 +807,138 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         if (Hc > 0) {
             const int qbits = bits_for(qb - qa - 1);
             const int gbits = (int)gbits_max;
+            const uint32_t nqc = qb - qa;
             DeviceArena carena(s);
-            uint64_t *keys = carena.alloc_n<uint64_t>(Hc);
-            uint64_t *keys_alt = carena.alloc_n<uint64_t>(Hc);
-            void *rs = carena.alloc(radix_scratch_bytes(Hc));
-            uint64_t gwarps = std::min<uint64_t>((xb - xa + 31) / 32, (uint64_t)num_sms() * 64);
-            GN_LAUNCH("k_seed_gather", Hc, s,
-                      k_seed_gather<<<blocks_for(gwarps * 32), 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ha, ix->off_d, ix->post_d,
-                                                                  qa, qbits, keys));
-            timer.mark("seed_gather");
-            bool fl = radix_sort(keys, keys_alt, nullptr, nullptr, Hc, 16 + qbits, 16 + qbits + gbits, rs, s,
-                                 TAG_HIT_SORT);
-            uint64_t *sorted = fl ? keys_alt : keys;
-            timer.mark("hit_sort");
-            if (keep_hits) {
-                uint32_t *quad = carena.alloc_n<uint32_t>(4 * Hc);
-                GN_LAUNCH("k_decode_hits", Hc, s,
-                          k_decode_hits<<<blocks_for(Hc), 256, 0, s>>>(sorted, Hc, qbits, qa, ix->seq_start_d, ix->n_seqs, quad));
-                std::vector<uint32_t> hh = to_host(quad, 4 * Hc, s);
-                hits_q.insert(hits_q.end(), hh.begin(), hh.end());
-            }
-            for (int attempt = 0; attempt < 2; ++attempt) {
-                GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
-                uint64_t threads = std::min<uint64_t>(Hc, (uint64_t)num_sms() * 2048);
-                GN_LAUNCH("k_hit_merge", Hc, s,
-                          k_hit_merge<<<blocks_for(threads), 256, 0, s>>>(sorted, Hc, qbits, qa, k, p.max_hit_distance,
-                                                                p.min_hsp_len, ix->seq_start_d, ix->n_seqs,
-                                                                hsp + n_hsp, counter, hsp_cap - n_hsp, status));
-                uint32_t got = 0;
-                GN_CUDA(cudaMemcpyAsync(&got, counter, 4, cudaMemcpyDeviceToHost, s));
-                GN_CUDA(cudaStreamSynchronize(s));
-                if (n_hsp + (uint64_t)got <= hsp_cap) {
-                    n_hsp += got;
-                    break;
+            // appends HSPs through `launch(out, room)`, growing the HSP buffer and relaunching on overflow
+            auto emit = [&](auto launch) {
+                for (int attempt = 0; attempt < 3; ++attempt) {
+                    GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
+                    launch(hsp + n_hsp, hsp_cap - n_hsp);
+                    uint32_t got = 0;
+                    GN_CUDA(cudaMemcpyAsync(&got, counter, 4, cudaMemcpyDeviceToHost, s));
+                    GN_CUDA(cudaStreamSynchronize(s));
+                    if (n_hsp + (uint64_t)got <= hsp_cap) {
+                        n_hsp += got;
+                        return;
+                    }
+                    uint64_t need = (uint64_t)n_hsp + got;
+                    GN_REQUIRE(need < (1ull << 32), GN_ETOOBIG, "more than 2^32 HSPs in one call");
+                    uint32_t ncap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull,
+                                                                 std::max<uint64_t>(need + need / 4, 2ull * hsp_cap));
+                    DevHsp *nh = arena.alloc_n<DevHsp>(ncap);
+                    if (n_hsp) GN_CUDA(cudaMemcpyAsync(nh, hsp, sizeof(DevHsp) * n_hsp, cudaMemcpyDeviceToDevice, s));
+                    hsp = nh;
+                    hsp_cap = ncap;
+                    GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
                 }
-                // grow the HSP buffer and redo this chunk's merge
-                uint64_t need = (uint64_t)n_hsp + got;
-                GN_REQUIRE(need < (1ull << 32), GN_ETOOBIG, "more than 2^32 HSPs in one call");
-                uint32_t ncap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(need + need / 4, 2ull * hsp_cap));
-                DevHsp *nh = arena.alloc_n<DevHsp>(ncap);
-                if (n_hsp) GN_CUDA(cudaMemcpyAsync(nh, hsp, sizeof(DevHsp) * n_hsp, cudaMemcpyDeviceToDevice, s));
-                hsp = nh;
-                hsp_cap = ncap;
-                GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
+                throw Error{GN_EINTERNAL, "HSP buffer growth did not converge"};
+            };
+            // global path: gather every hit, LSD radix sort by diagonal key, merge sorted runs
+            auto sort_path = [&](uint64_t *keys, uint64_t *keys_alt, uint64_t n, int lo_bit, const RadixTag &tag) {
+                void *rs = carena.alloc(radix_scratch_bytes(n));
+                bool fl = radix_sort(keys, keys_alt, nullptr, nullptr, n, lo_bit, 16 + qbits + gbits, rs, s, tag);
+                uint64_t *sorted = fl ? keys_alt : keys;
+                timer.mark("hit_sort");
+                emit([&](DevHsp *o, uint32_t room) {
+                    uint64_t threads = std::min<uint64_t>(n, (uint64_t)num_sms() * 2048);
+                    GN_LAUNCH("k_hit_merge", n, s,
+                              k_hit_merge<<<blocks_for(threads), 256, 0, s>>>(sorted, n, qbits, qa, k,
+                                                                             p.max_hit_distance, p.min_hsp_len,
+                                                                             ix->seq_start_d, ix->n_seqs, o, counter,
+                                                                             room, status));
+                });
+                return sorted;
+            };
+            const char *grouping = getenv("GN_HIT_GROUPING");
+            const bool bucketed = !keep_hits && !(grouping && strcmp(grouping, "sort") == 0);
+            if (!bucketed) {
+                uint64_t *keys = carena.alloc_n<uint64_t>(Hc);
+                uint64_t *keys_alt = carena.alloc_n<uint64_t>(Hc);
+                uint64_t gwarps = std::min<uint64_t>((xb - xa + 31) / 32, (uint64_t)num_sms() * 64);
+                GN_LAUNCH("k_seed_gather", Hc, s,
+                          k_seed_gather<<<blocks_for(gwarps * 32), 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ha,
+                                                                               ix->off_d, ix->post_d, qa, qbits,
+                                                                               keys));
+                timer.mark("seed_gather");
+                uint64_t *sorted = sort_path(keys, keys_alt, Hc, 16 + qbits, TAG_HIT_SORT);
+                if (keep_hits) {
+                    uint32_t *quad = carena.alloc_n<uint32_t>(4 * Hc);
+                    GN_LAUNCH("k_decode_hits", Hc, s,
+                              k_decode_hits<<<blocks_for(Hc), 256, 0, s>>>(sorted, Hc, qbits, qa, ix->seq_start_d,
+                                                                           ix->n_seqs, quad));
+                    std::vector<uint32_t> hh = to_host(quad, 4 * Hc, s);
+                    hits_q.insert(hits_q.end(), hh.begin(), hh.end());
+                }
+            } else {
+                // bucket plan: 2^lg buckets per query, about `target` hits each
+                uint32_t cap = 2048, target = 1024;
+                if (const char *e = getenv("GN_BUCKET_CAP")) cap = (uint32_t)std::max(64ul, std::min(4096ul, strtoul(e, nullptr, 10)));
+                while (cap & (cap - 1)) cap &= cap - 1;
+                target = cap / 2;
+                std::vector<uint32_t> bbase(nqc + 1), bshift(nqc);
+                const int min_lg = std::max(0, gbits - 31);
+                uint64_t nb64 = 0;
+                for (uint32_t i = 0; i < nqc; ++i) {
+                    const uint64_t hi = hq[qa + i + 1] - hq[qa + i];
+                    const uint64_t want = (hi + target - 1) / target;
+                    int lg = 0;
+                    while ((1ull << lg) < want) ++lg;
+                    lg = std::min(std::max(lg, min_lg), gbits);
+                    bshift[i] = (uint32_t)(gbits - lg);
+                    bbase[i] = (uint32_t)nb64;
+                    nb64 += 1ull << lg;
+                    GN_REQUIRE(nb64 < (1ull << 32), GN_ETOOBIG, "too many hit buckets in one chunk");
+                }
+                bbase[nqc] = (uint32_t)nb64;
+                const uint32_t NB = (uint32_t)nb64;
+                uint32_t *d_bbase = carena.alloc_n<uint32_t>(nqc + 1);
+                uint32_t *d_bshift = carena.alloc_n<uint32_t>(nqc);
+                GN_CUDA(cudaMemcpyAsync(d_bbase, bbase.data(), 4 * (nqc + 1), cudaMemcpyHostToDevice, s));
+                GN_CUDA(cudaMemcpyAsync(d_bshift, bshift.data(), 4 * nqc, cudaMemcpyHostToDevice, s));
+                uint32_t *bcnt = carena.alloc_n<uint32_t>(NB);
+                uint64_t *boff = carena.alloc_n<uint64_t>((uint64_t)NB + 1);
+                uint64_t *bkeys = carena.alloc_n<uint64_t>(Hc);
+                GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
+                uint64_t gwarps = std::min<uint64_t>((xb - xa + 31) / 32, (uint64_t)num_sms() * 64);
+                GN_LAUNCH("k_bucket_count", Hc, s,
+                          k_bucket_hits<false><<<blocks_for(gwarps * 32), 256, 0, s>>>(
+                              codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcnt, nullptr,
+                              nullptr));
+                {
+                    void *scr = carena.alloc(scan_scratch_bytes(NB));
+                    exclusive_scan_u32(bcnt, boff, NB, scr, s);
+                }
+                GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
+                GN_LAUNCH("k_bucket_scatter", Hc, s,
+                          k_bucket_hits<true><<<blocks_for(gwarps * 32), 256, 0, s>>>(
+                              codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcnt, boff,
+                              bkeys));
+                timer.mark("bucket_scatter");
+                unsigned long long *ovf_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
+                GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
+                GN_LAUNCH("k_bucket_overflow", NB, s,
+                          k_bucket_overflow<<<blocks_for(NB), 256, 0, s>>>(boff, NB, cap, ovf_count));
+                unsigned long long n_ovf = 0;
+                GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
+                GN_CUDA(cudaStreamSynchronize(s));
+                uint64_t *ovf = carena.alloc_n<uint64_t>(n_ovf);
+                uint64_t *ovf_alt = carena.alloc_n<uint64_t>(n_ovf);
+                const size_t smem = (size_t)cap * 32;
+                GN_CUDA(cudaFuncSetAttribute(k_bucket_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                int occ = 0;
+                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_group, 256, smem));
+                const unsigned ggrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(NB, (uint64_t)num_sms() * std::max(occ, 1)));
+                const int singles = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
+                emit([&](DevHsp *o, uint32_t room) {
+                    GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
+                    GN_LAUNCH("k_bucket_group", Hc, s,
+                              k_bucket_group<<<ggrid, 256, smem, s>>>(bkeys, boff, NB, d_bbase, d_bshift, nqc, qa,
+                                                                      qbits, k, p.max_hit_distance, p.min_hsp_len,
+                                                                      singles, cap, ix->seq_start_d, ix->n_seqs, o,
+                                                                      counter, room, ovf, ovf_count, status));
+                });
+                timer.mark("bucket_group");
+                if (n_ovf) sort_path(ovf, ovf_alt, n_ovf, 0, TAG_HIT_SORT);
             }
             timer.mark("hit_merge");
         }

@@ -174,6 +174,18 @@ def test_chunked_equals_unchunked(gn, mid_small, monkeypatch):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("env", [{"GN_HIT_GROUPING": "sort"}, {"GN_BUCKET_CAP": "64"},
+                                 {"GN_BUCKET_CAP": "64", "GN_MAX_CHUNK_HITS": "30000"}])
+def test_hit_grouping_paths_agree_with_oracle(gn, mid_small, monkeypatch, env):
+    """The global sort path, the bucketed path and its overflow fallback give the oracle's HSPs."""
+    bank, qs, ix, ox = mid_small
+    for k_, v in env.items():
+        monkeypatch.setenv(k_, v)
+    res = gn.search(ix, qs.start, qs.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
+    ref = ox.search(qs, oracle.Params(), threads=os.cpu_count() or 1)
+    check_stages(gn, res, ref, qs.n, str(env))
+
+
 def test_device_queries_equal_host_queries(gn, mid_small):
     import torch
     bank, qs, ix, ox = mid_small
@@ -184,7 +196,8 @@ def test_device_queries_equal_host_queries(gn, mid_small):
 
 
 @pytest.mark.parametrize("kw", [dict(max_alignments=0), dict(max_alignments=1), dict(band_w=0),
-                                dict(band_w=64), dict(xdrop=5), dict(max_hit_distance=11, min_hsp_len=33)])
+                                dict(band_w=64), dict(xdrop=5), dict(max_hit_distance=11, min_hsp_len=33),
+                                dict(min_hsp_len=11), dict(min_hsp_len=5)])
 def test_parameters_mid_small(gn, mid_small, kw):
     bank, qs, ix, ox = mid_small
     sub = qs.subset(range(0, qs.n, 3))
