@@ -176,59 +176,9 @@ __global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int q
 // Hits of query i are partitioned into 2^b_i buckets by the high bits of their
 // diagonal key G' = gpos - qpos + QBIAS (bucket = bbase[i] + (G' >> bshift[i])).
 // Every (query, diagonal) lies in one bucket, so each bucket is grouped on its
-// own in shared memory.  A diagonal holding a single hit cannot form an HSP when
-// min_hsp_len > k, so a hash count per diagonal drops those before the (small)
-// sort by (G', qpos) that the chaining needs.
-// Bucket entry: G' << 16 | qpos.
-template <bool SCATTER>
-__global__ void __launch_bounds__(256) k_bucket_hits(const uint32_t *__restrict__ codes,
-                                                     const uint32_t *__restrict__ qinfo,
-                                                     const uint64_t *__restrict__ hoff, uint64_t xa, uint64_t xb,
-                                                     const uint64_t *__restrict__ off,
-                                                     const uint32_t *__restrict__ post, uint32_t qa,
-                                                     const uint32_t *__restrict__ bbase,
-                                                     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcnt,
-                                                     const uint64_t *__restrict__ boff,
-                                                     uint64_t *__restrict__ bkeys) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (uint64_t x0 = xa + warp * 32; x0 < xb; x0 += nwarps * 32) {
-        uint64_t x = x0 + lane;
-        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
-        uint64_t my_src = 0;
-        if (x < xb) {
-            my_cnt = (uint32_t)(hoff[x + 1] - hoff[x]);
-            if (my_cnt) {
-                uint32_t qinf = qinfo[x];
-                my_src = off[codes[x]];
-                my_qpos = qinf & 0xFFFFu;
-                my_ql = (qinf >> 16) - qa;
-            }
-        }
-        uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
-        while (todo) {
-            int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
-            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
-            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
-            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
-            const uint32_t base = bbase[ql], sh = bshift[ql];
-            for (uint32_t j = lane; j < cnt; j += 32) {
-                const uint64_t gk = (uint64_t)post[sp + j] + QBIAS - qpos;
-                const uint32_t b = base + (uint32_t)(gk >> sh);
-                if (!SCATTER) {
-                    atomicAdd(&bcnt[b], 1u);
-                } else {
-                    const uint32_t slot = atomicAdd(&bcnt[b], 1u);
-                    bkeys[boff[b] + slot] = (gk << 16) | qpos;
-                }
-            }
-        }
-    }
-}
-
+// own.  A diagonal holding a single hit cannot form an HSP when min_hsp_len > k,
+// so such hits are dropped before the (small) sort by (G', qpos) that the
+// chaining needs.  Bucket entry: G' << 16 | qpos.
 __global__ void k_bucket_overflow(const uint64_t *__restrict__ boff, uint32_t NB, uint32_t cap,
                                   unsigned long long *__restrict__ total) {
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -248,98 +198,192 @@ __device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D,
            dev_upper_index(seq_start, n_seqs + 1, gk - QBIAS + qb);
 }
 
-constexpr uint32_t BG_EMPTY = 0xFFFFFFFFu;
+// Tile-level bucketing: a CTA takes 256 consecutive query offsets (8 warps x 32).
+// Bucket counts and output ranges are aggregated in shared memory over the
+// tile's bucket span, so global atomics are one per (tile, bucket), not per hit.
+// PASS 0 counts hits per bucket; PASS 1 reserves ranges and writes the entries.
+constexpr int BT_SPAN = 2048;  // buckets a tile can aggregate in shared memory
 
-// last index i in [0, n) with a[i] <= x (a non-decreasing 32-bit array, a[0] <= x)
-__device__ __forceinline__ uint32_t dev_upper_index32(const uint32_t *__restrict__ a, uint32_t n, uint32_t x) {
-    uint32_t lo = 0, hi = n;
-    while (hi - lo > 1) {
-        uint32_t mid = lo + (hi - lo) / 2;
-        if (a[mid] <= x) lo = mid; else hi = mid;
+template <int PASS>
+__global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict__ codes,
+                                                      const uint32_t *__restrict__ qinfo,
+                                                      const uint64_t *__restrict__ hoff, uint64_t xa, uint64_t xb,
+                                                      const uint64_t *__restrict__ off,
+                                                      const uint32_t *__restrict__ post, uint32_t qa, uint32_t NB,
+                                                      const uint32_t *__restrict__ bbase,
+                                                      const uint32_t *__restrict__ bshift,
+                                                      uint32_t *__restrict__ bcnt, const uint64_t *__restrict__ boff,
+                                                      uint64_t *__restrict__ bkeys) {
+    __shared__ uint32_t hist[BT_SPAN];
+    __shared__ unsigned long long base[PASS ? BT_SPAN : 1];
+    __shared__ uint32_t bmin_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < BT_SPAN; i += 256) hist[i] = 0;
+    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * 256; t0 < xb; t0 += (uint64_t)gridDim.x * 256) {
+        if (threadIdx.x == 0) bmin_s = bbase[(qinfo[t0] >> 16) - qa];
+        __syncthreads();
+        const uint32_t bmin = bmin_s;
+        const uint64_t x = t0 + warp * 32 + lane;
+        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
+        uint64_t my_src = 0;
+        if (x < xb) {
+            my_cnt = (uint32_t)(hoff[x + 1] - hoff[x]);
+            if (my_cnt) {
+                const uint32_t qinf = qinfo[x];
+                my_src = off[codes[x]];
+                my_qpos = qinf & 0xFFFFu;
+                my_ql = (qinf >> 16) - qa;
+            }
+        }
+        const uint32_t todo0 = __ballot_sync(0xffffffffu, my_cnt != 0);
+        // pass over the tile's hits: local counts (and, in PASS 1 after the reservation, placement)
+        for (int phase = 0; phase < (PASS ? 2 : 1); ++phase) {
+            if (phase == 1) {
+                __syncthreads();
+                // reserve each bucket's range for this tile; hist becomes the local cursor
+                for (uint32_t i = threadIdx.x; i < BT_SPAN; i += 256) {
+                    const uint32_t c = hist[i];
+                    if (c) {
+                        const uint32_t b = bmin + i;
+                        base[i] = boff[b] + atomicAdd(&bcnt[b], c);
+                        hist[i] = 0;
+                    }
+                }
+                __syncthreads();
+            }
+            uint32_t todo = todo0;
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
+                const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
+                const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
+                const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
+                const uint32_t bb = bbase[ql], sh = bshift[ql];
+                for (uint32_t j = lane; j < cnt; j += 32) {
+                    const uint64_t gk = (uint64_t)post[sp + j] + QBIAS - qpos;
+                    const uint32_t b = bb + (uint32_t)(gk >> sh);
+                    const uint32_t li = b - bmin;
+                    if (phase == 0) {
+                        if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
+                        else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
+                    } else {
+                        uint64_t dst;
+                        if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
+                        else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
+                        bkeys[dst] = (gk << 16) | qpos;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (PASS == 0) {
+            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += 256) {
+                const uint32_t c = hist[i];
+                if (c) {
+                    atomicAdd(&bcnt[bmin + i], c);
+                    hist[i] = 0;
+                }
+            }
+        } else {
+            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += 256) hist[i] = 0;
+        }
+        __syncthreads();
     }
-    return lo;
 }
 
-__global__ void __launch_bounds__(256) k_bucket_group(
+__global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc, uint32_t NB,
+                               uint16_t *__restrict__ bq) {
+    uint32_t q = blockIdx.x;
+    if (q >= nqc) return;
+    for (uint32_t b = bbase[q] + threadIdx.x; b < bbase[q + 1]; b += blockDim.x) bq[b] = (uint16_t)q;
+}
+
+// One warp per bucket.  Two bitmaps per warp mark diagonal hashes seen once and
+// seen twice; hits whose hash was seen twice are candidates (a hash collision
+// only adds a candidate that the exact chaining below then drops).  Candidates
+// are sorted by (G', qpos) with a warp bitonic sort and chained.  Buckets with
+// more than BGW_CAND candidates go to the global sort path.
+constexpr int BGW_WARPS = 8;
+constexpr int BGW_BITS = 16384;
+constexpr int BGW_CAND = 256;
+
+__global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
     const uint64_t *__restrict__ bkeys, const uint64_t *__restrict__ boff, uint32_t NB,
-    const uint32_t *__restrict__ bbase, const uint32_t *__restrict__ bshift, uint32_t nqc, uint32_t qa, int qbits,
-    int k, uint32_t D, uint32_t min_len, int singles, uint32_t cap, const uint64_t *__restrict__ seq_start,
-    uint32_t n_seqs, DevHsp *__restrict__ out, uint32_t *__restrict__ count, uint32_t out_cap,
-    uint64_t *__restrict__ ovf, unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status) {
-    extern __shared__ __align__(16) unsigned char bg_smem[];
-    uint64_t *skeys = reinterpret_cast<uint64_t *>(bg_smem);
-    uint64_t *cand = skeys + cap;
-    uint32_t *tkey = reinterpret_cast<uint32_t *>(cand + cap);
-    uint32_t *tcnt = tkey + 2 * cap;
-    __shared__ uint32_t nc_s;
-    __shared__ unsigned long long ovf_pos;
-    const int tid = threadIdx.x;
-    const int nth = blockDim.x;
-    for (uint32_t b = blockIdx.x; b < NB; b += gridDim.x) {
+    const uint16_t *__restrict__ bq, uint32_t qa, int qbits, int k, uint32_t D, uint32_t min_len, int singles,
+    const uint64_t *__restrict__ seq_start, uint32_t n_seqs, DevHsp *__restrict__ out, uint32_t *__restrict__ count,
+    uint32_t out_cap, uint64_t *__restrict__ ovf, unsigned long long ovf_cap,
+    unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status) {
+    extern __shared__ __align__(16) unsigned char gw_smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t *seen = reinterpret_cast<uint32_t *>(gw_smem) + wib * (2 * BGW_BITS / 32);
+    uint32_t *seen2 = seen + BGW_BITS / 32;
+    uint64_t *cand = reinterpret_cast<uint64_t *>(gw_smem + BGW_WARPS * 2 * BGW_BITS / 8) + wib * BGW_CAND;
+    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t total_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < NB; b += total_warps) {
         const uint64_t beg = boff[b];
         const uint32_t n = (uint32_t)(boff[b + 1] - beg);
         if (n == 0 || (n == 1 && !singles)) continue;
-        const uint32_t ql = dev_upper_index32(bbase, nqc + 1, b);
-        const uint32_t sh = bshift[ql];
-        const uint64_t glo = (uint64_t)(b - bbase[ql]) << sh;
-        if (n > cap) {
-            // too large for shared memory: hand the bucket to the global sort path, in its key format
-            if (tid == 0) ovf_pos = atomicAdd(ovf_count, (unsigned long long)n);
-            __syncthreads();
-            const unsigned long long p0 = ovf_pos;
-            for (uint32_t i = tid; i < n; i += nth) {
-                const uint64_t e = bkeys[beg + i];
-                ovf[p0 + i] = ((e >> 16) << (16 + qbits)) | ((uint64_t)ql << 16) | (e & 0xFFFFu);
+        const uint32_t ql = bq[b];
+        bool spill = false;
+        uint32_t nc = 0;
+        if (!singles) {
+            for (int i = lane; i < BGW_BITS / 32; i += 32) { seen[i] = 0u; seen2[i] = 0u; }
+            __syncwarp();
+            for (uint32_t i = lane; i < n; i += 32) {
+                const uint64_t g = bkeys[beg + i] >> 16;
+                const uint32_t h = (uint32_t)((g * 0x9E3779B97F4A7C15ull) >> 50);  // 14 bits
+                const uint32_t bit = 1u << (h & 31);
+                const uint32_t old = atomicOr(&seen[h >> 5], bit);
+                if (old & bit) atomicOr(&seen2[h >> 5], bit);
             }
-            __syncthreads();
+            __syncwarp();
+        }
+        for (uint32_t i0 = 0; i0 < n && !spill; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            uint64_t key = 0;
+            bool keep = false;
+            if (i < n) {
+                key = bkeys[beg + i];
+                if (singles) {
+                    keep = true;
+                } else {
+                    const uint32_t h = (uint32_t)(((key >> 16) * 0x9E3779B97F4A7C15ull) >> 50);
+                    keep = (seen2[h >> 5] >> (h & 31)) & 1u;
+                }
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, keep);
+            if (nc + __popc(m) > BGW_CAND) {
+                spill = true;
+            } else {
+                if (keep) cand[nc + __popc(m & lt)] = key;
+                nc += __popc(m);
+            }
+        }
+        if (spill) {
+            // too many candidates: hand the bucket to the global sort path, in its key format
+            unsigned long long p0 = 0;
+            if (lane == 0) p0 = atomicAdd(ovf_count, (unsigned long long)n);
+            p0 = __shfl_sync(0xffffffffu, p0, 0);
+            if (p0 + n <= ovf_cap) {  // else: counted only; the host enlarges the buffer and reruns
+                for (uint32_t i = lane; i < n; i += 32) {
+                    const uint64_t e = bkeys[beg + i];
+                    ovf[p0 + i] = ((e >> 16) << (16 + qbits)) | ((uint64_t)ql << 16) | (e & 0xFFFFu);
+                }
+            }
+            __syncwarp();
             continue;
         }
-        uint32_t ts = 2;
-        while (ts < 2 * n) ts <<= 1;
-        const int tbits = 31 - __clz(ts);
-        for (uint32_t i = tid; i < ts; i += nth) { tkey[i] = BG_EMPTY; tcnt[i] = 0; }
-        if (tid == 0) nc_s = 0;
-        for (uint32_t i = tid; i < n; i += nth) skeys[i] = bkeys[beg + i];
-        __syncthreads();
-        // count hits per diagonal (open addressing; the table is at most half full)
-        if (!singles) {
-            for (uint32_t i = tid; i < n; i += nth) {
-                const uint32_t rel = (uint32_t)((skeys[i] >> 16) - glo);
-                uint32_t h = (rel * 2654435761u) >> (32 - tbits);
-                for (uint32_t probe = 0; probe < ts; ++probe) {
-                    const uint32_t old = atomicCAS(&tkey[h], BG_EMPTY, rel);
-                    if (old == BG_EMPTY || old == rel) { atomicAdd(&tcnt[h], 1u); break; }
-                    h = (h + 1) & (ts - 1);
-                }
-            }
-            __syncthreads();
-        }
-        // candidates: hits whose diagonal holds at least two hits (all hits when single hits can be HSPs)
-        for (uint32_t i = tid; i < n; i += nth) {
-            bool keep = singles;
-            if (!keep) {
-                const uint32_t rel = (uint32_t)((skeys[i] >> 16) - glo);
-                uint32_t h = (rel * 2654435761u) >> (32 - tbits);
-                for (uint32_t probe = 0; probe < ts; ++probe) {
-                    const uint32_t kk = tkey[h];
-                    if (kk == rel) { keep = tcnt[h] >= 2u; break; }
-                    if (kk == BG_EMPTY) break;
-                    h = (h + 1) & (ts - 1);
-                }
-            }
-            if (keep) cand[atomicAdd(&nc_s, 1u)] = skeys[i];
-        }
-        __syncthreads();
-        const uint32_t nc = nc_s;
-        if (nc == 0) { __syncthreads(); continue; }
-        // bitonic sort of the candidates by (G', qpos)
+        if (nc < 2 && !singles) { __syncwarp(); continue; }
+        if (nc == 0) { __syncwarp(); continue; }
         uint32_t P = 1;
         while (P < nc) P <<= 1;
-        for (uint32_t i = nc + tid; i < P; i += nth) cand[i] = ~0ull;
-        __syncthreads();
+        for (uint32_t i = nc + lane; i < P; i += 32) cand[i] = ~0ull;
+        __syncwarp();
         for (uint32_t k2 = 2; k2 <= P; k2 <<= 1) {
             for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = tid; i < P; i += nth) {
+                for (uint32_t i = lane; i < P; i += 32) {
                     const uint32_t ixj = i ^ j;
                     if (ixj > i) {
                         const uint64_t a = cand[i], c = cand[ixj];
@@ -347,11 +391,10 @@ __global__ void __launch_bounds__(256) k_bucket_group(
                         if ((a > c) == up) { cand[i] = c; cand[ixj] = a; }
                     }
                 }
-                __syncthreads();
+                __syncwarp();
             }
         }
-        // chains: each chain start walks to its end
-        for (uint32_t i = tid; i < nc; i += nth) {
+        for (uint32_t i = lane; i < nc; i += 32) {
             const uint64_t key = cand[i];
             if (i > 0 && dev_linked_b(cand[i - 1], key, D, seq_start, n_seqs)) continue;
             uint32_t j = i;
@@ -377,7 +420,7 @@ __global__ void __launch_bounds__(256) k_bucket_group(
                 atomicOr(status, DEV_ERR_CAPACITY);
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -790,7 +833,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     const uint64_t gbits_max = (uint64_t)bits_for(ix->n_bases + QBIAS);
     const uint32_t max_chunk_q = (uint32_t)std::min<uint64_t>(MAX_QUERIES, 1ull << std::min<uint64_t>(48 - gbits_max, 31));
 
-    uint32_t hsp_cap = 1u << 16;
+    uint32_t hsp_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(1u << 20, hq[nq] / 128));
     DevHsp *hsp = arena.alloc_n<DevHsp>(hsp_cap);
     uint32_t n_hsp = 0;
     uint32_t *counter = arena.alloc_n<uint32_t>(4);
@@ -895,49 +938,70 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint32_t *d_bshift = carena.alloc_n<uint32_t>(nqc);
                 GN_CUDA(cudaMemcpyAsync(d_bbase, bbase.data(), 4 * (nqc + 1), cudaMemcpyHostToDevice, s));
                 GN_CUDA(cudaMemcpyAsync(d_bshift, bshift.data(), 4 * nqc, cudaMemcpyHostToDevice, s));
+                const int singles = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
                 uint32_t *bcnt = carena.alloc_n<uint32_t>(NB);
                 uint64_t *boff = carena.alloc_n<uint64_t>((uint64_t)NB + 1);
                 uint64_t *bkeys = carena.alloc_n<uint64_t>(Hc);
+                uint16_t *bq = carena.alloc_n<uint16_t>(NB);
                 GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
-                uint64_t gwarps = std::min<uint64_t>((xb - xa + 31) / 32, (uint64_t)num_sms() * 64);
+                const uint64_t tiles = (xb - xa + 255) / 256;
+                const unsigned tgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * 8));
                 GN_LAUNCH("k_bucket_count", Hc, s,
-                          k_bucket_hits<false><<<blocks_for(gwarps * 32), 256, 0, s>>>(
-                              codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcnt, nullptr,
-                              nullptr));
+                          k_bucket_tiles<0><<<tgrid, 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d,
+                                                                  qa, NB, d_bbase, d_bshift, bcnt, nullptr, nullptr));
                 {
                     void *scr = carena.alloc(scan_scratch_bytes(NB));
                     exclusive_scan_u32(bcnt, boff, NB, scr, s);
                 }
                 GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
                 GN_LAUNCH("k_bucket_scatter", Hc, s,
-                          k_bucket_hits<true><<<blocks_for(gwarps * 32), 256, 0, s>>>(
-                              codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcnt, boff,
-                              bkeys));
+                          k_bucket_tiles<1><<<tgrid, 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d,
+                                                                  qa, NB, d_bbase, d_bshift, bcnt, boff, bkeys));
+                GN_LAUNCH("k_bucket_query", NB, s, k_bucket_query<<<nqc, 256, 0, s>>>(d_bbase, nqc, NB, bq));
                 timer.mark("bucket_scatter");
                 unsigned long long *ovf_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
+                // buckets whose candidates may not fit a warp's buffer are bounded by their size; size the
+                // overflow buffer for the worst case of every bucket with more than BGW_CAND entries
                 GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
                 GN_LAUNCH("k_bucket_overflow", NB, s,
-                          k_bucket_overflow<<<blocks_for(NB), 256, 0, s>>>(boff, NB, cap, ovf_count));
-                unsigned long long n_ovf = 0;
-                GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
+                          k_bucket_overflow<<<blocks_for(NB), 256, 0, s>>>(boff, NB, singles ? BGW_CAND : 0xFFFFFFFFu,
+                                                                           ovf_count));
+                unsigned long long ovf_cap = 0;
+                GN_CUDA(cudaMemcpyAsync(&ovf_cap, ovf_count, 8, cudaMemcpyDeviceToHost, s));
                 GN_CUDA(cudaStreamSynchronize(s));
-                uint64_t *ovf = carena.alloc_n<uint64_t>(n_ovf);
-                uint64_t *ovf_alt = carena.alloc_n<uint64_t>(n_ovf);
-                const size_t smem = (size_t)cap * 32;
-                GN_CUDA(cudaFuncSetAttribute(k_bucket_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                // without single-hit HSPs, spills come from candidate overflow, which a retry sizes exactly
+                uint64_t ovf_room = singles ? ovf_cap : std::max<uint64_t>(1u << 20, Hc / 64);
+                uint64_t *ovf = carena.alloc_n<uint64_t>(ovf_room);
+                uint64_t *ovf_alt = nullptr;
+                const size_t smem = (size_t)BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8);
+                GN_CUDA(cudaFuncSetAttribute(k_bucket_group_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 int occ = 0;
-                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_group, 256, smem));
-                const unsigned ggrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(NB, (uint64_t)num_sms() * std::max(occ, 1)));
-                const int singles = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
-                emit([&](DevHsp *o, uint32_t room) {
-                    GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
-                    GN_LAUNCH("k_bucket_group", Hc, s,
-                              k_bucket_group<<<ggrid, 256, smem, s>>>(bkeys, boff, NB, d_bbase, d_bshift, nqc, qa,
-                                                                      qbits, k, p.max_hit_distance, p.min_hsp_len,
-                                                                      singles, cap, ix->seq_start_d, ix->n_seqs, o,
-                                                                      counter, room, ovf, ovf_count, status));
-                });
+                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_group_warp, BGW_WARPS * 32, smem));
+                const unsigned ggrid = (unsigned)std::max<uint64_t>(
+                    1, std::min<uint64_t>((NB + BGW_WARPS - 1) / BGW_WARPS, (uint64_t)num_sms() * std::max(occ, 1)));
+                unsigned long long n_ovf = 0;
+                for (int attempt = 0; attempt < 2; ++attempt) {
+                    const uint32_t hsp_before = n_hsp;
+                    emit([&](DevHsp *o, uint32_t room) {
+                        GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
+                        GN_LAUNCH("k_bucket_group", Hc, s,
+                                  k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
+                                      bkeys, boff, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len, singles,
+                                      ix->seq_start_d, ix->n_seqs, o, counter, room, ovf,
+                                      (unsigned long long)ovf_room, ovf_count, status));
+                    });
+                    GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
+                    GN_CUDA(cudaStreamSynchronize(s));
+                    if (n_ovf <= ovf_room) break;
+                    // spilled more than the buffer holds: enlarge it and redo this chunk's grouping
+                    n_hsp = hsp_before;
+                    ovf_room = n_ovf;
+                    ovf = carena.alloc_n<uint64_t>(ovf_room);
+                    GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
+                }
+                GN_REQUIRE(n_ovf <= ovf_room, GN_EINTERNAL, "hit-bucket spill buffer sizing did not converge");
                 timer.mark("bucket_group");
+                if (n_ovf) ovf_alt = carena.alloc_n<uint64_t>(n_ovf);
                 if (n_ovf) sort_path(ovf, ovf_alt, n_ovf, 0, TAG_HIT_SORT);
             }
             timer.mark("hit_merge");
