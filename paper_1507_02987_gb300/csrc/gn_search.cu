@@ -260,18 +260,30 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                 const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
                 const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
                 const uint32_t bb = bbase[ql], sh = bshift[ql];
-                for (uint32_t j = lane; j < cnt; j += 32) {
-                    const uint64_t gk = (uint64_t)post[sp + j] + QBIAS - qpos;
-                    const uint32_t b = bb + (uint32_t)(gk >> sh);
-                    const uint32_t li = b - bmin;
-                    if (phase == 0) {
-                        if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
-                        else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
-                    } else {
-                        uint64_t dst;
-                        if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
-                        else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
-                        bkeys[dst] = (gk << 16) | qpos;
+                for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
+                    // four list entries per lane in flight before any atomic
+                    uint32_t g[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t j = j0 + u * 32 + lane;
+                        g[u] = j < cnt ? post[sp + j] : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t j = j0 + u * 32 + lane;
+                        if (j >= cnt) break;
+                        const uint64_t gk = (uint64_t)g[u] + QBIAS - qpos;
+                        const uint32_t b = bb + (uint32_t)(gk >> sh);
+                        const uint32_t li = b - bmin;
+                        if (phase == 0) {
+                            if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
+                            else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
+                        } else {
+                            uint64_t dst;
+                            if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
+                            else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
+                            bkeys[dst] = (gk << 16) | qpos;
+                        }
                     }
                 }
             }
@@ -331,12 +343,21 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
         if (!singles) {
             for (int i = lane; i < BGW_BITS / 32; i += 32) { seen[i] = 0u; seen2[i] = 0u; }
             __syncwarp();
-            for (uint32_t i = lane; i < n; i += 32) {
-                const uint64_t g = bkeys[beg + i] >> 16;
-                const uint32_t h = (uint32_t)((g * 0x9E3779B97F4A7C15ull) >> 50);  // 14 bits
-                const uint32_t bit = 1u << (h & 31);
-                const uint32_t old = atomicOr(&seen[h >> 5], bit);
-                if (old & bit) atomicOr(&seen2[h >> 5], bit);
+            for (uint32_t i0 = 0; i0 < n; i0 += 128) {
+                uint64_t e[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t i = i0 + u * 32 + lane;
+                    e[u] = i < n ? bkeys[beg + i] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (i0 + u * 32 + lane >= n) break;
+                    const uint32_t h = (uint32_t)(((e[u] >> 16) * 0x9E3779B97F4A7C15ull) >> 50);  // 14 bits
+                    const uint32_t bit = 1u << (h & 31);
+                    const uint32_t old = atomicOr(&seen[h >> 5], bit);
+                    if (old & bit) atomicOr(&seen2[h >> 5], bit);
+                }
             }
             __syncwarp();
         }
@@ -443,6 +464,21 @@ __device__ __forceinline__ int32_t dev_pair(uint32_t a, uint32_t b, int32_t matc
     return (a < 4u && a == b) ? match : mismatch;
 }
 
+// Walks packed bases one at a time, reloading the code word every 16 bases and the
+// non-base word every 32 (instead of two loads per base).
+struct BaseCursor {
+    const uint32_t *pk, *nb;
+    uint64_t wpk_i = ~0ull, wnb_i = ~0ull;
+    uint32_t wpk = 0, wnb = 0;
+    __device__ __forceinline__ BaseCursor(const uint32_t *p, const uint32_t *n) : pk(p), nb(n) {}
+    __device__ __forceinline__ uint32_t at(uint64_t g) {  // 2-bit code, or 4 for a non-base
+        const uint64_t a = g >> 4, b = g >> 5;
+        if (a != wpk_i) { wpk_i = a; wpk = pk[a]; }
+        if (b != wnb_i) { wnb_i = b; wnb = nb[b]; }
+        return ((wnb >> (g & 31)) & 1u) ? 4u : (wpk >> (30 - 2 * (int)(g & 15))) & 3u;
+    }
+};
+
 __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__restrict__ qpk,
                         const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
                         const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
@@ -452,10 +488,11 @@ __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__re
     DevHsp r = h[i];
     const uint64_t qb = qstart[r.qi], sb = seq_start[r.seq];
     const uint32_t m = (uint32_t)(qstart[r.qi + 1] - qb), L = (uint32_t)(seq_start[r.seq + 1] - sb);
+    BaseCursor cq(qpk, qnb), cd(bpk, bnb);
     int32_t score = 0, best = 0;
     uint32_t ext = 0;
     for (uint32_t e = 1; e <= r.qs && e <= r.ds; ++e) {
-        score += dev_pair(dev_base(qpk, qnb, qb + r.qs - e), dev_base(bpk, bnb, sb + r.ds - e), match, mismatch);
+        score += dev_pair(cq.at(qb + r.qs - e), cd.at(sb + r.ds - e), match, mismatch);
         if (score > best) { best = score; ext = e; }
         else if (best - score > X) break;
     }
@@ -463,8 +500,7 @@ __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__re
     r.ds -= ext;
     score = 0; best = 0; ext = 0;
     for (uint32_t e = 1; r.qe + e - 1 < m && r.de + e - 1 < L; ++e) {
-        score += dev_pair(dev_base(qpk, qnb, qb + r.qe + e - 1), dev_base(bpk, bnb, sb + r.de + e - 1), match,
-                          mismatch);
+        score += dev_pair(cq.at(qb + r.qe + e - 1), cd.at(sb + r.de + e - 1), match, mismatch);
         if (score > best) { best = score; ext = e; }
         else if (best - score > X) break;
     }
@@ -551,6 +587,90 @@ __device__ __forceinline__ void scan_pair_max(int32_t &v, uint32_t &s, int lane)
     }
 }
 
+
+// Band of at most 32*C diagonals: lane l owns band offsets c*32 + l, and the
+// previous DP row stays in registers.  The vertical-gap input of offset b (cell
+// (i-1, j) = offset b+1 of the previous row) comes from the next lane by shuffle.
+// Same recurrence, tie-breaks and F max-scan as the strip version below.
+template <int C>
+__device__ __forceinline__ void sw_rows_regs(int64_t I0, int64_t I1, int64_t J0, int64_t J1, int64_t dlo, int64_t B,
+                                             uint64_t qb, uint64_t sb, const uint32_t *__restrict__ qpk,
+                                             const uint32_t *__restrict__ qnb, const uint32_t *__restrict__ bpk,
+                                             const uint32_t *__restrict__ bnb, int32_t match, int32_t mismatch,
+                                             int32_t goe, int32_t ge, int lane, int32_t &best, int64_t &bi,
+                                             int64_t &bj, uint32_t &bs) {
+    int32_t pH[C], pE[C];
+    uint32_t pSH[C], pSE[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) { pH[c] = 0; pE[c] = SW_NEG; pSH[c] = 0; pSE[c] = 0; }
+    for (int64_t i = I0; i < I1; ++i) {
+        const int64_t blo = max((int64_t)0, J0 - i - dlo), bhi = min(B - 1, J1 - 1 - i - dlo);
+        if (blo > bhi) continue;
+        const bool prow = i - 1 >= I0;
+        const int64_t pblo = max((int64_t)0, J0 - (i - 1) - dlo), pbhi = min(B - 1, J1 - 1 - (i - 1) - dlo);
+        const uint32_t qc = dev_base(qpk, qnb, qb + (uint64_t)i);
+        int32_t carry_v = SW_XNEG;
+        uint32_t carry_s = 0;
+        int32_t cH[C], cE[C];
+        uint32_t cSH[C], cSE[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            // previous-row values at offset b + 1
+            int32_t uH = __shfl_down_sync(0xffffffffu, pH[c], 1), uE = __shfl_down_sync(0xffffffffu, pE[c], 1);
+            uint32_t uSH = __shfl_down_sync(0xffffffffu, pSH[c], 1), uSE = __shfl_down_sync(0xffffffffu, pSE[c], 1);
+            if (c + 1 < C) {
+                const int32_t nH = __shfl_sync(0xffffffffu, pH[c + 1 < C ? c + 1 : c], 0);
+                const int32_t nE = __shfl_sync(0xffffffffu, pE[c + 1 < C ? c + 1 : c], 0);
+                const uint32_t nSH = __shfl_sync(0xffffffffu, pSH[c + 1 < C ? c + 1 : c], 0);
+                const uint32_t nSE = __shfl_sync(0xffffffffu, pSE[c + 1 < C ? c + 1 : c], 0);
+                if (lane == 31) { uH = nH; uE = nE; uSH = nSH; uSE = nSE; }
+            }
+            const int64_t b = (int64_t)c * 32 + lane;
+            if ((int64_t)c * 32 > bhi || (int64_t)c * 32 + 31 < blo) {  // chunk outside this row (warp-uniform)
+                cH[c] = pH[c]; cE[c] = pE[c]; cSH[c] = pSH[c]; cSE[c] = pSE[c];
+                continue;
+            }
+            const bool act = b >= blo && b <= bhi;
+            const bool ok_d = act && prow && b >= pblo && b <= pbhi;
+            const bool ok_u = act && prow && b + 1 >= pblo && b + 1 <= pbhi;
+            int32_t E = SW_NEG;
+            uint32_t SE = 0;
+            if (ok_u) {
+                const int32_t eo = uH + goe, ee = uE + ge;
+                if (eo >= ee) { E = eo; SE = uSH; } else { E = ee; SE = uSE; }
+            }
+            const int32_t Hd = ok_d ? pH[c] : 0;
+            const uint32_t SD = (Hd > 0) ? pSH[c] : ((uint32_t)(i - I0) << 16) | (uint32_t)b;
+            const int64_t j = i + dlo + b;
+            int32_t sigma = mismatch;
+            if (act) sigma = dev_pair(qc, dev_base(bpk, bnb, sb + (uint64_t)j), match, mismatch);
+            const int32_t Dg = Hd + sigma;
+            int32_t cand;
+            uint32_t Sc;
+            if (Dg >= E) { cand = Dg; Sc = SD; } else { cand = E; Sc = SE; }
+            const int32_t H0 = cand > 0 ? cand : 0;
+            int32_t xv = act ? H0 + goe - ge * (int32_t)b : SW_XNEG;
+            uint32_t xs = Sc;
+            scan_pair_max(xv, xs, lane);
+            int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1);
+            uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1);
+            if (lane == 0) { ev = carry_v; es = carry_s; }
+            else if (carry_v > ev) { ev = carry_v; es = carry_s; }
+            const int32_t last_v = __shfl_sync(0xffffffffu, xv, 31);
+            const uint32_t last_s = __shfl_sync(0xffffffffu, xs, 31);
+            if (last_v >= carry_v) { carry_v = last_v; carry_s = last_s; }
+            const int32_t F = (ev > SW_XNEG) ? ev + ge * (int32_t)(b - 1) : SW_NEG;
+            int32_t H;
+            uint32_t SH;
+            if (H0 >= F) { H = H0; SH = Sc; } else { H = F; SH = es; }
+            cH[c] = H; cE[c] = E; cSH[c] = SH; cSE[c] = SE;
+            if (act && H > best) { best = H; bi = i; bj = j; bs = SH; }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) { pH[c] = cH[c]; pE[c] = cE[c]; pSH[c] = cSH[c]; pSE[c] = cSE[c]; }
+    }
+}
+
 __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ sel, uint32_t n,
                                                    const uint64_t *__restrict__ strip_off, SwCell *__restrict__ strips,
                                                    const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
@@ -585,6 +705,13 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
         int64_t bi = INT64_MAX, bj = INT64_MAX;
         uint32_t bs = 0;
         const int32_t goe = go + ge;
+        if (B <= 32) {
+            sw_rows_regs<1>(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best,
+                            bi, bj, bs);
+        } else if (B <= 64) {
+            sw_rows_regs<2>(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best,
+                            bi, bj, bs);
+        } else
         for (int64_t i = I0; i < I1; ++i) {
             const int64_t blo = max((int64_t)0, J0 - i - dlo), bhi = min(B - 1, J1 - 1 - i - dlo);
             if (blo > bhi) continue;
