@@ -45,6 +45,11 @@ BYTES_PER_UNIT = {
     "record_sort_downsweep": 24.0,
     "record_sort_upsweep": 8.0,
     "k_query_codes": 17.0,
+    # bucketing (units = raw hits): count reads each occurrence twice (filter + count; the second
+    # read hits L2), scatter reads it three times; both write little (kept hits only)
+    "k_bucket_count": 4.0,
+    "k_bucket_scatter": 4.0,
+    "k_bucket_group": 8.0,   # units = kept hits: one 8-byte key read
 }
 ALU_KERNELS = {"k_banded_sw"}  # units = DP cells
 

@@ -198,11 +198,75 @@ __device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D,
            dev_upper_index(seq_start, n_seqs + 1, gk - QBIAS + qb);
 }
 
-// Tile-level bucketing: a CTA takes 256 consecutive query offsets (8 warps x 32).
-// Bucket counts and output ranges are aggregated in shared memory over the
-// tile's bucket span, so global atomics are one per (tile, bucket), not per hit.
-// PASS 0 counts hits per bucket; PASS 1 reserves ranges and writes the entries.
-constexpr int BT_SPAN = 2048;  // buckets a tile can aggregate in shared memory
+// Tile-level bucketing: a CTA takes BT_POS consecutive query offsets (the core).
+// With the repeat filter on (min_hsp_len > k and D <= BT_MAX_D), every hit of the
+// core and of the D offsets on either side (the halo) is first hashed by its
+// (query, diagonal) into two shared-memory bitmaps, "seen" and "seen twice".  A
+// core hit can only be part of a chain of two or more hits if another hit lies
+// on its diagonal within D query offsets, and all those offsets are inside core
+// + halo; so a core hit whose hash was not seen twice cannot reach min_hsp_len
+// and is dropped here (a hash collision only keeps an extra hit).  The kept hits
+// are counted (PASS 0) or written (PASS 1) per bucket, aggregated per tile in
+// shared memory so that global atomics are one per (tile, bucket).
+constexpr int BT_SPAN = 2048;      // buckets a tile can aggregate in shared memory
+constexpr int BT_POS = 256;        // core query offsets per tile
+constexpr int BT_MAX_D = 256;      // largest hit distance the tile filter supports
+constexpr int BT_FBITS = 18;       // log2 of the bits of each filter bitmap
+
+struct TileHit {
+    uint32_t ql, qpos;
+    uint64_t gk;
+};
+
+// Calls f(ql, qpos, gk) for every hit of query offsets [p0, p1): warps take 32-offset
+// blocks, lanes share each offset's occurrence list, four list entries per lane in flight.
+template <class F>
+__device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const uint32_t *__restrict__ codes,
+                                              const uint32_t *__restrict__ qinfo,
+                                              const uint64_t *__restrict__ hoff, const uint64_t *__restrict__ off,
+                                              const uint32_t *__restrict__ post, uint32_t qa, F &&f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t x0 = p0 + (uint64_t)warp * 32; x0 < p1; x0 += (uint64_t)(blockDim.x >> 5) * 32) {
+        const uint64_t x = x0 + lane;
+        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
+        uint64_t my_src = 0;
+        if (x < p1) {
+            my_cnt = (uint32_t)(hoff[x + 1] - hoff[x]);
+            if (my_cnt) {
+                const uint32_t qinf = qinfo[x];
+                my_src = off[codes[x]];
+                my_qpos = qinf & 0xFFFFu;
+                my_ql = (qinf >> 16) - qa;
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
+            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
+            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
+            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
+            for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
+                uint32_t g[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t j = j0 + u * 32 + lane;
+                    g[u] = j < cnt ? post[sp + j] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (j0 + u * 32 + lane >= cnt) break;
+                    f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk) {
+    return (uint32_t)(((gk ^ ((uint64_t)ql * 0x9E3779B97F4A7C15ull)) * 0xD6E8FEB86659FD93ull) >> (64 - BT_FBITS));
+}
 
 template <int PASS>
 __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict__ codes,
@@ -213,84 +277,49 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                                                       const uint32_t *__restrict__ bbase,
                                                       const uint32_t *__restrict__ bshift,
                                                       uint32_t *__restrict__ bcnt, const uint64_t *__restrict__ boff,
-                                                      uint64_t *__restrict__ bkeys) {
-    __shared__ uint32_t hist[BT_SPAN];
-    __shared__ unsigned long long base[PASS ? BT_SPAN : 1];
+                                                      uint64_t *__restrict__ bkeys, int filter, uint32_t D) {
+    extern __shared__ __align__(16) unsigned char bt_smem[];
+    uint32_t *seen = reinterpret_cast<uint32_t *>(bt_smem);
+    uint32_t *seen2 = seen + (1u << BT_FBITS) / 32;
+    uint32_t *hist = seen2 + (1u << BT_FBITS) / 32;
+    unsigned long long *base = reinterpret_cast<unsigned long long *>(hist + BT_SPAN);
     __shared__ uint32_t bmin_s;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < BT_SPAN; i += 256) hist[i] = 0;
-    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * 256; t0 < xb; t0 += (uint64_t)gridDim.x * 256) {
+    for (int i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
+    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * BT_POS; t0 < xb; t0 += (uint64_t)gridDim.x * BT_POS) {
+        const uint64_t t1 = min(xb, t0 + BT_POS);
         if (threadIdx.x == 0) bmin_s = bbase[(qinfo[t0] >> 16) - qa];
+        if (filter) {
+            for (uint32_t i = threadIdx.x; i < (2u << BT_FBITS) / 32; i += blockDim.x) seen[i] = 0u;
+        }
         __syncthreads();
         const uint32_t bmin = bmin_s;
-        const uint64_t x = t0 + warp * 32 + lane;
-        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
-        uint64_t my_src = 0;
-        if (x < xb) {
-            my_cnt = (uint32_t)(hoff[x + 1] - hoff[x]);
-            if (my_cnt) {
-                const uint32_t qinf = qinfo[x];
-                my_src = off[codes[x]];
-                my_qpos = qinf & 0xFFFFu;
-                my_ql = (qinf >> 16) - qa;
-            }
+        if (filter) {
+            auto insert = [&](uint32_t ql, uint32_t qpos, uint64_t gk) {
+                const uint32_t h = tile_hash(ql, gk);
+                const uint32_t bit = 1u << (h & 31);
+                const uint32_t old = atomicOr(&seen[h >> 5], bit);
+                if (old & bit) atomicOr(&seen2[h >> 5], bit);
+            };
+            for_tile_hits(t0 > xa + D ? t0 - D : xa, t0, codes, qinfo, hoff, off, post, qa, insert);
+            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, insert);
+            for_tile_hits(t1, min(xb, t1 + D), codes, qinfo, hoff, off, post, qa, insert);
+            __syncthreads();
         }
-        const uint32_t todo0 = __ballot_sync(0xffffffffu, my_cnt != 0);
-        // pass over the tile's hits: local counts (and, in PASS 1 after the reservation, placement)
-        for (int phase = 0; phase < (PASS ? 2 : 1); ++phase) {
-            if (phase == 1) {
-                __syncthreads();
-                // reserve each bucket's range for this tile; hist becomes the local cursor
-                for (uint32_t i = threadIdx.x; i < BT_SPAN; i += 256) {
-                    const uint32_t c = hist[i];
-                    if (c) {
-                        const uint32_t b = bmin + i;
-                        base[i] = boff[b] + atomicAdd(&bcnt[b], c);
-                        hist[i] = 0;
-                    }
-                }
-                __syncthreads();
-            }
-            uint32_t todo = todo0;
-            while (todo) {
-                const int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
-                const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
-                const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
-                const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
-                const uint32_t bb = bbase[ql], sh = bshift[ql];
-                for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
-                    // four list entries per lane in flight before any atomic
-                    uint32_t g[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t j = j0 + u * 32 + lane;
-                        g[u] = j < cnt ? post[sp + j] : 0u;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t j = j0 + u * 32 + lane;
-                        if (j >= cnt) break;
-                        const uint64_t gk = (uint64_t)g[u] + QBIAS - qpos;
-                        const uint32_t b = bb + (uint32_t)(gk >> sh);
-                        const uint32_t li = b - bmin;
-                        if (phase == 0) {
-                            if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
-                            else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
-                        } else {
-                            uint64_t dst;
-                            if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
-                            else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
-                            bkeys[dst] = (gk << 16) | qpos;
-                        }
-                    }
-                }
-            }
-        }
+        auto kept = [&](uint32_t ql, uint64_t gk) {
+            if (!filter) return true;
+            const uint32_t h = tile_hash(ql, gk);
+            return ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
+        };
+        for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, [&](uint32_t ql, uint32_t qpos, uint64_t gk) {
+            if (!kept(ql, gk)) return;
+            const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
+            const uint32_t li = b - bmin;
+            if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
+            else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
+        });
         __syncthreads();
         if (PASS == 0) {
-            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += 256) {
+            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
                 const uint32_t c = hist[i];
                 if (c) {
                     atomicAdd(&bcnt[bmin + i], c);
@@ -298,7 +327,27 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                 }
             }
         } else {
-            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += 256) hist[i] = 0;
+            // reserve each bucket's range for this tile; hist becomes the local cursor
+            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
+                const uint32_t c = hist[i];
+                if (c) {
+                    const uint32_t b = bmin + i;
+                    base[i] = boff[b] + atomicAdd(&bcnt[b], c);
+                    hist[i] = 0;
+                }
+            }
+            __syncthreads();
+            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, [&](uint32_t ql, uint32_t qpos, uint64_t gk) {
+                if (!kept(ql, gk)) return;
+                const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
+                const uint32_t li = b - bmin;
+                uint64_t dst;
+                if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
+                else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
+                bkeys[dst] = (gk << 16) | qpos;
+            });
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
         }
         __syncthreads();
     }
@@ -1045,6 +1094,12 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 if (const char *e = getenv("GN_BUCKET_CAP")) cap = (uint32_t)std::max(64ul, std::min(4096ul, strtoul(e, nullptr, 10)));
                 while (cap & (cap - 1)) cap &= cap - 1;
                 target = cap / 2;
+                // the tile filter keeps roughly a tenth of the hits: size buckets for the kept ones
+                const int singles0 = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
+                const char *fenv = getenv("GN_TILE_FILTER");
+                const int filter = (!singles0 && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
+                                    !(fenv && strcmp(fenv, "0") == 0)) ? 1 : 0;
+                if (filter) target *= 8;
                 std::vector<uint32_t> bbase(nqc + 1), bshift(nqc);
                 const int min_lg = std::max(0, gbits - 31);
                 uint64_t nb64 = 0;
@@ -1068,22 +1123,32 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const int singles = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
                 uint32_t *bcnt = carena.alloc_n<uint32_t>(NB);
                 uint64_t *boff = carena.alloc_n<uint64_t>((uint64_t)NB + 1);
-                uint64_t *bkeys = carena.alloc_n<uint64_t>(Hc);
                 uint16_t *bq = carena.alloc_n<uint16_t>(NB);
                 GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
-                const uint64_t tiles = (xb - xa + 255) / 256;
+                const uint64_t tiles = (xb - xa + BT_POS - 1) / BT_POS;
                 const unsigned tgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * 8));
+                const size_t bt_smem0 = (2u << BT_FBITS) / 8 + BT_SPAN * 4;
+                const size_t bt_smem1 = bt_smem0 + BT_SPAN * 8;
+                GN_CUDA(cudaFuncSetAttribute(k_bucket_tiles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem0));
+                GN_CUDA(cudaFuncSetAttribute(k_bucket_tiles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem1));
                 GN_LAUNCH("k_bucket_count", Hc, s,
-                          k_bucket_tiles<0><<<tgrid, 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d,
-                                                                  qa, NB, d_bbase, d_bshift, bcnt, nullptr, nullptr));
+                          k_bucket_tiles<0><<<tgrid, 256, bt_smem0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
+                                                                         ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
+                                                                         nullptr, nullptr, filter,
+                                                                         p.max_hit_distance));
                 {
                     void *scr = carena.alloc(scan_scratch_bytes(NB));
                     exclusive_scan_u32(bcnt, boff, NB, scr, s);
                 }
                 GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
+                uint64_t n_kept = 0;
+                GN_CUDA(cudaMemcpyAsync(&n_kept, boff + NB, 8, cudaMemcpyDeviceToHost, s));
+                GN_CUDA(cudaStreamSynchronize(s));
+                uint64_t *bkeys = carena.alloc_n<uint64_t>(n_kept);
                 GN_LAUNCH("k_bucket_scatter", Hc, s,
-                          k_bucket_tiles<1><<<tgrid, 256, 0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d,
-                                                                  qa, NB, d_bbase, d_bshift, bcnt, boff, bkeys));
+                          k_bucket_tiles<1><<<tgrid, 256, bt_smem1, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
+                                                                         ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
+                                                                         boff, bkeys, filter, p.max_hit_distance));
                 GN_LAUNCH("k_bucket_query", NB, s, k_bucket_query<<<nqc, 256, 0, s>>>(d_bbase, nqc, NB, bq));
                 timer.mark("bucket_scatter");
                 unsigned long long *ovf_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
@@ -1097,7 +1162,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 GN_CUDA(cudaMemcpyAsync(&ovf_cap, ovf_count, 8, cudaMemcpyDeviceToHost, s));
                 GN_CUDA(cudaStreamSynchronize(s));
                 // without single-hit HSPs, spills come from candidate overflow, which a retry sizes exactly
-                uint64_t ovf_room = singles ? ovf_cap : std::max<uint64_t>(1u << 20, Hc / 64);
+                uint64_t ovf_room = singles ? ovf_cap : std::max<uint64_t>(1u << 20, n_kept / 16);
                 uint64_t *ovf = carena.alloc_n<uint64_t>(ovf_room);
                 uint64_t *ovf_alt = nullptr;
                 const size_t smem = (size_t)BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8);
@@ -1111,7 +1176,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     const uint32_t hsp_before = n_hsp;
                     emit([&](DevHsp *o, uint32_t room) {
                         GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
-                        GN_LAUNCH("k_bucket_group", Hc, s,
+                        GN_LAUNCH("k_bucket_group", n_kept, s,
                                   k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
                                       bkeys, boff, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len, singles,
                                       ix->seq_start_d, ix->n_seqs, o, counter, room, ovf,
