@@ -218,8 +218,10 @@ struct TileHit {
     uint64_t gk;
 };
 
-// Calls f(ql, qpos, gk) for every hit of query offsets [p0, p1): warps take 32-offset
-// blocks, lanes share each offset's occurrence list, four list entries per lane in flight.
+// Calls f(ql, qpos, gk, hit index, valid) for every hit of query offsets [p0, p1): warps
+// take 32-offset blocks, lanes share each offset's occurrence list, four list entries per
+// lane in flight.  All lanes of a warp call f together (valid is false past a list's end),
+// so f may use warp votes; consecutive lanes hold consecutive hit indices.
 template <class F>
 __device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const uint32_t *__restrict__ codes,
                                               const uint32_t *__restrict__ qinfo,
@@ -229,9 +231,10 @@ __device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const ui
     for (uint64_t x0 = p0 + (uint64_t)warp * 32; x0 < p1; x0 += (uint64_t)(blockDim.x >> 5) * 32) {
         const uint64_t x = x0 + lane;
         uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
-        uint64_t my_src = 0;
+        uint64_t my_src = 0, my_h = 0;
         if (x < p1) {
-            my_cnt = (uint32_t)(hoff[x + 1] - hoff[x]);
+            my_h = hoff[x];
+            my_cnt = (uint32_t)(hoff[x + 1] - my_h);
             if (my_cnt) {
                 const uint32_t qinf = qinfo[x];
                 my_src = off[codes[x]];
@@ -247,6 +250,7 @@ __device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const ui
             const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
             const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
             const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
+            const uint64_t h0 = __shfl_sync(0xffffffffu, my_h, src);
             for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
                 uint32_t g[4];
 #pragma unroll
@@ -256,8 +260,8 @@ __device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const ui
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (j0 + u * 32 + lane >= cnt) break;
-                    f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos);
+                    const uint32_t j = j0 + u * 32 + lane;
+                    f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos, h0 + j, j < cnt);
                 }
             }
         }
@@ -277,24 +281,27 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                                                       const uint32_t *__restrict__ bbase,
                                                       const uint32_t *__restrict__ bshift,
                                                       uint32_t *__restrict__ bcnt, const uint64_t *__restrict__ boff,
-                                                      uint64_t *__restrict__ bkeys, int filter, uint32_t D) {
+                                                      uint64_t *__restrict__ bkeys, int filter, uint32_t D,
+                                                      uint32_t *__restrict__ keep_bits, uint64_t ha) {
     extern __shared__ __align__(16) unsigned char bt_smem[];
-    uint32_t *seen = reinterpret_cast<uint32_t *>(bt_smem);
-    uint32_t *seen2 = seen + (1u << BT_FBITS) / 32;
-    uint32_t *hist = seen2 + (1u << BT_FBITS) / 32;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(bt_smem);
     unsigned long long *base = reinterpret_cast<unsigned long long *>(hist + BT_SPAN);
+    uint32_t *seen = reinterpret_cast<uint32_t *>(base + (PASS ? BT_SPAN : 0));
+    uint32_t *seen2 = seen + (1u << BT_FBITS) / 32;
     __shared__ uint32_t bmin_s;
+    const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
     for (uint64_t t0 = xa + (uint64_t)blockIdx.x * BT_POS; t0 < xb; t0 += (uint64_t)gridDim.x * BT_POS) {
         const uint64_t t1 = min(xb, t0 + BT_POS);
         if (threadIdx.x == 0) bmin_s = bbase[(qinfo[t0] >> 16) - qa];
-        if (filter) {
+        if (PASS == 0 && filter) {
             for (uint32_t i = threadIdx.x; i < (2u << BT_FBITS) / 32; i += blockDim.x) seen[i] = 0u;
         }
         __syncthreads();
         const uint32_t bmin = bmin_s;
-        if (filter) {
-            auto insert = [&](uint32_t ql, uint32_t qpos, uint64_t gk) {
+        if (PASS == 0 && filter) {
+            auto insert = [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid) {
+                if (!valid) return;
                 const uint32_t h = tile_hash(ql, gk);
                 const uint32_t bit = 1u << (h & 31);
                 const uint32_t old = atomicOr(&seen[h >> 5], bit);
@@ -305,18 +312,35 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
             for_tile_hits(t1, min(xb, t1 + D), codes, qinfo, hoff, off, post, qa, insert);
             __syncthreads();
         }
-        auto kept = [&](uint32_t ql, uint64_t gk) {
-            if (!filter) return true;
-            const uint32_t h = tile_hash(ql, gk);
-            return ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
-        };
-        for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, [&](uint32_t ql, uint32_t qpos, uint64_t gk) {
-            if (!kept(ql, gk)) return;
-            const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
-            const uint32_t li = b - bmin;
-            if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
-            else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
-        });
+        // PASS 0: keep decision (recorded one bit per hit) and local counts; PASS 1: counts from the bits
+        for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa,
+                      [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid) {
+                          const uint64_t hl = hidx - ha;
+                          bool keep = valid;
+                          if (PASS == 0) {
+                              if (filter && valid) {
+                                  const uint32_t h = tile_hash(ql, gk);
+                                  keep = ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
+                              }
+                              if (filter) {
+                                  // lanes hold consecutive hit indices: at most two words per warp
+                                  const uint32_t votes = __ballot_sync(0xffffffffu, keep);
+                                  const uint64_t lo = __shfl_sync(0xffffffffu, hl, 0);
+                                  if (lane == 0 && votes) {
+                                      const uint32_t sh = (uint32_t)(lo & 31);
+                                      atomicOr(&keep_bits[lo >> 5], votes << sh);
+                                      if (sh && (votes >> (32 - sh))) atomicOr(&keep_bits[(lo >> 5) + 1], votes >> (32 - sh));
+                                  }
+                              }
+                          } else if (filter && valid) {
+                              keep = ((keep_bits[hl >> 5] >> (hl & 31)) & 1u) != 0u;
+                          }
+                          if (!keep) return;
+                          const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
+                          const uint32_t li = b - bmin;
+                          if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
+                          else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
+                      });
         __syncthreads();
         if (PASS == 0) {
             for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
@@ -337,15 +361,18 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                 }
             }
             __syncthreads();
-            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, [&](uint32_t ql, uint32_t qpos, uint64_t gk) {
-                if (!kept(ql, gk)) return;
-                const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
-                const uint32_t li = b - bmin;
-                uint64_t dst;
-                if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
-                else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
-                bkeys[dst] = (gk << 16) | qpos;
-            });
+            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa,
+                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid) {
+                              if (!valid) return;
+                              const uint64_t hl = hidx - ha;
+                              if (filter && !((keep_bits[hl >> 5] >> (hl & 31)) & 1u)) return;
+                              const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
+                              const uint32_t li = b - bmin;
+                              uint64_t dst;
+                              if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
+                              else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
+                              bkeys[dst] = (gk << 16) | qpos;
+                          });
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
         }
@@ -1126,16 +1153,18 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint16_t *bq = carena.alloc_n<uint16_t>(NB);
                 GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
                 const uint64_t tiles = (xb - xa + BT_POS - 1) / BT_POS;
-                const unsigned tgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * 8));
-                const size_t bt_smem0 = (2u << BT_FBITS) / 8 + BT_SPAN * 4;
-                const size_t bt_smem1 = bt_smem0 + BT_SPAN * 8;
+                const unsigned tgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * 16));
+                const size_t bt_smem0 = BT_SPAN * 4 + (filter ? (2u << BT_FBITS) / 8 : 0);
+                const size_t bt_smem1 = BT_SPAN * 4 + BT_SPAN * 8;
+                uint32_t *keep_bits = carena.alloc_n<uint32_t>(filter ? (Hc + 31) / 32 + 2 : 1);
+                if (filter) GN_CUDA(cudaMemsetAsync(keep_bits, 0, 4 * ((Hc + 31) / 32 + 2), s));
                 GN_CUDA(cudaFuncSetAttribute(k_bucket_tiles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem0));
                 GN_CUDA(cudaFuncSetAttribute(k_bucket_tiles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem1));
                 GN_LAUNCH("k_bucket_count", Hc, s,
                           k_bucket_tiles<0><<<tgrid, 256, bt_smem0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
                                                                          ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
                                                                          nullptr, nullptr, filter,
-                                                                         p.max_hit_distance));
+                                                                         p.max_hit_distance, keep_bits, ha));
                 {
                     void *scr = carena.alloc(scan_scratch_bytes(NB));
                     exclusive_scan_u32(bcnt, boff, NB, scr, s);
@@ -1148,7 +1177,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 GN_LAUNCH("k_bucket_scatter", Hc, s,
                           k_bucket_tiles<1><<<tgrid, 256, bt_smem1, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
                                                                          ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
-                                                                         boff, bkeys, filter, p.max_hit_distance));
+                                                                         boff, bkeys, filter, p.max_hit_distance,
+                                                                         keep_bits, ha));
                 GN_LAUNCH("k_bucket_query", NB, s, k_bucket_query<<<nqc, 256, 0, s>>>(d_bbase, nqc, NB, bq));
                 timer.mark("bucket_scatter");
                 unsigned long long *ovf_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
