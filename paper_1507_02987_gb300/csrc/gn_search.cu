@@ -198,7 +198,7 @@ __device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D,
            dev_upper_index(seq_start, n_seqs + 1, gk - QBIAS + qb);
 }
 
-// Tile-level bucketing: a CTA takes BT_POS consecutive query offsets (the core).
+// Tile-level bucketing: a CTA takes tpos consecutive query offsets (the core).
 // With the repeat filter on (min_hsp_len > k and D <= BT_MAX_D), every hit of the
 // core and of the D offsets on either side (the halo) is first hashed by its
 // (query, diagonal) into two shared-memory bitmaps, "seen" and "seen twice".  A
@@ -209,9 +209,7 @@ __device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D,
 // are counted (PASS 0) or written (PASS 1) per bucket, aggregated per tile in
 // shared memory so that global atomics are one per (tile, bucket).
 constexpr int BT_SPAN = 2048;      // buckets a tile can aggregate in shared memory
-constexpr int BT_POS = 256;        // core query offsets per tile
 constexpr int BT_MAX_D = 256;      // largest hit distance the tile filter supports
-constexpr int BT_FBITS = 18;       // log2 of the bits of each filter bitmap
 
 struct TileHit {
     uint32_t ql, qpos;
@@ -226,7 +224,9 @@ template <class F>
 __device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const uint32_t *__restrict__ codes,
                                               const uint32_t *__restrict__ qinfo,
                                               const uint64_t *__restrict__ hoff, const uint64_t *__restrict__ off,
-                                              const uint32_t *__restrict__ post, uint32_t qa, F &&f) {
+                                              const uint32_t *__restrict__ post, uint32_t qa,
+                                              const uint32_t *__restrict__ bbase,
+                                              const uint32_t *__restrict__ bshift, F &&f) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint64_t x0 = p0 + (uint64_t)warp * 32; x0 < p1; x0 += (uint64_t)(blockDim.x >> 5) * 32) {
         const uint64_t x = x0 + lane;
@@ -251,6 +251,7 @@ __device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const ui
             const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
             const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
             const uint64_t h0 = __shfl_sync(0xffffffffu, my_h, src);
+            const uint32_t bb = bbase[ql], bs = bshift[ql];
             for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
                 uint32_t g[4];
 #pragma unroll
@@ -261,15 +262,19 @@ __device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const ui
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const uint32_t j = j0 + u * 32 + lane;
-                    f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos, h0 + j, j < cnt);
+                    f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos, h0 + j, j < cnt, bb, bs);
                 }
             }
         }
     }
 }
 
-__device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk) {
-    return (uint32_t)(((gk ^ ((uint64_t)ql * 0x9E3779B97F4A7C15ull)) * 0xD6E8FEB86659FD93ull) >> (64 - BT_FBITS));
+__device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk, int fbits) {
+    uint32_t h = (uint32_t)gk * 0x9E3779B1u + ql * 0x85EBCA77u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 13;
+    return h >> (32 - fbits);
 }
 
 template <int PASS>
@@ -282,44 +287,47 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                                                       const uint32_t *__restrict__ bshift,
                                                       uint32_t *__restrict__ bcnt, const uint64_t *__restrict__ boff,
                                                       uint64_t *__restrict__ bkeys, int filter, uint32_t D,
-                                                      uint32_t *__restrict__ keep_bits, uint64_t ha) {
+                                                      uint32_t *__restrict__ keep_bits, uint64_t ha, int tpos,
+                                                      int fbits) {
     extern __shared__ __align__(16) unsigned char bt_smem[];
     uint32_t *hist = reinterpret_cast<uint32_t *>(bt_smem);
     unsigned long long *base = reinterpret_cast<unsigned long long *>(hist + BT_SPAN);
     uint32_t *seen = reinterpret_cast<uint32_t *>(base + (PASS ? BT_SPAN : 0));
-    uint32_t *seen2 = seen + (1u << BT_FBITS) / 32;
+    uint32_t *seen2 = seen + (1u << fbits) / 32;
     __shared__ uint32_t bmin_s;
     const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
-    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * BT_POS; t0 < xb; t0 += (uint64_t)gridDim.x * BT_POS) {
-        const uint64_t t1 = min(xb, t0 + BT_POS);
+    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tpos; t0 < xb; t0 += (uint64_t)gridDim.x * tpos) {
+        const uint64_t t1 = min(xb, t0 + (uint64_t)tpos);
         if (threadIdx.x == 0) bmin_s = bbase[(qinfo[t0] >> 16) - qa];
         if (PASS == 0 && filter) {
-            for (uint32_t i = threadIdx.x; i < (2u << BT_FBITS) / 32; i += blockDim.x) seen[i] = 0u;
+            for (uint32_t i = threadIdx.x; i < (2u << fbits) / 32; i += blockDim.x) seen[i] = 0u;
         }
         __syncthreads();
         const uint32_t bmin = bmin_s;
         if (PASS == 0 && filter) {
-            auto insert = [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid) {
+            auto insert = [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid, uint32_t bb,
+                              uint32_t bs) {
                 if (!valid) return;
-                const uint32_t h = tile_hash(ql, gk);
+                const uint32_t h = tile_hash(ql, gk, fbits);
                 const uint32_t bit = 1u << (h & 31);
                 const uint32_t old = atomicOr(&seen[h >> 5], bit);
                 if (old & bit) atomicOr(&seen2[h >> 5], bit);
             };
-            for_tile_hits(t0 > xa + D ? t0 - D : xa, t0, codes, qinfo, hoff, off, post, qa, insert);
-            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, insert);
-            for_tile_hits(t1, min(xb, t1 + D), codes, qinfo, hoff, off, post, qa, insert);
+            for_tile_hits(t0 > xa + D ? t0 - D : xa, t0, codes, qinfo, hoff, off, post, qa, bbase, bshift, insert);
+            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, bbase, bshift, insert);
+            for_tile_hits(t1, min(xb, t1 + D), codes, qinfo, hoff, off, post, qa, bbase, bshift, insert);
             __syncthreads();
         }
         // PASS 0: keep decision (recorded one bit per hit) and local counts; PASS 1: counts from the bits
-        for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa,
-                      [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid) {
+        for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                      [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid, uint32_t bb,
+                          uint32_t bs) {
                           const uint64_t hl = hidx - ha;
                           bool keep = valid;
                           if (PASS == 0) {
                               if (filter && valid) {
-                                  const uint32_t h = tile_hash(ql, gk);
+                                  const uint32_t h = tile_hash(ql, gk, fbits);
                                   keep = ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
                               }
                               if (filter) {
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                               keep = ((keep_bits[hl >> 5] >> (hl & 31)) & 1u) != 0u;
                           }
                           if (!keep) return;
-                          const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
+                          const uint32_t b = bb + (uint32_t)(gk >> bs);
                           const uint32_t li = b - bmin;
                           if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
                           else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
@@ -361,12 +369,13 @@ __global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict
                 }
             }
             __syncthreads();
-            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa,
-                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid) {
+            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid, uint32_t bb,
+                              uint32_t bs) {
                               if (!valid) return;
                               const uint64_t hl = hidx - ha;
                               if (filter && !((keep_bits[hl >> 5] >> (hl & 31)) & 1u)) return;
-                              const uint32_t b = bbase[ql] + (uint32_t)(gk >> bshift[ql]);
+                              const uint32_t b = bb + (uint32_t)(gk >> bs);
                               const uint32_t li = b - bmin;
                               uint64_t dst;
                               if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
@@ -1126,7 +1135,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const char *fenv = getenv("GN_TILE_FILTER");
                 const int filter = (!singles0 && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
                                     !(fenv && strcmp(fenv, "0") == 0)) ? 1 : 0;
-                if (filter) target *= 8;
+                int tpos = 256, fbits = 18;
+                if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
+                if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
+                if (filter) target *= 2;
                 std::vector<uint32_t> bbase(nqc + 1), bshift(nqc);
                 const int min_lg = std::max(0, gbits - 31);
                 uint64_t nb64 = 0;
@@ -1152,9 +1164,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint64_t *boff = carena.alloc_n<uint64_t>((uint64_t)NB + 1);
                 uint16_t *bq = carena.alloc_n<uint16_t>(NB);
                 GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
-                const uint64_t tiles = (xb - xa + BT_POS - 1) / BT_POS;
+                const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
                 const unsigned tgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * 16));
-                const size_t bt_smem0 = BT_SPAN * 4 + (filter ? (2u << BT_FBITS) / 8 : 0);
+                const size_t bt_smem0 = BT_SPAN * 4 + (filter ? (2u << fbits) / 8 : 0);
                 const size_t bt_smem1 = BT_SPAN * 4 + BT_SPAN * 8;
                 uint32_t *keep_bits = carena.alloc_n<uint32_t>(filter ? (Hc + 31) / 32 + 2 : 1);
                 if (filter) GN_CUDA(cudaMemsetAsync(keep_bits, 0, 4 * ((Hc + 31) / 32 + 2), s));
@@ -1164,7 +1176,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                           k_bucket_tiles<0><<<tgrid, 256, bt_smem0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
                                                                          ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
                                                                          nullptr, nullptr, filter,
-                                                                         p.max_hit_distance, keep_bits, ha));
+                                                                         p.max_hit_distance, keep_bits, ha, tpos,
+                                                                         fbits));
                 {
                     void *scr = carena.alloc(scan_scratch_bytes(NB));
                     exclusive_scan_u32(bcnt, boff, NB, scr, s);
@@ -1178,7 +1191,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                           k_bucket_tiles<1><<<tgrid, 256, bt_smem1, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
                                                                          ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
                                                                          boff, bkeys, filter, p.max_hit_distance,
-                                                                         keep_bits, ha));
+                                                                         keep_bits, ha, tpos, fbits));
                 GN_LAUNCH("k_bucket_query", NB, s, k_bucket_query<<<nqc, 256, 0, s>>>(d_bbase, nqc, NB, bq));
                 timer.mark("bucket_scatter");
                 unsigned long long *ovf_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
@@ -1192,7 +1205,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 GN_CUDA(cudaMemcpyAsync(&ovf_cap, ovf_count, 8, cudaMemcpyDeviceToHost, s));
                 GN_CUDA(cudaStreamSynchronize(s));
                 // without single-hit HSPs, spills come from candidate overflow, which a retry sizes exactly
-                uint64_t ovf_room = singles ? ovf_cap : std::max<uint64_t>(1u << 20, n_kept / 16);
+                uint64_t ovf_room = singles ? ovf_cap : std::max<uint64_t>(1u << 20, n_kept / 4);
                 uint64_t *ovf = carena.alloc_n<uint64_t>(ovf_room);
                 uint64_t *ovf_alt = nullptr;
                 const size_t smem = (size_t)BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8);
