@@ -1135,7 +1135,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const char *fenv = getenv("GN_TILE_FILTER");
                 const int filter = (!singles0 && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
                                     !(fenv && strcmp(fenv, "0") == 0)) ? 1 : 0;
-                int tpos = 256, fbits = 18;
+                int tpos = 256, fbits = 17;
                 if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
                 if (filter) target *= 2;
