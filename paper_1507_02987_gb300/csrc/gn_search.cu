@@ -564,35 +564,77 @@ struct BaseCursor {
     }
 };
 
+// One direction of the X-drop walk, 32 steps per round for a whole warp.  Step e
+// (1-based) compares query base qg(e) with bank base dg(e).  The sequential rule
+// (score += s; if score > best: best = score, ext = e; else if best - score > X:
+// stop) stops at the first e where max(best so far, score_e) - score_e > X, and
+// ext is the first step that reached the final best.  Returns ext.
+template <int DIR>
+__device__ __forceinline__ uint32_t xdrop_walk_warp(const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
+                                                    const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                                                    uint64_t qg0, uint64_t dg0, uint32_t emax, int32_t match,
+                                                    int32_t mismatch, int32_t X, int lane) {
+    int32_t carry_score = 0, carry_best = 0;
+    uint32_t carry_ext = 0;
+    for (uint32_t e0 = 1; e0 <= emax; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const bool in = e <= emax;
+        int32_t sc = 0;
+        if (in) {
+            const uint64_t qg = DIR > 0 ? qg0 + (e - 1) : qg0 - e;
+            const uint64_t dg = DIR > 0 ? dg0 + (e - 1) : dg0 - e;
+            sc = dev_pair(dev_base(qpk, qnb, qg), dev_base(bpk, bnb, dg), match, mismatch);
+        }
+        // running score (inclusive prefix sum) and running best (inclusive prefix max)
+        int32_t S = sc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, S, o);
+            if (lane >= o) S += t;
+        }
+        S += carry_score;
+        int32_t M = in ? S : INT32_MIN;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, M, o);
+            if (lane >= o) M = max(M, t);
+        }
+        M = max(M, carry_best);
+        const uint32_t stop = __ballot_sync(0xffffffffu, in && M - S > X);
+        const uint32_t last = stop ? (uint32_t)(__ffs(stop) - 1) : 31u;  // last lane that counts this round
+        const int32_t Mlast = __shfl_sync(0xffffffffu, M, last);
+        if (Mlast > carry_best) {
+            // first step of this round that reached the new best
+            const uint32_t hit = __ballot_sync(0xffffffffu, in && (uint32_t)lane <= last && S == Mlast);
+            carry_ext = e0 + (uint32_t)(__ffs(hit) - 1);
+            carry_best = Mlast;
+        }
+        if (stop) break;
+        carry_score = __shfl_sync(0xffffffffu, S, 31);
+    }
+    return carry_ext;
+}
+
+// One warp per HSP: left end, then right end.
 __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__restrict__ qpk,
                         const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
                         const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
                         const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch, int32_t X) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    DevHsp r = h[i];
-    const uint64_t qb = qstart[r.qi], sb = seq_start[r.seq];
-    const uint32_t m = (uint32_t)(qstart[r.qi + 1] - qb), L = (uint32_t)(seq_start[r.seq + 1] - sb);
-    BaseCursor cq(qpk, qnb), cd(bpk, bnb);
-    int32_t score = 0, best = 0;
-    uint32_t ext = 0;
-    for (uint32_t e = 1; e <= r.qs && e <= r.ds; ++e) {
-        score += dev_pair(cq.at(qb + r.qs - e), cd.at(sb + r.ds - e), match, mismatch);
-        if (score > best) { best = score; ext = e; }
-        else if (best - score > X) break;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+        DevHsp r = h[i];
+        const uint64_t qb = qstart[r.qi], sb = seq_start[r.seq];
+        const uint32_t m = (uint32_t)(qstart[r.qi + 1] - qb), L = (uint32_t)(seq_start[r.seq + 1] - sb);
+        const uint32_t el = xdrop_walk_warp<-1>(qpk, qnb, bpk, bnb, qb + r.qs, sb + r.ds, min(r.qs, r.ds), match,
+                                               mismatch, X, lane);
+        const uint32_t er = xdrop_walk_warp<1>(qpk, qnb, bpk, bnb, qb + r.qe, sb + r.de, min(m - r.qe, L - r.de),
+                                              match, mismatch, X, lane);
+        r.qs -= el; r.ds -= el;
+        r.qe += er; r.de += er;
+        r.len = min(r.qe - r.qs, r.de - r.ds);
+        if (lane == 0) h[i] = r;
     }
-    r.qs -= ext;
-    r.ds -= ext;
-    score = 0; best = 0; ext = 0;
-    for (uint32_t e = 1; r.qe + e - 1 < m && r.de + e - 1 < L; ++e) {
-        score += dev_pair(cq.at(qb + r.qe + e - 1), cd.at(sb + r.de + e - 1), match, mismatch);
-        if (score > best) { best = score; ext = e; }
-        else if (best - score > X) break;
-    }
-    r.qe += ext;
-    r.de += ext;
-    r.len = min(r.qe - r.qs, r.de - r.ds);
-    h[i] = r;
 }
 
 // -------------------------------------------------- a10: overlap merging --
@@ -673,88 +715,94 @@ __device__ __forceinline__ void scan_pair_max(int32_t &v, uint32_t &s, int lane)
 }
 
 
-// Band of at most 32*C diagonals: lane l owns band offsets c*32 + l, and the
-// previous DP row stays in registers.  The vertical-gap input of offset b (cell
-// (i-1, j) = offset b+1 of the previous row) comes from the next lane by shuffle.
-// Same recurrence, tie-breaks and F max-scan as the strip version below.
-template <int C>
-__device__ __forceinline__ void sw_rows_regs(int64_t I0, int64_t I1, int64_t J0, int64_t J1, int64_t dlo, int64_t B,
+// Band of at most 64 diagonals: lane l owns the two adjacent band offsets 2l and
+// 2l+1 and keeps their previous-row states in registers.  The vertical-gap input of
+// offset 2l is the lane's own offset 2l+1; that of 2l+1 comes from the next lane.
+// One warp max-scan per row resolves horizontal gaps for all 64 offsets: each lane
+// contributes the later-wins maximum of its two X values.  Bases are read through
+// per-lane word cursors (one load per 16 rows).
+__device__ __forceinline__ void sw_rows_pair(int64_t I0, int64_t I1, int64_t J0, int64_t J1, int64_t dlo, int64_t B,
                                              uint64_t qb, uint64_t sb, const uint32_t *__restrict__ qpk,
                                              const uint32_t *__restrict__ qnb, const uint32_t *__restrict__ bpk,
                                              const uint32_t *__restrict__ bnb, int32_t match, int32_t mismatch,
                                              int32_t goe, int32_t ge, int lane, int32_t &best, int64_t &bi,
                                              int64_t &bj, uint32_t &bs) {
-    int32_t pH[C], pE[C];
-    uint32_t pSH[C], pSE[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) { pH[c] = 0; pE[c] = SW_NEG; pSH[c] = 0; pSE[c] = 0; }
-    for (int64_t i = I0; i < I1; ++i) {
-        const int64_t blo = max((int64_t)0, J0 - i - dlo), bhi = min(B - 1, J1 - 1 - i - dlo);
+    int32_t pH0 = 0, pE0 = SW_NEG, pH1 = 0, pE1 = SW_NEG;
+    uint32_t pSH0 = 0, pSE0 = 0, pSH1 = 0, pSE1 = 0;
+    const int32_t b0 = 2 * lane, b1 = 2 * lane + 1;
+    BaseCursor cq(qpk, qnb), cd(bpk, bnb);
+    const int32_t irows = (int32_t)(I1 - I0);
+    const int32_t jlo = (int32_t)(J0 - I0 - dlo), jhi = (int32_t)(J1 - 1 - I0 - dlo);  // band offset limits at row I0
+    for (int32_t r = 0; r < irows; ++r) {
+        // row i = I0 + r: band offsets with J0 <= i + dlo + b <= J1 - 1
+        const int32_t blo = max(0, jlo - r), bhi = min((int32_t)B - 1, jhi - r);
         if (blo > bhi) continue;
-        const bool prow = i - 1 >= I0;
-        const int64_t pblo = max((int64_t)0, J0 - (i - 1) - dlo), pbhi = min(B - 1, J1 - 1 - (i - 1) - dlo);
-        const uint32_t qc = dev_base(qpk, qnb, qb + (uint64_t)i);
-        int32_t carry_v = SW_XNEG;
-        uint32_t carry_s = 0;
-        int32_t cH[C], cE[C];
-        uint32_t cSH[C], cSE[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            // previous-row values at offset b + 1
-            int32_t uH = __shfl_down_sync(0xffffffffu, pH[c], 1), uE = __shfl_down_sync(0xffffffffu, pE[c], 1);
-            uint32_t uSH = __shfl_down_sync(0xffffffffu, pSH[c], 1), uSE = __shfl_down_sync(0xffffffffu, pSE[c], 1);
-            if (c + 1 < C) {
-                const int32_t nH = __shfl_sync(0xffffffffu, pH[c + 1 < C ? c + 1 : c], 0);
-                const int32_t nE = __shfl_sync(0xffffffffu, pE[c + 1 < C ? c + 1 : c], 0);
-                const uint32_t nSH = __shfl_sync(0xffffffffu, pSH[c + 1 < C ? c + 1 : c], 0);
-                const uint32_t nSE = __shfl_sync(0xffffffffu, pSE[c + 1 < C ? c + 1 : c], 0);
-                if (lane == 31) { uH = nH; uE = nE; uSH = nSH; uSE = nSE; }
-            }
-            const int64_t b = (int64_t)c * 32 + lane;
-            if ((int64_t)c * 32 > bhi || (int64_t)c * 32 + 31 < blo) {  // chunk outside this row (warp-uniform)
-                cH[c] = pH[c]; cE[c] = pE[c]; cSH[c] = pSH[c]; cSE[c] = pSE[c];
-                continue;
-            }
-            const bool act = b >= blo && b <= bhi;
-            const bool ok_d = act && prow && b >= pblo && b <= pbhi;
-            const bool ok_u = act && prow && b + 1 >= pblo && b + 1 <= pbhi;
-            int32_t E = SW_NEG;
-            uint32_t SE = 0;
-            if (ok_u) {
-                const int32_t eo = uH + goe, ee = uE + ge;
-                if (eo >= ee) { E = eo; SE = uSH; } else { E = ee; SE = uSE; }
-            }
-            const int32_t Hd = ok_d ? pH[c] : 0;
-            const uint32_t SD = (Hd > 0) ? pSH[c] : ((uint32_t)(i - I0) << 16) | (uint32_t)b;
-            const int64_t j = i + dlo + b;
-            int32_t sigma = mismatch;
-            if (act) sigma = dev_pair(qc, dev_base(bpk, bnb, sb + (uint64_t)j), match, mismatch);
-            const int32_t Dg = Hd + sigma;
-            int32_t cand;
-            uint32_t Sc;
-            if (Dg >= E) { cand = Dg; Sc = SD; } else { cand = E; Sc = SE; }
-            const int32_t H0 = cand > 0 ? cand : 0;
-            int32_t xv = act ? H0 + goe - ge * (int32_t)b : SW_XNEG;
-            uint32_t xs = Sc;
-            scan_pair_max(xv, xs, lane);
-            int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1);
-            uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1);
-            if (lane == 0) { ev = carry_v; es = carry_s; }
-            else if (carry_v > ev) { ev = carry_v; es = carry_s; }
-            const int32_t last_v = __shfl_sync(0xffffffffu, xv, 31);
-            const uint32_t last_s = __shfl_sync(0xffffffffu, xs, 31);
-            if (last_v >= carry_v) { carry_v = last_v; carry_s = last_s; }
-            const int32_t F = (ev > SW_XNEG) ? ev + ge * (int32_t)(b - 1) : SW_NEG;
-            int32_t H;
-            uint32_t SH;
-            if (H0 >= F) { H = H0; SH = Sc; } else { H = F; SH = es; }
-            cH[c] = H; cE[c] = E; cSH[c] = SH; cSE[c] = SE;
-            if (act && H > best) { best = H; bi = i; bj = j; bs = SH; }
+        const bool prow = r > 0;
+        const int32_t pblo = max(0, jlo - r + 1), pbhi = min((int32_t)B - 1, jhi - r + 1);
+        const uint64_t i = (uint64_t)(I0 + r);
+        const uint32_t qc = cq.at(qb + i);
+        // previous-row state at offset b1 + 1 = next lane's b0
+        const int32_t uH = __shfl_down_sync(0xffffffffu, pH0, 1), uE = __shfl_down_sync(0xffffffffu, pE0, 1);
+        const uint32_t uSH = __shfl_down_sync(0xffffffffu, pSH0, 1), uSE = __shfl_down_sync(0xffffffffu, pSE0, 1);
+        const bool act0 = b0 >= blo && b0 <= bhi, act1 = b1 >= blo && b1 <= bhi;
+        const uint64_t j0g = sb + (uint64_t)((int64_t)i + dlo + b0);
+        uint32_t d0 = 4u, d1 = 4u;
+        if (act0) d0 = cd.at(j0g);
+        if (act1) d1 = cd.at(j0g + 1);
+        // cell b0
+        int32_t E0 = SW_NEG;
+        uint32_t SE0 = 0;
+        if (act0 && prow && b1 >= pblo && b1 <= pbhi) {
+            const int32_t eo = pH1 + goe, ee = pE1 + ge;
+            if (eo >= ee) { E0 = eo; SE0 = pSH1; } else { E0 = ee; SE0 = pSE1; }
         }
-#pragma unroll
-        for (int c = 0; c < C; ++c) { pH[c] = cH[c]; pE[c] = cE[c]; pSH[c] = cSH[c]; pSE[c] = cSE[c]; }
+        const bool okd0 = act0 && prow && b0 >= pblo && b0 <= pbhi;
+        const int32_t Hd0 = okd0 ? pH0 : 0;
+        const uint32_t SD0 = (Hd0 > 0) ? pSH0 : ((uint32_t)r << 16) | (uint32_t)b0;
+        const int32_t Dg0 = Hd0 + dev_pair(qc, d0, match, mismatch);
+        int32_t c0v; uint32_t c0s;
+        if (Dg0 >= E0) { c0v = Dg0; c0s = SD0; } else { c0v = E0; c0s = SE0; }
+        const int32_t H00 = c0v > 0 ? c0v : 0;
+        // cell b1
+        int32_t E1 = SW_NEG;
+        uint32_t SE1 = 0;
+        if (act1 && prow && b1 + 1 >= pblo && b1 + 1 <= pbhi) {
+            const int32_t eo = uH + goe, ee = uE + ge;
+            if (eo >= ee) { E1 = eo; SE1 = uSH; } else { E1 = ee; SE1 = uSE; }
+        }
+        const bool okd1 = act1 && prow && b1 >= pblo && b1 <= pbhi;
+        const int32_t Hd1 = okd1 ? pH1 : 0;
+        const uint32_t SD1 = (Hd1 > 0) ? pSH1 : ((uint32_t)r << 16) | (uint32_t)b1;
+        const int32_t Dg1 = Hd1 + dev_pair(qc, d1, match, mismatch);
+        int32_t c1v; uint32_t c1s;
+        if (Dg1 >= E1) { c1v = Dg1; c1s = SD1; } else { c1v = E1; c1s = SE1; }
+        const int32_t H01 = c1v > 0 ? c1v : 0;
+        // horizontal gaps: F(b) = max_{b'<b} X(b') + ge*(b-1), X(b') = H0(b') + go + ge - ge*b'
+        const int32_t x0 = act0 ? H00 + goe - ge * b0 : SW_XNEG;
+        const int32_t x1 = act1 ? H01 + goe - ge * b1 : SW_XNEG;
+        int32_t xv = x1 >= x0 ? x1 : x0;
+        uint32_t xs = x1 >= x0 ? c1s : c0s;
+        scan_pair_max(xv, xs, lane);
+        int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1);
+        uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1);
+        if (lane == 0) { ev = SW_XNEG; es = 0; }
+        const int32_t F0 = (ev > SW_XNEG) ? ev + ge * (b0 - 1) : SW_NEG;
+        const uint32_t SF0 = es;
+        int32_t e1v = ev;
+        uint32_t e1s = es;
+        if (x0 >= e1v) { e1v = x0; e1s = c0s; }
+        const int32_t F1 = (e1v > SW_XNEG) ? e1v + ge * (b1 - 1) : SW_NEG;
+        int32_t H0v, H1v;
+        uint32_t S0, S1;
+        if (H00 >= F0) { H0v = H00; S0 = c0s; } else { H0v = F0; S0 = SF0; }
+        if (H01 >= F1) { H1v = H01; S1 = c1s; } else { H1v = F1; S1 = e1s; }
+        if (act0 && H0v > best) { best = H0v; bi = (int64_t)i; bj = (int64_t)i + dlo + b0; bs = S0; }
+        if (act1 && H1v > best) { best = H1v; bi = (int64_t)i; bj = (int64_t)i + dlo + b1; bs = S1; }
+        pH0 = H0v; pE0 = E0; pSH0 = S0; pSE0 = SE0;
+        pH1 = H1v; pE1 = E1; pSH1 = S1; pSE1 = SE1;
     }
 }
+
 
 __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ sel, uint32_t n,
                                                    const uint64_t *__restrict__ strip_off, SwCell *__restrict__ strips,
@@ -790,12 +838,9 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
         int64_t bi = INT64_MAX, bj = INT64_MAX;
         uint32_t bs = 0;
         const int32_t goe = go + ge;
-        if (B <= 32) {
-            sw_rows_regs<1>(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best,
-                            bi, bj, bs);
-        } else if (B <= 64) {
-            sw_rows_regs<2>(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best,
-                            bi, bj, bs);
+        if (B <= 64) {
+            sw_rows_pair(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best, bi,
+                         bj, bs);
         } else
         for (int64_t i = I0; i < I1; ++i) {
             const int64_t blo = max((int64_t)0, J0 - i - dlo), bhi = min(B - 1, J1 - 1 - i - dlo);
@@ -1252,9 +1297,11 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
 
     // a9: extension
     if (n_hsp) {
+        const uint64_t xwarps = std::min<uint64_t>(n_hsp, (uint64_t)num_sms() * 64);
         GN_LAUNCH("k_xdrop", n_hsp, s,
-                  k_xdrop<<<blocks_for(n_hsp, 128), 128, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d, ix->bank.pk, ix->bank.nb,
-                                                       ix->seq_start_d, sc.match, sc.mismatch, p.xdrop));
+                  k_xdrop<<<blocks_for(xwarps * 32, 256), 256, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d,
+                                                                      ix->bank.pk, ix->bank.nb, ix->seq_start_d,
+                                                                      sc.match, sc.mismatch, p.xdrop));
     }
     timer.mark("xdrop_extend");
     if (keep) {
