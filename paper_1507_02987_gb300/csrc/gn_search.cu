@@ -179,13 +179,6 @@ __global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int q
 // own.  A diagonal holding a single hit cannot form an HSP when min_hsp_len > k,
 // so such hits are dropped before the (small) sort by (G', qpos) that the
 // chaining needs.  Bucket entry: G' << 16 | qpos.
-__global__ void k_bucket_overflow(const uint64_t *__restrict__ boff, uint32_t NB, uint32_t cap,
-                                  unsigned long long *__restrict__ total) {
-    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= NB) return;
-    uint64_t n = boff[b + 1] - boff[b];
-    if (n > cap) atomicAdd(total, (unsigned long long)n);
-}
 
 // bucket entries a, b (a first): consecutive hits of one chain?
 __device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D, const uint64_t *__restrict__ seq_start,
@@ -277,114 +270,146 @@ __device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk, int fbit
     return h >> (32 - fbits);
 }
 
-template <int PASS>
-__global__ void __launch_bounds__(256) k_bucket_tiles(const uint32_t *__restrict__ codes,
-                                                      const uint32_t *__restrict__ qinfo,
-                                                      const uint64_t *__restrict__ hoff, uint64_t xa, uint64_t xb,
-                                                      const uint64_t *__restrict__ off,
-                                                      const uint32_t *__restrict__ post, uint32_t qa, uint32_t NB,
-                                                      const uint32_t *__restrict__ bbase,
-                                                      const uint32_t *__restrict__ bshift,
-                                                      uint32_t *__restrict__ bcnt, const uint64_t *__restrict__ boff,
-                                                      uint64_t *__restrict__ bkeys, int filter, uint32_t D,
-                                                      uint32_t *__restrict__ keep_bits, uint64_t ha, int tpos,
-                                                      int fbits) {
-    extern __shared__ __align__(16) unsigned char bt_smem[];
-    uint32_t *hist = reinterpret_cast<uint32_t *>(bt_smem);
-    unsigned long long *base = reinterpret_cast<unsigned long long *>(hist + BT_SPAN);
-    uint32_t *seen = reinterpret_cast<uint32_t *>(base + (PASS ? BT_SPAN : 0));
-    uint32_t *seen2 = seen + (1u << fbits) / 32;
-    __shared__ uint32_t bmin_s;
+// Like for_tile_hits, but warps take 32-offset blocks of [p0, p1) from a shared
+// counter (reset by the caller between passes), which balances uneven lists.
+template <class F>
+__device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint32_t *blk,
+                                                  const uint32_t *__restrict__ codes,
+                                                  const uint32_t *__restrict__ qinfo,
+                                                  const uint64_t *__restrict__ hoff, const uint64_t *__restrict__ off,
+                                                  const uint32_t *__restrict__ post, uint32_t qa,
+                                                  const uint32_t *__restrict__ bbase,
+                                                  const uint32_t *__restrict__ bshift, F &&f) {
     const int lane = threadIdx.x & 31;
+    const uint32_t nblk = (uint32_t)((p1 - p0 + 31) / 32);
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(blk, 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nblk) break;
+        const uint64_t x0 = p0 + (uint64_t)k * 32;
+        const uint64_t x = x0 + lane;
+        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
+        uint64_t my_src = 0, my_h = 0;
+        if (x < p1) {
+            my_h = hoff[x];
+            my_cnt = (uint32_t)(hoff[x + 1] - my_h);
+            if (my_cnt) {
+                const uint32_t qinf = qinfo[x];
+                my_src = off[codes[x]];
+                my_qpos = qinf & 0xFFFFu;
+                my_ql = (qinf >> 16) - qa;
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
+            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
+            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
+            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
+            const uint32_t bb = bbase[ql], bs = bshift[ql];
+            for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
+                uint32_t g[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t j = j0 + u * 32 + lane;
+                    g[u] = j < cnt ? post[sp + j] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t j = j0 + u * 32 + lane;
+                    if (j < cnt) f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos, bb, bs);
+                }
+            }
+        }
+    }
+}
+
+// Bucket fill: one kernel per chunk.  Each tile (tpos core offsets) hashes the hits
+// of core + halo into the "seen" / "seen twice" bitmaps (repeat filter), counts the
+// kept core hits per bucket in shared memory, reserves each bucket's slots with
+// one global atomic per (tile, bucket), and writes the kept hits.  Buckets have a
+// fixed capacity bcap; hits past it (and hits of buckets outside the tile's
+// shared-memory span, if any overflow) go to the spill list in global hit-key
+// format, which the global sort path handles.
+__global__ void __launch_bounds__(256) k_bucket_fill(
+    const uint32_t *__restrict__ codes, const uint32_t *__restrict__ qinfo, const uint64_t *__restrict__ hoff,
+    uint64_t xa, uint64_t xb, const uint64_t *__restrict__ off, const uint32_t *__restrict__ post, uint32_t qa,
+    const uint32_t *__restrict__ bbase, const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount,
+    uint64_t *__restrict__ bkeys, uint32_t bcap, uint64_t *__restrict__ spill,
+    unsigned long long *__restrict__ spill_count, unsigned long long spill_cap, int qbits, int filter, uint32_t D,
+    int tpos, int fbits) {
+    extern __shared__ __align__(16) unsigned char bf_smem[];
+    uint32_t *hist = reinterpret_cast<uint32_t *>(bf_smem);
+    uint32_t *base = hist + BT_SPAN;
+    uint32_t *seen = base + BT_SPAN;
+    uint32_t *seen2 = seen + (1u << fbits) / 32;
+    __shared__ uint32_t bmin_s, blk;
     for (int i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
+    auto put = [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t b, uint64_t slot) {
+        if (slot < bcap) {
+            bkeys[(uint64_t)b * bcap + slot] = (gk << 16) | qpos;
+        } else {
+            const unsigned long long at = atomicAdd(spill_count, 1ull);
+            if (at < spill_cap) spill[at] = (gk << (16 + qbits)) | ((uint64_t)ql << 16) | qpos;
+        }
+    };
     for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tpos; t0 < xb; t0 += (uint64_t)gridDim.x * tpos) {
         const uint64_t t1 = min(xb, t0 + (uint64_t)tpos);
-        if (threadIdx.x == 0) bmin_s = bbase[(qinfo[t0] >> 16) - qa];
-        if (PASS == 0 && filter) {
+        if (threadIdx.x == 0) { bmin_s = bbase[(qinfo[t0] >> 16) - qa]; blk = 0; }
+        if (filter) {
             for (uint32_t i = threadIdx.x; i < (2u << fbits) / 32; i += blockDim.x) seen[i] = 0u;
         }
         __syncthreads();
         const uint32_t bmin = bmin_s;
-        if (PASS == 0 && filter) {
-            auto insert = [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid, uint32_t bb,
-                              uint32_t bs) {
-                if (!valid) return;
-                const uint32_t h = tile_hash(ql, gk, fbits);
-                const uint32_t bit = 1u << (h & 31);
-                const uint32_t old = atomicOr(&seen[h >> 5], bit);
-                if (old & bit) atomicOr(&seen2[h >> 5], bit);
-            };
-            for_tile_hits(t0 > xa + D ? t0 - D : xa, t0, codes, qinfo, hoff, off, post, qa, bbase, bshift, insert);
-            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, bbase, bshift, insert);
-            for_tile_hits(t1, min(xb, t1 + D), codes, qinfo, hoff, off, post, qa, bbase, bshift, insert);
+        if (filter) {
+            const uint64_t lo = t0 > xa + D ? t0 - D : xa, hi = min(xb, t1 + D);
+            for_tile_hits_dyn(lo, hi, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                              [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
+                                  const uint32_t h = tile_hash(ql, gk, fbits);
+                                  const uint32_t bit = 1u << (h & 31);
+                                  const uint32_t old = atomicOr(&seen[h >> 5], bit);
+                                  if (old & bit) atomicOr(&seen2[h >> 5], bit);
+                              });
+            __syncthreads();
+            if (threadIdx.x == 0) blk = 0;
             __syncthreads();
         }
-        // PASS 0: keep decision (recorded one bit per hit) and local counts; PASS 1: counts from the bits
-        for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                      [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid, uint32_t bb,
-                          uint32_t bs) {
-                          const uint64_t hl = hidx - ha;
-                          bool keep = valid;
-                          if (PASS == 0) {
-                              if (filter && valid) {
-                                  const uint32_t h = tile_hash(ql, gk, fbits);
-                                  keep = ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
-                              }
-                              if (filter) {
-                                  // lanes hold consecutive hit indices: at most two words per warp
-                                  const uint32_t votes = __ballot_sync(0xffffffffu, keep);
-                                  const uint64_t lo = __shfl_sync(0xffffffffu, hl, 0);
-                                  if (lane == 0 && votes) {
-                                      const uint32_t sh = (uint32_t)(lo & 31);
-                                      atomicOr(&keep_bits[lo >> 5], votes << sh);
-                                      if (sh && (votes >> (32 - sh))) atomicOr(&keep_bits[(lo >> 5) + 1], votes >> (32 - sh));
-                                  }
-                              }
-                          } else if (filter && valid) {
-                              keep = ((keep_bits[hl >> 5] >> (hl & 31)) & 1u) != 0u;
-                          }
-                          if (!keep) return;
-                          const uint32_t b = bb + (uint32_t)(gk >> bs);
-                          const uint32_t li = b - bmin;
-                          if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
-                          else if (PASS == 0) atomicAdd(&bcnt[b], 1u);
-                      });
-        __syncthreads();
-        if (PASS == 0) {
-            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
-                const uint32_t c = hist[i];
-                if (c) {
-                    atomicAdd(&bcnt[bmin + i], c);
-                    hist[i] = 0;
-                }
-            }
-        } else {
-            // reserve each bucket's range for this tile; hist becomes the local cursor
-            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
-                const uint32_t c = hist[i];
-                if (c) {
-                    const uint32_t b = bmin + i;
-                    base[i] = boff[b] + atomicAdd(&bcnt[b], c);
-                    hist[i] = 0;
-                }
-            }
-            __syncthreads();
-            for_tile_hits(t0, t1, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint64_t hidx, bool valid, uint32_t bb,
-                              uint32_t bs) {
-                              if (!valid) return;
-                              const uint64_t hl = hidx - ha;
-                              if (filter && !((keep_bits[hl >> 5] >> (hl & 31)) & 1u)) return;
+        auto kept = [&](uint32_t ql, uint64_t gk) {
+            if (!filter) return true;
+            const uint32_t h = tile_hash(ql, gk, fbits);
+            return ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
+        };
+        // count kept core hits per bucket (buckets outside the span are placed right away)
+        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
+                              if (!kept(ql, gk)) return;
                               const uint32_t b = bb + (uint32_t)(gk >> bs);
                               const uint32_t li = b - bmin;
-                              uint64_t dst;
-                              if (li < BT_SPAN) dst = base[li] + atomicAdd(&hist[li], 1u);
-                              else dst = boff[b] + atomicAdd(&bcnt[b], 1u);
-                              bkeys[dst] = (gk << 16) | qpos;
+                              if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
+                              else put(ql, qpos, gk, b, atomicAdd(&bcount[b], 1u));
                           });
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
+            const uint32_t c = hist[i];
+            if (c) {
+                base[i] = atomicAdd(&bcount[bmin + i], c);
+                hist[i] = 0;
+            }
         }
+        if (threadIdx.x == 0) blk = 0;
+        __syncthreads();
+        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
+                              if (!kept(ql, gk)) return;
+                              const uint32_t b = bb + (uint32_t)(gk >> bs);
+                              const uint32_t li = b - bmin;
+                              if (li < BT_SPAN) put(ql, qpos, gk, b, (uint64_t)base[li] + atomicAdd(&hist[li], 1u));
+                          });
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
         __syncthreads();
     }
 }
@@ -406,7 +431,7 @@ constexpr int BGW_BITS = 16384;
 constexpr int BGW_CAND = 256;
 
 __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
-    const uint64_t *__restrict__ bkeys, const uint64_t *__restrict__ boff, uint32_t NB,
+    const uint64_t *__restrict__ bkeys, const uint32_t *__restrict__ bcount, uint32_t bcap, uint32_t NB,
     const uint16_t *__restrict__ bq, uint32_t qa, int qbits, int k, uint32_t D, uint32_t min_len, int singles,
     const uint64_t *__restrict__ seq_start, uint32_t n_seqs, DevHsp *__restrict__ out, uint32_t *__restrict__ count,
     uint32_t out_cap, uint64_t *__restrict__ ovf, unsigned long long ovf_cap,
@@ -419,8 +444,8 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t total_warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < NB; b += total_warps) {
-        const uint64_t beg = boff[b];
-        const uint32_t n = (uint32_t)(boff[b + 1] - beg);
+        const uint64_t beg = (uint64_t)b * bcap;
+        const uint32_t n = min(bcount[b], bcap);
         if (n == 0 || (n == 1 && !singles)) continue;
         const uint32_t ql = bq[b];
         bool spill = false;
@@ -1082,7 +1107,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     // a6-a8 per chunk of queries whose hits fit the budget
     size_t free_b = 0, total_b = 0;
     GN_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    uint64_t hit_budget = std::max<uint64_t>(1ull << 20, (uint64_t)(free_b * 0.55) / 16);
+    // bytes per hit of a chunk: hit keys and their ping-pong buffer on the sort path, or the
+    // fixed-capacity buckets (up to ~22 B per hit without the repeat filter) and spill lists
+    uint64_t hit_budget = std::max<uint64_t>(1ull << 20, (uint64_t)(free_b * 0.55) / 24);
     if (const char *e = getenv("GN_MAX_CHUNK_HITS")) {  // smaller chunks (exercises the multi-chunk path)
         uint64_t v = strtoull(e, nullptr, 10);
         if (v) hit_budget = v;
@@ -1170,20 +1197,20 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     hits_q.insert(hits_q.end(), hh.begin(), hh.end());
                 }
             } else {
-                // bucket plan: 2^lg buckets per query, about `target` hits each
-                uint32_t cap = 2048, target = 1024;
-                if (const char *e = getenv("GN_BUCKET_CAP")) cap = (uint32_t)std::max(64ul, std::min(4096ul, strtoul(e, nullptr, 10)));
-                while (cap & (cap - 1)) cap &= cap - 1;
-                target = cap / 2;
-                // the tile filter keeps roughly a tenth of the hits: size buckets for the kept ones
-                const int singles0 = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
+                // bucket plan: 2^lg buckets per query, about `target` raw hits each
+                const int singles = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
                 const char *fenv = getenv("GN_TILE_FILTER");
-                const int filter = (!singles0 && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
+                const int filter = (!singles && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
                                     !(fenv && strcmp(fenv, "0") == 0)) ? 1 : 0;
                 int tpos = 256, fbits = 17;
                 if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
-                if (filter) target *= 2;
+                // the filter keeps about a fifth of the hits; capacity has ~2x slack over the expected fill
+                uint32_t target = filter ? 2048 : 512, bcap = 1024;
+                if (const char *e = getenv("GN_BUCKET_CAP")) {  // small buckets (exercises the spill path)
+                    bcap = (uint32_t)std::max(8ul, std::min(65536ul, strtoul(e, nullptr, 10)));
+                    target = std::max<uint32_t>(2, bcap / 2);
+                }
                 std::vector<uint32_t> bbase(nqc + 1), bshift(nqc);
                 const int min_lg = std::max(0, gbits - 31);
                 uint64_t nb64 = 0;
@@ -1204,85 +1231,76 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint32_t *d_bshift = carena.alloc_n<uint32_t>(nqc);
                 GN_CUDA(cudaMemcpyAsync(d_bbase, bbase.data(), 4 * (nqc + 1), cudaMemcpyHostToDevice, s));
                 GN_CUDA(cudaMemcpyAsync(d_bshift, bshift.data(), 4 * nqc, cudaMemcpyHostToDevice, s));
-                const int singles = p.min_hsp_len <= (uint32_t)k ? 1 : 0;
-                uint32_t *bcnt = carena.alloc_n<uint32_t>(NB);
-                uint64_t *boff = carena.alloc_n<uint64_t>((uint64_t)NB + 1);
+                uint32_t *bcount = carena.alloc_n<uint32_t>(NB);
+                uint64_t *bkeys = carena.alloc_n<uint64_t>((uint64_t)NB * bcap);
                 uint16_t *bq = carena.alloc_n<uint16_t>(NB);
-                GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
+                unsigned long long *spill_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
+                uint64_t spill_room = std::max<uint64_t>(1u << 20, Hc / 32);
+                uint64_t *spill = carena.alloc_n<uint64_t>(spill_room);
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
-                const unsigned tgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * 16));
-                const size_t bt_smem0 = BT_SPAN * 4 + (filter ? (2u << fbits) / 8 : 0);
-                const size_t bt_smem1 = BT_SPAN * 4 + BT_SPAN * 8;
-                uint32_t *keep_bits = carena.alloc_n<uint32_t>(filter ? (Hc + 31) / 32 + 2 : 1);
-                if (filter) GN_CUDA(cudaMemsetAsync(keep_bits, 0, 4 * ((Hc + 31) / 32 + 2), s));
-                GN_CUDA(cudaFuncSetAttribute(k_bucket_tiles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem0));
-                GN_CUDA(cudaFuncSetAttribute(k_bucket_tiles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem1));
-                GN_LAUNCH("k_bucket_count", Hc, s,
-                          k_bucket_tiles<0><<<tgrid, 256, bt_smem0, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
-                                                                         ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
-                                                                         nullptr, nullptr, filter,
-                                                                         p.max_hit_distance, keep_bits, ha, tpos,
-                                                                         fbits));
-                {
-                    void *scr = carena.alloc(scan_scratch_bytes(NB));
-                    exclusive_scan_u32(bcnt, boff, NB, scr, s);
+                const size_t bf_smem = BT_SPAN * 8 + (filter ? (2u << fbits) / 8 : 0);
+                GN_CUDA(cudaFuncSetAttribute(k_bucket_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
+                int focc = 0;
+                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, k_bucket_fill, 256, bf_smem));
+                const unsigned fgrid = (unsigned)std::max<uint64_t>(
+                    1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(focc, 1) * 4));
+                unsigned long long n_spill = 0;
+                for (int attempt = 0; attempt < 2; ++attempt) {
+                    GN_CUDA(cudaMemsetAsync(bcount, 0, 4ull * NB, s));
+                    GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
+                    GN_LAUNCH("k_bucket_fill", Hc, s,
+                              k_bucket_fill<<<fgrid, 256, bf_smem, s>>>(
+                                  codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcount,
+                                  bkeys, bcap, spill, spill_count, (unsigned long long)spill_room, qbits, filter,
+                                  p.max_hit_distance, tpos, fbits));
+                    GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
+                    GN_CUDA(cudaStreamSynchronize(s));
+                    if (n_spill <= spill_room) break;
+                    spill_room = n_spill;  // rerun with room for every spilled hit
+                    spill = carena.alloc_n<uint64_t>(spill_room);
                 }
-                GN_CUDA(cudaMemsetAsync(bcnt, 0, 4ull * NB, s));
-                uint64_t n_kept = 0;
-                GN_CUDA(cudaMemcpyAsync(&n_kept, boff + NB, 8, cudaMemcpyDeviceToHost, s));
-                GN_CUDA(cudaStreamSynchronize(s));
-                uint64_t *bkeys = carena.alloc_n<uint64_t>(n_kept);
-                GN_LAUNCH("k_bucket_scatter", Hc, s,
-                          k_bucket_tiles<1><<<tgrid, 256, bt_smem1, s>>>(codes, qinfo, hoff, xa, xb, ix->off_d,
-                                                                         ix->post_d, qa, NB, d_bbase, d_bshift, bcnt,
-                                                                         boff, bkeys, filter, p.max_hit_distance,
-                                                                         keep_bits, ha, tpos, fbits));
+                GN_REQUIRE(n_spill <= spill_room, GN_EINTERNAL, "hit-bucket spill sizing did not converge");
                 GN_LAUNCH("k_bucket_query", NB, s, k_bucket_query<<<nqc, 256, 0, s>>>(d_bbase, nqc, NB, bq));
-                timer.mark("bucket_scatter");
-                unsigned long long *ovf_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
-                // buckets whose candidates may not fit a warp's buffer are bounded by their size; size the
-                // overflow buffer for the worst case of every bucket with more than BGW_CAND entries
-                GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
-                GN_LAUNCH("k_bucket_overflow", NB, s,
-                          k_bucket_overflow<<<blocks_for(NB), 256, 0, s>>>(boff, NB, singles ? BGW_CAND : 0xFFFFFFFFu,
-                                                                           ovf_count));
-                unsigned long long ovf_cap = 0;
-                GN_CUDA(cudaMemcpyAsync(&ovf_cap, ovf_count, 8, cudaMemcpyDeviceToHost, s));
-                GN_CUDA(cudaStreamSynchronize(s));
-                // without single-hit HSPs, spills come from candidate overflow, which a retry sizes exactly
-                uint64_t ovf_room = singles ? ovf_cap : std::max<uint64_t>(1u << 20, n_kept / 4);
-                uint64_t *ovf = carena.alloc_n<uint64_t>(ovf_room);
-                uint64_t *ovf_alt = nullptr;
+                timer.mark("bucket_fill");
+                // group each bucket; buckets with too many candidates are appended to the spill list too
                 const size_t smem = (size_t)BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8);
                 GN_CUDA(cudaFuncSetAttribute(k_bucket_group_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 int occ = 0;
                 GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_group_warp, BGW_WARPS * 32, smem));
                 const unsigned ggrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>((NB + BGW_WARPS - 1) / BGW_WARPS, (uint64_t)num_sms() * std::max(occ, 1)));
+                const uint64_t spilled_fill = n_spill;
+                uint64_t group_room = std::max<uint64_t>(1u << 20, Hc / 16);
+                uint64_t *gsp = carena.alloc_n<uint64_t>(spilled_fill + group_room);
+                if (spilled_fill)
+                    GN_CUDA(cudaMemcpyAsync(gsp, spill, 8 * spilled_fill, cudaMemcpyDeviceToDevice, s));
                 unsigned long long n_ovf = 0;
+                unsigned long long *ovf_count = spill_count;
                 for (int attempt = 0; attempt < 2; ++attempt) {
                     const uint32_t hsp_before = n_hsp;
                     emit([&](DevHsp *o, uint32_t room) {
                         GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
-                        GN_LAUNCH("k_bucket_group", n_kept, s,
+                        GN_LAUNCH("k_bucket_group", Hc, s,
                                   k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
-                                      bkeys, boff, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len, singles,
-                                      ix->seq_start_d, ix->n_seqs, o, counter, room, ovf,
-                                      (unsigned long long)ovf_room, ovf_count, status));
+                                      bkeys, bcount, bcap, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len,
+                                      singles, ix->seq_start_d, ix->n_seqs, o, counter, room, gsp + spilled_fill,
+                                      (unsigned long long)group_room, ovf_count, status));
                     });
                     GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
-                    if (n_ovf <= ovf_room) break;
-                    // spilled more than the buffer holds: enlarge it and redo this chunk's grouping
+                    if (n_ovf <= group_room) break;
                     n_hsp = hsp_before;
-                    ovf_room = n_ovf;
-                    ovf = carena.alloc_n<uint64_t>(ovf_room);
+                    group_room = n_ovf;
+                    uint64_t *ng = carena.alloc_n<uint64_t>(spilled_fill + group_room);
+                    if (spilled_fill)
+                        GN_CUDA(cudaMemcpyAsync(ng, spill, 8 * spilled_fill, cudaMemcpyDeviceToDevice, s));
+                    gsp = ng;
                     GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
                 }
-                GN_REQUIRE(n_ovf <= ovf_room, GN_EINTERNAL, "hit-bucket spill buffer sizing did not converge");
+                GN_REQUIRE(n_ovf <= group_room, GN_EINTERNAL, "hit-bucket spill buffer sizing did not converge");
                 timer.mark("bucket_group");
-                if (n_ovf) ovf_alt = carena.alloc_n<uint64_t>(n_ovf);
-                if (n_ovf) sort_path(ovf, ovf_alt, n_ovf, 0, TAG_HIT_SORT);
+                const uint64_t n_sp = spilled_fill + n_ovf;
+                if (n_sp) sort_path(gsp, carena.alloc_n<uint64_t>(n_sp), n_sp, 0, TAG_HIT_SORT);
             }
             timer.mark("hit_merge");
         }
