@@ -445,12 +445,15 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
     const uint32_t total_warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < NB; b += total_warps) {
         const uint64_t beg = (uint64_t)b * bcap;
-        const uint32_t n = min(bcount[b], bcap);
-        if (n == 0 || (n == 1 && !singles)) continue;
+        const uint32_t total = bcount[b];
+        const uint32_t n = min(total, bcap);
+        if (total <= bcap && (n == 0 || (n == 1 && !singles))) continue;
         const uint32_t ql = bq[b];
-        bool spill = false;
+        // a bucket that overflowed its capacity has entries in the spill list already: send the
+        // stored part there as well, so that every (query, diagonal) stays on one path
+        bool spill = total > bcap;
         uint32_t nc = 0;
-        if (!singles) {
+        if (!singles && !spill) {
             for (int i = lane; i < BGW_BITS / 32; i += 32) { seen[i] = 0u; seen2[i] = 0u; }
             __syncwarp();
             for (uint32_t i0 = 0; i0 < n; i0 += 128) {
