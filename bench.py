@@ -65,6 +65,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-queries", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle time of the CPU baseline")
+    ap.add_argument("--queries", type=int, default=0, help="use only the first N queries (profiling runs)")
     return ap.parse_args()
 
 
@@ -173,7 +174,7 @@ def ncu_traffic(kernel: str):
     return k.get("dram_bytes_per_unit") if k else None
 
 
-def workload(name: str, stride: int, rank: int):
+def workload(name: str, stride: int, rank: int, n_queries: int = 0):
     import dataclasses
 
     import numpy as np
@@ -186,6 +187,8 @@ def workload(name: str, stride: int, rank: int):
     if rank:
         spec = dataclasses.replace(spec, seed=spec.seed + 1000 * rank)
     queries = synth.make_queries(spec, bank)
+    if n_queries and n_queries < queries.n:
+        queries = queries.subset(range(n_queries))
     desc = {
         "tiny": "tiny bank (1,000 uniform sequences, ~1.25 Mbp), 10 mutated-copy queries",
         "mid": "mid bank (200,000 log-normal sequences, ~400 Mbp, GC 0.35-0.65, 20% repeats), 1,000 homolog queries 80-10,000 bp",
@@ -219,7 +222,7 @@ def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0):
 def run_reference(args, dist):
     if dist.rank != 0:
         return 0
-    bank, queries, desc = workload(args.workload, args.stride, 0)
+    bank, queries, desc = workload(args.workload, args.stride, 0, args.queries)
     import oracle
     threads = os.cpu_count() or 1
     ox = oracle.Index(bank, k=11, stride=args.stride)
@@ -269,7 +272,7 @@ def run_ours(args, dist):
     log = lambda *a: print(f"[rank {dist.rank}]", *a, file=sys.stderr, flush=True)
 
     t = time.perf_counter()
-    bank, queries, desc = workload(args.workload, args.stride, dist.rank)
+    bank, queries, desc = workload(args.workload, args.stride, dist.rank, args.queries)
     log(f"workload generated in {time.perf_counter() - t:.1f}s: {bank.n_seqs} seqs, {bank.n_bases} bases, "
         f"{queries.n} queries, {int(queries.start[-1])} query bases")
     stream = torch.cuda.current_stream()

@@ -203,12 +203,38 @@ __global__ void k_scan_down(const uint32_t *__restrict__ in, uint64_t n, const u
     }
 }
 
+// One block scans up to SC_SMALL elements: each thread sums a contiguous run, the block
+// scans the run totals, then each thread writes its run's prefixes.
+constexpr uint64_t SC_SMALL = 1u << 17;
+
+__global__ void __launch_bounds__(1024) k_scan_small(const uint32_t *__restrict__ in, uint64_t n,
+                                                     uint64_t *__restrict__ out) {
+    constexpr int T = 1024;
+    __shared__ uint64_t ws[T / 32];
+    __shared__ uint64_t tot;
+    const uint64_t per = (n + T - 1) / T;
+    const uint64_t b = threadIdx.x * per, e = min(n, b + per);
+    uint64_t s = 0;
+    for (uint64_t i = b; i < e; ++i) s += in[i];
+    uint64_t off = block_excl_scan<uint64_t, T>(s, ws, &tot);
+    for (uint64_t i = b; i < e; ++i) {
+        const uint64_t v = in[i];
+        out[i] = off;
+        off += v;
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 size_t scan_scratch_bytes(uint64_t n) { return sizeof(uint64_t) * ((n + SC_TILE - 1) / SC_TILE + 1); }
 
 void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scratch, cudaStream_t s) {
     uint64_t nb = (n + SC_TILE - 1) / SC_TILE;
     if (nb == 0) {
         GN_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), s));
+        return;
+    }
+    if (n <= SC_SMALL) {
+        GN_LAUNCH("k_scan_small", n, s, k_scan_small<<<1, 1024, 0, s>>>(in, n, out));
         return;
     }
     uint64_t *sums = static_cast<uint64_t *>(scratch);

@@ -993,6 +993,129 @@ __global__ void k_finalize(const DevAln *__restrict__ a, uint32_t n, const uint3
     flag[i] = (h.evalue <= max_e) ? 1u : 0u;
 }
 
+
+// Per-query ranking (alignments of a query are contiguous and at most RQ_CAP): one
+// CTA per query sorts record indices in shared memory with a bitonic network - first
+// by (seq, q_start, q_end, db_start, db_end, score desc) to drop records that repeat
+// an earlier one's sequence and ranges (and records with score <= 0), then by
+// (score desc, seq, q_start, db_start, q_end, db_end) - and writes the ranked hits
+// with e-value and bit score at the query's input offset.
+constexpr int RQ_CAP = 1024;
+
+__device__ __forceinline__ bool rq_less_dedupe(const DevAln &a, const DevAln &b) {
+    if (a.seq != b.seq) return a.seq < b.seq;
+    if (a.qs != b.qs) return a.qs < b.qs;
+    if (a.qe != b.qe) return a.qe < b.qe;
+    if (a.ds != b.ds) return a.ds < b.ds;
+    if (a.de != b.de) return a.de < b.de;
+    return a.score > b.score;
+}
+
+__device__ __forceinline__ bool rq_less_rank(const DevAln &a, const DevAln &b) {
+    if (a.score != b.score) return a.score > b.score;
+    if (a.seq != b.seq) return a.seq < b.seq;
+    if (a.qs != b.qs) return a.qs < b.qs;
+    if (a.ds != b.ds) return a.ds < b.ds;
+    if (a.qe != b.qe) return a.qe < b.qe;
+    return a.de < b.de;
+}
+
+template <int MODE>  // 0: dedupe order, 1: rank order (dropped records last)
+__device__ void rq_bitonic(uint16_t *idx, const DevAln *rec, const uint8_t *keep, uint32_t P) {
+    for (uint32_t k2 = 2; k2 <= P; k2 <<= 1) {
+        for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint16_t a = idx[i], c = idx[ixj];
+                    bool a_gt_c;  // a sorts after c
+                    if (a == 0xFFFFu) a_gt_c = c != 0xFFFFu;
+                    else if (c == 0xFFFFu) a_gt_c = false;
+                    else if (MODE == 1 && keep[a] != keep[c]) a_gt_c = !keep[a];
+                    else a_gt_c = MODE == 0 ? rq_less_dedupe(rec[c], rec[a]) : rq_less_rank(rec[c], rec[a]);
+                    const bool up = (i & k2) == 0;
+                    if (a_gt_c == up) { idx[i] = c; idx[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rank_query(const DevAln *__restrict__ aln, const uint32_t *__restrict__ qrange,
+                                                    uint32_t nq, const uint64_t *__restrict__ qstart, double n_bank,
+                                                    double lambda, double K, double max_e, gn_hit *__restrict__ out,
+                                                    uint32_t *__restrict__ qcount) {
+    __shared__ DevAln rec[RQ_CAP];
+    __shared__ uint16_t idx[RQ_CAP];
+    __shared__ uint8_t keep[RQ_CAP];
+    __shared__ uint32_t nk_s, ne_s;
+    for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+        const uint32_t start = qrange[2 * q], n = qrange[2 * q + 1] - start;
+        if (n == 0) {
+            if (threadIdx.x == 0) qcount[q] = 0;
+            continue;
+        }
+        uint32_t P = 1;
+        while (P < n) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+            if (i < n) rec[i] = aln[start + i];
+            idx[i] = i < n ? (uint16_t)i : (uint16_t)0xFFFFu;
+        }
+        if (threadIdx.x == 0) { nk_s = 0; ne_s = 0; }
+        __syncthreads();
+        rq_bitonic<0>(idx, rec, keep, P);
+        for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+            const DevAln &a = rec[idx[k]];
+            bool kk = a.score > 0;
+            if (kk && k > 0) {
+                const DevAln &b = rec[idx[k - 1]];
+                kk = !(a.seq == b.seq && a.qs == b.qs && a.qe == b.qe && a.ds == b.ds && a.de == b.de);
+            }
+            keep[idx[k]] = kk ? 1 : 0;
+            if (kk) atomicAdd(&nk_s, 1u);
+        }
+        __syncthreads();
+        rq_bitonic<1>(idx, rec, keep, P);
+        const uint32_t nk = nk_s;
+        const double m = (double)(qstart[rec[0].qi + 1] - qstart[rec[0].qi]);
+        for (uint32_t k = threadIdx.x; k < nk; k += blockDim.x) {
+            const DevAln &x = rec[idx[k]];
+            gn_hit h;
+            h.query = x.qi; h.seq = x.seq; h.q_start = x.qs; h.q_end = x.qe; h.db_start = x.ds; h.db_end = x.de;
+            h.score = x.score;
+            h.rank = k;
+            h.evalue = K * m * n_bank * exp(-lambda * (double)x.score);
+            h.bits = (lambda * (double)x.score - log(K)) / log(2.0);
+            // e-values rise as scores fall, so the cut keeps a prefix of the ranking
+            if (h.evalue <= max_e) {
+                out[start + k] = h;
+                atomicAdd(&ne_s, 1u);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) qcount[q] = ne_s;
+        __syncthreads();
+    }
+}
+
+__global__ void k_query_ranges(const DevAln *__restrict__ a, uint32_t n, uint32_t *__restrict__ qrange) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t q = a[i].qi;
+    if (i == 0 || a[i - 1].qi != q) qrange[2 * q] = i;
+    if (i == n - 1 || a[i + 1].qi != q) qrange[2 * q + 1] = i + 1;
+}
+
+__global__ void k_gather_ranked(const gn_hit *__restrict__ in, const uint32_t *__restrict__ qrange,
+                                const uint64_t *__restrict__ qoff, uint32_t nq, gn_hit *__restrict__ out) {
+    for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+        const uint32_t start = qrange[2 * q];
+        const uint64_t o = qoff[q], c = qoff[q + 1] - o;
+        for (uint32_t k = threadIdx.x; k < c; k += blockDim.x) out[o + k] = in[start + k];
+    }
+}
+
 // ------------------------------------------------------------ compaction --
 __global__ void k_scatter_flagged(const uint32_t *__restrict__ in, int W, const uint32_t *__restrict__ flags,
                                   const uint64_t *__restrict__ pos, uint32_t n, uint32_t *__restrict__ out) {
@@ -1343,7 +1466,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         uint32_t *perm = arena.alloc_n<uint32_t>(n_hsp);
         sort_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, n_hsp,
                      {{W_QI, qib, false}, {W_SEQ, seqb, false}, {W_QS, qposb, false}, {W_DS, posb, false},
-                      {W_QE, qposb + 1, false}, {W_DE, posb + 1, false}},
+                      {W_QE, qposb, false}, {W_DE, posb, false}},
                      perm, arena, s);
         DevHsp *srt = arena.alloc_n<DevHsp>(n_hsp);
         gather_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, perm, n_hsp,
@@ -1369,8 +1492,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     if (n_mg) {
         uint32_t *perm = arena.alloc_n<uint32_t>(n_mg);
         sort_records(reinterpret_cast<const uint32_t *>(merged), HSP_WORDS, n_mg,
-                     {{W_QI, qib, false}, {W_LEN, qposb + 1, true}, {W_SEQ, seqb, false}, {W_QS, qposb, false},
-                      {W_DS, posb, false}, {W_QE, qposb + 1, false}, {W_DE, posb + 1, false}},
+                     {{W_QI, qib, false}, {W_LEN, qposb, true}, {W_SEQ, seqb, false}, {W_QS, qposb, false},
+                      {W_DS, posb, false}, {W_QE, qposb, false}, {W_DE, posb, false}},
                      perm, arena, s);
         DevHsp *srt = arena.alloc_n<DevHsp>(n_mg);
         gather_records(reinterpret_cast<const uint32_t *>(merged), HSP_WORDS, perm, n_mg,
@@ -1425,12 +1548,34 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     // a13: duplicates (same query, sequence and ranges: keep the best score), rank by score, statistics
     uint32_t n_out = 0;
     gn_hit *fin = arena.alloc_n<gn_hit>(n_sel);
-    if (n_sel) {
+    const char *renv = getenv("GN_RANK_PATH");
+    const bool per_query_rank = p.max_alignments != 0 && p.max_alignments <= (uint32_t)RQ_CAP &&
+                                !(renv && strcmp(renv, "sort") == 0);
+    if (n_sel && per_query_rank) {
+        uint32_t *qrange = arena.alloc_n<uint32_t>(2ull * nq);
+        GN_CUDA(cudaMemsetAsync(qrange, 0, 8ull * nq, s));
+        GN_LAUNCH("k_query_ranges", n_sel, s, k_query_ranges<<<blocks_for(n_sel), 256, 0, s>>>(aln, n_sel, qrange));
+        gn_hit *hits = arena.alloc_n<gn_hit>(n_sel);
+        uint32_t *qcount = arena.alloc_n<uint32_t>(nq);
+        const unsigned rgrid = (unsigned)std::min<uint64_t>(nq, (uint64_t)num_sms() * 8);
+        GN_LAUNCH("k_rank_query", n_sel, s,
+                  k_rank_query<<<rgrid, 256, 0, s>>>(aln, qrange, nq, qstart_d, (double)ix->n_bases, sc.lambda, sc.K,
+                                                     p.max_evalue, hits, qcount));
+        uint64_t *qoff = arena.alloc_n<uint64_t>(nq + 1);
+        void *scr = arena.alloc(scan_scratch_bytes(nq));
+        exclusive_scan_u32(qcount, qoff, nq, scr, s);
+        uint64_t tot = 0;
+        GN_CUDA(cudaMemcpyAsync(&tot, qoff + nq, 8, cudaMemcpyDeviceToHost, s));
+        GN_CUDA(cudaStreamSynchronize(s));
+        n_out = (uint32_t)tot;
+        GN_LAUNCH("k_gather_ranked", n_out, s,
+                  k_gather_ranked<<<rgrid, 256, 0, s>>>(hits, qrange, qoff, nq, fin));
+    } else if (n_sel) {
         const int scb = std::min(31, bits_for((uint64_t)65535 * (uint64_t)std::max(1, sc.match)));
         uint32_t *perm = arena.alloc_n<uint32_t>(n_sel);
         sort_records(reinterpret_cast<const uint32_t *>(aln), ALN_WORDS, n_sel,
-                     {{A_QI, qib, false}, {A_SEQ, seqb, false}, {A_QS, qposb, false}, {A_QE, qposb + 1, false},
-                      {A_DS, posb, false}, {A_DE, posb + 1, false}, {A_SCORE, scb, true}},
+                     {{A_QI, qib, false}, {A_SEQ, seqb, false}, {A_QS, qposb, false}, {A_QE, qposb, false},
+                      {A_DS, posb, false}, {A_DE, posb, false}, {A_SCORE, scb, true}},
                      perm, arena, s);
         DevAln *srt = arena.alloc_n<DevAln>(n_sel);
         gather_records(reinterpret_cast<const uint32_t *>(aln), ALN_WORDS, perm, n_sel, reinterpret_cast<uint32_t *>(srt), s);
@@ -1444,7 +1589,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
             uint32_t *perm2 = arena.alloc_n<uint32_t>(nu);
             sort_records(reinterpret_cast<const uint32_t *>(uniq), ALN_WORDS, nu,
                          {{A_QI, qib, false}, {A_SCORE, scb, true}, {A_SEQ, seqb, false}, {A_QS, qposb, false},
-                          {A_DS, posb, false}, {A_QE, qposb + 1, false}, {A_DE, posb + 1, false}},
+                          {A_DS, posb, false}, {A_QE, qposb, false}, {A_DE, posb, false}},
                          perm2, arena, s);
             DevAln *ranked = arena.alloc_n<DevAln>(nu);
             gather_records(reinterpret_cast<const uint32_t *>(uniq), ALN_WORDS, perm2, nu,
