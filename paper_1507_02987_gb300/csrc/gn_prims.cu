@@ -205,7 +205,7 @@ __global__ void k_scan_down(const uint32_t *__restrict__ in, uint64_t n, const u
 
 // One block scans up to SC_SMALL elements: each thread sums a contiguous run, the block
 // scans the run totals, then each thread writes its run's prefixes.
-constexpr uint64_t SC_SMALL = 1u << 17;
+constexpr uint64_t SC_SMALL = 4096;
 
 __global__ void __launch_bounds__(1024) k_scan_small(const uint32_t *__restrict__ in, uint64_t n,
                                                      uint64_t *__restrict__ out) {
