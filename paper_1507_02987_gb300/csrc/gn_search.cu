@@ -302,25 +302,40 @@ __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint
             }
         }
         uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
+        // lists are taken two at a time so that both lists' loads are in flight together
         while (todo) {
-            const int src = __ffs(todo) - 1;
+            const int srcA = __ffs(todo) - 1;
             todo &= todo - 1;
-            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
-            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
-            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
-            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
-            const uint32_t bb = bbase[ql], bs = bshift[ql];
-            for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
-                uint32_t g[4];
+            const int srcB = todo ? __ffs(todo) - 1 : srcA;
+            const bool twoB = todo != 0;
+            if (twoB) todo &= todo - 1;
+            const uint32_t cntA = __shfl_sync(0xffffffffu, my_cnt, srcA);
+            const uint64_t spA = __shfl_sync(0xffffffffu, my_src, srcA);
+            const uint32_t qposA = __shfl_sync(0xffffffffu, my_qpos, srcA);
+            const uint32_t qlA = __shfl_sync(0xffffffffu, my_ql, srcA);
+            const uint32_t cntB = twoB ? __shfl_sync(0xffffffffu, my_cnt, srcB) : 0u;
+            const uint64_t spB = __shfl_sync(0xffffffffu, my_src, srcB);
+            const uint32_t qposB = __shfl_sync(0xffffffffu, my_qpos, srcB);
+            const uint32_t qlB = __shfl_sync(0xffffffffu, my_ql, srcB);
+            const uint32_t bbA = bbase[qlA], bsA = bshift[qlA], bbB = bbase[qlB], bsB = bshift[qlB];
+            const uint32_t cmax = max(cntA, cntB);
+            for (uint32_t j0 = 0; j0 < cmax; j0 += 128) {
+                uint32_t ga[4], gb[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const uint32_t j = j0 + u * 32 + lane;
-                    g[u] = j < cnt ? post[sp + j] : 0u;
+                    ga[u] = j < cntA ? post[spA + j] : 0u;
+                    gb[u] = j < cntB ? post[spB + j] : 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const uint32_t j = j0 + u * 32 + lane;
-                    if (j < cnt) f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos, bb, bs);
+                    if (j < cntA) f(qlA, qposA, (uint64_t)ga[u] + QBIAS - qposA, bbA, bsA);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t j = j0 + u * 32 + lane;
+                    if (j < cntB) f(qlB, qposB, (uint64_t)gb[u] + QBIAS - qposB, bbB, bsB);
                 }
             }
         }
@@ -427,7 +442,7 @@ __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc,
 // are sorted by (G', qpos) with a warp bitonic sort and chained.  Buckets with
 // more than BGW_CAND candidates go to the global sort path.
 constexpr int BGW_WARPS = 8;
-constexpr int BGW_BITS = 16384;
+constexpr int BGW_BITS = 8192;
 constexpr int BGW_CAND = 256;
 
 __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
@@ -435,15 +450,18 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
     const uint16_t *__restrict__ bq, uint32_t qa, int qbits, int k, uint32_t D, uint32_t min_len, int singles,
     const uint64_t *__restrict__ seq_start, uint32_t n_seqs, DevHsp *__restrict__ out, uint32_t *__restrict__ count,
     uint32_t out_cap, uint64_t *__restrict__ ovf, unsigned long long ovf_cap,
-    unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status) {
+    unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status, uint32_t *__restrict__ next_bucket) {
     extern __shared__ __align__(16) unsigned char gw_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *seen = reinterpret_cast<uint32_t *>(gw_smem) + wib * (2 * BGW_BITS / 32);
     uint32_t *seen2 = seen + BGW_BITS / 32;
     uint64_t *cand = reinterpret_cast<uint64_t *>(gw_smem + BGW_WARPS * 2 * BGW_BITS / 8) + wib * BGW_CAND;
     const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t total_warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < NB; b += total_warps) {
+    for (;;) {
+        uint32_t b = 0;
+        if (lane == 0) b = atomicAdd(next_bucket, 1u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= NB) break;
         const uint64_t beg = (uint64_t)b * bcap;
         const uint32_t total = bcount[b];
         const uint32_t n = min(total, bcap);
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (i0 + u * 32 + lane >= n) break;
-                    const uint32_t h = (uint32_t)(((e[u] >> 16) * 0x9E3779B97F4A7C15ull) >> 50);  // 14 bits
+                    const uint32_t h = (uint32_t)(((e[u] >> 16) * 0x9E3779B97F4A7C15ull) >> 51);  // 13 bits
                     const uint32_t bit = 1u << (h & 31);
                     const uint32_t old = atomicOr(&seen[h >> 5], bit);
                     if (old & bit) atomicOr(&seen2[h >> 5], bit);
@@ -483,7 +501,7 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
                 if (singles) {
                     keep = true;
                 } else {
-                    const uint32_t h = (uint32_t)(((key >> 16) * 0x9E3779B97F4A7C15ull) >> 50);
+                    const uint32_t h = (uint32_t)(((key >> 16) * 0x9E3779B97F4A7C15ull) >> 51);
                     keep = (seen2[h >> 5] >> (h & 31)) & 1u;
                 }
             }
@@ -1406,11 +1424,12 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     const uint32_t hsp_before = n_hsp;
                     emit([&](DevHsp *o, uint32_t room) {
                         GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
+                        GN_CUDA(cudaMemsetAsync(counter + 1, 0, 4, s));
                         GN_LAUNCH("k_bucket_group", Hc, s,
                                   k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
                                       bkeys, bcount, bcap, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len,
                                       singles, ix->seq_start_d, ix->n_seqs, o, counter, room, gsp + spilled_fill,
-                                      (unsigned long long)group_room, ovf_count, status));
+                                      (unsigned long long)group_room, ovf_count, status, counter + 1));
                     });
                     GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
