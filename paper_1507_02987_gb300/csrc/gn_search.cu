@@ -271,8 +271,10 @@ __device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk, int fbit
 }
 
 // Like for_tile_hits, but warps take 32-offset blocks of [p0, p1) from a shared
-// counter (reset by the caller between passes), which balances uneven lists.
-template <class F>
+// counter (reset by the caller between passes), which balances uneven lists, and
+// the occurrence lists are walked LB at a time so that LB lists' loads are in flight
+// together.
+template <int LB, class F>
 __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint32_t *blk,
                                                   const uint32_t *__restrict__ codes,
                                                   const uint32_t *__restrict__ qinfo,
@@ -283,17 +285,17 @@ __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint
     const int lane = threadIdx.x & 31;
     const uint32_t nblk = (uint32_t)((p1 - p0 + 31) / 32);
     for (;;) {
-        uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(blk, 1u);
-        k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= nblk) break;
-        const uint64_t x0 = p0 + (uint64_t)k * 32;
+        uint32_t kb = 0;
+        if (lane == 0) kb = atomicAdd(blk, 1u);
+        kb = __shfl_sync(0xffffffffu, kb, 0);
+        if (kb >= nblk) break;
+        const uint64_t x0 = p0 + (uint64_t)kb * 32;
         const uint64_t x = x0 + lane;
         uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
-        uint64_t my_src = 0, my_h = 0;
+        uint64_t my_src = 0;
         if (x < p1) {
-            my_h = hoff[x];
-            my_cnt = (uint32_t)(hoff[x + 1] - my_h);
+            const uint64_t h = hoff[x];
+            my_cnt = (uint32_t)(hoff[x + 1] - h);
             if (my_cnt) {
                 const uint32_t qinf = qinfo[x];
                 my_src = off[codes[x]];
@@ -302,41 +304,39 @@ __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint
             }
         }
         uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
-        // lists are taken two at a time so that both lists' loads are in flight together
         while (todo) {
-            const int srcA = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int srcB = todo ? __ffs(todo) - 1 : srcA;
-            const bool twoB = todo != 0;
-            if (twoB) todo &= todo - 1;
-            const uint32_t cntA = __shfl_sync(0xffffffffu, my_cnt, srcA);
-            const uint64_t spA = __shfl_sync(0xffffffffu, my_src, srcA);
-            const uint32_t qposA = __shfl_sync(0xffffffffu, my_qpos, srcA);
-            const uint32_t qlA = __shfl_sync(0xffffffffu, my_ql, srcA);
-            const uint32_t cntB = twoB ? __shfl_sync(0xffffffffu, my_cnt, srcB) : 0u;
-            const uint64_t spB = __shfl_sync(0xffffffffu, my_src, srcB);
-            const uint32_t qposB = __shfl_sync(0xffffffffu, my_qpos, srcB);
-            const uint32_t qlB = __shfl_sync(0xffffffffu, my_ql, srcB);
-            const uint32_t bbA = bbase[qlA], bsA = bshift[qlA], bbB = bbase[qlB], bsB = bshift[qlB];
-            const uint32_t cmax = max(cntA, cntB);
+            uint32_t cnt[LB], qpos[LB], ql[LB], bb[LB], bs[LB];
+            uint64_t sp[LB];
+            uint32_t cmax = 0;
+#pragma unroll
+            for (int l = 0; l < LB; ++l) {
+                const int src = todo ? __ffs(todo) - 1 : 0;
+                const bool has = todo != 0;
+                if (has) todo &= todo - 1;
+                cnt[l] = has ? __shfl_sync(0xffffffffu, my_cnt, src) : 0u;
+                sp[l] = __shfl_sync(0xffffffffu, my_src, src);
+                qpos[l] = __shfl_sync(0xffffffffu, my_qpos, src);
+                ql[l] = __shfl_sync(0xffffffffu, my_ql, src);
+                bb[l] = bbase[ql[l]];
+                bs[l] = bshift[ql[l]];
+                cmax = max(cmax, cnt[l]);
+            }
             for (uint32_t j0 = 0; j0 < cmax; j0 += 128) {
-                uint32_t ga[4], gb[4];
+                uint32_t g[LB][4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    ga[u] = j < cntA ? post[spA + j] : 0u;
-                    gb[u] = j < cntB ? post[spB + j] : 0u;
-                }
+                for (int l = 0; l < LB; ++l)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    if (j < cntA) f(qlA, qposA, (uint64_t)ga[u] + QBIAS - qposA, bbA, bsA);
-                }
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t j = j0 + u * 32 + lane;
+                        g[l][u] = j < cnt[l] ? post[sp[l] + j] : 0u;
+                    }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    if (j < cntB) f(qlB, qposB, (uint64_t)gb[u] + QBIAS - qposB, bbB, bsB);
-                }
+                for (int l = 0; l < LB; ++l)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t j = j0 + u * 32 + lane;
+                        if (j < cnt[l]) f(ql[l], qpos[l], (uint64_t)g[l][u] + QBIAS - qpos[l], bb[l], bs[l]);
+                    }
             }
         }
     }
@@ -349,13 +349,14 @@ __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint
 // fixed capacity bcap; hits past it (and hits of buckets outside the tile's
 // shared-memory span, if any overflow) go to the spill list in global hit-key
 // format, which the global sort path handles.
+template <int LB>
 __global__ void __launch_bounds__(256) k_bucket_fill(
     const uint32_t *__restrict__ codes, const uint32_t *__restrict__ qinfo, const uint64_t *__restrict__ hoff,
     uint64_t xa, uint64_t xb, const uint64_t *__restrict__ off, const uint32_t *__restrict__ post, uint32_t qa,
     const uint32_t *__restrict__ bbase, const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount,
     uint64_t *__restrict__ bkeys, uint32_t bcap, uint64_t *__restrict__ spill,
     unsigned long long *__restrict__ spill_count, unsigned long long spill_cap, int qbits, int filter, uint32_t D,
-    int tpos, int fbits) {
+    int tpos, int fbits, int direct) {
     extern __shared__ __align__(16) unsigned char bf_smem[];
     uint32_t *hist = reinterpret_cast<uint32_t *>(bf_smem);
     uint32_t *base = hist + BT_SPAN;
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
         const uint32_t bmin = bmin_s;
         if (filter) {
             const uint64_t lo = t0 > xa + D ? t0 - D : xa, hi = min(xb, t1 + D);
-            for_tile_hits_dyn(lo, hi, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+            for_tile_hits_dyn<LB>(lo, hi, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
                               [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
                                   const uint32_t h = tile_hash(ql, gk, fbits);
                                   const uint32_t bit = 1u << (h & 31);
@@ -398,15 +399,16 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
             return ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
         };
         // count kept core hits per bucket (buckets outside the span are placed right away)
-        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+        for_tile_hits_dyn<LB>(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
                           [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
                               if (!kept(ql, gk)) return;
                               const uint32_t b = bb + (uint32_t)(gk >> bs);
                               const uint32_t li = b - bmin;
-                              if (li < BT_SPAN) atomicAdd(&hist[li], 1u);
+                              if (!direct && li < BT_SPAN) atomicAdd(&hist[li], 1u);
                               else put(ql, qpos, gk, b, atomicAdd(&bcount[b], 1u));
                           });
         __syncthreads();
+        if (direct) continue;  // every kept hit was placed with a global atomic (bitmaps reset at the next tile)
         for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
             const uint32_t c = hist[i];
             if (c) {
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
         }
         if (threadIdx.x == 0) blk = 0;
         __syncthreads();
-        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+        for_tile_hits_dyn<LB>(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
                           [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
                               if (!kept(ql, gk)) return;
                               const uint32_t b = bb + (uint32_t)(gk >> bs);
@@ -1383,9 +1385,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint64_t *spill = carena.alloc_n<uint64_t>(spill_room);
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
                 const size_t bf_smem = BT_SPAN * 8 + (filter ? (2u << fbits) / 8 : 0);
-                GN_CUDA(cudaFuncSetAttribute(k_bucket_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
+                int lb = 2, direct = 0;
+                if (const char *e = getenv("GN_FILL_LISTS")) lb = atoi(e) >= 4 ? 4 : (atoi(e) <= 1 ? 1 : 2);
+                if (const char *e = getenv("GN_FILL_DIRECT")) direct = atoi(e) ? 1 : 0;
+                auto fill_kernel = lb == 4 ? k_bucket_fill<4> : (lb == 1 ? k_bucket_fill<1> : k_bucket_fill<2>);
+                GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
                 int focc = 0;
-                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, k_bucket_fill, 256, bf_smem));
+                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fill_kernel, 256, bf_smem));
                 const unsigned fgrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(focc, 1) * 4));
                 unsigned long long n_spill = 0;
@@ -1393,10 +1399,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     GN_CUDA(cudaMemsetAsync(bcount, 0, 4ull * NB, s));
                     GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
                     GN_LAUNCH("k_bucket_fill", Hc, s,
-                              k_bucket_fill<<<fgrid, 256, bf_smem, s>>>(
+                              fill_kernel<<<fgrid, 256, bf_smem, s>>>(
                                   codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcount,
                                   bkeys, bcap, spill, spill_count, (unsigned long long)spill_room, qbits, filter,
-                                  p.max_hit_distance, tpos, fbits));
+                                  p.max_hit_distance, tpos, fbits, direct));
                     GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
                     if (n_spill <= spill_room) break;
