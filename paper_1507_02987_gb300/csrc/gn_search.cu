@@ -358,12 +358,13 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
     unsigned long long *__restrict__ spill_count, unsigned long long spill_cap, int qbits, int filter, uint32_t D,
     int tpos, int fbits, int direct) {
     extern __shared__ __align__(16) unsigned char bf_smem[];
-    uint32_t *hist = reinterpret_cast<uint32_t *>(bf_smem);
+    uint32_t *seen = reinterpret_cast<uint32_t *>(bf_smem);
+    uint32_t *seen2 = seen + (filter ? (1u << fbits) / 32 : 0);
+    uint32_t *hist = seen2 + (filter ? (1u << fbits) / 32 : 0);  // per-tile counts (not used with direct placement)
     uint32_t *base = hist + BT_SPAN;
-    uint32_t *seen = base + BT_SPAN;
-    uint32_t *seen2 = seen + (1u << fbits) / 32;
     __shared__ uint32_t bmin_s, blk;
-    for (int i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
+    if (!direct)
+        for (int i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
     auto put = [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t b, uint64_t slot) {
         if (slot < bcap) {
             bkeys[(uint64_t)b * bcap + slot] = (gk << 16) | qpos;
@@ -1384,10 +1385,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint64_t spill_room = std::max<uint64_t>(1u << 20, Hc / 32);
                 uint64_t *spill = carena.alloc_n<uint64_t>(spill_room);
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
-                const size_t bf_smem = BT_SPAN * 8 + (filter ? (2u << fbits) / 8 : 0);
-                int lb = 2, direct = 0;
+                int lb = 1, direct = 1;
                 if (const char *e = getenv("GN_FILL_LISTS")) lb = atoi(e) >= 4 ? 4 : (atoi(e) <= 1 ? 1 : 2);
                 if (const char *e = getenv("GN_FILL_DIRECT")) direct = atoi(e) ? 1 : 0;
+                const size_t bf_smem = (direct ? 0 : BT_SPAN * 8) + (filter ? (2u << fbits) / 8 : 0) + 16;
                 auto fill_kernel = lb == 4 ? k_bucket_fill<4> : (lb == 1 ? k_bucket_fill<1> : k_bucket_fill<2>);
                 GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
                 int focc = 0;
