@@ -45,11 +45,10 @@ BYTES_PER_UNIT = {
     "record_sort_downsweep": 24.0,
     "record_sort_upsweep": 8.0,
     "k_query_codes": 17.0,
-    # bucketing (units = raw hits): count reads each occurrence twice (filter + count; the second
-    # read hits L2), scatter reads it three times; both write little (kept hits only)
-    "k_bucket_count": 4.0,
-    "k_bucket_scatter": 4.0,
-    "k_bucket_group": 8.0,   # units = kept hits: one 8-byte key read
+    # bucket fill (units = hits): one 4-byte occurrence read per hit; the 8-byte writes of the
+    # kept hits are added from k_bucket_group's units (kept hits) in roofline()
+    "k_bucket_fill": 4.0,
+    "k_bucket_group": 8.0,   # units = kept hits: one 8-byte bucket entry read
 }
 ALU_KERNELS = {"k_banded_sw"}  # units = DP cells
 
@@ -374,14 +373,15 @@ def run_ours(args, dist):
                     "peak": None, "frac": None, "traffic": None}
         else:
             bpu = BYTES_PER_UNIT.get(name)
-            achieved = (un * bpu) / (ms / 1e3) / 1e9 if bpu else None
+            extra = 8.0 * kern["k_bucket_group"][2] if (name == "k_bucket_fill" and "k_bucket_group" in kern) else 0.0
+            achieved = (un * bpu + extra) / (ms / 1e3) / 1e9 if bpu else None
             peak = peaks.get("hbm_gbs")
             tpu = ncu_traffic(name)
             roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
                     "peak_source": "measured" if peak else None, "unit": "GB/s",
                     "frac": (achieved / peak) if (achieved and peak) else None,
                     "traffic": (tpu * un / la) if tpu else None,
-                    "algorithmic_bytes_per_launch": (un * bpu / la) if bpu else None,
+                    "algorithmic_bytes_per_launch": ((un * bpu + extra) / la) if bpu else None,
                     "avg_launch_ms": ms / la, "launches": la}
     kernels_out = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                        "units_per_step": v[2] / args.steps} for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}

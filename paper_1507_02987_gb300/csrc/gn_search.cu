@@ -271,10 +271,10 @@ __device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk, int fbit
 }
 
 // Like for_tile_hits, but warps take 32-offset blocks of [p0, p1) from a shared
-// counter (reset by the caller between passes), which balances uneven lists, and
-// the occurrence lists are walked LB at a time so that LB lists' loads are in flight
-// together.
-template <int LB, class F>
+// counter (reset by the caller between passes), which balances uneven lists, and f
+// receives a lane's four list entries of a round at once (gk[4], valid[4]) so that
+// it can issue their memory operations back to back.
+template <class F>
 __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint32_t *blk,
                                                   const uint32_t *__restrict__ codes,
                                                   const uint32_t *__restrict__ qinfo,
@@ -289,8 +289,7 @@ __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint
         if (lane == 0) kb = atomicAdd(blk, 1u);
         kb = __shfl_sync(0xffffffffu, kb, 0);
         if (kb >= nblk) break;
-        const uint64_t x0 = p0 + (uint64_t)kb * 32;
-        const uint64_t x = x0 + lane;
+        const uint64_t x = p0 + (uint64_t)kb * 32 + lane;
         uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
         uint64_t my_src = 0;
         if (x < p1) {
@@ -305,38 +304,23 @@ __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint
         }
         uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
         while (todo) {
-            uint32_t cnt[LB], qpos[LB], ql[LB], bb[LB], bs[LB];
-            uint64_t sp[LB];
-            uint32_t cmax = 0;
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
+            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
+            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
+            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
+            const uint32_t bb = bbase[ql], bs = bshift[ql];
+            for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
+                uint64_t gk[4];
+                bool ok[4];
 #pragma unroll
-            for (int l = 0; l < LB; ++l) {
-                const int src = todo ? __ffs(todo) - 1 : 0;
-                const bool has = todo != 0;
-                if (has) todo &= todo - 1;
-                cnt[l] = has ? __shfl_sync(0xffffffffu, my_cnt, src) : 0u;
-                sp[l] = __shfl_sync(0xffffffffu, my_src, src);
-                qpos[l] = __shfl_sync(0xffffffffu, my_qpos, src);
-                ql[l] = __shfl_sync(0xffffffffu, my_ql, src);
-                bb[l] = bbase[ql[l]];
-                bs[l] = bshift[ql[l]];
-                cmax = max(cmax, cnt[l]);
-            }
-            for (uint32_t j0 = 0; j0 < cmax; j0 += 128) {
-                uint32_t g[LB][4];
-#pragma unroll
-                for (int l = 0; l < LB; ++l)
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t j = j0 + u * 32 + lane;
-                        g[l][u] = j < cnt[l] ? post[sp[l] + j] : 0u;
-                    }
-#pragma unroll
-                for (int l = 0; l < LB; ++l)
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t j = j0 + u * 32 + lane;
-                        if (j < cnt[l]) f(ql[l], qpos[l], (uint64_t)g[l][u] + QBIAS - qpos[l], bb[l], bs[l]);
-                    }
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t j = j0 + u * 32 + lane;
+                    ok[u] = j < cnt;
+                    gk[u] = (uint64_t)(ok[u] ? post[sp + j] : 0u) + QBIAS - qpos;
+                }
+                f(ql, qpos, gk, ok, bb, bs);
             }
         }
     }
@@ -349,15 +333,15 @@ __device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint
 // fixed capacity bcap; hits past it (and hits of buckets outside the tile's
 // shared-memory span, if any overflow) go to the spill list in global hit-key
 // format, which the global sort path handles.
-template <int LB>
 __global__ void __launch_bounds__(256) k_bucket_fill(
     const uint32_t *__restrict__ codes, const uint32_t *__restrict__ qinfo, const uint64_t *__restrict__ hoff,
     uint64_t xa, uint64_t xb, const uint64_t *__restrict__ off, const uint32_t *__restrict__ post, uint32_t qa,
     const uint32_t *__restrict__ bbase, const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount,
     uint64_t *__restrict__ bkeys, uint32_t bcap, uint64_t *__restrict__ spill,
     unsigned long long *__restrict__ spill_count, unsigned long long spill_cap, int qbits, int filter, uint32_t D,
-    int tpos, int fbits, int direct) {
+    int tpos, int fbits, int direct, unsigned long long *__restrict__ kept_total) {
     extern __shared__ __align__(16) unsigned char bf_smem[];
+    uint32_t my_kept = 0;
     uint32_t *seen = reinterpret_cast<uint32_t *>(bf_smem);
     uint32_t *seen2 = seen + (filter ? (1u << fbits) / 32 : 0);
     uint32_t *hist = seen2 + (filter ? (1u << fbits) / 32 : 0);  // per-tile counts (not used with direct placement)
@@ -383,12 +367,17 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
         const uint32_t bmin = bmin_s;
         if (filter) {
             const uint64_t lo = t0 > xa + D ? t0 - D : xa, hi = min(xb, t1 + D);
-            for_tile_hits_dyn<LB>(lo, hi, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                              [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
-                                  const uint32_t h = tile_hash(ql, gk, fbits);
-                                  const uint32_t bit = 1u << (h & 31);
-                                  const uint32_t old = atomicOr(&seen[h >> 5], bit);
-                                  if (old & bit) atomicOr(&seen2[h >> 5], bit);
+            for_tile_hits_dyn(lo, hi, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                              [&](uint32_t ql, uint32_t qpos, const uint64_t *gk, const bool *ok, uint32_t bb,
+                                  uint32_t bs) {
+#pragma unroll
+                                  for (int u = 0; u < 4; ++u) {
+                                      if (!ok[u]) continue;
+                                      const uint32_t h = tile_hash(ql, gk[u], fbits);
+                                      const uint32_t bit = 1u << (h & 31);
+                                      const uint32_t old = atomicOr(&seen[h >> 5], bit);
+                                      if (old & bit) atomicOr(&seen2[h >> 5], bit);
+                                  }
                               });
             __syncthreads();
             if (threadIdx.x == 0) blk = 0;
@@ -400,13 +389,27 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
             return ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
         };
         // count kept core hits per bucket (buckets outside the span are placed right away)
-        for_tile_hits_dyn<LB>(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
-                              if (!kept(ql, gk)) return;
-                              const uint32_t b = bb + (uint32_t)(gk >> bs);
-                              const uint32_t li = b - bmin;
-                              if (!direct && li < BT_SPAN) atomicAdd(&hist[li], 1u);
-                              else put(ql, qpos, gk, b, atomicAdd(&bcount[b], 1u));
+        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                          [&](uint32_t ql, uint32_t qpos, const uint64_t *gk, const bool *ok, uint32_t bb,
+                              uint32_t bs) {
+                              uint32_t b[4], slot[4];
+                              bool glob[4];
+#pragma unroll
+                              for (int u = 0; u < 4; ++u) {
+                                  const bool kk = ok[u] && kept(ql, gk[u]);
+                                  my_kept += kk ? 1u : 0u;
+                                  b[u] = bb + (uint32_t)(gk[u] >> bs);
+                                  const uint32_t li = b[u] - bmin;
+                                  glob[u] = kk && (direct || li >= BT_SPAN);
+                                  if (kk && !glob[u]) atomicAdd(&hist[li], 1u);
+                              }
+                              // the global slot reservations first, then the dependent stores
+#pragma unroll
+                              for (int u = 0; u < 4; ++u)
+                                  if (glob[u]) slot[u] = atomicAdd(&bcount[b[u]], 1u);
+#pragma unroll
+                              for (int u = 0; u < 4; ++u)
+                                  if (glob[u]) put(ql, qpos, gk[u], b[u], slot[u]);
                           });
         __syncthreads();
         if (direct) continue;  // every kept hit was placed with a global atomic (bitmaps reset at the next tile)
@@ -419,17 +422,23 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
         }
         if (threadIdx.x == 0) blk = 0;
         __syncthreads();
-        for_tile_hits_dyn<LB>(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                          [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t bb, uint32_t bs) {
-                              if (!kept(ql, gk)) return;
-                              const uint32_t b = bb + (uint32_t)(gk >> bs);
-                              const uint32_t li = b - bmin;
-                              if (li < BT_SPAN) put(ql, qpos, gk, b, (uint64_t)base[li] + atomicAdd(&hist[li], 1u));
+        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
+                          [&](uint32_t ql, uint32_t qpos, const uint64_t *gk, const bool *ok, uint32_t bb,
+                              uint32_t bs) {
+#pragma unroll
+                              for (int u = 0; u < 4; ++u) {
+                                  if (!ok[u] || !kept(ql, gk[u])) continue;
+                                  const uint32_t b = bb + (uint32_t)(gk[u] >> bs);
+                                  const uint32_t li = b - bmin;
+                                  if (li < BT_SPAN)
+                                      put(ql, qpos, gk[u], b, (uint64_t)base[li] + atomicAdd(&hist[li], 1u));
+                              }
                           });
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
         __syncthreads();
     }
+    if (my_kept) atomicAdd(kept_total, (unsigned long long)my_kept);
 }
 
 __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc, uint32_t NB,
@@ -1389,22 +1398,26 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 if (const char *e = getenv("GN_FILL_LISTS")) lb = atoi(e) >= 4 ? 4 : (atoi(e) <= 1 ? 1 : 2);
                 if (const char *e = getenv("GN_FILL_DIRECT")) direct = atoi(e) ? 1 : 0;
                 const size_t bf_smem = (direct ? 0 : BT_SPAN * 8) + (filter ? (2u << fbits) / 8 : 0) + 16;
-                auto fill_kernel = lb == 4 ? k_bucket_fill<4> : (lb == 1 ? k_bucket_fill<1> : k_bucket_fill<2>);
+                (void)lb;
+                auto fill_kernel = k_bucket_fill;
                 GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
                 int focc = 0;
                 GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fill_kernel, 256, bf_smem));
                 const unsigned fgrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(focc, 1) * 4));
-                unsigned long long n_spill = 0;
+                unsigned long long n_spill = 0, n_kept = 0;
+                unsigned long long *kept_total = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
                 for (int attempt = 0; attempt < 2; ++attempt) {
                     GN_CUDA(cudaMemsetAsync(bcount, 0, 4ull * NB, s));
                     GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
+                    GN_CUDA(cudaMemsetAsync(kept_total, 0, 8, s));
                     GN_LAUNCH("k_bucket_fill", Hc, s,
                               fill_kernel<<<fgrid, 256, bf_smem, s>>>(
                                   codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcount,
                                   bkeys, bcap, spill, spill_count, (unsigned long long)spill_room, qbits, filter,
-                                  p.max_hit_distance, tpos, fbits, direct));
+                                  p.max_hit_distance, tpos, fbits, direct, kept_total));
                     GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
+                    GN_CUDA(cudaMemcpyAsync(&n_kept, kept_total, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
                     if (n_spill <= spill_room) break;
                     spill_room = n_spill;  // rerun with room for every spilled hit
@@ -1432,7 +1445,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     emit([&](DevHsp *o, uint32_t room) {
                         GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
                         GN_CUDA(cudaMemsetAsync(counter + 1, 0, 4, s));
-                        GN_LAUNCH("k_bucket_group", Hc, s,
+                        GN_LAUNCH("k_bucket_group", n_kept, s,
                                   k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
                                       bkeys, bcount, bcap, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len,
                                       singles, ix->seq_start_d, ix->n_seqs, o, counter, room, gsp + spilled_fill,
