@@ -65,6 +65,11 @@ def parse_args():
     ap.add_argument("--plain-queries", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle time of the CPU baseline")
     ap.add_argument("--queries", type=int, default=0, help="use only the first N queries (profiling runs)")
+    ap.add_argument("--serve-rates", default="50,200,2000,max",
+                    help="Poisson arrival rates (queries/s) of the serving leg ('max': every request arrives "
+                         "at once, a saturation run of all requests); empty to skip it")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
+    ap.add_argument("--serve-budget-gib", type=float, default=16.0, help="server memory budget")
     return ap.parse_args()
 
 
@@ -217,6 +222,98 @@ def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0):
         n = min(queries.n, max(n + 1, int(n * min(8.0, max(2.0, target_s / max(dt, 1e-3))))))
 
 
+def percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
+    """Open-loop run of the request loop: submits reqs[i] at t0 + arrivals[i], collects results from
+    the completion queue on another thread.  Latency = result on the host - scheduled arrival."""
+    srv = gn.Server(ix, budget)
+    n = len(reqs)
+    done_at = {}
+
+    def collector():
+        end = time.perf_counter() + timeout_s
+        while len(done_at) < n and time.perf_counter() < end:
+            got = srv.poll_any(200)
+            if got is None:
+                continue
+            t, res = got
+            done_at[t] = time.perf_counter()
+            res.close()
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for i in range(n):
+        wait = t0 + float(arrivals[i]) - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append(srv.submit(reqs[i]))
+    th.join(timeout_s)
+    stats = srv.stats()
+    srv.stop()
+    lat = [1e3 * (done_at[t] - (t0 + float(arrivals[i]))) for i, t in enumerate(tickets) if t in done_at]
+    wall = (max(done_at.values()) - t0) if done_at else float("nan")
+    return {"requests": n, "completed": len(lat), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+            "kbp_s": sum(len(r) for r in reqs) / 1e3 / wall, "batches": stats["batches"],
+            "max_batch": stats["max_batch"], "max_concurrent_batches": stats["max_concurrent"]}
+
+
+def plain_leg(gn, ix, reqs, arrivals, stream):
+    """The same arrivals served by the plain path: one gn_search per query, in arrival order, with host
+    queries and host results."""
+    import numpy as np
+    t0 = time.perf_counter()
+    lat = []
+    for i, q in enumerate(reqs):
+        wait = t0 + float(arrivals[i]) - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        st = np.array([0, len(q)], dtype=np.uint64)
+        gn.search(ix, st, np.frombuffer(q, dtype=np.uint8), stream=stream).close()
+        lat.append(1e3 * (time.perf_counter() - (t0 + float(arrivals[i]))))
+    wall = time.perf_counter() - t0
+    return {"requests": len(reqs), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+            "kbp_s": sum(len(r) for r in reqs) / 1e3 / wall}
+
+
+def serving(args, gn, ix, bank, stream, log):
+    """Serving leg: open-loop Poisson arrivals of the serving request mix against the resident index,
+    through the request loop and through the plain path, at each rate."""
+    import numpy as np
+    import synth
+    rates = [r.strip() for r in args.serve_rates.split(",") if r.strip()]
+    if not rates or args.workload != "large":
+        return None
+    spec = synth.QUERIES["serving"]
+    qs = synth.make_queries(spec, bank)
+    reqs = [qs.query(i) for i in range(qs.n)]
+    budget = int(args.serve_budget_gib * 2**30)
+    out = {"requests_from": f"{qs.n} requests, log-uniform 50-20,000 bp, 30% planted homologs",
+           "budget_gib": args.serve_budget_gib, "rates": []}
+    for r in rates:
+        if r == "max":
+            rate, n = None, len(reqs)
+            arr = np.zeros(n)
+        else:
+            rate = float(r)
+            n = int(min(len(reqs), max(50, rate * args.serve_seconds)))
+            arr = synth.poisson_arrivals(rate, n, seed=spec.seed + int(rate))
+        served = serve_leg(gn, ix, reqs[:n], arr, budget)
+        n_plain = min(n, 1000)
+        plain = plain_leg(gn, ix, reqs[:n_plain], arr[:n_plain], stream)
+        log(f"serving at {r} q/s: served {served['kbp_s']:.0f} kbp/s p50 {served['p50_ms']:.1f} ms "
+            f"p99 {served['p99_ms']:.1f} ms; plain {plain['kbp_s']:.0f} kbp/s p50 {plain['p50_ms']:.1f} ms "
+            f"p99 {plain['p99_ms']:.1f} ms")
+        out["rates"].append({"rate_qps": rate if rate is not None else "max (all at t=0)",
+                             "served": served, "plain": plain})
+    return out
+
+
 # ----------------------------------------------------------------- arms --
 def run_reference(args, dist):
     if dist.rank != 0:
@@ -362,6 +459,9 @@ def run_ours(args, dist):
         plain = {"value": int(sub.start[-1]) / 1e3 / dt, "unit": UNIT,
                  "sample": f"{sub.n} evenly spaced queries, one gn_search call per query"}
 
+    # ---- serving: Poisson arrivals through the request loop and through the plain path
+    serve = serving(args, gn, ix, bank, sh, log) if dist.rank == 0 else None
+
     # ---- roofline of the dominant kernel
     peaks = measured_peaks()
     dom = max(kern.items(), key=lambda kv: kv[1][0]) if kern else None
@@ -413,12 +513,14 @@ def run_ours(args, dist):
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": desc, "bank_bases": bank.n_bases, "bank_seqs": bank.n_seqs,
                            "n_queries": queries.n, "query_bases_per_rank": M, "k": 11, "stride": args.stride,
-                           "hits_per_step": kern.get("k_seed_gather", [0, 0, 0])[2] / max(1, args.steps),
+                           "hits_per_step": (kern.get("k_bucket_fill") or kern.get("k_seed_gather") or [0, 0, 0])[2]
+                           / max(1, args.steps),
                            "parallelism": f"replicas x{dist.world}",
                            "l2": "inputs larger than L2 (postings and hit keys are GBs per step); no flush"},
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / max(1, args.steps), "roofline": roof,
-                "cpu_baseline": cpu, "plain_per_query": plain, "oracle_parity_on_sample": parity,
+                "cpu_baseline": cpu, "plain_per_query": plain, "serving": serve,
+                "oracle_parity_on_sample": parity,
                 "index_build": {"seconds": t_index, "bank_gbp_per_s": bank.n_bases / 1e9 / t_index,
                                 "postings": info.n_postings, "device_gib": info.device_bytes / 2**30,
                                 "includes": "host-to-device copy of the bank + pack + windows + scan + sort"},

@@ -201,19 +201,39 @@ GN_API uint64_t gn_kernel_launch_count(void);
 
 /* ----------------------------------------------------------- serving ---
  * Request loop with continuous batching (the paper's web-services interface,
- * "Implementation" section, as a resident-index service).  A server thread
- * admits submitted queries while their footprint (hit buffer + alignment
- * bytes) fits mem_budget, launches them as a micro-batch on one of its streams
- * while earlier micro-batches still run, and makes each result available to
- * gn_serve_poll.  Each query's result is identical to a gn_search of that query
- * alone. */
+ * "Implementation" section, as a resident-index service).  Three worker
+ * threads, each with its own CUDA stream, take submitted queries in arrival
+ * order while their footprint fits mem_budget, run them as one micro-batch
+ * (a gn_search on that worker's stream) while other micro-batches still run,
+ * and make each result available to gn_serve_poll / gn_serve_poll_any.
+ * A query's footprint is its exact hit count (from the index's bucket starts)
+ * times 24 bytes, plus 64 bytes per base, 16 KiB of hit buckets and the
+ * records of its selected HSPs; each micro-batch also counts 16 MiB of fixed
+ * device memory.  Each query's result is identical to a gn_search of that
+ * query alone.  mem_budget must exceed 16 MiB (GN_EINVAL otherwise). */
 GN_API gn_status gn_serve_start(const gn_index *index, const gn_scoring *scoring, const gn_params *params,
                          uint64_t mem_budget, gn_server **out);
 /* Thread-safe; copies the query.  GN_ETOOBIG if the query alone exceeds the budget. */
 GN_API gn_status gn_serve_submit(gn_server *server, const char *bases, uint32_t len, uint64_t *ticket);
-/* Waits up to timeout_ms; GN_ETIMEOUT if not done yet.  On GN_OK *out holds a
- * one-query result owned by the caller (gn_results_free). */
+/* Waits up to timeout_ms for the given ticket; GN_ETIMEOUT if not done yet.  On
+ * GN_OK *out holds a one-query result owned by the caller (gn_results_free).  A
+ * failed micro-batch returns GN_ECUDA for each of its tickets. */
 GN_API gn_status gn_serve_poll(gn_server *server, uint64_t ticket, uint32_t timeout_ms, gn_results **out);
+/* Completion queue: waits up to timeout_ms for any finished ticket and returns
+ * the oldest one in *ticket (GN_ETIMEOUT and *ticket = 0 if none finished).  On
+ * GN_OK *out holds its one-query result; on GN_ECUDA that ticket failed. */
+GN_API gn_status gn_serve_poll_any(gn_server *server, uint32_t timeout_ms, uint64_t *ticket, gn_results **out);
+/* Counters of a server since its start (for monitoring and tests). */
+typedef struct {
+    uint64_t requests;        /* queries admitted to micro-batches */
+    uint64_t batches;         /* micro-batches launched */
+    uint64_t max_batch;       /* most queries in one micro-batch */
+    uint64_t max_concurrent;  /* most micro-batches in flight at once */
+    uint64_t peak_in_use;     /* most budget bytes admitted at once */
+    uint64_t in_use;          /* budget bytes admitted now */
+    uint64_t queued;          /* submitted queries not admitted yet */
+} gn_serve_stats;
+GN_API gn_status gn_serve_get_stats(gn_server *server, gn_serve_stats *out);
 /* Finishes admitted work, rejects new submissions, joins the server thread, frees the server. */
 GN_API gn_status gn_serve_stop(gn_server *server);
 

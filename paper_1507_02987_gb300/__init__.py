@@ -58,6 +58,11 @@ class gn_params(ctypes.Structure):
                 ("max_evalue", ctypes.c_double), ("flags", ctypes.c_uint32)]
 
 
+class gn_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "batches", "max_batch", "max_concurrent",
+                                                 "peak_in_use", "in_use", "queued")]
+
+
 class gn_index_info(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("stride", ctypes.c_int32), ("n_seqs", ctypes.c_uint32),
                 ("n_bases", ctypes.c_uint64), ("n_postings", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
@@ -108,6 +113,8 @@ def load():
                                     ctypes.POINTER(vp)]),
             "gn_serve_submit": (st, [vp, ctypes.c_char_p, u32, ctypes.POINTER(u64)]),
             "gn_serve_poll": (st, [vp, u64, u32, ctypes.POINTER(vp)]),
+            "gn_serve_poll_any": (st, [vp, u32, ctypes.POINTER(u64), ctypes.POINTER(vp)]),
+            "gn_serve_get_stats": (st, [vp, ctypes.POINTER(gn_serve_stats)]),
             "gn_serve_stop": (st, [vp]),
             "gn_align_hsps_static": (st, [vp, vp, vp, u32, vp, u32, ctypes.POINTER(gn_scoring), u32, vp, vp]),
             "gn_last_error": (ctypes.c_char_p, []),
@@ -235,6 +242,24 @@ def gn_serve_poll(s: int, ticket: int, timeout_ms: int):
     return r.value
 
 
+def gn_serve_poll_any(s: int, timeout_ms: int):
+    """(ticket, results handle) of the oldest finished request, or None on GN_ETIMEOUT.
+    A failed request raises GnError."""
+    r = ctypes.c_void_p()
+    t = ctypes.c_uint64()
+    st = load().gn_serve_poll_any(ctypes.c_void_p(s), timeout_ms, ctypes.byref(t), ctypes.byref(r))
+    if st == GN_ETIMEOUT:
+        return None
+    _check(st)
+    return t.value, r.value
+
+
+def gn_serve_get_stats(s: int) -> dict:
+    o = gn_serve_stats()
+    _check(load().gn_serve_get_stats(ctypes.c_void_p(s), ctypes.byref(o)))
+    return {n: int(getattr(o, n)) for n, _ in gn_serve_stats._fields_}
+
+
 def gn_serve_stop(s: int):
     _check(load().gn_serve_stop(ctypes.c_void_p(s)))
 
@@ -359,6 +384,42 @@ class Results:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A request loop over a resident index (gn_serve_*); results are Results of one query."""
+
+    def __init__(self, index: Index, mem_budget: int, scoring: gn_scoring | None = None,
+                 params: gn_params | None = None):
+        self.index = index  # keeps the index alive while the server runs
+        sc = scoring if scoring is not None else make_scoring()
+        p = params if params is not None else make_params()
+        self.handle = gn_serve_start(index.handle, sc, p, mem_budget)
+
+    def submit(self, bases) -> int:
+        return gn_serve_submit(self.handle, bytes(bases))
+
+    def poll(self, ticket: int, timeout_ms: int = 60000):
+        h = gn_serve_poll(self.handle, ticket, timeout_ms)
+        return None if h is None else Results(h)
+
+    def poll_any(self, timeout_ms: int = 60000):
+        got = gn_serve_poll_any(self.handle, timeout_ms)
+        return None if got is None else (got[0], Results(got[1]))
+
+    def stats(self) -> dict:
+        return gn_serve_get_stats(self.handle)
+
+    def stop(self):
+        if getattr(self, "handle", None):
+            gn_serve_stop(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass
 

@@ -87,18 +87,44 @@ struct gn_server {
     std::map<uint64_t, std::string> failed;
     uint64_t next_ticket = 1;
     std::vector<std::thread> workers;
+    std::vector<uint64_t> off_h;  // host copy of the bucket starts: exact hit counts for admission
     int device = 0;
+    gn_serve_stats stats{};
+    uint64_t running = 0;  // micro-batches on the device now
 };
 
 namespace gn {
-static uint64_t footprint_of(const gn_index *ix, const SearchOptions &o, uint64_t len) {
-    // expected hits (mean list length, with a margin for skewed lists) x 16 bytes of keys, plus the
-    // alignment strips of the selected HSPs and per-offset arrays
-    double mean_list = (double)ix->n_postings / (double)(1ull << (2 * ix->k));
-    double hits = (double)len * std::max(1.0, mean_list) * 4.0;
-    double sw = (double)std::max<uint32_t>(o.p.max_alignments ? o.p.max_alignments : 1000, 1) *
-                (2.0 * o.p.band_w + 2.0) * 16.0;
-    return (uint64_t)(hits * 16.0 + sw + (double)len * 32.0) + (1u << 20);
+// Device bytes one batch needs besides its queries' own footprints (initial HSP and spill
+// buffers, counters, scan scratch).
+constexpr uint64_t BATCH_FIXED_BYTES = 16ull << 20;
+
+static int host_base(char c) {
+    switch (c) {
+        case 'A': case 'a': return 0;
+        case 'C': case 'c': return 1;
+        case 'G': case 'g': return 2;
+        case 'T': case 't': case 'U': case 'u': return 3;
+        default: return -1;
+    }
+}
+
+// Admission footprint of one query: its exact hit count (from the bucket starts) times the bytes
+// a chunk budgets per hit, its per-offset arrays, its smallest set of hit buckets (two of 1,024
+// entries), and the alignment records of its selected HSPs.
+static uint64_t footprint_of(const gn_server *sv, const char *bases, uint32_t len) {
+    const int k = sv->ix->k;
+    const uint32_t mask = (uint32_t)((1ull << (2 * k)) - 1ull);
+    uint64_t hits = 0;
+    uint32_t code = 0;
+    int valid = 0;  // bases since the last non-base
+    for (uint32_t i = 0; i < len; ++i) {
+        const int b = host_base(bases[i]);
+        if (b < 0) { valid = 0; code = 0; continue; }
+        code = ((code << 2) | (uint32_t)b) & mask;
+        if (++valid >= k) hits += sv->off_h[code + 1] - sv->off_h[code];
+    }
+    const uint64_t n_sel = sv->opt.p.max_alignments ? sv->opt.p.max_alignments : 4096;
+    return hits * HIT_BYTES + (uint64_t)len * 64 + 2 * 1024 * 8 + n_sel * (64 + 16 * (2ull * sv->opt.p.band_w + 2));
 }
 
 static void serve_worker(gn_server *sv) {
@@ -114,10 +140,12 @@ static void serve_worker(gn_server *sv) {
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv_work.wait(lk, [&] {
                 return (sv->stopping && sv->queue.empty()) ||
-                       (!sv->queue.empty() && sv->in_use + sv->queue.front().footprint <= sv->budget);
+                       (!sv->queue.empty() &&
+                        sv->in_use + BATCH_FIXED_BYTES + sv->queue.front().footprint <= sv->budget);
             });
             if (sv->queue.empty()) break;
             // admit arrivals in order while they fit the memory budget (continuous batching)
+            taken = BATCH_FIXED_BYTES;
             while (!sv->queue.empty() && batch.size() < MAX_QUERIES &&
                    sv->in_use + taken + sv->queue.front().footprint <= sv->budget) {
                 taken += sv->queue.front().footprint;
@@ -125,6 +153,12 @@ static void serve_worker(gn_server *sv) {
                 sv->queue.pop_front();
             }
             sv->in_use += taken;
+            sv->stats.batches += 1;
+            sv->stats.requests += batch.size();
+            sv->stats.max_batch = std::max<uint64_t>(sv->stats.max_batch, batch.size());
+            sv->running += 1;
+            sv->stats.max_concurrent = std::max(sv->stats.max_concurrent, sv->running);
+            sv->stats.peak_in_use = std::max(sv->stats.peak_in_use, sv->in_use);
         }
         std::vector<uint64_t> qstart(batch.size() + 1, 0);
         for (size_t i = 0; i < batch.size(); ++i) qstart[i + 1] = qstart[i] + batch[i].bases.size();
@@ -142,7 +176,9 @@ static void serve_worker(gn_server *sv) {
             host.reserve(M);
             for (auto &r : batch) host += r.bases;
             if (M) GN_CUDA(cudaMemcpyAsync(dbuf, host.data(), M, cudaMemcpyHostToDevice, s));
-            search(const_cast<gn_index *>(sv->ix), dbuf, qstart, sv->opt, s, &all);
+            SearchOptions o = sv->opt;
+            o.mem_cap = taken - BATCH_FIXED_BYTES;  // the hit storage stays inside what was admitted
+            search(const_cast<gn_index *>(sv->ix), dbuf, qstart, o, s, &all);
         });
         if (st != GN_OK) err = g_last_error;
         {
@@ -160,6 +196,7 @@ static void serve_worker(gn_server *sv) {
                 sv->done[batch[i].ticket] = r;
             }
             sv->in_use -= taken;
+            sv->running -= 1;
         }
         sv->cv_done.notify_all();
         sv->cv_work.notify_all();
@@ -341,9 +378,13 @@ gn_status gn_serve_start(const gn_index *ix, const gn_scoring *sc, const gn_para
     gn_status st = guarded([&] {
         resolve(ix, sc, p, sv->opt);
         sv->opt.p.flags &= ~(GN_FLAG_KEEP_STAGES | GN_FLAG_KEEP_HITS);
+        GN_REQUIRE(mem_budget > BATCH_FIXED_BYTES, GN_EINVAL, "mem_budget must exceed 16 MiB");
         sv->ix = ix;
         sv->budget = mem_budget;
         sv->device = ix->device;
+        GN_CUDA(cudaSetDevice(ix->device));
+        sv->off_h.resize((1ull << (2 * ix->k)) + 1);
+        GN_CUDA(cudaMemcpy(sv->off_h.data(), ix->off_d, 8 * sv->off_h.size(), cudaMemcpyDeviceToHost));
         for (int w = 0; w < 3; ++w) sv->workers.emplace_back(serve_worker, sv);
     });
     if (st != GN_OK) { delete sv; return st; }
@@ -354,8 +395,11 @@ gn_status gn_serve_start(const gn_index *ix, const gn_scoring *sc, const gn_para
 gn_status gn_serve_submit(gn_server *sv, const char *bases, uint32_t len, uint64_t *ticket) {
     if (!sv || !ticket || (len && !bases)) { g_last_error = "server, bases and ticket are required"; return GN_EINVAL; }
     if (len > MAX_QUERY_LEN) { g_last_error = "a query holds 65,536 bases or more"; return GN_ETOOBIG; }
-    uint64_t fp = footprint_of(sv->ix, sv->opt, len);
-    if (fp > sv->budget) { g_last_error = "the query alone exceeds the server's memory budget"; return GN_ETOOBIG; }
+    const uint64_t fp = footprint_of(sv, bases, len);
+    if (fp + BATCH_FIXED_BYTES > sv->budget) {
+        g_last_error = "the query alone exceeds the server's memory budget";
+        return GN_ETOOBIG;
+    }
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stopping) { g_last_error = "server is stopping"; return GN_EBUSY; }
@@ -390,6 +434,43 @@ gn_status gn_serve_poll(gn_server *sv, uint64_t ticket, uint32_t timeout_ms, gn_
     *out = it->second;
     sv->done.erase(it);
     g_last_error.clear();
+    return GN_OK;
+}
+
+gn_status gn_serve_poll_any(gn_server *sv, uint32_t timeout_ms, uint64_t *ticket, gn_results **out) {
+    if (!sv || !out || !ticket) { g_last_error = "server, ticket and out are required"; return GN_EINVAL; }
+    *out = nullptr;
+    *ticket = 0;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto ready = [&] { return !sv->done.empty() || !sv->failed.empty(); };
+    if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+        g_last_error = "nothing done yet";
+        return GN_ETIMEOUT;
+    }
+    // the oldest finished ticket first
+    const bool take_failed = sv->done.empty() ||
+                             (!sv->failed.empty() && sv->failed.begin()->first < sv->done.begin()->first);
+    if (take_failed) {
+        auto f = sv->failed.begin();
+        *ticket = f->first;
+        g_last_error = f->second;
+        sv->failed.erase(f);
+        return GN_ECUDA;
+    }
+    auto it = sv->done.begin();
+    *ticket = it->first;
+    *out = it->second;
+    sv->done.erase(it);
+    g_last_error.clear();
+    return GN_OK;
+}
+
+gn_status gn_serve_get_stats(gn_server *sv, gn_serve_stats *out) {
+    if (!sv || !out) { g_last_error = "server and out are required"; return GN_EINVAL; }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    out->in_use = sv->in_use;
+    out->queued = sv->queue.size();
     return GN_OK;
 }
 

@@ -85,6 +85,7 @@ enum : uint32_t {
 constexpr uint32_t QBIAS = 65536;          // > any query offset: diagonal key = gpos - qpos + QBIAS > 0
 constexpr uint32_t MAX_QUERY_LEN = 65535;
 constexpr uint32_t MAX_QUERIES = 65536;
+constexpr uint64_t HIT_BYTES = 24;  // device bytes budgeted per raw hit of a query chunk
 
 // --------------------------------------------------------- device memory --
 // Stream-ordered allocations from the device's default memory pool.
@@ -240,7 +241,8 @@ void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq
 
 struct SearchOptions {
     gn_scoring sc;
-    gn_params p;      // resolved (no zero defaults left)
+    gn_params p;           // resolved (no zero defaults left)
+    uint64_t mem_cap = 0;  // device bytes the hit storage of one query chunk may take (0: 55 % of free)
 };
 // Device-resident query set: bases (ASCII) on the device, starts on the host.
 void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart, const SearchOptions &o,

@@ -1265,7 +1265,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     GN_CUDA(cudaMemGetInfo(&free_b, &total_b));
     // bytes per hit of a chunk: hit keys and their ping-pong buffer on the sort path, or the
     // fixed-capacity buckets (up to ~22 B per hit without the repeat filter) and spill lists
-    uint64_t hit_budget = std::max<uint64_t>(1ull << 20, (uint64_t)(free_b * 0.55) / 24);
+    uint64_t mem_for_hits = (uint64_t)(free_b * 0.55);
+    if (o.mem_cap) mem_for_hits = std::min(mem_for_hits, o.mem_cap);
+    uint64_t hit_budget = std::max<uint64_t>(1ull << 20, mem_for_hits / HIT_BYTES);
     if (const char *e = getenv("GN_MAX_CHUNK_HITS")) {  // smaller chunks (exercises the multi-chunk path)
         uint64_t v = strtoull(e, nullptr, 10);
         if (v) hit_budget = v;
@@ -1273,7 +1275,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     const uint64_t gbits_max = (uint64_t)bits_for(ix->n_bases + QBIAS);
     const uint32_t max_chunk_q = (uint32_t)std::min<uint64_t>(MAX_QUERIES, 1ull << std::min<uint64_t>(48 - gbits_max, 31));
 
-    uint32_t hsp_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(1u << 20, hq[nq] / 128));
+    uint32_t hsp_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(1u << 16, hq[nq] / 128));
     DevHsp *hsp = arena.alloc_n<DevHsp>(hsp_cap);
     uint32_t n_hsp = 0;
     uint32_t *counter = arena.alloc_n<uint32_t>(4);
@@ -1391,14 +1393,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint64_t *bkeys = carena.alloc_n<uint64_t>((uint64_t)NB * bcap);
                 uint16_t *bq = carena.alloc_n<uint16_t>(NB);
                 unsigned long long *spill_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
-                uint64_t spill_room = std::max<uint64_t>(1u << 20, Hc / 32);
+                uint64_t spill_room = std::max<uint64_t>(1u << 16, Hc / 32);
                 uint64_t *spill = carena.alloc_n<uint64_t>(spill_room);
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
-                int lb = 1, direct = 1;
-                if (const char *e = getenv("GN_FILL_LISTS")) lb = atoi(e) >= 4 ? 4 : (atoi(e) <= 1 ? 1 : 2);
+                // direct placement: one global slot atomic per kept hit; 0 aggregates per (tile, bucket)
+                int direct = 1;
                 if (const char *e = getenv("GN_FILL_DIRECT")) direct = atoi(e) ? 1 : 0;
                 const size_t bf_smem = (direct ? 0 : BT_SPAN * 8) + (filter ? (2u << fbits) / 8 : 0) + 16;
-                (void)lb;
                 auto fill_kernel = k_bucket_fill;
                 GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
                 int focc = 0;
@@ -1434,7 +1435,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const unsigned ggrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>((NB + BGW_WARPS - 1) / BGW_WARPS, (uint64_t)num_sms() * std::max(occ, 1)));
                 const uint64_t spilled_fill = n_spill;
-                uint64_t group_room = std::max<uint64_t>(1u << 20, Hc / 16);
+                uint64_t group_room = std::max<uint64_t>(1u << 16, Hc / 16);
                 uint64_t *gsp = carena.alloc_n<uint64_t>(spilled_fill + group_room);
                 if (spilled_fill)
                     GN_CUDA(cudaMemcpyAsync(gsp, spill, 8 * spilled_fill, cudaMemcpyDeviceToDevice, s));
