@@ -155,6 +155,19 @@ def test_search_stages_mid_small(gn, mid_small):
     assert sum(len(r.ranked) for r in ref) > 100
 
 
+@pytest.mark.parametrize("stride", [1, 4])
+def test_search_stages_mid_small_stride(gn, mid_small, stride):
+    """Index at stride 1 (every window) and 4: D = 3 stride, so chains are short-gapped."""
+    bank, qs, _, _ = mid_small
+    sub = qs.subset(range(0, qs.n, 2))
+    ix = gn.Index.from_bank(bank, stride=stride)
+    ox = oracle.Index(bank, stride=stride)
+    res = gn.search(ix, sub.start, sub.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
+    ref = ox.search(sub, oracle.Params(stride=stride), threads=os.cpu_count() or 1)
+    check_stages(gn, res, ref, sub.n, f"stride {stride}")
+    ix.close()
+
+
 def test_batched_equals_plain(gn, mid_small):
     bank, qs, ix, ox = mid_small
     allq = gn.search(ix, qs.start, qs.bases)
