@@ -44,20 +44,24 @@ enum { A_QI = 0, A_SEQ = 1, A_QS = 2, A_QE = 3, A_DS = 4, A_DE = 5, A_SCORE = 6 
 __global__ void k_query_codes(const uint64_t *__restrict__ qstart, uint32_t nq, uint64_t M,
                               const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb, int k,
                               const uint64_t *__restrict__ off, uint32_t *__restrict__ codes,
-                              uint32_t *__restrict__ qinfo, uint32_t *__restrict__ cnt) {
+                              uint32_t *__restrict__ qinfo, uint32_t *__restrict__ cnt,
+                              uint32_t *__restrict__ src) {
     uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= M) return;
     uint32_t qi = dev_upper_index(qstart, nq + 1, x);
     uint64_t qpos = x - qstart[qi];
     uint64_t m = qstart[qi + 1] - qstart[qi];
     uint32_t c = 0, n = 0;
+    uint64_t o = 0;
     if (qpos + (uint64_t)k <= m && !dev_has_nonbase(qnb, x, k)) {
         c = dev_kmer(qpk, x, k);
-        n = (uint32_t)(off[c + 1] - off[c]);
+        o = off[c];
+        n = (uint32_t)(off[c + 1] - o);
     }
     codes[x] = c;
     qinfo[x] = (qi << 16) | (uint32_t)qpos;
     cnt[x] = n;
+    src[x] = (uint32_t)o;  // occurrence indices fit 32 bits: the bank holds < 2^32 bases
 }
 
 __global__ void k_gather_u64(const uint64_t *__restrict__ src, const uint64_t *__restrict__ idx, uint32_t n,
@@ -198,247 +202,226 @@ __device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D,
 // core hit can only be part of a chain of two or more hits if another hit lies
 // on its diagonal within D query offsets, and all those offsets are inside core
 // + halo; so a core hit whose hash was not seen twice cannot reach min_hsp_len
-// and is dropped here (a hash collision only keeps an extra hit).  The kept hits
-// are counted (PASS 0) or written (PASS 1) per bucket, aggregated per tile in
-// shared memory so that global atomics are one per (tile, bucket).
-constexpr int BT_SPAN = 2048;      // buckets a tile can aggregate in shared memory
-constexpr int BT_MAX_D = 256;      // largest hit distance the tile filter supports
+// and is dropped here (a hash collision only keeps an extra hit).
+constexpr int BT_MAX_D = 256;  // largest hit distance the tile filter supports
+constexpr int BF_CHUNK = 128;  // hits a warp takes at a time (four per lane)
 
-struct TileHit {
-    uint32_t ql, qpos;
-    uint64_t gk;
+// Hash of (query, diagonal) into fbits bits: multiplicative (Fibonacci) hashing keeps
+// nearby diagonals apart.
+__device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk, int fbits) {
+    return (((uint32_t)gk ^ (ql * 0x85EBCA77u)) * 0x9E3779B1u) >> (32 - fbits);
+}
+
+// Shared-memory table of a tile's query offsets lo + i, i in [0, span): hit prefix
+// relative to the tile's first hit (span + 1 entries), occurrence-list start,
+// (query in chunk << 16 | query offset), and the query's bucket base and shift;
+// cs[c] is the offset holding hit c * BF_CHUNK for the first BF_CMAX chunks.
+// Tile-relative hit indices fit 32 bits: a query chunk holds < 2^32 hits.
+constexpr int BF_CMAX = 1024;
+struct TileTable {
+    uint32_t *hs, *src, *qq, *bb, *cs;
+    uint8_t *bs;
+    uint32_t span, nchunks;
 };
 
-// Calls f(ql, qpos, gk, hit index, valid) for every hit of query offsets [p0, p1): warps
-// take 32-offset blocks, lanes share each offset's occurrence list, four list entries per
-// lane in flight.  All lanes of a warp call f together (valid is false past a list's end),
-// so f may use warp votes; consecutive lanes hold consecutive hit indices.
-template <class F>
-__device__ __forceinline__ void for_tile_hits(uint64_t p0, uint64_t p1, const uint32_t *__restrict__ codes,
-                                              const uint32_t *__restrict__ qinfo,
-                                              const uint64_t *__restrict__ hoff, const uint64_t *__restrict__ off,
-                                              const uint32_t *__restrict__ post, uint32_t qa,
-                                              const uint32_t *__restrict__ bbase,
-                                              const uint32_t *__restrict__ bshift, F &&f) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint64_t x0 = p0 + (uint64_t)warp * 32; x0 < p1; x0 += (uint64_t)(blockDim.x >> 5) * 32) {
-        const uint64_t x = x0 + lane;
-        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
-        uint64_t my_src = 0, my_h = 0;
-        if (x < p1) {
-            my_h = hoff[x];
-            my_cnt = (uint32_t)(hoff[x + 1] - my_h);
-            if (my_cnt) {
-                const uint32_t qinf = qinfo[x];
-                my_src = off[codes[x]];
-                my_qpos = qinf & 0xFFFFu;
-                my_ql = (qinf >> 16) - qa;
-            }
-        }
-        uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
-            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
-            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
-            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
-            const uint64_t h0 = __shfl_sync(0xffffffffu, my_h, src);
-            const uint32_t bb = bbase[ql], bs = bshift[ql];
-            for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
-                uint32_t g[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    g[u] = j < cnt ? post[sp + j] : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    f(ql, qpos, (uint64_t)g[u] + QBIAS - qpos, h0 + j, j < cnt, bb, bs);
-                }
-            }
-        }
+// Last table index i in [i_lo, i_hi] with hs[i] <= h: the offset whose list holds hit h.
+__device__ __forceinline__ uint32_t tile_find(const uint32_t *hs, uint32_t i_lo, uint32_t i_hi, uint32_t h) {
+    while (i_lo < i_hi) {
+        const uint32_t mid = (i_lo + i_hi + 1) >> 1;
+        if (hs[mid] <= h) i_lo = mid;
+        else i_hi = mid - 1;
     }
+    return i_lo;
 }
 
-__device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk, int fbits) {
-    uint32_t h = (uint32_t)gk * 0x9E3779B1u + ql * 0x85EBCA77u;
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 13;
-    return h >> (32 - fbits);
+__device__ __forceinline__ uint32_t tile_chunk_offset(const TileTable &t, uint32_t c) {
+    return c < BF_CMAX ? t.cs[c] : tile_find(t.hs, 0, t.span - 1, c * BF_CHUNK);
 }
 
-// Like for_tile_hits, but warps take 32-offset blocks of [p0, p1) from a shared
-// counter (reset by the caller between passes), which balances uneven lists, and f
-// receives a lane's four list entries of a round at once (gk[4], valid[4]) so that
-// it can issue their memory operations back to back.
-template <class F>
-__device__ __forceinline__ void for_tile_hits_dyn(uint64_t p0, uint64_t p1, uint32_t *blk,
-                                                  const uint32_t *__restrict__ codes,
-                                                  const uint32_t *__restrict__ qinfo,
-                                                  const uint64_t *__restrict__ hoff, const uint64_t *__restrict__ off,
-                                                  const uint32_t *__restrict__ post, uint32_t qa,
-                                                  const uint32_t *__restrict__ bbase,
-                                                  const uint32_t *__restrict__ bshift, F &&f) {
+// The four hits a lane holds of one chunk: occurrence entries (loads in flight until
+// used), table index of each, and which are inside the pass's hit range.
+struct ChunkLoad {
+    uint32_t ent[4], idx[4];
+    bool ok[4];
+};
+
+// Issues the loads of chunk c, masked to the hit range [r0, r1).  Lane l takes the
+// four consecutive hits c * BF_CHUNK + 4l + v, which nearly always lie in one list:
+// one search per lane, then a boundary check per hit.
+__device__ __forceinline__ void tile_chunk_load(const TileTable &t, uint32_t c, uint32_t r0, uint32_t r1,
+                                                const uint32_t *__restrict__ post, ChunkLoad &L) {
     const int lane = threadIdx.x & 31;
-    const uint32_t nblk = (uint32_t)((p1 - p0 + 31) / 32);
-    for (;;) {
-        uint32_t kb = 0;
-        if (lane == 0) kb = atomicAdd(blk, 1u);
-        kb = __shfl_sync(0xffffffffu, kb, 0);
-        if (kb >= nblk) break;
-        const uint64_t x = p0 + (uint64_t)kb * 32 + lane;
-        uint32_t my_cnt = 0, my_qpos = 0, my_ql = 0;
-        uint64_t my_src = 0;
-        if (x < p1) {
-            const uint64_t h = hoff[x];
-            my_cnt = (uint32_t)(hoff[x + 1] - h);
-            if (my_cnt) {
-                const uint32_t qinf = qinfo[x];
-                my_src = off[codes[x]];
-                my_qpos = qinf & 0xFFFFu;
-                my_ql = (qinf >> 16) - qa;
-            }
-        }
-        uint32_t todo = __ballot_sync(0xffffffffu, my_cnt != 0);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
-            const uint64_t sp = __shfl_sync(0xffffffffu, my_src, src);
-            const uint32_t qpos = __shfl_sync(0xffffffffu, my_qpos, src);
-            const uint32_t ql = __shfl_sync(0xffffffffu, my_ql, src);
-            const uint32_t bb = bbase[ql], bs = bshift[ql];
-            for (uint32_t j0 = 0; j0 < cnt; j0 += 128) {
-                uint64_t gk[4];
-                bool ok[4];
+    const uint32_t hl = c * BF_CHUNK + 4 * lane;
+    const uint32_t i0 = tile_chunk_offset(t, c);
+    const uint32_t i1 = c + 1 < t.nchunks ? tile_chunk_offset(t, c + 1) : t.span - 1;
+    uint32_t i = tile_find(t.hs, i0, i1, max(hl, t.hs[i0]));
+    uint32_t hb = t.hs[i], he = t.hs[i + 1];
+    uint64_t base = (uint64_t)t.src[i] - hb;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    ok[u] = j < cnt;
-                    gk[u] = (uint64_t)(ok[u] ? post[sp + j] : 0u) + QBIAS - qpos;
-                }
-                f(ql, qpos, gk, ok, bb, bs);
-            }
+    for (int v = 0; v < 4; ++v) {
+        const uint32_t h = hl + v;
+        L.ok[v] = h >= r0 && h < r1;
+        while (h >= he && i < i1) {  // the next non-empty list
+            ++i;
+            hb = he;
+            he = t.hs[i + 1];
+            base = (uint64_t)t.src[i] - hb;
         }
+        L.idx[v] = i;
+        L.ent[v] = L.ok[v] ? post[base + h] : 0u;
     }
 }
 
-// Bucket fill: one kernel per chunk.  Each tile (tpos core offsets) hashes the hits
-// of core + halo into the "seen" / "seen twice" bitmaps (repeat filter), counts the
-// kept core hits per bucket in shared memory, reserves each bucket's slots with
-// one global atomic per (tile, bucket), and writes the kept hits.  Buckets have a
-// fixed capacity bcap; hits past it (and hits of buckets outside the tile's
-// shared-memory span, if any overflow) go to the spill list in global hit-key
-// format, which the global sort path handles.
-__global__ void __launch_bounds__(256) k_bucket_fill(
-    const uint32_t *__restrict__ codes, const uint32_t *__restrict__ qinfo, const uint64_t *__restrict__ hoff,
-    uint64_t xa, uint64_t xb, const uint64_t *__restrict__ off, const uint32_t *__restrict__ post, uint32_t qa,
-    const uint32_t *__restrict__ bbase, const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount,
-    uint64_t *__restrict__ bkeys, uint32_t bcap, uint64_t *__restrict__ spill,
-    unsigned long long *__restrict__ spill_count, unsigned long long spill_cap, int qbits, int filter, uint32_t D,
-    int tpos, int fbits, int direct, unsigned long long *__restrict__ kept_total) {
-    extern __shared__ __align__(16) unsigned char bf_smem[];
-    uint32_t my_kept = 0;
-    uint32_t *seen = reinterpret_cast<uint32_t *>(bf_smem);
-    uint32_t *seen2 = seen + (filter ? (1u << fbits) / 32 : 0);
-    uint32_t *hist = seen2 + (filter ? (1u << fbits) / 32 : 0);  // per-tile counts (not used with direct placement)
-    uint32_t *base = hist + BT_SPAN;
-    __shared__ uint32_t bmin_s, blk;
-    if (!direct)
-        for (int i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
-    auto put = [&](uint32_t ql, uint32_t qpos, uint64_t gk, uint32_t b, uint64_t slot) {
-        if (slot < bcap) {
-            bkeys[(uint64_t)b * bcap + slot] = (gk << 16) | qpos;
-        } else {
-            const unsigned long long at = atomicAdd(spill_count, 1ull);
-            if (at < spill_cap) spill[at] = (gk << (16 + qbits)) | ((uint64_t)ql << 16) | qpos;
-        }
+// Calls f(idx[4], entry[4], ok[4]) for every hit of [r0, r1) (tile-relative hit
+// indices).  The tile's hits form one index space cut into BF_CHUNK-hit chunks; warps
+// take the chunks that meet [r0, r1) from a shared counter, whatever lists they fall
+// in, so every lane has work and a long list is shared by many warps.  A warp issues
+// the loads of its next chunk before it processes the current one.  Lane l holds hits
+// c * BF_CHUNK + 4l + v (v < 4); all lanes of a warp call f together.
+template <class F>
+__device__ __forceinline__ void for_tile_chunks(const TileTable &t, uint32_t r0, uint32_t r1, uint32_t *ctr,
+                                                const uint32_t *__restrict__ post, F &&f) {
+    const int lane = threadIdx.x & 31;
+    if (r0 >= r1) return;
+    const uint32_t c0 = r0 / BF_CHUNK, nc = (r1 + BF_CHUNK - 1) / BF_CHUNK - c0;
+    auto claim = [&]() {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(ctr, 1u);
+        return __shfl_sync(0xffffffffu, c, 0);
     };
+    uint32_t c = claim();
+    if (c >= nc) return;
+    ChunkLoad cur, nxt;
+    tile_chunk_load(t, c0 + c, r0, r1, post, cur);
+    for (;;) {
+        const uint32_t cn = claim();
+        const bool more = cn < nc;
+        if (more) tile_chunk_load(t, c0 + cn, r0, r1, post, nxt);
+        f(cur.idx, cur.ent, cur.ok);
+        if (!more) break;
+        cur = nxt;
+    }
+}
+
+// Bucket fill: one kernel per query chunk.  Each tile (tpos core offsets) hashes the
+// hits of core + halo into the "seen" / "seen twice" bitmaps (repeat filter), then
+// places every kept core hit: one global atomic reserves its slot in its bucket.
+// Buckets have a fixed capacity bcap; hits past it go to the spill list in global
+// hit-key format, which the global sort path handles.
+__global__ void __launch_bounds__(256) k_bucket_fill(
+    const uint32_t *__restrict__ qinfo, const uint32_t *__restrict__ src, const uint64_t *__restrict__ hoff,
+    uint64_t xa, uint64_t xb, const uint32_t *__restrict__ post, uint32_t qa, const uint32_t *__restrict__ bbase,
+    const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount, uint64_t *__restrict__ bkeys, uint32_t bcap,
+    uint64_t *__restrict__ spill, unsigned long long *__restrict__ spill_count, unsigned long long spill_cap,
+    int qbits, int filter, uint32_t D, int tpos, int fbits, unsigned long long *__restrict__ kept_total) {
+    extern __shared__ __align__(16) unsigned char bf_smem[];
+    const uint32_t halo = filter ? D : 0u;
+    const uint32_t span_max = (uint32_t)tpos + 2u * halo;
+    const uint32_t nwords = filter ? (1u << fbits) / 32 : 0u;
+    TileTable t;
+    t.hs = reinterpret_cast<uint32_t *>(bf_smem);
+    t.src = t.hs + span_max + 1;
+    t.qq = t.src + span_max;
+    t.bb = t.qq + span_max;
+    t.cs = t.bb + span_max;
+    uint32_t *seen = t.cs + BF_CMAX;
+    uint32_t *seen2 = seen + nwords;
+    t.bs = reinterpret_cast<uint8_t *>(seen2 + nwords);
+    __shared__ uint32_t ctr;
+    uint32_t my_kept = 0;
     for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tpos; t0 < xb; t0 += (uint64_t)gridDim.x * tpos) {
         const uint64_t t1 = min(xb, t0 + (uint64_t)tpos);
-        if (threadIdx.x == 0) { bmin_s = bbase[(qinfo[t0] >> 16) - qa]; blk = 0; }
-        if (filter) {
-            for (uint32_t i = threadIdx.x; i < (2u << fbits) / 32; i += blockDim.x) seen[i] = 0u;
-        }
-        __syncthreads();
-        const uint32_t bmin = bmin_s;
-        if (filter) {
-            const uint64_t lo = t0 > xa + D ? t0 - D : xa, hi = min(xb, t1 + D);
-            for_tile_hits_dyn(lo, hi, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                              [&](uint32_t ql, uint32_t qpos, const uint64_t *gk, const bool *ok, uint32_t bb,
-                                  uint32_t bs) {
-#pragma unroll
-                                  for (int u = 0; u < 4; ++u) {
-                                      if (!ok[u]) continue;
-                                      const uint32_t h = tile_hash(ql, gk[u], fbits);
-                                      const uint32_t bit = 1u << (h & 31);
-                                      const uint32_t old = atomicOr(&seen[h >> 5], bit);
-                                      if (old & bit) atomicOr(&seen2[h >> 5], bit);
-                                  }
-                              });
-            __syncthreads();
-            if (threadIdx.x == 0) blk = 0;
-            __syncthreads();
-        }
-        auto kept = [&](uint32_t ql, uint64_t gk) {
-            if (!filter) return true;
-            const uint32_t h = tile_hash(ql, gk, fbits);
-            return ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
-        };
-        // count kept core hits per bucket (buckets outside the span are placed right away)
-        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                          [&](uint32_t ql, uint32_t qpos, const uint64_t *gk, const bool *ok, uint32_t bb,
-                              uint32_t bs) {
-                              uint32_t b[4], slot[4];
-                              bool glob[4];
-#pragma unroll
-                              for (int u = 0; u < 4; ++u) {
-                                  const bool kk = ok[u] && kept(ql, gk[u]);
-                                  my_kept += kk ? 1u : 0u;
-                                  b[u] = bb + (uint32_t)(gk[u] >> bs);
-                                  const uint32_t li = b[u] - bmin;
-                                  glob[u] = kk && (direct || li >= BT_SPAN);
-                                  if (kk && !glob[u]) atomicAdd(&hist[li], 1u);
-                              }
-                              // the global slot reservations first, then the dependent stores
-#pragma unroll
-                              for (int u = 0; u < 4; ++u)
-                                  if (glob[u]) slot[u] = atomicAdd(&bcount[b[u]], 1u);
-#pragma unroll
-                              for (int u = 0; u < 4; ++u)
-                                  if (glob[u]) put(ql, qpos, gk[u], b[u], slot[u]);
-                          });
-        __syncthreads();
-        if (direct) continue;  // every kept hit was placed with a global atomic (bitmaps reset at the next tile)
-        for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) {
-            const uint32_t c = hist[i];
-            if (c) {
-                base[i] = atomicAdd(&bcount[bmin + i], c);
-                hist[i] = 0;
+        const uint64_t lo = t0 - xa > halo ? t0 - halo : xa, hi = min(xb, t1 + halo);
+        const uint32_t span = (uint32_t)(hi - lo);
+        const uint64_t hbase = hoff[lo];
+        for (uint32_t i = threadIdx.x; i <= span; i += blockDim.x) {
+            const uint64_t x = lo + i;
+            t.hs[i] = (uint32_t)(hoff[x] - hbase);
+            if (i < span) {
+                t.src[i] = src[x];
+                const uint32_t qinf = qinfo[x];
+                const uint32_t ql = (qinf >> 16) - qa;
+                t.qq[i] = (ql << 16) | (qinf & 0xFFFFu);
+                t.bb[i] = bbase[ql];
+                t.bs[i] = (uint8_t)bshift[ql];
             }
         }
-        if (threadIdx.x == 0) blk = 0;
+        for (uint32_t i = threadIdx.x; i < 2 * nwords; i += blockDim.x) seen[i] = 0u;
+        if (threadIdx.x == 0) ctr = 0;
         __syncthreads();
-        for_tile_hits_dyn(t0, t1, &blk, codes, qinfo, hoff, off, post, qa, bbase, bshift,
-                          [&](uint32_t ql, uint32_t qpos, const uint64_t *gk, const bool *ok, uint32_t bb,
-                              uint32_t bs) {
+        t.span = span;
+        t.nchunks = (t.hs[span] + BF_CHUNK - 1) / BF_CHUNK;
+        // chunk -> offset of its first hit
+        for (uint32_t i = threadIdx.x; i < span; i += blockDim.x) {
+            const uint32_t ca = (t.hs[i] + BF_CHUNK - 1) / BF_CHUNK;
+            const uint32_t cb = min((t.hs[i + 1] + BF_CHUNK - 1) / BF_CHUNK, (uint32_t)BF_CMAX);
+            for (uint32_t c = ca; c < cb; ++c) t.cs[c] = i;
+        }
+        __syncthreads();
+        if (filter) {
+            for_tile_chunks(t, 0, t.hs[span], &ctr, post, [&](const uint32_t *idx, const uint32_t *ent,
+                                                              const bool *ok) {
+                uint32_t qq = t.qq[idx[0]];
 #pragma unroll
-                              for (int u = 0; u < 4; ++u) {
-                                  if (!ok[u] || !kept(ql, gk[u])) continue;
-                                  const uint32_t b = bb + (uint32_t)(gk[u] >> bs);
-                                  const uint32_t li = b - bmin;
-                                  if (li < BT_SPAN)
-                                      put(ql, qpos, gk[u], b, (uint64_t)base[li] + atomicAdd(&hist[li], 1u));
-                              }
-                          });
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < BT_SPAN; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
+                for (int u = 0; u < 4; ++u) {
+                    if (u && idx[u] != idx[u - 1]) qq = t.qq[idx[u]];
+                    if (!ok[u]) continue;
+                    const uint64_t gk = (uint64_t)ent[u] + QBIAS - (qq & 0xFFFFu);
+                    const uint32_t h = tile_hash(qq >> 16, gk, fbits);
+                    const uint32_t bit = 1u << (h & 31);
+                    const uint32_t old = atomicOr(&seen[h >> 5], bit);
+                    if (old & bit) atomicOr(&seen2[h >> 5], bit);
+                }
+            });
+            __syncthreads();
+            if (threadIdx.x == 0) ctr = 0;
+            __syncthreads();
+        }
+        // place the kept core hits
+        for_tile_chunks(t, t.hs[t0 - lo], t.hs[t1 - lo], &ctr, post, [&](const uint32_t *idx, const uint32_t *ent,
+                                                                            const bool *ok) {
+            uint64_t key[4];
+            uint32_t b[4], slot[4];
+            bool kk[4];
+            uint32_t qq = t.qq[idx[0]], bb = t.bb[idx[0]], bs = t.bs[idx[0]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u && idx[u] != idx[u - 1]) { qq = t.qq[idx[u]]; bb = t.bb[idx[u]]; bs = t.bs[idx[u]]; }
+                const uint64_t gk = (uint64_t)ent[u] + QBIAS - (qq & 0xFFFFu);
+                kk[u] = ok[u];
+                if (filter && kk[u]) {
+                    const uint32_t h = tile_hash(qq >> 16, gk, fbits);
+                    kk[u] = ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
+                }
+                my_kept += kk[u] ? 1u : 0u;
+                b[u] = bb + (uint32_t)(gk >> bs);
+                key[u] = (gk << 16) | (qq & 0xFFFFu);
+            }
+            // the global slot reservations first, then the dependent stores
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (kk[u]) slot[u] = atomicAdd(&bcount[b[u]], 1u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!kk[u]) continue;
+                if (slot[u] < bcap) {
+                    bkeys[(uint64_t)b[u] * bcap + slot[u]] = key[u];
+                } else {
+                    const unsigned long long at = atomicAdd(spill_count, 1ull);
+                    const uint64_t gk = key[u] >> 16, qq = t.qq[idx[u]];
+                    if (at < spill_cap) spill[at] = (gk << (16 + qbits)) | ((qq >> 16) << 16) | (qq & 0xFFFFu);
+                }
+            }
+        });
+        __syncthreads();  // the table and bitmaps are rebuilt for the next tile
     }
     if (my_kept) atomicAdd(kept_total, (unsigned long long)my_kept);
+}
+
+// Dynamic shared memory of k_bucket_fill.
+static size_t bucket_fill_smem(int tpos, uint32_t halo, int filter, int fbits) {
+    const size_t span_max = (size_t)tpos + 2 * halo;
+    return (span_max + 1) * 4 + span_max * 13 + 4 * BF_CMAX + (filter ? (2u << fbits) / 8 : 0);
 }
 
 __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc, uint32_t NB,
@@ -1240,10 +1223,12 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     uint32_t *codes = arena.alloc_n<uint32_t>(M);
     uint32_t *qinfo = arena.alloc_n<uint32_t>(M);
     uint32_t *cnt = arena.alloc_n<uint32_t>(M);
+    uint32_t *src = arena.alloc_n<uint32_t>(M);
     uint64_t *hoff = arena.alloc_n<uint64_t>(M + 1);
     if (M) {
         GN_LAUNCH("k_query_codes", M, s,
-                  k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, k, ix->off_d, codes, qinfo, cnt));
+                  k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, k, ix->off_d, codes, qinfo,
+                                                              cnt, src));
     }
     {
         void *scr = arena.alloc(scan_scratch_bytes(M));
@@ -1267,10 +1252,11 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     // fixed-capacity buckets (up to ~22 B per hit without the repeat filter) and spill lists
     uint64_t mem_for_hits = (uint64_t)(free_b * 0.55);
     if (o.mem_cap) mem_for_hits = std::min(mem_for_hits, o.mem_cap);
-    uint64_t hit_budget = std::max<uint64_t>(1ull << 20, mem_for_hits / HIT_BYTES);
+    // (a query chunk holds < 2^32 hits: the fill kernel indexes a tile's hits in 32 bits)
+    uint64_t hit_budget = std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(1ull << 20, mem_for_hits / HIT_BYTES));
     if (const char *e = getenv("GN_MAX_CHUNK_HITS")) {  // smaller chunks (exercises the multi-chunk path)
         uint64_t v = strtoull(e, nullptr, 10);
-        if (v) hit_budget = v;
+        if (v) hit_budget = std::min<uint64_t>(v, 0xFFFFFFFFull);
     }
     const uint64_t gbits_max = (uint64_t)bits_for(ix->n_bases + QBIAS);
     const uint32_t max_chunk_q = (uint32_t)std::min<uint64_t>(MAX_QUERIES, 1ull << std::min<uint64_t>(48 - gbits_max, 31));
@@ -1289,6 +1275,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         while (qb < nq && qb - qa < max_chunk_q && hq[qb + 1] - hq[qa] <= hit_budget) ++qb;
         const uint64_t xa = qstart_h[qa], xb = qstart_h[qb];
         const uint64_t ha = hq[qa], Hc = hq[qb] - hq[qa];
+        GN_REQUIRE(Hc < (1ull << 32), GN_ETOOBIG, "a query has 2^32 seed hits or more");
         if (Hc > 0) {
             const int qbits = bits_for(qb - qa - 1);
             const int gbits = (int)gbits_max;
@@ -1396,10 +1383,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint64_t spill_room = std::max<uint64_t>(1u << 16, Hc / 32);
                 uint64_t *spill = carena.alloc_n<uint64_t>(spill_room);
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
-                // direct placement: one global slot atomic per kept hit; 0 aggregates per (tile, bucket)
-                int direct = 1;
-                if (const char *e = getenv("GN_FILL_DIRECT")) direct = atoi(e) ? 1 : 0;
-                const size_t bf_smem = (direct ? 0 : BT_SPAN * 8) + (filter ? (2u << fbits) / 8 : 0) + 16;
+                const size_t bf_smem = bucket_fill_smem(tpos, filter ? p.max_hit_distance : 0u, filter, fbits);
                 auto fill_kernel = k_bucket_fill;
                 GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
                 int focc = 0;
@@ -1414,9 +1398,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     GN_CUDA(cudaMemsetAsync(kept_total, 0, 8, s));
                     GN_LAUNCH("k_bucket_fill", Hc, s,
                               fill_kernel<<<fgrid, 256, bf_smem, s>>>(
-                                  codes, qinfo, hoff, xa, xb, ix->off_d, ix->post_d, qa, d_bbase, d_bshift, bcount,
-                                  bkeys, bcap, spill, spill_count, (unsigned long long)spill_room, qbits, filter,
-                                  p.max_hit_distance, tpos, fbits, direct, kept_total));
+                                  qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
+                                  spill, spill_count, (unsigned long long)spill_room, qbits, filter,
+                                  p.max_hit_distance, tpos, fbits, kept_total));
                     GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaMemcpyAsync(&n_kept, kept_total, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
