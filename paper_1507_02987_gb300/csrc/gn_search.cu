@@ -206,18 +206,20 @@ __device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D,
 constexpr int BT_MAX_D = 256;  // largest hit distance the tile filter supports
 constexpr int BF_CHUNK = 128;  // hits a warp takes at a time (four per lane)
 
-// Hash of (query, diagonal) into fbits bits: multiplicative (Fibonacci) hashing keeps
-// nearby diagonals apart.
-__device__ __forceinline__ uint32_t tile_hash(uint32_t ql, uint64_t gk, int fbits) {
-    return (((uint32_t)gk ^ (ql * 0x85EBCA77u)) * 0x9E3779B1u) >> (32 - fbits);
-}
+// Two hashes of (query, diagonal), into the "seen" and the "seen twice" bitmaps:
+// multiplicative (Fibonacci) hashing with two constants keeps nearby diagonals apart,
+// and a key that collides with another in "seen" marks a "seen twice" slot of its own
+// rather than the other key's.
+__device__ __forceinline__ uint32_t tile_key(uint32_t ql, uint64_t gk) { return (uint32_t)gk ^ (ql * 0x85EBCA77u); }
+__device__ __forceinline__ uint32_t tile_h1(uint32_t key, int fbits) { return (key * 0x9E3779B1u) >> (32 - fbits); }
+__device__ __forceinline__ uint32_t tile_h2(uint32_t key, int fbits2) { return (key * 0xC2B2AE35u) >> (32 - fbits2); }
 
 // Shared-memory table of a tile's query offsets lo + i, i in [0, span): hit prefix
 // relative to the tile's first hit (span + 1 entries), occurrence-list start,
 // (query in chunk << 16 | query offset), and the query's bucket base and shift;
 // cs[c] is the offset holding hit c * BF_CHUNK for the first BF_CMAX chunks.
 // Tile-relative hit indices fit 32 bits: a query chunk holds < 2^32 hits.
-constexpr int BF_CMAX = 1024;
+constexpr int BF_CMAX = 512;
 struct TileTable {
     uint32_t *hs, *src, *qq, *bb, *cs;
     uint8_t *bs;
@@ -313,11 +315,11 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
     uint64_t xa, uint64_t xb, const uint32_t *__restrict__ post, uint32_t qa, const uint32_t *__restrict__ bbase,
     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount, uint64_t *__restrict__ bkeys, uint32_t bcap,
     uint64_t *__restrict__ spill, unsigned long long *__restrict__ spill_count, unsigned long long spill_cap,
-    int qbits, int filter, uint32_t D, int tpos, int fbits, unsigned long long *__restrict__ kept_total) {
+    int qbits, int filter, uint32_t D, int tpos, int fbits, int fbits2, unsigned long long *__restrict__ kept_total) {
     extern __shared__ __align__(16) unsigned char bf_smem[];
     const uint32_t halo = filter ? D : 0u;
     const uint32_t span_max = (uint32_t)tpos + 2u * halo;
-    const uint32_t nwords = filter ? (1u << fbits) / 32 : 0u;
+    const uint32_t nwords = filter ? (1u << fbits) / 32 : 0u, nwords2 = filter ? (1u << fbits2) / 32 : 0u;
     TileTable t;
     t.hs = reinterpret_cast<uint32_t *>(bf_smem);
     t.src = t.hs + span_max + 1;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
     t.cs = t.bb + span_max;
     uint32_t *seen = t.cs + BF_CMAX;
     uint32_t *seen2 = seen + nwords;
-    t.bs = reinterpret_cast<uint8_t *>(seen2 + nwords);
+    t.bs = reinterpret_cast<uint8_t *>(seen2 + nwords2);
     __shared__ uint32_t ctr;
     uint32_t my_kept = 0;
     for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tpos; t0 < xb; t0 += (uint64_t)gridDim.x * tpos) {
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
                 t.bs[i] = (uint8_t)bshift[ql];
             }
         }
-        for (uint32_t i = threadIdx.x; i < 2 * nwords; i += blockDim.x) seen[i] = 0u;
+        for (uint32_t i = threadIdx.x; i < nwords + nwords2; i += blockDim.x) seen[i] = 0u;
         if (threadIdx.x == 0) ctr = 0;
         __syncthreads();
         t.span = span;
@@ -367,10 +369,14 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
                     if (u && idx[u] != idx[u - 1]) qq = t.qq[idx[u]];
                     if (!ok[u]) continue;
                     const uint64_t gk = (uint64_t)ent[u] + QBIAS - (qq & 0xFFFFu);
-                    const uint32_t h = tile_hash(qq >> 16, gk, fbits);
+                    const uint32_t key = tile_key(qq >> 16, gk);
+                    const uint32_t h = tile_h1(key, fbits);
                     const uint32_t bit = 1u << (h & 31);
                     const uint32_t old = atomicOr(&seen[h >> 5], bit);
-                    if (old & bit) atomicOr(&seen2[h >> 5], bit);
+                    if (old & bit) {
+                        const uint32_t h2 = tile_h2(key, fbits2);
+                        atomicOr(&seen2[h2 >> 5], 1u << (h2 & 31));
+                    }
                 }
             });
             __syncthreads();
@@ -390,8 +396,8 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
                 const uint64_t gk = (uint64_t)ent[u] + QBIAS - (qq & 0xFFFFu);
                 kk[u] = ok[u];
                 if (filter && kk[u]) {
-                    const uint32_t h = tile_hash(qq >> 16, gk, fbits);
-                    kk[u] = ((seen2[h >> 5] >> (h & 31)) & 1u) != 0u;
+                    const uint32_t h2 = tile_h2(tile_key(qq >> 16, gk), fbits2);
+                    kk[u] = ((seen2[h2 >> 5] >> (h2 & 31)) & 1u) != 0u;
                 }
                 my_kept += kk[u] ? 1u : 0u;
                 b[u] = bb + (uint32_t)(gk >> bs);
@@ -419,9 +425,9 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
 }
 
 // Dynamic shared memory of k_bucket_fill.
-static size_t bucket_fill_smem(int tpos, uint32_t halo, int filter, int fbits) {
+static size_t bucket_fill_smem(int tpos, uint32_t halo, int filter, int fbits, int fbits2) {
     const size_t span_max = (size_t)tpos + 2 * halo;
-    return (span_max + 1) * 4 + span_max * 13 + 4 * BF_CMAX + (filter ? (2u << fbits) / 8 : 0);
+    return (span_max + 1) * 4 + span_max * 13 + 4 * BF_CMAX + (filter ? ((1u << fbits) + (1u << fbits2)) / 8 : 0);
 }
 
 __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc, uint32_t NB,
@@ -1347,11 +1353,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const char *fenv = getenv("GN_TILE_FILTER");
                 const int filter = (!singles && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
                                     !(fenv && strcmp(fenv, "0") == 0)) ? 1 : 0;
-                int tpos = 256, fbits = 17;
+                int tpos = 256, fbits = 18, fbits2 = 16;
                 if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
+                if (const char *e = getenv("GN_TILE_FBITS2")) fbits2 = std::max(12, std::min(19, atoi(e)));
                 // the filter keeps about a fifth of the hits; capacity has ~2x slack over the expected fill
                 uint32_t target = filter ? 2048 : 512, bcap = 1024;
+                if (const char *e = getenv("GN_BUCKET_TARGET")) target = std::max(64, std::min(65536, atoi(e)));
                 if (const char *e = getenv("GN_BUCKET_CAP")) {  // small buckets (exercises the spill path)
                     bcap = (uint32_t)std::max(8ul, std::min(65536ul, strtoul(e, nullptr, 10)));
                     target = std::max<uint32_t>(2, bcap / 2);
@@ -1381,9 +1389,12 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 uint16_t *bq = carena.alloc_n<uint16_t>(NB);
                 unsigned long long *spill_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
                 uint64_t spill_room = std::max<uint64_t>(1u << 16, Hc / 32);
+                uint64_t min_room = 0;  // GN_SPILL_ROOM: small first rooms (exercises the reruns)
+                if (const char *e = getenv("GN_SPILL_ROOM")) min_room = std::max<uint64_t>(1, strtoull(e, nullptr, 10));
+                if (min_room) spill_room = min_room;
                 uint64_t *spill = carena.alloc_n<uint64_t>(spill_room);
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
-                const size_t bf_smem = bucket_fill_smem(tpos, filter ? p.max_hit_distance : 0u, filter, fbits);
+                const size_t bf_smem = bucket_fill_smem(tpos, filter ? p.max_hit_distance : 0u, filter, fbits, fbits2);
                 auto fill_kernel = k_bucket_fill;
                 GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
                 int focc = 0;
@@ -1392,7 +1403,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(focc, 1) * 4));
                 unsigned long long n_spill = 0, n_kept = 0;
                 unsigned long long *kept_total = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
-                for (int attempt = 0; attempt < 2; ++attempt) {
+                // Which of two colliding keys the filter keeps depends on arrival order, so the spill
+                // count varies a little between runs: a rerun gets room with a margin, and the loop
+                // ends on the run whose spills all fit.
+                for (int attempt = 0;; ++attempt) {
                     GN_CUDA(cudaMemsetAsync(bcount, 0, 4ull * NB, s));
                     GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
                     GN_CUDA(cudaMemsetAsync(kept_total, 0, 8, s));
@@ -1400,15 +1414,15 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                               fill_kernel<<<fgrid, 256, bf_smem, s>>>(
                                   qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
                                   spill, spill_count, (unsigned long long)spill_room, qbits, filter,
-                                  p.max_hit_distance, tpos, fbits, kept_total));
+                                  p.max_hit_distance, tpos, fbits, fbits2, kept_total));
                     GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaMemcpyAsync(&n_kept, kept_total, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
                     if (n_spill <= spill_room) break;
-                    spill_room = n_spill;  // rerun with room for every spilled hit
+                    GN_REQUIRE(attempt < 3, GN_EINTERNAL, "hit-bucket spill sizing did not converge");
+                    spill_room = n_spill + n_spill / 8 + 1024;
                     spill = carena.alloc_n<uint64_t>(spill_room);
                 }
-                GN_REQUIRE(n_spill <= spill_room, GN_EINTERNAL, "hit-bucket spill sizing did not converge");
                 GN_LAUNCH("k_bucket_query", NB, s, k_bucket_query<<<nqc, 256, 0, s>>>(d_bbase, nqc, NB, bq));
                 timer.mark("bucket_fill");
                 // group each bucket; buckets with too many candidates are appended to the spill list too
@@ -1419,13 +1433,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const unsigned ggrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>((NB + BGW_WARPS - 1) / BGW_WARPS, (uint64_t)num_sms() * std::max(occ, 1)));
                 const uint64_t spilled_fill = n_spill;
-                uint64_t group_room = std::max<uint64_t>(1u << 16, Hc / 16);
+                uint64_t group_room = min_room ? min_room : std::max<uint64_t>(1u << 16, Hc / 16);
                 uint64_t *gsp = carena.alloc_n<uint64_t>(spilled_fill + group_room);
                 if (spilled_fill)
                     GN_CUDA(cudaMemcpyAsync(gsp, spill, 8 * spilled_fill, cudaMemcpyDeviceToDevice, s));
                 unsigned long long n_ovf = 0;
                 unsigned long long *ovf_count = spill_count;
-                for (int attempt = 0; attempt < 2; ++attempt) {
+                for (int attempt = 0;; ++attempt) {
                     const uint32_t hsp_before = n_hsp;
                     emit([&](DevHsp *o, uint32_t room) {
                         GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
@@ -1439,15 +1453,15 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
                     if (n_ovf <= group_room) break;
-                    n_hsp = hsp_before;
-                    group_room = n_ovf;
+                    GN_REQUIRE(attempt < 3, GN_EINTERNAL, "hit-bucket overflow sizing did not converge");
+                    n_hsp = hsp_before;  // the rerun emits this chunk's bucket HSPs again
+                    group_room = n_ovf + n_ovf / 8 + 1024;
                     uint64_t *ng = carena.alloc_n<uint64_t>(spilled_fill + group_room);
                     if (spilled_fill)
                         GN_CUDA(cudaMemcpyAsync(ng, spill, 8 * spilled_fill, cudaMemcpyDeviceToDevice, s));
                     gsp = ng;
                     GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
                 }
-                GN_REQUIRE(n_ovf <= group_room, GN_EINTERNAL, "hit-bucket spill buffer sizing did not converge");
                 timer.mark("bucket_group");
                 const uint64_t n_sp = spilled_fill + n_ovf;
                 if (n_sp) sort_path(gsp, carena.alloc_n<uint64_t>(n_sp), n_sp, 0, TAG_HIT_SORT);

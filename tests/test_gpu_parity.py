@@ -155,10 +155,13 @@ def test_search_stages_mid_small(gn, mid_small):
     assert sum(len(r.ranked) for r in ref) > 100
 
 
-@pytest.mark.parametrize("stride", [1, 4])
-def test_search_stages_mid_small_stride(gn, mid_small, stride):
-    """Index at stride 1 (every window) and 4: D = 3 stride, so chains are short-gapped."""
+@pytest.mark.parametrize("stride,env", [(1, {}), (4, {}), (1, {"GN_SPILL_ROOM": "64"})])
+def test_search_stages_mid_small_stride(gn, mid_small, stride, env, monkeypatch):
+    """Index at stride 1 (every window) and 4: D = 3 stride, so chains are short-gapped.  At
+    stride 1 most hits pass the repeat filter and many buckets overflow into the spill path."""
     bank, qs, _, _ = mid_small
+    for k_, v in env.items():
+        monkeypatch.setenv(k_, v)
     sub = qs.subset(range(0, qs.n, 2))
     ix = gn.Index.from_bank(bank, stride=stride)
     ox = oracle.Index(bank, stride=stride)
@@ -189,7 +192,8 @@ def test_chunked_equals_unchunked(gn, mid_small, monkeypatch):
 
 @pytest.mark.parametrize("env", [{"GN_HIT_GROUPING": "sort"}, {"GN_BUCKET_CAP": "64"}, {"GN_TILE_FILTER": "0"},
                                  {"GN_RANK_PATH": "sort"}, {"GN_TILE_POS": "64"},
-                                 {"GN_BUCKET_CAP": "64", "GN_MAX_CHUNK_HITS": "30000"}])
+                                 {"GN_BUCKET_CAP": "64", "GN_MAX_CHUNK_HITS": "30000"},
+                                 {"GN_BUCKET_CAP": "64", "GN_SPILL_ROOM": "16"}])
 def test_hit_grouping_paths_agree_with_oracle(gn, mid_small, monkeypatch, env):
     """The global sort path, the bucketed path and its overflow fallback give the oracle's HSPs."""
     bank, qs, ix, ox = mid_small
