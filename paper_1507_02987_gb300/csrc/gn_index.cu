@@ -58,6 +58,16 @@ __global__ void k_low_words(const uint64_t *__restrict__ keys, uint64_t n, uint3
     if (i < n) out[i] = (uint32_t)keys[i];
 }
 
+// lut[j] = last sequence s with start[s] <= j << SEQ_LUT_SHIFT (positions past the bank
+// map to the last sequence).
+__global__ void k_seq_lut(const uint64_t *__restrict__ start, uint32_t ns, uint64_t n, uint64_t nlut,
+                          uint32_t *__restrict__ lut) {
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nlut) return;
+    const uint64_t x = min(j << SEQ_LUT_SHIFT, n > 0 ? n - 1 : 0);
+    lut[j] = dev_upper_index(start, ns, x);  // over the ns starts: the result is < ns
+}
+
 void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) {
     GN_REQUIRE(db && db->seq_start, GN_EINVAL, "bank and bank.seq_start are required");
     GN_REQUIRE(k >= 1 && k <= 16, GN_EINVAL, "k must be in 1..16");
@@ -92,6 +102,15 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     bytes += sizeof(uint64_t) * (nbk + 1);
     GN_CUDA(cudaMemcpyAsync(ix->seq_start_d, ix->seq_start_h.data(), sizeof(uint64_t) * (ns + 1),
                             cudaMemcpyHostToDevice, s));
+    // sequence lookup table: the sequence holding each block of 2^SEQ_LUT_SHIFT bases
+    const uint64_t nlut = (n >> SEQ_LUT_SHIFT) + 1;
+    GN_CUDA(cudaMalloc(&ix->seq_lut_d, sizeof(uint32_t) * nlut));
+    bytes += sizeof(uint32_t) * nlut;
+    if (ns > 0)
+        GN_LAUNCH("k_seq_lut", nlut, s,
+                  k_seq_lut<<<(unsigned)((nlut + 255) / 256), 256, 0, s>>>(ix->seq_start_d, ns, n, nlut, ix->seq_lut_d));
+    else
+        GN_CUDA(cudaMemsetAsync(ix->seq_lut_d, 0, sizeof(uint32_t) * nlut, s));
 
     DeviceArena arena(s);
     // K1: 2-bit packing of the bank
@@ -161,6 +180,7 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
 void index_free(gn_index *ix) {
     if (!ix) return;
     cudaFree(ix->seq_start_d);
+    cudaFree(ix->seq_lut_d);
     cudaFree(ix->bank.pk);
     cudaFree(ix->bank.nb);
     cudaFree(ix->off_d);

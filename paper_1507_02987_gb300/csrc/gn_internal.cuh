@@ -195,6 +195,22 @@ __device__ __forceinline__ uint32_t dev_upper_index(const uint64_t *__restrict__
     return lo;
 }
 
+// Sequence lookup: lut[j] is the sequence holding bank position j << SEQ_LUT_SHIFT, so
+// the sequence of position x is found by a short forward walk from lut[x >> shift]
+// (sequences of >= 1 base; a block of 2^SEQ_LUT_SHIFT bases starts few of them).
+constexpr int SEQ_LUT_SHIFT = 10;
+struct SeqMap {
+    const uint64_t *start;  // n_seqs + 1 sequence starts (start[n_seqs] = bank length)
+    const uint32_t *lut;
+    uint32_t n_seqs;
+};
+// sequence holding bank position x (x < bank length); empty sequences are skipped
+__device__ __forceinline__ uint32_t dev_seq_of(const SeqMap &m, uint64_t x) {
+    uint32_t s = m.lut[x >> SEQ_LUT_SHIFT];
+    while (m.start[s + 1] <= x) ++s;
+    return s;
+}
+
 }  // namespace gn
 
 // --------------------------------------------------------------- handles --
@@ -207,6 +223,7 @@ struct gn_index {
     uint32_t max_seq_len = 0;
     std::vector<uint64_t> seq_start_h;
     uint64_t *seq_start_d = nullptr;  // n_seqs + 1
+    uint32_t *seq_lut_d = nullptr;    // (n_bases >> SEQ_LUT_SHIFT) + 1 entries, see SeqMap
     gn::Packed bank;                  // packed bank + non-base bitmap
     uint64_t *off_d = nullptr;        // 4^k + 1 bucket starts
     uint32_t *post_d = nullptr;       // occurrences: global base offset of the window
@@ -239,6 +256,7 @@ void index_build(const gn_bank *db, int k, int stride, cudaStream_t s, gn_index 
 void index_free(gn_index *ix);
 void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos);
 
+inline SeqMap seq_map(const gn_index *ix) { return SeqMap{ix->seq_start_d, ix->seq_lut_d, ix->n_seqs}; }
 struct SearchOptions {
     gn_scoring sc;
     gn_params p;           // resolved (no zero defaults left)

@@ -131,40 +131,37 @@ __device__ __forceinline__ HitKey dec_key(uint64_t key, int qbits) {
     return h;
 }
 
-// b directly follows a in one chain: same diagonal key and query, query gap <= D, same bank sequence
-__device__ __forceinline__ bool dev_linked(uint64_t a, uint64_t b, int qbits, uint32_t D,
-                                           const uint64_t *__restrict__ seq_start, uint32_t n_seqs) {
-    if ((a >> 16) != (b >> 16)) return false;
-    uint32_t qa = (uint32_t)(a & 0xFFFFu), qb = (uint32_t)(b & 0xFFFFu);
-    if (qb - qa > D) return false;
-    uint64_t gk = b >> (16 + qbits);
-    uint64_t ga = gk - QBIAS + qa, gb = gk - QBIAS + qb;
-    return dev_upper_index(seq_start, n_seqs + 1, ga) == dev_upper_index(seq_start, n_seqs + 1, gb);
-}
-
+// Chains of sorted hit keys: a hit starts a chain unless the previous key has the same
+// diagonal and query, lies at most D query offsets before it and in the same bank
+// sequence; the head walks its chain, whose hits must end before its sequence does.
 __global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int qbits, uint32_t qa, int k,
-                            uint32_t D, uint32_t min_len, const uint64_t *__restrict__ seq_start, uint32_t n_seqs,
-                            DevHsp *__restrict__ out, uint32_t *__restrict__ count, uint32_t cap,
-                            uint32_t *__restrict__ status) {
+                            uint32_t D, uint32_t min_len, SeqMap sm, DevHsp *__restrict__ out,
+                            uint32_t *__restrict__ count, uint32_t cap, uint32_t *__restrict__ status) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        uint64_t key = keys[i];
-        if (i > 0 && dev_linked(keys[i - 1], key, qbits, D, seq_start, n_seqs)) continue;
+        const uint64_t key = keys[i];
+        const HitKey a = dec_key(key, qbits);
+        const uint64_t gpos = a.gkey - QBIAS + a.qpos;
+        const uint32_t sq = dev_seq_of(sm, gpos);
+        if (i > 0) {
+            const uint64_t prev = keys[i - 1];
+            const uint32_t qp = (uint32_t)(prev & 0xFFFFu);
+            if ((prev >> 16) == (key >> 16) && a.qpos - qp <= D && sm.start[sq] <= gpos - (a.qpos - qp)) continue;
+        }
+        const uint64_t seq_end = sm.start[sq + 1];
         uint64_t j = i, kj = key;
         while (j + 1 < n) {
-            uint64_t kn = keys[j + 1];
-            if (!dev_linked(kj, kn, qbits, D, seq_start, n_seqs)) break;
+            const uint64_t kn = keys[j + 1];
+            const uint32_t qn = (uint32_t)(kn & 0xFFFFu);
+            if ((kn >> 16) != (key >> 16) || qn - (uint32_t)(kj & 0xFFFFu) > D || a.gkey - QBIAS + qn >= seq_end) break;
             kj = kn;
             ++j;
         }
-        HitKey a = dec_key(key, qbits), b = dec_key(kj, qbits);
-        uint32_t qs = a.qpos, qe = b.qpos + (uint32_t)k;
-        uint32_t len = qe - qs;
+        const uint32_t qs = a.qpos, qe = (uint32_t)(kj & 0xFFFFu) + (uint32_t)k;
+        const uint32_t len = qe - qs;
         if (len < min_len) continue;
-        uint64_t gpos = a.gkey - QBIAS + a.qpos;
-        uint32_t sq = dev_upper_index(seq_start, n_seqs + 1, gpos);
-        uint32_t ds = (uint32_t)(gpos - seq_start[sq]);
-        uint32_t slot = atomicAdd(count, 1u);
+        const uint32_t ds = (uint32_t)(gpos - sm.start[sq]);
+        const uint32_t slot = atomicAdd(count, 1u);
         if (slot < cap) {
             DevHsp h;
             h.qi = qa + a.ql; h.seq = sq; h.qs = qs; h.qe = qe; h.ds = ds; h.de = ds + len; h.len = len;
@@ -175,7 +172,6 @@ __global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int q
     }
 }
 
-
 // ------------------------------------------ a6-a8: bucketed hit grouping --
 // Hits of query i are partitioned into 2^b_i buckets by the high bits of their
 // diagonal key G' = gpos - qpos + QBIAS (bucket = bbase[i] + (G' >> bshift[i])).
@@ -183,17 +179,6 @@ __global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int q
 // own.  A diagonal holding a single hit cannot form an HSP when min_hsp_len > k,
 // so such hits are dropped before the (small) sort by (G', qpos) that the
 // chaining needs.  Bucket entry: G' << 16 | qpos.
-
-// bucket entries a, b (a first): consecutive hits of one chain?
-__device__ __forceinline__ bool dev_linked_b(uint64_t a, uint64_t b, uint32_t D, const uint64_t *__restrict__ seq_start,
-                                             uint32_t n_seqs) {
-    if ((a >> 16) != (b >> 16)) return false;
-    const uint32_t qa = (uint32_t)(a & 0xFFFFu), qb = (uint32_t)(b & 0xFFFFu);
-    if (qb - qa > D) return false;
-    const uint64_t gk = b >> 16;
-    return dev_upper_index(seq_start, n_seqs + 1, gk - QBIAS + qa) ==
-           dev_upper_index(seq_start, n_seqs + 1, gk - QBIAS + qb);
-}
 
 // Tile-level bucketing: a CTA takes tpos consecutive query offsets (the core).
 // With the repeat filter on (min_hsp_len > k and D <= BT_MAX_D), every hit of the
@@ -449,7 +434,7 @@ constexpr int BGW_CAND = 256;
 __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
     const uint64_t *__restrict__ bkeys, const uint32_t *__restrict__ bcount, uint32_t bcap, uint32_t NB,
     const uint16_t *__restrict__ bq, uint32_t qa, int qbits, int k, uint32_t D, uint32_t min_len, int singles,
-    const uint64_t *__restrict__ seq_start, uint32_t n_seqs, DevHsp *__restrict__ out, uint32_t *__restrict__ count,
+    SeqMap sm, DevHsp *__restrict__ out, uint32_t *__restrict__ count,
     uint32_t out_cap, uint64_t *__restrict__ ovf, unsigned long long ovf_cap,
     unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status, uint32_t *__restrict__ next_bucket) {
     extern __shared__ __align__(16) unsigned char gw_smem[];
@@ -502,7 +487,7 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
                 if (singles) {
                     keep = true;
                 } else {
-                    const uint32_t h = (uint32_t)(((key >> 16) * 0x9E3779B97F4A7C15ull) >> 51);
+                    const uint32_t h = (uint32_t)(((key >> 16) * 0x9E3779B97F4A7C15ull) >> 51);  // 13 bits
                     keep = (seen2[h >> 5] >> (h & 31)) & 1u;
                 }
             }
@@ -549,21 +534,28 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
         }
         for (uint32_t i = lane; i < nc; i += 32) {
             const uint64_t key = cand[i];
-            if (i > 0 && dev_linked_b(cand[i - 1], key, D, seq_start, n_seqs)) continue;
+            const uint32_t qs = (uint32_t)(key & 0xFFFFu);
+            const uint64_t gpos = (key >> 16) - QBIAS + qs;
+            const uint32_t sq = dev_seq_of(sm, gpos);
+            if (i > 0) {
+                const uint64_t prev = cand[i - 1];
+                const uint32_t qp = (uint32_t)(prev & 0xFFFFu);
+                if ((prev >> 16) == (key >> 16) && qs - qp <= D && sm.start[sq] <= gpos - (qs - qp)) continue;
+            }
+            const uint64_t seq_end = sm.start[sq + 1];
             uint32_t j = i;
             uint64_t kj = key;
             while (j + 1 < nc) {
                 const uint64_t kn = cand[j + 1];
-                if (!dev_linked_b(kj, kn, D, seq_start, n_seqs)) break;
+                const uint32_t qn = (uint32_t)(kn & 0xFFFFu);
+                if ((kn >> 16) != (key >> 16) || qn - (uint32_t)(kj & 0xFFFFu) > D || gpos - qs + qn >= seq_end) break;
                 kj = kn;
                 ++j;
             }
-            const uint32_t qs = (uint32_t)(key & 0xFFFFu), qe = (uint32_t)(kj & 0xFFFFu) + (uint32_t)k;
+            const uint32_t qe = (uint32_t)(kj & 0xFFFFu) + (uint32_t)k;
             const uint32_t len = qe - qs;
             if (len < min_len) continue;
-            const uint64_t gpos = (key >> 16) - QBIAS + qs;
-            const uint32_t sq = dev_upper_index(seq_start, n_seqs + 1, gpos);
-            const uint32_t ds = (uint32_t)(gpos - seq_start[sq]);
+            const uint32_t ds = (uint32_t)(gpos - sm.start[sq]);
             const uint32_t slot = atomicAdd(count, 1u);
             if (slot < out_cap) {
                 DevHsp hh;
@@ -1322,8 +1314,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     GN_LAUNCH("k_hit_merge", n, s,
                               k_hit_merge<<<blocks_for(threads), 256, 0, s>>>(sorted, n, qbits, qa, k,
                                                                              p.max_hit_distance, p.min_hsp_len,
-                                                                             ix->seq_start_d, ix->n_seqs, o, counter,
-                                                                             room, status));
+                                                                             seq_map(ix), o, counter, room, status));
                 });
                 return sorted;
             };
@@ -1447,7 +1438,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                         GN_LAUNCH("k_bucket_group", n_kept, s,
                                   k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
                                       bkeys, bcount, bcap, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len,
-                                      singles, ix->seq_start_d, ix->n_seqs, o, counter, room, gsp + spilled_fill,
+                                      singles, seq_map(ix), o, counter, room, gsp + spilled_fill,
                                       (unsigned long long)group_room, ovf_count, status, counter + 1));
                     });
                     GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
