@@ -843,6 +843,273 @@ __device__ __forceinline__ void sw_rows_pair(int64_t I0, int64_t I1, int64_t J0,
 }
 
 
+// One HSP aligned by a whole warp: the pair path for bands of at most 64 diagonals,
+// else the strip path (the band in chunks of 32 offsets, previous row in scratch).
+__device__ void sw_task_warp(const DevHsp *__restrict__ sel, uint32_t task, const uint64_t *__restrict__ strip_off,
+                             SwCell *__restrict__ strips, const uint32_t *__restrict__ qpk,
+                             const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
+                             const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                             const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch, int32_t go,
+                             int32_t ge, int32_t w, DevAln *__restrict__ out, uint32_t *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const DevHsp h = sel[task];
+    const uint64_t qb = qstart[h.qi], sb = seq_start[h.seq];
+    const int64_t m = (int64_t)(qstart[h.qi + 1] - qb), L = (int64_t)(seq_start[h.seq + 1] - sb);
+    const int64_t d_s = (int64_t)h.ds - h.qs, d_e = (int64_t)h.de - h.qe;
+    const int64_t dlo = min(d_s, d_e) - w, dhi = max(d_s, d_e) + w;
+    const int64_t I0 = max((int64_t)0, (int64_t)h.qs - w), I1 = min(m, (int64_t)h.qe + w);
+    const int64_t J0 = max((int64_t)0, (int64_t)h.ds - w), J1 = min(L, (int64_t)h.de + w);
+    const int64_t B = dhi - dlo + 1;
+    DevAln res;
+    res.qi = h.qi; res.seq = h.seq; res.qs = res.qe = res.ds = res.de = 0; res.score = 0; res.pad = 0;
+    if (B > 65535 || I1 - I0 > 65535) {
+        if (lane == 0) { atomicOr(status, DEV_ERR_BAND_TOO_WIDE); out[task] = res; }
+        return;
+    }
+    SwCell *row = strips + strip_off[task];
+    int32_t best = 0;
+    int64_t bi = INT64_MAX, bj = INT64_MAX;
+    uint32_t bs = 0;
+    const int32_t goe = go + ge;
+    if (B <= 64) {
+        sw_rows_pair(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best, bi,
+                     bj, bs);
+    } else
+    for (int64_t i = I0; i < I1; ++i) {
+        const int64_t blo = max((int64_t)0, J0 - i - dlo), bhi = min(B - 1, J1 - 1 - i - dlo);
+        if (blo > bhi) continue;
+        const bool prow = i - 1 >= I0;
+        const int64_t pblo = max((int64_t)0, J0 - (i - 1) - dlo), pbhi = min(B - 1, J1 - 1 - (i - 1) - dlo);
+        const uint32_t qc = dev_base(qpk, qnb, qb + (uint64_t)i);
+        int32_t carry_v = SW_XNEG;
+        uint32_t carry_s = 0;
+        for (int64_t c0 = blo; c0 <= bhi; c0 += 32) {
+            const int64_t b = c0 + lane;
+            const bool act = b <= bhi;
+            SwCell pd{0, SW_NEG, 0, 0}, pu{0, SW_NEG, 0, 0};
+            const bool ok_d = act && prow && b >= pblo && b <= pbhi;
+            const bool ok_u = act && prow && b + 1 >= pblo && b + 1 <= pbhi;
+            if (ok_d) pd = row[b];
+            if (ok_u) pu = row[b + 1];
+            __syncwarp();
+            int32_t E = SW_NEG;
+            uint32_t SE = 0;
+            if (ok_u) {
+                int32_t eo = pu.H + goe, ee = pu.E + ge;
+                if (eo >= ee) { E = eo; SE = pu.SH; } else { E = ee; SE = pu.SE; }
+            }
+            const int32_t Hd = ok_d ? pd.H : 0;
+            const uint32_t SD = (Hd > 0) ? pd.SH : ((uint32_t)(i - I0) << 16) | (uint32_t)b;
+            const int64_t j = i + dlo + b;
+            int32_t sigma = mismatch;
+            if (act) sigma = dev_pair(qc, dev_base(bpk, bnb, sb + (uint64_t)j), match, mismatch);
+            const int32_t Dg = Hd + sigma;
+            int32_t cand;
+            uint32_t Sc;
+            if (Dg >= E) { cand = Dg; Sc = SD; } else { cand = E; Sc = SE; }
+            const int32_t H0 = cand > 0 ? cand : 0;
+            // F by max-scan with carry from earlier chunks of this row
+            int32_t xv = act ? H0 + goe - ge * (int32_t)b : SW_XNEG;
+            uint32_t xs = Sc;
+            scan_pair_max(xv, xs, lane);
+            int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1);
+            uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1);
+            // the carry (earlier chunks) wins only when strictly larger
+            if (lane == 0) { ev = carry_v; es = carry_s; }
+            else if (carry_v > ev) { ev = carry_v; es = carry_s; }
+            int32_t last_v = __shfl_sync(0xffffffffu, xv, 31);
+            uint32_t last_s = __shfl_sync(0xffffffffu, xs, 31);
+            if (last_v >= carry_v) { carry_v = last_v; carry_s = last_s; }
+            int32_t F = (ev > SW_XNEG) ? ev + ge * (int32_t)(b - 1) : SW_NEG;
+            uint32_t SF = es;
+            int32_t H;
+            uint32_t SH;
+            if (H0 >= F) { H = H0; SH = Sc; } else { H = F; SH = SF; }
+            if (act) {
+                SwCell c;
+                c.H = H; c.E = E; c.SH = SH; c.SE = SE;
+                row[b] = c;
+                if (H > best) { best = H; bi = i; bj = j; bs = SH; }
+            }
+            __syncwarp();
+        }
+    }
+    // reduce: highest score, then smallest i, then smallest j
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        int32_t ob = __shfl_down_sync(0xffffffffu, best, o);
+        int64_t oi = __shfl_down_sync(0xffffffffu, bi, o);
+        int64_t oj = __shfl_down_sync(0xffffffffu, bj, o);
+        uint32_t os = __shfl_down_sync(0xffffffffu, bs, o);
+        if (ob > best || (ob == best && (oi < bi || (oi == bi && oj < bj)))) {
+            best = ob; bi = oi; bj = oj; bs = os;
+        }
+    }
+    if (lane == 0) {
+        if (best > 0) {
+            int64_t i0 = I0 + (int64_t)(bs >> 16);
+            int64_t j0 = i0 + dlo + (int64_t)(bs & 0xFFFFu);
+            res.qs = (uint32_t)i0; res.qe = (uint32_t)(bi + 1);
+            res.ds = (uint32_t)j0; res.de = (uint32_t)(bj + 1);
+            res.score = best;
+        }
+        out[task] = res;
+    }
+}
+
+// 32 consecutive bases of a packed sequence starting at a 16-aligned position: 2-bit
+// codes (first base most significant) and non-base flags (bit = offset).
+struct BaseWin {
+    uint64_t p0 = ~0ull, codes = 0;
+    uint32_t bad = 0;
+    __device__ __forceinline__ void load(const uint32_t *__restrict__ pk, const uint32_t *__restrict__ nb, uint64_t p) {
+        p0 = p & ~15ull;
+        const uint64_t w = p0 >> 4;
+        codes = ((uint64_t)pk[w] << 32) | pk[w + 1];
+        const uint64_t v = p0 >> 5;
+        bad = (p0 & 31) ? ((nb[v] >> 16) | (nb[v + 1] << 16)) : nb[v];
+    }
+    // code of base p (p0 <= p < p0 + 32), 4 for a non-base
+    __device__ __forceinline__ uint32_t at(uint64_t p) const {
+        const uint32_t o = (uint32_t)(p - p0);
+        return ((bad >> o) & 1u) ? 4u : (uint32_t)(codes >> (62 - 2 * o)) & 3u;
+    }
+};
+
+// 32 / G HSPs per warp: segment s (lanes sG .. sG + G - 1) aligns its own HSP, lane l of
+// the segment owns band offsets K l .. K l + K - 1 and keeps their previous-row states
+// in registers.  All segments step through rows together.  The vertical-gap input of
+// offset b is offset b + 1 of the previous row (own state, or the next lane's first
+// offset); horizontal gaps come from a segmented warp max-scan as in the pair path.
+// Returns false (and computes nothing) for an HSP whose band exceeds G K offsets.
+template <int G, int K>
+__device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint32_t *__restrict__ qpk,
+                                         const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
+                                         const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                                         const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch,
+                                         int32_t goe, int32_t ge, int32_t w, bool &handled, DevAln &res) {
+    const int lane = threadIdx.x & 31, sl = lane % G;
+    int64_t I0 = 0, I1 = 0, J0 = 0, J1 = 0, dlo = 0, B = 0;
+    uint64_t qb = 0, sb = 0;
+    if (valid) {
+        qb = qstart[h.qi];
+        sb = seq_start[h.seq];
+        const int64_t m = (int64_t)(qstart[h.qi + 1] - qb), L = (int64_t)(seq_start[h.seq + 1] - sb);
+        const int64_t d_s = (int64_t)h.ds - h.qs, d_e = (int64_t)h.de - h.qe;
+        dlo = min(d_s, d_e) - w;
+        B = max(d_s, d_e) + w - dlo + 1;
+        I0 = max((int64_t)0, (int64_t)h.qs - w);
+        I1 = min(m, (int64_t)h.qe + w);
+        J0 = max((int64_t)0, (int64_t)h.ds - w);
+        J1 = min(L, (int64_t)h.de + w);
+    }
+    handled = valid && B <= G * K && I1 - I0 <= 65535;
+    const int32_t rows = handled ? (int32_t)(I1 - I0) : 0;
+    const int32_t max_rows = __reduce_max_sync(0xffffffffu, (uint32_t)rows);
+    const int32_t jlo = (int32_t)(J0 - I0 - dlo), jhi = (int32_t)(J1 - 1 - I0 - dlo);
+    const int32_t Bm1 = (int32_t)B - 1;
+    int32_t pH[K], pE[K];
+    uint32_t pSH[K], pSE[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { pH[k] = 0; pE[k] = SW_NEG; pSH[k] = 0; pSE[k] = 0; }
+    int32_t best = 0, br = INT32_MAX, bb = INT32_MAX;
+    uint32_t bs = 0;
+    BaseWin wq, wd;
+    for (int32_t r = 0; r < max_rows; ++r) {
+        const bool seg_on = r < rows;
+        const int32_t blo = max(0, jlo - r), bhi = min(Bm1, jhi - r);
+        const int32_t pblo = max(0, jlo - r + 1), pbhi = min(Bm1, jhi - r + 1);
+        const bool prow = r > 0;
+        // previous-row state of offset K (sl + 1) (the next lane's first offset)
+        const int32_t uH = __shfl_down_sync(0xffffffffu, pH[0], 1, G), uE = __shfl_down_sync(0xffffffffu, pE[0], 1, G);
+        const uint32_t uSH = __shfl_down_sync(0xffffffffu, pSH[0], 1, G);
+        const uint32_t uSE = __shfl_down_sync(0xffffffffu, pSE[0], 1, G);
+        const int32_t b0 = K * sl;
+        bool lane_on = seg_on && b0 <= bhi && b0 + K - 1 >= blo;
+        uint32_t qc = 4u;
+        const uint64_t i = (uint64_t)(I0 + r);
+        const uint64_t jb = sb + (uint64_t)((int64_t)i + dlo + b0);  // bank position of offset b0
+        if (lane_on) {
+            if (i + qb < wq.p0 || i + qb >= wq.p0 + 32) wq.load(qpk, qnb, qb + i);
+            qc = wq.at(qb + i);
+            const uint64_t jfirst = jb + (uint64_t)max(0, blo - b0), jlast = jb + (uint64_t)min(K - 1, bhi - b0);
+            if (jfirst < wd.p0 || jlast >= wd.p0 + 32) wd.load(bpk, bnb, jfirst);
+        }
+        int32_t H0[K], E[K], X[K];
+        uint32_t C[K], SE[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int32_t b = b0 + k;
+            const bool act = lane_on && b >= blo && b <= bhi;
+            // vertical gap from offset b + 1 of the previous row
+            const int32_t vH = k + 1 < K ? pH[k + 1] : uH, vE = k + 1 < K ? pE[k + 1] : uE;
+            const uint32_t vSH = k + 1 < K ? pSH[k + 1] : uSH, vSE = k + 1 < K ? pSE[k + 1] : uSE;
+            E[k] = SW_NEG;
+            SE[k] = 0;
+            if (act && prow && b + 1 >= pblo && b + 1 <= pbhi) {
+                const int32_t eo = vH + goe, ee = vE + ge;
+                if (eo >= ee) { E[k] = eo; SE[k] = vSH; } else { E[k] = ee; SE[k] = vSE; }
+            }
+            const bool okd = act && prow && b >= pblo && b <= pbhi;
+            const int32_t Hd = okd ? pH[k] : 0;
+            const uint32_t SD = (Hd > 0) ? pSH[k] : ((uint32_t)r << 16) | (uint32_t)b;
+            const uint32_t d = act ? wd.at(jb + k) : 4u;
+            const int32_t Dg = Hd + dev_pair(qc, d, match, mismatch);
+            int32_t cv;
+            if (Dg >= E[k]) { cv = Dg; C[k] = SD; } else { cv = E[k]; C[k] = SE[k]; }
+            H0[k] = cv > 0 ? cv : 0;
+            X[k] = act ? H0[k] + goe - ge * b : SW_XNEG;
+        }
+        // lane aggregate of X (later offsets win ties), then the segmented scan over lanes
+        int32_t xv = X[0];
+        uint32_t xs = C[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k)
+            if (X[k] >= xv) { xv = X[k]; xs = C[k]; }
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const int32_t ov = __shfl_up_sync(0xffffffffu, xv, o, G);
+            const uint32_t os = __shfl_up_sync(0xffffffffu, xs, o, G);
+            if (sl >= o && ov > xv) { xv = ov; xs = os; }
+        }
+        int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1, G);
+        uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1, G);
+        if (sl == 0) { ev = SW_XNEG; es = 0; }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int32_t b = b0 + k;
+            const bool act = lane_on && b >= blo && b <= bhi;
+            const int32_t F = (ev > SW_XNEG) ? ev + ge * (b - 1) : SW_NEG;
+            int32_t Hv;
+            uint32_t S;
+            if (H0[k] >= F) { Hv = H0[k]; S = C[k]; } else { Hv = F; S = es; }
+            if (X[k] >= ev) { ev = X[k]; es = C[k]; }
+            if (act && Hv > best) { best = Hv; br = r; bb = b; bs = S; }
+            pH[k] = Hv; pE[k] = E[k]; pSH[k] = S; pSE[k] = SE[k];
+        }
+    }
+    // segment reduction: highest score, then smallest row, then smallest offset (smallest j)
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const int32_t ob = __shfl_down_sync(0xffffffffu, best, o, G);
+        const int32_t orr = __shfl_down_sync(0xffffffffu, br, o, G), obb = __shfl_down_sync(0xffffffffu, bb, o, G);
+        const uint32_t os = __shfl_down_sync(0xffffffffu, bs, o, G);
+        if (ob > best || (ob == best && (orr < br || (orr == br && obb < bb)))) { best = ob; br = orr; bb = obb; bs = os; }
+    }
+    res.qi = h.qi; res.seq = h.seq; res.qs = res.qe = res.ds = res.de = 0; res.score = 0; res.pad = 0;
+    if (handled && best > 0) {
+        const int64_t bi = I0 + br, bj = bi + dlo + bb;
+        const int64_t i0 = I0 + (int64_t)(bs >> 16), j0 = i0 + dlo + (int64_t)(bs & 0xFFFFu);
+        res.qs = (uint32_t)i0; res.qe = (uint32_t)(bi + 1);
+        res.ds = (uint32_t)j0; res.de = (uint32_t)(bj + 1);
+        res.score = best;
+    }
+}
+
+// Warps take 32 / SWG_G selected HSPs at a time; each segment of SWG_G lanes aligns one
+// whose band fits SWG_G x SWG_K offsets, and the whole warp then aligns the others one by
+// one (pair or strip path).
+constexpr int SWG_G = 8, SWG_K = 5;
 __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ sel, uint32_t n,
                                                    const uint64_t *__restrict__ strip_off, SwCell *__restrict__ strips,
                                                    const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
@@ -852,125 +1119,46 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
                                                    int32_t mismatch, int32_t go, int32_t ge, int32_t w,
                                                    uint32_t *__restrict__ next_task, DevAln *__restrict__ out,
                                                    uint32_t *__restrict__ status) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, seg = lane / SWG_G;
+    constexpr int NG = 32 / SWG_G;
     for (;;) {
-        uint32_t task = 0;
-        if (lane == 0) task = atomicAdd(next_task, 1u);
-        task = __shfl_sync(0xffffffffu, task, 0);
-        if (task >= n) return;
-        const DevHsp h = sel[task];
-        const uint64_t qb = qstart[h.qi], sb = seq_start[h.seq];
-        const int64_t m = (int64_t)(qstart[h.qi + 1] - qb), L = (int64_t)(seq_start[h.seq + 1] - sb);
-        const int64_t d_s = (int64_t)h.ds - h.qs, d_e = (int64_t)h.de - h.qe;
-        const int64_t dlo = min(d_s, d_e) - w, dhi = max(d_s, d_e) + w;
-        const int64_t I0 = max((int64_t)0, (int64_t)h.qs - w), I1 = min(m, (int64_t)h.qe + w);
-        const int64_t J0 = max((int64_t)0, (int64_t)h.ds - w), J1 = min(L, (int64_t)h.de + w);
-        const int64_t B = dhi - dlo + 1;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(next_task, (uint32_t)NG);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) return;
+        const uint32_t task = base + seg;
+        const bool valid = task < n;
+        DevHsp h{};
+        if (valid) h = sel[task];
+        bool handled = false;
         DevAln res;
-        res.qi = h.qi; res.seq = h.seq; res.qs = res.qe = res.ds = res.de = 0; res.score = 0; res.pad = 0;
-        if (B > 65535 || I1 - I0 > 65535) {
-            if (lane == 0) { atomicOr(status, DEV_ERR_BAND_TOO_WIDE); out[task] = res; }
-            continue;
+        sw_group<SWG_G, SWG_K>(valid, h, qpk, qnb, qstart, bpk, bnb, seq_start, match, mismatch, go + ge, ge, w,
+                               handled, res);
+        if (handled && lane % SWG_G == 0) out[task] = res;
+        // wider bands: one HSP at a time with the whole warp
+        uint32_t rest = __ballot_sync(0xffffffffu, valid && !handled && lane % SWG_G == 0);
+        while (rest) {
+            const int src = __ffs(rest) - 1;
+            rest &= rest - 1;
+            sw_task_warp(sel, base + (uint32_t)(src / SWG_G), strip_off, strips, qpk, qnb, qstart, bpk, bnb,
+                         seq_start, match, mismatch, go, ge, w, out, status);
+            __syncwarp();
         }
-        SwCell *row = strips + strip_off[task];
-        int32_t best = 0;
-        int64_t bi = INT64_MAX, bj = INT64_MAX;
-        uint32_t bs = 0;
-        const int32_t goe = go + ge;
-        if (B <= 64) {
-            sw_rows_pair(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best, bi,
-                         bj, bs);
-        } else
-        for (int64_t i = I0; i < I1; ++i) {
-            const int64_t blo = max((int64_t)0, J0 - i - dlo), bhi = min(B - 1, J1 - 1 - i - dlo);
-            if (blo > bhi) continue;
-            const bool prow = i - 1 >= I0;
-            const int64_t pblo = max((int64_t)0, J0 - (i - 1) - dlo), pbhi = min(B - 1, J1 - 1 - (i - 1) - dlo);
-            const uint32_t qc = dev_base(qpk, qnb, qb + (uint64_t)i);
-            int32_t carry_v = SW_XNEG;
-            uint32_t carry_s = 0;
-            for (int64_t c0 = blo; c0 <= bhi; c0 += 32) {
-                const int64_t b = c0 + lane;
-                const bool act = b <= bhi;
-                SwCell pd{0, SW_NEG, 0, 0}, pu{0, SW_NEG, 0, 0};
-                const bool ok_d = act && prow && b >= pblo && b <= pbhi;
-                const bool ok_u = act && prow && b + 1 >= pblo && b + 1 <= pbhi;
-                if (ok_d) pd = row[b];
-                if (ok_u) pu = row[b + 1];
-                __syncwarp();
-                int32_t E = SW_NEG;
-                uint32_t SE = 0;
-                if (ok_u) {
-                    int32_t eo = pu.H + goe, ee = pu.E + ge;
-                    if (eo >= ee) { E = eo; SE = pu.SH; } else { E = ee; SE = pu.SE; }
-                }
-                const int32_t Hd = ok_d ? pd.H : 0;
-                const uint32_t SD = (Hd > 0) ? pd.SH : ((uint32_t)(i - I0) << 16) | (uint32_t)b;
-                const int64_t j = i + dlo + b;
-                int32_t sigma = mismatch;
-                if (act) sigma = dev_pair(qc, dev_base(bpk, bnb, sb + (uint64_t)j), match, mismatch);
-                const int32_t Dg = Hd + sigma;
-                int32_t cand;
-                uint32_t Sc;
-                if (Dg >= E) { cand = Dg; Sc = SD; } else { cand = E; Sc = SE; }
-                const int32_t H0 = cand > 0 ? cand : 0;
-                // F by max-scan with carry from earlier chunks of this row
-                int32_t xv = act ? H0 + goe - ge * (int32_t)b : SW_XNEG;
-                uint32_t xs = Sc;
-                scan_pair_max(xv, xs, lane);
-                int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1);
-                uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1);
-                // the carry (earlier chunks) wins only when strictly larger
-                if (lane == 0) { ev = carry_v; es = carry_s; }
-                else if (carry_v > ev) { ev = carry_v; es = carry_s; }
-                int32_t last_v = __shfl_sync(0xffffffffu, xv, 31);
-                uint32_t last_s = __shfl_sync(0xffffffffu, xs, 31);
-                if (last_v >= carry_v) { carry_v = last_v; carry_s = last_s; }
-                int32_t F = (ev > SW_XNEG) ? ev + ge * (int32_t)(b - 1) : SW_NEG;
-                uint32_t SF = es;
-                int32_t H;
-                uint32_t SH;
-                if (H0 >= F) { H = H0; SH = Sc; } else { H = F; SH = SF; }
-                if (act) {
-                    SwCell c;
-                    c.H = H; c.E = E; c.SH = SH; c.SE = SE;
-                    row[b] = c;
-                    if (H > best) { best = H; bi = i; bj = j; bs = SH; }
-                }
-                __syncwarp();
-            }
-        }
-        // reduce: highest score, then smallest i, then smallest j
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            int32_t ob = __shfl_down_sync(0xffffffffu, best, o);
-            int64_t oi = __shfl_down_sync(0xffffffffu, bi, o);
-            int64_t oj = __shfl_down_sync(0xffffffffu, bj, o);
-            uint32_t os = __shfl_down_sync(0xffffffffu, bs, o);
-            if (ob > best || (ob == best && (oi < bi || (oi == bi && oj < bj)))) {
-                best = ob; bi = oi; bj = oj; bs = os;
-            }
-        }
-        if (lane == 0) {
-            if (best > 0) {
-                int64_t i0 = I0 + (int64_t)(bs >> 16);
-                int64_t j0 = i0 + dlo + (int64_t)(bs & 0xFFFFu);
-                res.qs = (uint32_t)i0; res.qe = (uint32_t)(bi + 1);
-                res.ds = (uint32_t)j0; res.de = (uint32_t)(bj + 1);
-                res.score = best;
-            }
-            out[task] = res;
-        }
-        __syncwarp();
     }
 }
 
-__global__ void k_band_width(const DevHsp *__restrict__ h, uint32_t n, int32_t w, uint32_t *__restrict__ B) {
+// Strip length of each HSP's band (B + 1), and the band area (DP-window rows x B, the
+// cells the alignment kernel evaluates) summed into *cells.
+__global__ void k_band_width(const DevHsp *__restrict__ h, uint32_t n, int32_t w, const uint64_t *__restrict__ qstart,
+                             uint32_t *__restrict__ B, unsigned long long *__restrict__ cells) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t d_s = (int64_t)h[i].ds - h[i].qs, d_e = (int64_t)h[i].de - h[i].qe;
     int64_t b = (max(d_s, d_e) + w) - (min(d_s, d_e) - w) + 1;
     B[i] = (uint32_t)min(b + 1, (int64_t)65537);  // +1: the strip is read at b + 1
+    const int64_t m = (int64_t)(qstart[h[i].qi + 1] - qstart[h[i].qi]);
+    const int64_t rows = min(m, (int64_t)h[i].qe + w) - max((int64_t)0, (int64_t)h[i].qs - w);
+    if (rows > 0) atomicAdd(cells, (unsigned long long)(rows * b));
 }
 
 // ------------------------------------------------------ a13: ranking --
@@ -1547,17 +1735,21 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     if (n_sel) {
         uint32_t *B = arena.alloc_n<uint32_t>(n_sel);
         uint64_t *soff = arena.alloc_n<uint64_t>(n_sel + 1);
+        unsigned long long *dp_cells = reinterpret_cast<unsigned long long *>(arena.alloc_n<uint64_t>(1));
+        GN_CUDA(cudaMemsetAsync(dp_cells, 0, 8, s));
         GN_LAUNCH("k_band_width", n_sel, s,
-                  k_band_width<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, B));
+                  k_band_width<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, B,
+                                                                  dp_cells));
         void *scr = arena.alloc(scan_scratch_bytes(n_sel));
         exclusive_scan_u32(B, soff, n_sel, scr, s);
-        uint64_t cells = 0;
+        uint64_t cells = 0, area = 0;
         GN_CUDA(cudaMemcpyAsync(&cells, soff + n_sel, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        GN_CUDA(cudaMemcpyAsync(&area, dp_cells, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         GN_CUDA(cudaStreamSynchronize(s));
         SwCell *strips = arena.alloc_n<SwCell>(cells);
         GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
-        unsigned warps = (unsigned)std::min<uint64_t>(n_sel, (uint64_t)num_sms() * 32);
-        GN_LAUNCH("k_banded_sw", cells, s,
+        unsigned warps = (unsigned)std::min<uint64_t>((n_sel + 3) / 4, (uint64_t)num_sms() * 32);
+        GN_LAUNCH("k_banded_sw", area, s,
                   k_banded_sw<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
                                                             ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
                                                             sc.mismatch, sc.gap_open, sc.gap_extend,
