@@ -712,6 +712,138 @@ __global__ void k_overlap_sweep(const DevHsp *__restrict__ in, uint32_t n, DevHs
 }
 
 // ----------------------------------------------------- a11: selection --
+// Per-query selection on records sorted by (qi, seq, qs, ds, qe, de): a block per
+// query keeps its N longest records, ties broken by that order (a stable choice by
+// length), and writes them by (length desc, seq, qs, ds, qe, de).  The N-th largest
+// length T comes from two 256-bin histograms (high and low byte of the length); the
+// selected records are those longer than T and the first ones of length T.
+constexpr int SQ_CAP = 1024;  // largest N this kernel handles
+constexpr int SQ_THREADS = 256;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;  // inclusive warp prefix
+    }
+    __syncthreads();
+    total = warp_tot[nw - 1];
+    const uint32_t before = wid ? warp_tot[wid - 1] : 0u;
+    __syncthreads();  // warp_tot is reused by the next call
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SQ_THREADS) k_select_query(const DevHsp *__restrict__ rec,
+                                                             const uint32_t *__restrict__ qfirst,
+                                                             const uint64_t *__restrict__ qout, uint32_t N,
+                                                             DevHsp *__restrict__ sel) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t warp_tot[SQ_THREADS / 32];
+    __shared__ uint64_t keys[SQ_CAP];
+    __shared__ uint32_t T_s, gt_s;
+    const uint32_t q = blockIdx.x;
+    const uint32_t a = qfirst[q], b = qfirst[q + 1], n = b - a;
+    const uint64_t out0 = qout[q];
+    const uint32_t nsel = (uint32_t)(qout[q + 1] - out0);
+    if (nsel == 0) return;
+    uint32_t T = 0, r_eq = n;  // n <= N: every record is selected
+    if (n > N) {
+        uint32_t above = 0, hb = 0;
+        for (int level = 0; level < 2; ++level) {
+            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+                const uint32_t len = min(rec[i].len, 65535u);
+                if (level == 0) atomicAdd(&hist[len >> 8], 1u);
+                else if ((len >> 8) == hb) atomicAdd(&hist[len & 0xFFu], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t acc = above;
+                int x = 255;
+                while (acc + hist[x] < N) acc += hist[x--];
+                T_s = level == 0 ? (uint32_t)x : ((hb << 8) | (uint32_t)x);
+                gt_s = acc;
+            }
+            __syncthreads();
+            if (level == 0) { hb = T_s; above = gt_s; }
+            else { T = T_s; above = gt_s; }
+            __syncthreads();
+        }
+        r_eq = N - above;  // records of length T to take, in array order
+    }
+    // ordered compaction of the selected records (array order), keyed by (length desc, position)
+    uint32_t base = 0, eq_seen = 0;
+    for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
+        const uint32_t i = i0 + threadIdx.x;
+        uint32_t len = 0;
+        bool eq = false, gt = false;
+        if (i < n) {
+            len = min(rec[a + i].len, 65535u);
+            gt = n <= N || len > T;
+            eq = !gt && len == T;
+        }
+        uint32_t eq_tot = 0, take_tot = 0;
+        const uint32_t eq_rank = eq_seen + block_excl_scan(eq ? 1u : 0u, warp_tot, eq_tot);
+        const bool take = gt || (eq && eq_rank < r_eq);
+        const uint32_t pos = base + block_excl_scan(take ? 1u : 0u, warp_tot, take_tot);
+        if (take) keys[pos] = ((uint64_t)(65535u - len) << 32) | i;
+        base += take_tot;
+        eq_seen += eq_tot;
+    }
+    __syncthreads();
+    // bitonic sort of the nsel keys (unique: they carry the position)
+    uint32_t P = 1;
+    while (P < nsel) P <<= 1;
+    for (uint32_t i = nsel + threadIdx.x; i < P; i += blockDim.x) keys[i] = ~0ull;
+    __syncthreads();
+    for (uint32_t k2 = 2; k2 <= P; k2 <<= 1) {
+        for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x = keys[i], y = keys[ixj];
+                    if ((x > y) == ((i & k2) == 0)) { keys[i] = y; keys[ixj] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t k = threadIdx.x; k < nsel; k += blockDim.x) sel[out0 + k] = rec[a + (uint32_t)(keys[k] & 0xFFFFFFFFu)];
+}
+
+// first[q] = first record of query q in records sorted by query (first[nq] = n)
+__global__ void k_query_bounds(const DevHsp *__restrict__ rec, uint32_t n, uint32_t nq, uint32_t *__restrict__ first) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > nq) return;
+    uint32_t lo = 0, hi = n;  // first index with qi >= q
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (rec[mid].qi < q) lo = mid + 1;
+        else hi = mid;
+    }
+    first[q] = lo;
+}
+
+// counts of the selected records per query: min(N, records of the query)
+__global__ void k_select_counts(const uint32_t *__restrict__ first, uint32_t nq, uint32_t N, uint32_t *__restrict__ cnt) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nq) cnt[q] = min(N, first[q + 1] - first[q]);
+}
+
 __global__ void k_first_of_query(const uint32_t *__restrict__ recs, int W, uint32_t n, uint32_t *__restrict__ first) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1706,7 +1838,25 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     uint32_t n_sel = 0;
     DevHsp *sel = arena.alloc_n<DevHsp>(n_mg);
     uint32_t *first = arena.alloc_n<uint32_t>(nq);
-    if (n_mg) {
+    const char *senv = getenv("GN_SELECT_PATH");
+    const bool per_query_select = p.max_alignments > 0 && p.max_alignments <= (uint32_t)SQ_CAP &&
+                                  !(senv && strcmp(senv, "sort") == 0);
+    if (n_mg && per_query_select) {
+        uint32_t *qb = arena.alloc_n<uint32_t>(nq + 1);
+        GN_LAUNCH("k_query_bounds", nq + 1, s, k_query_bounds<<<blocks_for(nq + 1), 256, 0, s>>>(merged, n_mg, nq, qb));
+        uint32_t *cnt = arena.alloc_n<uint32_t>(nq);
+        GN_LAUNCH("k_select_counts", nq, s,
+                  k_select_counts<<<blocks_for(nq), 256, 0, s>>>(qb, nq, p.max_alignments, cnt));
+        uint64_t *qo = arena.alloc_n<uint64_t>(nq + 1);
+        void *scr = arena.alloc(scan_scratch_bytes(nq));
+        exclusive_scan_u32(cnt, qo, nq, scr, s);
+        uint64_t tot = 0;
+        GN_CUDA(cudaMemcpyAsync(&tot, qo + nq, 8, cudaMemcpyDeviceToHost, s));
+        GN_LAUNCH("k_select_query", n_mg, s,
+                  k_select_query<<<nq, SQ_THREADS, 0, s>>>(merged, qb, qo, p.max_alignments, sel));
+        GN_CUDA(cudaStreamSynchronize(s));
+        n_sel = (uint32_t)tot;
+    } else if (n_mg) {
         uint32_t *perm = arena.alloc_n<uint32_t>(n_mg);
         sort_records(reinterpret_cast<const uint32_t *>(merged), HSP_WORDS, n_mg,
                      {{W_QI, qib, false}, {W_LEN, qposb, true}, {W_SEQ, seqb, false}, {W_QS, qposb, false},

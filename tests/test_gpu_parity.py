@@ -191,7 +191,7 @@ def test_chunked_equals_unchunked(gn, mid_small, monkeypatch):
 
 
 @pytest.mark.parametrize("env", [{"GN_HIT_GROUPING": "sort"}, {"GN_BUCKET_CAP": "64"}, {"GN_TILE_FILTER": "0"},
-                                 {"GN_RANK_PATH": "sort"}, {"GN_TILE_POS": "64"},
+                                 {"GN_RANK_PATH": "sort"}, {"GN_TILE_POS": "64"}, {"GN_SELECT_PATH": "sort"},
                                  {"GN_BUCKET_CAP": "64", "GN_MAX_CHUNK_HITS": "30000"},
                                  {"GN_BUCKET_CAP": "64", "GN_SPILL_ROOM": "16"}])
 def test_hit_grouping_paths_agree_with_oracle(gn, mid_small, monkeypatch, env):
