@@ -397,25 +397,18 @@ def run_ours(args, dist):
         gn.search(ix, qstart, qd, stream=sh).close()
     torch.cuda.synchronize()
 
-    # ---- timed region: device-resident queries, per-kernel events on the launching stream
+    # ---- timed region: device-resident queries, events on the launching stream around the K steps
     dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(dev)
     time.sleep(0.4)
     launches0 = gn.gn_kernel_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kern = {}
-    phases = {}
     n_hits = 0
     e0.record(stream)
     for _ in range(args.steps):
-        r = gn.search(ix, qstart, qd, params=gn.make_params(flags=flags_t), stream=sh)
+        r = gn.search(ix, qstart, qd, stream=sh)
         n_hits = r.n_queries and gn.gn_results_count(r.handle)[1]
-        for name, (ms, la, un) in ix.kernel_times().items():
-            a = kern.setdefault(name, [0.0, 0, 0])
-            a[0] += ms; a[1] += la; a[2] += un
-        for name, ms in ix.phase_times().items():
-            phases[name] = phases.get(name, 0.0) + ms
         r.close()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -426,6 +419,20 @@ def run_ours(args, dist):
     ms_step = dist.max(ms_local)
     bases_all = dist.sum(float(M))
     value = bases_all / 1e3 / (ms_step / 1e3)
+
+    # ---- the same steps again with per-kernel CUDA events (each launch bracketed on its stream):
+    # kernel times and work units for the rooflines (this pass is not the timed one)
+    kern = {}
+    phases = {}
+    for _ in range(args.steps):
+        r = gn.search(ix, qstart, qd, params=gn.make_params(flags=flags_t), stream=sh)
+        for name, (ms, la, un) in ix.kernel_times().items():
+            a = kern.setdefault(name, [0.0, 0, 0])
+            a[0] += ms; a[1] += la; a[2] += un
+        for name, ms in ix.phase_times().items():
+            phases[name] = phases.get(name, 0.0) + ms
+        r.close()
+    torch.cuda.synchronize()
 
     # ---- end to end through the public call with pinned host queries and host results
     dist.barrier()
@@ -541,7 +548,9 @@ def run_ours(args, dist):
                                 "postings": info.n_postings, "device_gib": info.device_bytes / 2**30,
                                 "includes": "host-to-device copy of the bank + pack + windows + scan + sort"},
                 "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()},
-                "kernels": kernels_out, "alignments_per_step": n_hits}
+                "kernels": kernels_out, "alignments_per_step": n_hits,
+                "kernel_timing": "per-kernel CUDA events from a second, instrumented pass of the same K steps; "
+                                 "the timed pass records events only around the K steps"}
         print(json.dumps(line), flush=True)
     ix.close()
     return 0
