@@ -300,7 +300,8 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
     uint64_t xa, uint64_t xb, const uint32_t *__restrict__ post, uint32_t qa, const uint32_t *__restrict__ bbase,
     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount, uint64_t *__restrict__ bkeys, uint32_t bcap,
     uint64_t *__restrict__ spill, unsigned long long *__restrict__ spill_count, unsigned long long spill_cap,
-    int qbits, int filter, uint32_t D, int tpos, int fbits, int fbits2, unsigned long long *__restrict__ kept_total) {
+    int qbits, int filter, uint32_t D, int tpos, int fbits, int fbits2, unsigned long long *__restrict__ kept_total,
+    uint32_t tile_step, int count_only) {
     extern __shared__ __align__(16) unsigned char bf_smem[];
     const uint32_t halo = filter ? D : 0u;
     const uint32_t span_max = (uint32_t)tpos + 2u * halo;
@@ -316,7 +317,10 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
     t.bs = reinterpret_cast<uint8_t *>(seen2 + nwords2);
     __shared__ uint32_t ctr;
     uint32_t my_kept = 0;
-    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tpos; t0 < xb; t0 += (uint64_t)gridDim.x * tpos) {
+    uint32_t my_core = 0;  // core hits seen (count-only runs)
+    // tiles 0, tile_step, 2 tile_step, ... (every tile unless sampling)
+    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tile_step * tpos; t0 < xb;
+         t0 += (uint64_t)gridDim.x * tile_step * tpos) {
         const uint64_t t1 = min(xb, t0 + (uint64_t)tpos);
         const uint64_t lo = t0 - xa > halo ? t0 - halo : xa, hi = min(xb, t1 + halo);
         const uint32_t span = (uint32_t)(hi - lo);
@@ -368,7 +372,8 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
             if (threadIdx.x == 0) ctr = 0;
             __syncthreads();
         }
-        // place the kept core hits
+        // place the kept core hits (count them only, when sampling the keep rate)
+        if (count_only && threadIdx.x == 0) my_core += t.hs[t1 - lo] - t.hs[t0 - lo];
         for_tile_chunks(t, t.hs[t0 - lo], t.hs[t1 - lo], &ctr, post, [&](const uint32_t *idx, const uint32_t *ent,
                                                                             const bool *ok) {
             uint64_t key[4];
@@ -388,6 +393,7 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
                 b[u] = bb + (uint32_t)(gk >> bs);
                 key[u] = (gk << 16) | (qq & 0xFFFFu);
             }
+            if (count_only) return;
             // the global slot reservations first, then the dependent stores
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -407,6 +413,7 @@ __global__ void __launch_bounds__(256) k_bucket_fill(
         __syncthreads();  // the table and bitmaps are rebuilt for the next tile
     }
     if (my_kept) atomicAdd(kept_total, (unsigned long long)my_kept);
+    if (my_core) atomicAdd(kept_total + 1, (unsigned long long)my_core);
 }
 
 // Dynamic shared memory of k_bucket_fill.
@@ -422,6 +429,70 @@ __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc,
     for (uint32_t b = bbase[q] + threadIdx.x; b < bbase[q + 1]; b += blockDim.x) bq[b] = (uint16_t)q;
 }
 
+// Chains of candidates sorted by (G', qpos) within one bucket (one query): candidate i
+// starts a chain unless candidate i - 1 has the same diagonal, lies at most D query
+// offsets before it and in the same bank sequence.  The threads of a warp (NW = 1) or of
+// a block mark the chain heads in a bitmask (words at heads[], one per 32 candidates);
+// each head's chain ends before the next head, and an HSP is emitted for every chain of
+// length >= min_len.  Threads are tid, tid + nthreads, ...; sync() orders the two steps.
+template <class Sync>
+__device__ __forceinline__ void chain_emit(const uint64_t *cand, uint32_t nc, uint32_t *heads, uint32_t tid,
+                                           uint32_t nthreads, Sync sync, uint32_t ql, uint32_t qa, int k, uint32_t D,
+                                           uint32_t min_len, const SeqMap &sm, DevHsp *__restrict__ out,
+                                           uint32_t *__restrict__ count, uint32_t out_cap,
+                                           uint32_t *__restrict__ status) {
+    const uint32_t nw = (nc + 31) / 32;
+    for (uint32_t i0 = tid & ~31u; i0 < nw * 32; i0 += nthreads) {
+        const uint32_t i = i0 + (tid & 31);
+        bool head = false;
+        if (i < nc) {
+            const uint64_t key = cand[i];
+            const uint32_t qs = (uint32_t)(key & 0xFFFFu);
+            const uint64_t gpos = (key >> 16) - QBIAS + qs;
+            head = true;
+            if (i > 0) {
+                const uint64_t prev = cand[i - 1];
+                const uint32_t qp = (uint32_t)(prev & 0xFFFFu);
+                if ((prev >> 16) == (key >> 16) && qs - qp <= D) {
+                    const uint32_t sq = dev_seq_of(sm, gpos);
+                    head = sm.start[sq] > gpos - (qs - qp);  // a sequence starts between them
+                }
+            }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, head);
+        if ((tid & 31) == 0) heads[i0 / 32] = m;
+    }
+    sync();
+    for (uint32_t i = tid; i < nc; i += nthreads) {
+        if (!((heads[i / 32] >> (i & 31)) & 1u)) continue;
+        // the next head after i
+        uint32_t w = i / 32, rest = heads[w] & ~((2u << (i & 31)) - 1u);
+        while (!rest && ++w < nw) rest = heads[w];
+        const uint32_t end = (rest ? w * 32 + (uint32_t)(__ffs(rest) - 1) : nc) - 1;
+        const uint64_t key = cand[i], kj = cand[end];
+        const uint32_t qs = (uint32_t)(key & 0xFFFFu), qe = (uint32_t)(kj & 0xFFFFu) + (uint32_t)k;
+        const uint32_t len = qe - qs;
+        if (len < min_len) continue;
+        const uint64_t gpos = (key >> 16) - QBIAS + qs;
+        const uint32_t sq = dev_seq_of(sm, gpos);
+        const uint32_t ds = (uint32_t)(gpos - sm.start[sq]);
+        const uint32_t slot = atomicAdd(count, 1u);
+        if (slot < out_cap) {
+            DevHsp hh;
+            hh.qi = qa + ql; hh.seq = sq; hh.qs = qs; hh.qe = qe; hh.ds = ds; hh.de = ds + len; hh.len = len;
+            out[slot] = hh;
+        } else {
+            atomicOr(status, DEV_ERR_CAPACITY);
+        }
+    }
+}
+struct WarpSync {
+    __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
 // One warp per bucket.  Two bitmaps per warp mark diagonal hashes seen once and
 // seen twice; hits whose hash was seen twice are candidates (a hash collision
 // only adds a candidate that the exact chaining below then drops).  Candidates
@@ -430,18 +501,22 @@ __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc,
 constexpr int BGW_WARPS = 8;
 constexpr int BGW_BITS = 8192;
 constexpr int BGW_CAND = 256;
+constexpr int BGC_CAND = 1024;  // entries a block-level bucket group takes
 
 __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
     const uint64_t *__restrict__ bkeys, const uint32_t *__restrict__ bcount, uint32_t bcap, uint32_t NB,
     const uint16_t *__restrict__ bq, uint32_t qa, int qbits, int k, uint32_t D, uint32_t min_len, int singles,
     SeqMap sm, DevHsp *__restrict__ out, uint32_t *__restrict__ count,
     uint32_t out_cap, uint64_t *__restrict__ ovf, unsigned long long ovf_cap,
-    unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status, uint32_t *__restrict__ next_bucket) {
+    unsigned long long *__restrict__ ovf_count, uint32_t *__restrict__ status, uint32_t *__restrict__ next_bucket,
+    uint32_t *__restrict__ big, uint32_t *__restrict__ big_count) {
     extern __shared__ __align__(16) unsigned char gw_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *seen = reinterpret_cast<uint32_t *>(gw_smem) + wib * (2 * BGW_BITS / 32);
     uint32_t *seen2 = seen + BGW_BITS / 32;
     uint64_t *cand = reinterpret_cast<uint64_t *>(gw_smem + BGW_WARPS * 2 * BGW_BITS / 8) + wib * BGW_CAND;
+    uint32_t *heads = reinterpret_cast<uint32_t *>(gw_smem + BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8)) +
+                      wib * (BGW_CAND / 32);
     const uint32_t lt = (1u << lane) - 1u;
     for (;;) {
         uint32_t b = 0;
@@ -493,6 +568,11 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
             }
             const uint32_t m = __ballot_sync(0xffffffffu, keep);
             if (nc + __popc(m) > BGW_CAND) {
+                if (n <= BGC_CAND) {  // the block kernel takes it
+                    if (lane == 0) big[atomicAdd(big_count, 1u)] = b;
+                    nc = 0;
+                    break;
+                }
                 spill = true;
             } else {
                 if (keep) cand[nc + __popc(m & lt)] = key;
@@ -532,40 +612,99 @@ __global__ void __launch_bounds__(BGW_WARPS * 32) k_bucket_group_warp(
                 __syncwarp();
             }
         }
-        for (uint32_t i = lane; i < nc; i += 32) {
-            const uint64_t key = cand[i];
-            const uint32_t qs = (uint32_t)(key & 0xFFFFu);
-            const uint64_t gpos = (key >> 16) - QBIAS + qs;
-            const uint32_t sq = dev_seq_of(sm, gpos);
-            if (i > 0) {
-                const uint64_t prev = cand[i - 1];
-                const uint32_t qp = (uint32_t)(prev & 0xFFFFu);
-                if ((prev >> 16) == (key >> 16) && qs - qp <= D && sm.start[sq] <= gpos - (qs - qp)) continue;
+        chain_emit(cand, nc, heads, lane, 32, WarpSync(), ql, qa, k, D, min_len, sm, out, count, out_cap, status);
+        __syncwarp();
+    }
+}
+
+// Exclusive prefix sum of v over the block (all threads call it); *total gets the sum.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;  // inclusive warp prefix
+    }
+    __syncthreads();
+    total = warp_tot[nw - 1];
+    const uint32_t before = wid ? warp_tot[wid - 1] : 0u;
+    __syncthreads();  // warp_tot is reused by the next call
+    return before + x - v;
+}
+
+// One block per bucket that has more candidates than a warp holds (at most BGC_CAND
+// entries in all): the same filter, sort and chaining as k_bucket_group_warp, over
+// the whole block.  Blocks take the listed buckets in turn.
+__global__ void __launch_bounds__(256) k_bucket_group_block(
+    const uint64_t *__restrict__ bkeys, const uint32_t *__restrict__ bcount, uint32_t bcap,
+    const uint16_t *__restrict__ bq, const uint32_t *__restrict__ big, const uint32_t *__restrict__ big_count,
+    uint32_t qa, int k, uint32_t D, uint32_t min_len, int singles, SeqMap sm, DevHsp *__restrict__ out,
+    uint32_t *__restrict__ count, uint32_t out_cap, uint32_t *__restrict__ status) {
+    __shared__ uint32_t seen[BGW_BITS / 32], seen2[BGW_BITS / 32];
+    __shared__ uint64_t cand[BGC_CAND];
+    __shared__ uint32_t heads[BGC_CAND / 32];
+    __shared__ uint32_t warp_tot[8];
+    const uint32_t nbig = *big_count;
+    for (uint32_t j = blockIdx.x; j < nbig; j += gridDim.x) {
+        const uint32_t b = big[j];
+        const uint64_t beg = (uint64_t)b * bcap;
+        const uint32_t n = min(bcount[b], bcap);
+        const uint32_t ql = bq[b];
+        for (uint32_t i = threadIdx.x; i < BGW_BITS / 32; i += blockDim.x) { seen[i] = 0u; seen2[i] = 0u; }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t h = (uint32_t)(((bkeys[beg + i] >> 16) * 0x9E3779B97F4A7C15ull) >> 51);  // 13 bits
+            const uint32_t bit = 1u << (h & 31);
+            const uint32_t old = atomicOr(&seen[h >> 5], bit);
+            if (old & bit) atomicOr(&seen2[h >> 5], bit);
+        }
+        __syncthreads();
+        uint32_t nc = 0;
+        for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
+            const uint32_t i = i0 + threadIdx.x;
+            uint64_t key = 0;
+            bool keep = false;
+            if (i < n) {
+                key = bkeys[beg + i];
+                const uint32_t h = (uint32_t)(((key >> 16) * 0x9E3779B97F4A7C15ull) >> 51);
+                keep = singles || ((seen2[h >> 5] >> (h & 31)) & 1u);
             }
-            const uint64_t seq_end = sm.start[sq + 1];
-            uint32_t j = i;
-            uint64_t kj = key;
-            while (j + 1 < nc) {
-                const uint64_t kn = cand[j + 1];
-                const uint32_t qn = (uint32_t)(kn & 0xFFFFu);
-                if ((kn >> 16) != (key >> 16) || qn - (uint32_t)(kj & 0xFFFFu) > D || gpos - qs + qn >= seq_end) break;
-                kj = kn;
-                ++j;
-            }
-            const uint32_t qe = (uint32_t)(kj & 0xFFFFu) + (uint32_t)k;
-            const uint32_t len = qe - qs;
-            if (len < min_len) continue;
-            const uint32_t ds = (uint32_t)(gpos - sm.start[sq]);
-            const uint32_t slot = atomicAdd(count, 1u);
-            if (slot < out_cap) {
-                DevHsp hh;
-                hh.qi = qa + ql; hh.seq = sq; hh.qs = qs; hh.qe = qe; hh.ds = ds; hh.de = ds + len; hh.len = len;
-                out[slot] = hh;
-            } else {
-                atomicOr(status, DEV_ERR_CAPACITY);
+            uint32_t tot = 0;
+            const uint32_t pos = nc + block_excl_scan(keep ? 1u : 0u, warp_tot, tot);
+            if (keep) cand[pos] = key;
+            nc += tot;
+        }
+        uint32_t P = 1;
+        while (P < nc) P <<= 1;
+        for (uint32_t i = nc + threadIdx.x; i < P; i += blockDim.x) cand[i] = ~0ull;
+        __syncthreads();
+        for (uint32_t k2 = 2; k2 <= P; k2 <<= 1) {
+            for (uint32_t jj = k2 >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    const uint32_t ixj = i ^ jj;
+                    if (ixj > i) {
+                        const uint64_t x = cand[i], y = cand[ixj];
+                        if ((x > y) == ((i & k2) == 0)) { cand[i] = y; cand[ixj] = x; }
+                    }
+                }
+                __syncthreads();
             }
         }
-        __syncwarp();
+        chain_emit(cand, nc, heads, threadIdx.x, blockDim.x, BlockSync(), ql, qa, k, D, min_len, sm, out, count,
+                   out_cap, status);
+        __syncthreads();
     }
 }
 
@@ -719,32 +858,6 @@ __global__ void k_overlap_sweep(const DevHsp *__restrict__ in, uint32_t n, DevHs
 // selected records are those longer than T and the first ones of length T.
 constexpr int SQ_CAP = 1024;  // largest N this kernel handles
 constexpr int SQ_THREADS = 256;
-
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *warp_tot, uint32_t &total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t t = lane < nw ? warp_tot[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        if (lane < nw) warp_tot[lane] = t;  // inclusive warp prefix
-    }
-    __syncthreads();
-    total = warp_tot[nw - 1];
-    const uint32_t before = wid ? warp_tot[wid - 1] : 0u;
-    __syncthreads();  // warp_tot is reused by the next call
-    return before + x - v;
-}
 
 __global__ void __launch_bounds__(SQ_THREADS) k_select_query(const DevHsp *__restrict__ rec,
                                                              const uint32_t *__restrict__ qfirst,
@@ -1664,7 +1777,12 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const char *fenv = getenv("GN_TILE_FILTER");
                 const int filter = (!singles && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
                                     !(fenv && strcmp(fenv, "0") == 0)) ? 1 : 0;
-                int tpos = 256, fbits = 18, fbits2 = 16;
+                // tiles of about 25,000 hits: 256 offsets at ~88 hits per offset (stride 11 on a 4 Gbp
+                // bank), fewer where lists are long (small strides), up to 512 where they are short
+                const double per_offset = (double)Hc / (double)std::max<uint64_t>(1, xb - xa);
+                int tpos = 32;
+                while (tpos < 512 && tpos * 2 * per_offset <= 25000.0 * 1.5) tpos *= 2;
+                int fbits = 18, fbits2 = 16;
                 if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS2")) fbits2 = std::max(12, std::min(19, atoi(e)));
@@ -1675,29 +1793,40 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     bcap = (uint32_t)std::max(8ul, std::min(65536ul, strtoul(e, nullptr, 10)));
                     target = std::max<uint32_t>(2, bcap / 2);
                 }
+                const bool fixed_cap = getenv("GN_BUCKET_CAP") != nullptr;
                 std::vector<uint32_t> bbase(nqc + 1), bshift(nqc);
                 const int min_lg = std::max(0, gbits - 31);
-                uint64_t nb64 = 0;
-                for (uint32_t i = 0; i < nqc; ++i) {
-                    const uint64_t hi = hq[qa + i + 1] - hq[qa + i];
-                    const uint64_t want = (hi + target - 1) / target;
-                    int lg = 0;
-                    while ((1ull << lg) < want) ++lg;
-                    lg = std::min(std::max(lg, min_lg), gbits);
-                    bshift[i] = (uint32_t)(gbits - lg);
-                    bbase[i] = (uint32_t)nb64;
-                    nb64 += 1ull << lg;
-                    GN_REQUIRE(nb64 < (1ull << 32), GN_ETOOBIG, "too many hit buckets in one chunk");
-                }
-                bbase[nqc] = (uint32_t)nb64;
-                const uint32_t NB = (uint32_t)nb64;
+                uint32_t NB = 0;
                 uint32_t *d_bbase = carena.alloc_n<uint32_t>(nqc + 1);
                 uint32_t *d_bshift = carena.alloc_n<uint32_t>(nqc);
-                GN_CUDA(cudaMemcpyAsync(d_bbase, bbase.data(), 4 * (nqc + 1), cudaMemcpyHostToDevice, s));
-                GN_CUDA(cudaMemcpyAsync(d_bshift, bshift.data(), 4 * nqc, cudaMemcpyHostToDevice, s));
-                uint32_t *bcount = carena.alloc_n<uint32_t>(NB);
-                uint64_t *bkeys = carena.alloc_n<uint64_t>((uint64_t)NB * bcap);
-                uint16_t *bq = carena.alloc_n<uint16_t>(NB);
+                uint32_t *bcount = nullptr;
+                uint64_t *bkeys = nullptr;
+                uint16_t *bq = nullptr;
+                // 2^lg buckets per query, about `target` raw hits each
+                auto plan = [&](uint64_t target) {
+                    uint64_t nb64 = 0;
+                    for (uint32_t i = 0; i < nqc; ++i) {
+                        const uint64_t hi = hq[qa + i + 1] - hq[qa + i];
+                        const uint64_t want = (hi + target - 1) / target;
+                        int lg = 0;
+                        while ((1ull << lg) < want) ++lg;
+                        lg = std::min(std::max(lg, min_lg), gbits);
+                        bshift[i] = (uint32_t)(gbits - lg);
+                        bbase[i] = (uint32_t)nb64;
+                        nb64 += 1ull << lg;
+                        GN_REQUIRE(nb64 < (1ull << 32), GN_ETOOBIG, "too many hit buckets in one chunk");
+                    }
+                    bbase[nqc] = (uint32_t)nb64;
+                    NB = (uint32_t)nb64;
+                    GN_CUDA(cudaMemcpyAsync(d_bbase, bbase.data(), 4 * (nqc + 1), cudaMemcpyHostToDevice, s));
+                    GN_CUDA(cudaMemcpyAsync(d_bshift, bshift.data(), 4 * nqc, cudaMemcpyHostToDevice, s));
+                };
+                auto alloc_buckets = [&]() {
+                    bcount = carena.alloc_n<uint32_t>(NB);
+                    bkeys = carena.alloc_n<uint64_t>((uint64_t)NB * bcap);
+                    bq = carena.alloc_n<uint16_t>(NB);
+                };
+                plan(target);
                 unsigned long long *spill_count = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
                 uint64_t spill_room = std::max<uint64_t>(1u << 16, Hc / 32);
                 uint64_t min_room = 0;  // GN_SPILL_ROOM: small first rooms (exercises the reruns)
@@ -1713,31 +1842,87 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const unsigned fgrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(focc, 1) * 4));
                 unsigned long long n_spill = 0, n_kept = 0;
-                unsigned long long *kept_total = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(1));
+                unsigned long long *kept_total = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(2));
+                // Keep rate of the repeat filter, measured on a sample of tiles (no placement): the plan
+                // above assumes the stride-11 rate; where far more hits are kept (small strides, where
+                // overlapping k-mers put most hits next to another on their diagonal) the buckets are
+                // planned smaller.
+                // With a keep rate above a quarter, 256-entry buckets of about 128 kept hits are planned:
+                // the grouping warps take every such bucket whole.
+                auto plan_for_keep = [&](double keep, uint32_t &t_new, uint32_t &cap_new) {
+                    if (keep > 0.25) {
+                        cap_new = 256;
+                        t_new = (uint32_t)std::max(64.0, 128.0 / keep);
+                    } else {
+                        cap_new = bcap;
+                        t_new = (uint32_t)std::max(64.0, std::min((double)target, bcap / 2.0 / keep));
+                    }
+                };
+                if (filter && !fixed_cap && !getenv("GN_BUCKET_TARGET") && ix->t < 8) {
+                    const uint32_t tile_step = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(256, tiles / 256));
+                    const uint64_t stiles = (tiles + tile_step - 1) / tile_step;
+                    unsigned long long got[2] = {0, 0};
+                    GN_CUDA(cudaMemsetAsync(kept_total, 0, 16, s));
+                    GN_LAUNCH("k_bucket_fill_sample", Hc / tile_step, s,
+                              fill_kernel<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(stiles, fgrid)), 256,
+                                            bf_smem, s>>>(
+                                  qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, nullptr, nullptr, bcap,
+                                  nullptr, nullptr, 0ull, qbits, filter, p.max_hit_distance, tpos, fbits, fbits2,
+                                  kept_total, tile_step, 1));
+                    GN_CUDA(cudaMemcpyAsync(got, kept_total, 16, cudaMemcpyDeviceToHost, s));
+                    GN_CUDA(cudaStreamSynchronize(s));
+                    if (got[1]) {
+                        uint32_t t_new = target, cap_new = bcap;
+                        plan_for_keep(std::max(1e-6, (double)got[0] / (double)got[1]), t_new, cap_new);
+                        if (t_new != target || cap_new != bcap) {
+                            target = t_new;
+                            bcap = cap_new;
+                            plan(target);
+                        }
+                    }
+                }
+                alloc_buckets();
                 // Which of two colliding keys the filter keeps depends on arrival order, so the spill
                 // count varies a little between runs: a rerun gets room with a margin, and the loop
                 // ends on the run whose spills all fit.
-                for (int attempt = 0;; ++attempt) {
-                    GN_CUDA(cudaMemsetAsync(bcount, 0, 4ull * NB, s));
-                    GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
-                    GN_CUDA(cudaMemsetAsync(kept_total, 0, 8, s));
-                    GN_LAUNCH("k_bucket_fill", Hc, s,
-                              fill_kernel<<<fgrid, 256, bf_smem, s>>>(
-                                  qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
-                                  spill, spill_count, (unsigned long long)spill_room, qbits, filter,
-                                  p.max_hit_distance, tpos, fbits, fbits2, kept_total));
-                    GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
-                    GN_CUDA(cudaMemcpyAsync(&n_kept, kept_total, 8, cudaMemcpyDeviceToHost, s));
-                    GN_CUDA(cudaStreamSynchronize(s));
-                    if (n_spill <= spill_room) break;
-                    GN_REQUIRE(attempt < 3, GN_EINTERNAL, "hit-bucket spill sizing did not converge");
-                    spill_room = n_spill + n_spill / 8 + 1024;
-                    spill = carena.alloc_n<uint64_t>(spill_room);
+                auto run_fill = [&]() {
+                    for (int attempt = 0;; ++attempt) {
+                        GN_CUDA(cudaMemsetAsync(bcount, 0, 4ull * NB, s));
+                        GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
+                        GN_CUDA(cudaMemsetAsync(kept_total, 0, 8, s));
+                        GN_LAUNCH("k_bucket_fill", Hc, s,
+                                  fill_kernel<<<fgrid, 256, bf_smem, s>>>(
+                                      qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
+                                      spill, spill_count, (unsigned long long)spill_room, qbits, filter,
+                                      p.max_hit_distance, tpos, fbits, fbits2, kept_total, 1u, 0));
+                        GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
+                        GN_CUDA(cudaMemcpyAsync(&n_kept, kept_total, 8, cudaMemcpyDeviceToHost, s));
+                        GN_CUDA(cudaStreamSynchronize(s));
+                        if (n_spill <= spill_room) break;
+                        GN_REQUIRE(attempt < 3, GN_EINTERNAL, "hit-bucket spill sizing did not converge");
+                        spill_room = n_spill + n_spill / 8 + 1024;
+                        spill = carena.alloc_n<uint64_t>(spill_room);
+                    }
+                };
+                run_fill();
+                // The plan assumes the stride-11 keep rate of the repeat filter.  Where far more hits
+                // are kept (small strides: overlapping k-mers put most hits next to another on their
+                // diagonal) the buckets overflow; plan again from the measured keep rate, once.
+                if (!fixed_cap && n_kept && n_spill > std::max<unsigned long long>(1u << 16, n_kept / 32)) {
+                    uint32_t t_new = target, cap_new = bcap;
+                    plan_for_keep((double)n_kept / (double)Hc, t_new, cap_new);
+                    if (t_new * 4 < target * 3 || cap_new != bcap) {
+                        target = t_new;
+                        bcap = cap_new;
+                        plan(target);
+                        alloc_buckets();
+                        run_fill();
+                    }
                 }
                 GN_LAUNCH("k_bucket_query", NB, s, k_bucket_query<<<nqc, 256, 0, s>>>(d_bbase, nqc, NB, bq));
                 timer.mark("bucket_fill");
                 // group each bucket; buckets with too many candidates are appended to the spill list too
-                const size_t smem = (size_t)BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8);
+                const size_t smem = (size_t)BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8 + BGW_CAND / 8);
                 GN_CUDA(cudaFuncSetAttribute(k_bucket_group_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 int occ = 0;
                 GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_group_warp, BGW_WARPS * 32, smem));
@@ -1750,18 +1935,24 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     GN_CUDA(cudaMemcpyAsync(gsp, spill, 8 * spilled_fill, cudaMemcpyDeviceToDevice, s));
                 unsigned long long n_ovf = 0;
                 unsigned long long *ovf_count = spill_count;
+                uint32_t *big = carena.alloc_n<uint32_t>(NB);  // buckets for the block-level grouping
+                uint32_t *big_count = carena.alloc_n<uint32_t>(1);
+                uint32_t n_big = 0;
                 for (int attempt = 0;; ++attempt) {
                     const uint32_t hsp_before = n_hsp;
                     emit([&](DevHsp *o, uint32_t room) {
                         GN_CUDA(cudaMemsetAsync(ovf_count, 0, 8, s));
                         GN_CUDA(cudaMemsetAsync(counter + 1, 0, 4, s));
+                        GN_CUDA(cudaMemsetAsync(big_count, 0, 4, s));
                         GN_LAUNCH("k_bucket_group", n_kept, s,
                                   k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
                                       bkeys, bcount, bcap, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len,
                                       singles, seq_map(ix), o, counter, room, gsp + spilled_fill,
-                                      (unsigned long long)group_room, ovf_count, status, counter + 1));
+                                      (unsigned long long)group_room, ovf_count, status, counter + 1, big,
+                                      big_count));
                     });
                     GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
+                    GN_CUDA(cudaMemcpyAsync(&n_big, big_count, 4, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
                     if (n_ovf <= group_room) break;
                     GN_REQUIRE(attempt < 3, GN_EINTERNAL, "hit-bucket overflow sizing did not converge");
@@ -1773,6 +1964,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     gsp = ng;
                     GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
                 }
+                // buckets with more candidates than a warp holds: a block each
+                if (n_big) emit([&](DevHsp *o, uint32_t room) {
+                    GN_LAUNCH("k_bucket_group_block", n_big, s,
+                              k_bucket_group_block<<<num_sms() * 4, 256, 0, s>>>(
+                                  bkeys, bcount, bcap, bq, big, big_count, qa, k, p.max_hit_distance, p.min_hsp_len,
+                                  singles, seq_map(ix), o, counter, room, status));
+                });
                 timer.mark("bucket_group");
                 const uint64_t n_sp = spilled_fill + n_ovf;
                 if (n_sp) sort_path(gsp, carena.alloc_n<uint64_t>(n_sp), n_sp, 0, TAG_HIT_SORT);
