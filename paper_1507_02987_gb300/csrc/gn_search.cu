@@ -295,7 +295,7 @@ __device__ __forceinline__ void for_tile_chunks(const TileTable &t, uint32_t r0,
 // places every kept core hit: one global atomic reserves its slot in its bucket.
 // Buckets have a fixed capacity bcap; hits past it go to the spill list in global
 // hit-key format, which the global sort path handles.
-__global__ void __launch_bounds__(256) k_bucket_fill(
+__global__ void __launch_bounds__(512) k_bucket_fill(
     const uint32_t *__restrict__ qinfo, const uint32_t *__restrict__ src, const uint64_t *__restrict__ hoff,
     uint64_t xa, uint64_t xb, const uint32_t *__restrict__ post, uint32_t qa, const uint32_t *__restrict__ bbase,
     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount, uint64_t *__restrict__ bkeys, uint32_t bcap,
@@ -1777,12 +1777,14 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const char *fenv = getenv("GN_TILE_FILTER");
                 const int filter = (!singles && p.max_hit_distance <= (uint32_t)BT_MAX_D &&
                                     !(fenv && strcmp(fenv, "0") == 0)) ? 1 : 0;
-                // tiles of about 25,000 hits: 256 offsets at ~88 hits per offset (stride 11 on a 4 Gbp
-                // bank), fewer where lists are long (small strides), up to 512 where they are short
+                // 512-thread tiles of about 50,000 hits: 512 offsets at ~88 hits per offset (stride 11 on
+                // a 4 Gbp bank), fewer where lists are long (small strides), up to 1,024 where they are
+                // short; 2^19-bit "seen" and 2^17-bit "seen twice" bitmaps (two tiles per SM)
                 const double per_offset = (double)Hc / (double)std::max<uint64_t>(1, xb - xa);
                 int tpos = 32;
-                while (tpos < 512 && tpos * 2 * per_offset <= 25000.0 * 1.5) tpos *= 2;
-                int fbits = 18, fbits2 = 16;
+                while (tpos < 1024 && tpos * 2 * per_offset <= 50000.0 * 1.5) tpos *= 2;
+                int fbits = 19, fbits2 = 17, fthreads = 512;
+                if (const char *e = getenv("GN_FILL_THREADS")) fthreads = atoi(e) >= 512 ? 512 : 256;
                 if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS2")) fbits2 = std::max(12, std::min(19, atoi(e)));
@@ -1838,7 +1840,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 auto fill_kernel = k_bucket_fill;
                 GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
                 int focc = 0;
-                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fill_kernel, 256, bf_smem));
+                GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fill_kernel, fthreads, bf_smem));
                 const unsigned fgrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(focc, 1) * 4));
                 unsigned long long n_spill = 0, n_kept = 0;
@@ -1864,7 +1866,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     unsigned long long got[2] = {0, 0};
                     GN_CUDA(cudaMemsetAsync(kept_total, 0, 16, s));
                     GN_LAUNCH("k_bucket_fill_sample", Hc / tile_step, s,
-                              fill_kernel<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(stiles, fgrid)), 256,
+                              fill_kernel<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(stiles, fgrid)), fthreads,
                                             bf_smem, s>>>(
                                   qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, nullptr, nullptr, bcap,
                                   nullptr, nullptr, 0ull, qbits, filter, p.max_hit_distance, tpos, fbits, fbits2,
@@ -1891,7 +1893,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                         GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
                         GN_CUDA(cudaMemsetAsync(kept_total, 0, 8, s));
                         GN_LAUNCH("k_bucket_fill", Hc, s,
-                                  fill_kernel<<<fgrid, 256, bf_smem, s>>>(
+                                  fill_kernel<<<fgrid, fthreads, bf_smem, s>>>(
                                       qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
                                       spill, spill_count, (unsigned long long)spill_room, qbits, filter,
                                       p.max_hit_distance, tpos, fbits, fbits2, kept_total, 1u, 0));
