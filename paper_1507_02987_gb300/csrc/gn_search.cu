@@ -1362,8 +1362,8 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
                                                    const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
                                                    const uint64_t *__restrict__ seq_start, int32_t match,
                                                    int32_t mismatch, int32_t go, int32_t ge, int32_t w,
-                                                   uint32_t *__restrict__ next_task, DevAln *__restrict__ out,
-                                                   uint32_t *__restrict__ status) {
+                                                   uint32_t *__restrict__ next_task, const uint64_t *__restrict__ order,
+                                                   DevAln *__restrict__ out, uint32_t *__restrict__ status) {
     const int lane = threadIdx.x & 31, seg = lane / SWG_G;
     constexpr int NG = 32 / SWG_G;
     for (;;) {
@@ -1371,8 +1371,8 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
         if (lane == 0) base = atomicAdd(next_task, (uint32_t)NG);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= n) return;
-        const uint32_t task = base + seg;
-        const bool valid = task < n;
+        const bool valid = base + seg < n;
+        const uint32_t task = valid ? (uint32_t)order[base + seg] : 0u;  // longest alignments first
         DevHsp h{};
         if (valid) h = sel[task];
         bool handled = false;
@@ -1385,11 +1385,24 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
         while (rest) {
             const int src = __ffs(rest) - 1;
             rest &= rest - 1;
-            sw_task_warp(sel, base + (uint32_t)(src / SWG_G), strip_off, strips, qpk, qnb, qstart, bpk, bnb,
-                         seq_start, match, mismatch, go, ge, w, out, status);
+            sw_task_warp(sel, (uint32_t)order[base + (uint32_t)(src / SWG_G)], strip_off, strips, qpk, qnb, qstart,
+                         bpk, bnb, seq_start, match, mismatch, go, ge, w, out, status);
             __syncwarp();
         }
     }
+}
+
+// Alignment order: key = (65535 - DP-window rows) << 32 | task, so that an ascending
+// sort on bits 32..47 hands out the longest alignments first (they bound the kernel's
+// time) and groups alignments of similar length.
+__global__ void k_sw_order_keys(const DevHsp *__restrict__ h, uint32_t n, int32_t w,
+                                const uint64_t *__restrict__ qstart, uint64_t *__restrict__ keys) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t m = (int64_t)(qstart[h[i].qi + 1] - qstart[h[i].qi]);
+    const int64_t rows = min(m, (int64_t)h[i].qe + w) - max((int64_t)0, (int64_t)h[i].qs - w);
+    const int64_t r = rows < 0 ? 0 : (rows > 65535 ? 65535 : rows);
+    keys[i] = ((uint64_t)(65535 - (uint32_t)r) << 32) | i;
 }
 
 // Strip length of each HSP's band (B + 1), and the band area (DP-window rows x B, the
@@ -2097,13 +2110,19 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         GN_CUDA(cudaMemcpyAsync(&area, dp_cells, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         GN_CUDA(cudaStreamSynchronize(s));
         SwCell *strips = arena.alloc_n<SwCell>(cells);
+        uint64_t *okeys = arena.alloc_n<uint64_t>(n_sel), *okeys_alt = arena.alloc_n<uint64_t>(n_sel);
+        GN_LAUNCH("k_sw_order_keys", n_sel, s,
+                  k_sw_order_keys<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, okeys));
+        void *rs = arena.alloc(radix_scratch_bytes(n_sel));
+        const uint64_t *order = radix_sort(okeys, okeys_alt, nullptr, nullptr, n_sel, 32, 48, rs, s, TAG_RECORD_SORT)
+                                    ? okeys_alt : okeys;
         GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
         unsigned warps = (unsigned)std::min<uint64_t>((n_sel + 3) / 4, (uint64_t)num_sms() * 32);
         GN_LAUNCH("k_banded_sw", area, s,
                   k_banded_sw<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
                                                             ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
                                                             sc.mismatch, sc.gap_open, sc.gap_extend,
-                                                            (int32_t)p.band_w, counter, aln, status));
+                                                            (int32_t)p.band_w, counter, order, aln, status));
     }
     timer.mark("banded_sw");
     if (keep) {
