@@ -1633,6 +1633,26 @@ std::vector<T> to_host(const T *d, size_t n, cudaStream_t s) {
 }
 
 unsigned blocks_for(uint64_t n, unsigned t = 256) { return (unsigned)std::max<uint64_t>(1, (n + t - 1) / t); }
+
+// Lets the kernels with a per-call dynamic shared-memory size use up to the device's opt-in
+// maximum.  Set once per device: concurrent searches (serving threads) launch with different
+// sizes, and a per-call attribute change by one thread could undercut another's launch.
+void allow_max_smem(int device) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64 || done[device]) return;
+    int optin = 0;
+    GN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    auto allow = [&](const void *fn) {  // the opt-in maximum less the kernel's static shared memory
+        cudaFuncAttributes fa;
+        GN_CUDA(cudaFuncGetAttributes(&fa, fn));
+        GN_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    };
+    allow(reinterpret_cast<const void *>(k_bucket_fill));
+    allow(reinterpret_cast<const void *>(k_bucket_group_warp));
+    done[device] = true;
+}
 }  // namespace
 
 void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart_h, const SearchOptions &o,
@@ -1851,7 +1871,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
                 const size_t bf_smem = bucket_fill_smem(tpos, filter ? p.max_hit_distance : 0u, filter, fbits, fbits2);
                 auto fill_kernel = k_bucket_fill;
-                GN_CUDA(cudaFuncSetAttribute(fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf_smem));
+                allow_max_smem(ix->device);
                 int focc = 0;
                 GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fill_kernel, fthreads, bf_smem));
                 const unsigned fgrid = (unsigned)std::max<uint64_t>(
@@ -1938,7 +1958,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 timer.mark("bucket_fill");
                 // group each bucket; buckets with too many candidates are appended to the spill list too
                 const size_t smem = (size_t)BGW_WARPS * (2 * BGW_BITS / 8 + BGW_CAND * 8 + BGW_CAND / 8);
-                GN_CUDA(cudaFuncSetAttribute(k_bucket_group_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+
                 int occ = 0;
                 GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bucket_group_warp, BGW_WARPS * 32, smem));
                 const unsigned ggrid = (unsigned)std::max<uint64_t>(
