@@ -513,8 +513,18 @@ def run_ours(args, dist):
     parity = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        kbps, dt, sample, idx, ref, _ = oracle_run(bank, queries, args.stride, threads, args.cpu_seconds)
+        kbps, dt, sample, idx, ref, ox = oracle_run(bank, queries, args.stride, threads, args.cpu_seconds)
         cpu = {"value": kbps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample, "seconds": dt}
+        # the same oracle on one host thread, on an evenly spaced sample of about cpu_seconds / 4
+        import oracle
+        one = list(range(0, queries.n, max(1, queries.n // 64)))[:64]
+        sub1 = queries.subset(one)
+        t0 = time.perf_counter()
+        ox.search(sub1, oracle.Params(stride=args.stride), threads=1)
+        dt1 = time.perf_counter() - t0
+        cpu["single_thread"] = {"value": int(sub1.start[-1]) / 1e3 / dt1, "unit": UNIT, "cores": 1,
+                                "sample": f"{sub1.n} evenly spaced queries, {int(sub1.start[-1])} bases",
+                                "seconds": dt1}
         full = gn.search(ix, qstart, qd, stream=sh)
         mism = 0
         for j, qi in enumerate(idx):
