@@ -143,6 +143,17 @@ typedef struct {
 } gn_index_info;
 GN_API gn_status gn_index_get_info(const gn_index *index, gn_index_info *info);
 
+/* Index persistence (the paper keeps its index on disk and loads it at start-up,
+ * "Inverted Indexes" section).  gn_index_save writes the whole device-resident
+ * index (sequence starts, packed bank, bucket starts, occurrences, sequence lookup
+ * table) to a file; gn_index_load reads such a file onto the current device and
+ * returns a new index owned by the caller (gn_index_free) that searches exactly like
+ * the saved one.  Both stage the data through a 64 MiB host buffer.  Errors:
+ * GN_EINVAL (file cannot be opened, written or read, not an index file, another
+ * format version, inconsistent sizes), GN_ENOMEM, GN_ECUDA. */
+GN_API gn_status gn_index_save(const gn_index *index, const char *path);
+GN_API gn_status gn_index_load(const char *path, gn_index **out);
+
 /* Copies the index to host memory: bucket_start (4^k + 1 entries) and, for each
  * occurrence, its sequence id and position (n_postings entries each).  Any
  * pointer may be NULL to skip it.  Intended for tests. */

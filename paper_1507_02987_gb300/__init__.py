@@ -109,6 +109,8 @@ def load():
                                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32),
                                                     ctypes.POINTER(u64), ctypes.c_int]),
             "gn_kernel_launch_count": (u64, []),
+            "gn_index_save": (st, [vp, ctypes.c_char_p]),
+            "gn_index_load": (st, [ctypes.c_char_p, ctypes.POINTER(vp)]),
             "gn_serve_start": (st, [vp, ctypes.POINTER(gn_scoring), ctypes.POINTER(gn_params), u64,
                                     ctypes.POINTER(vp)]),
             "gn_serve_submit": (st, [vp, ctypes.c_char_p, u32, ctypes.POINTER(u64)]),
@@ -143,6 +145,16 @@ def gn_index_build(bank: gn_bank, k: int, stride: int, stream: int = 0) -> int:
     h = ctypes.c_void_p()
     _check(load().gn_index_build(ctypes.byref(bank), k, stride, ctypes.c_void_p(stream), ctypes.byref(h)))
     return h.value
+
+
+def gn_index_save(h: int, path: str):
+    _check(load().gn_index_save(ctypes.c_void_p(h), os.fsencode(path)))
+
+
+def gn_index_load(path: str) -> int:
+    r = ctypes.c_void_p()
+    _check(load().gn_index_load(os.fsencode(path), ctypes.byref(r)))
+    return r.value
 
 
 def gn_index_free(h: int):
@@ -327,6 +339,19 @@ class Index:
     @classmethod
     def from_bank(cls, bank, k=11, stride=11, stream=0):
         return cls(bank.seq_start, bank.bases, k, stride, stream)
+
+    @classmethod
+    def load(cls, path: str) -> "Index":
+        """An index read back from a file written by save()."""
+        self = cls.__new__(cls)
+        self._keep = None
+        self.handle = gn_index_load(path)
+        info = gn_index_get_info(self.handle)
+        self.k, self.stride = info.k, info.stride
+        return self
+
+    def save(self, path: str):
+        gn_index_save(self.handle, path)
 
     def info(self) -> gn_index_info:
         return gn_index_get_info(self.handle)

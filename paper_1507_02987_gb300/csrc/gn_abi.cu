@@ -248,6 +248,28 @@ gn_status gn_index_build(const gn_bank *db, int k, int stride, void *cuda_stream
     return GN_OK;
 }
 
+gn_status gn_index_save(const gn_index *ix, const char *path) {
+    if (!ix) { g_last_error = "index is required"; return GN_EINVAL; }
+    return guarded([&] { index_save(ix, path); });
+}
+
+gn_status gn_index_load(const char *path, gn_index **out) {
+    if (!out) { g_last_error = "out is required"; return GN_EINVAL; }
+    *out = nullptr;
+    gn_index *ix = new (std::nothrow) gn_index();
+    if (!ix) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
+    gn_status st = guarded([&] { index_load(path, ix); });
+    if (st != GN_OK) {
+        std::string msg = g_last_error;
+        index_free(ix);
+        delete ix;
+        g_last_error = msg;
+        return st;
+    }
+    *out = ix;
+    return GN_OK;
+}
+
 void gn_index_free(gn_index *ix) {
     if (!ix) return;
     index_free(ix);

@@ -6,6 +6,9 @@
 // (sequence, position) order, stored as the window's global base offset.
 #include <algorithm>
 
+#include <cstdio>
+#include <string>
+
 #include "gn_internal.cuh"
 
 namespace gn {
@@ -201,6 +204,117 @@ void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq
         if (post_seq) post_seq[i] = sidx;
         if (post_pos) post_pos[i] = (uint32_t)(g[i] - st[sidx]);
     }
+}
+
+// --------------------------------------------------------- persistence --
+// File layout (little-endian): a header of 16 uint64 (magic, version, k, stride,
+// n_seqs, n_bases, n_postings, max_seq_len, then word counts of the sections that
+// follow), then the sections in order: sequence starts (n_seqs + 1 uint64), packed
+// bank words, non-base words, bucket starts (4^k + 1 uint64), occurrences
+// (n_postings uint32), sequence lookup table.  Device arrays move through a bounded
+// host buffer, so an index of any size needs only that much host memory.
+constexpr uint64_t IX_MAGIC = 0x31584449474F4E47ull;  // "GNOGIDX1"
+constexpr uint64_t IX_VERSION = 1;
+constexpr size_t IX_CHUNK = 64ull << 20;
+
+namespace {
+struct FileCloser {
+    FILE *f;
+    ~FileCloser() { if (f) fclose(f); }
+};
+void write_all(FILE *f, const void *p, size_t bytes) {
+    GN_REQUIRE(bytes == 0 || fwrite(p, 1, bytes, f) == bytes, GN_EINVAL, "index file: write failed");
+}
+void read_all(FILE *f, void *p, size_t bytes) {
+    GN_REQUIRE(bytes == 0 || fread(p, 1, bytes, f) == bytes, GN_EINVAL, "index file: truncated or unreadable");
+}
+void write_device(FILE *f, const void *d, size_t bytes, std::vector<uint8_t> &buf) {
+    for (size_t o = 0; o < bytes; o += IX_CHUNK) {
+        const size_t n = std::min(IX_CHUNK, bytes - o);
+        GN_CUDA(cudaMemcpy(buf.data(), static_cast<const uint8_t *>(d) + o, n, cudaMemcpyDeviceToHost));
+        write_all(f, buf.data(), n);
+    }
+}
+void read_device(FILE *f, void *d, size_t bytes, std::vector<uint8_t> &buf) {
+    for (size_t o = 0; o < bytes; o += IX_CHUNK) {
+        const size_t n = std::min(IX_CHUNK, bytes - o);
+        read_all(f, buf.data(), n);
+        GN_CUDA(cudaMemcpy(static_cast<uint8_t *>(d) + o, buf.data(), n, cudaMemcpyHostToDevice));
+    }
+}
+}  // namespace
+
+void index_save(const gn_index *ix, const char *path) {
+    GN_REQUIRE(path, GN_EINVAL, "path is required");
+    FILE *f = fopen(path, "wb");
+    GN_REQUIRE(f, GN_EINVAL, std::string("cannot create ") + path);
+    FileCloser fc{f};
+    GN_CUDA(cudaSetDevice(ix->device));
+    const uint64_t npk = Packed::pk_words(ix->n_bases), nnb = Packed::nb_words(ix->n_bases);
+    const uint64_t nbk = (1ull << (2 * ix->k)) + 1, nlut = (ix->n_bases >> SEQ_LUT_SHIFT) + 1;
+    uint64_t hdr[16] = {IX_MAGIC, IX_VERSION, (uint64_t)ix->k, (uint64_t)ix->t, ix->n_seqs, ix->n_bases,
+                        ix->n_postings, ix->max_seq_len, npk, nnb, nbk, nlut, 0, 0, 0, 0};
+    write_all(f, hdr, sizeof(hdr));
+    write_all(f, ix->seq_start_h.data(), sizeof(uint64_t) * (ix->n_seqs + 1));
+    std::vector<uint8_t> buf(IX_CHUNK);
+    write_device(f, ix->bank.pk, 4 * npk, buf);
+    write_device(f, ix->bank.nb, 4 * nnb, buf);
+    write_device(f, ix->off_d, 8 * nbk, buf);
+    write_device(f, ix->post_d, 4 * ix->n_postings, buf);
+    write_device(f, ix->seq_lut_d, 4 * nlut, buf);
+    GN_REQUIRE(fflush(f) == 0, GN_EINVAL, "index file: write failed");
+}
+
+void index_load(const char *path, gn_index *ix) {
+    GN_REQUIRE(path, GN_EINVAL, "path is required");
+    FILE *f = fopen(path, "rb");
+    GN_REQUIRE(f, GN_EINVAL, std::string("cannot open ") + path);
+    FileCloser fc{f};
+    uint64_t hdr[16];
+    read_all(f, hdr, sizeof(hdr));
+    GN_REQUIRE(hdr[0] == IX_MAGIC, GN_EINVAL, "not an index file");
+    GN_REQUIRE(hdr[1] == IX_VERSION, GN_EINVAL, "unsupported index file version");
+    const int k = (int)hdr[2], t = (int)hdr[3];
+    GN_REQUIRE(k >= 1 && k <= 16 && t >= 1, GN_EINVAL, "index file: bad k or stride");
+    const uint64_t ns = hdr[4], n = hdr[5], np = hdr[6];
+    GN_REQUIRE(ns < (1ull << 32) && n < (1ull << 32) && np <= n, GN_EINVAL, "index file: bad sizes");
+    const uint64_t npk = Packed::pk_words(n), nnb = Packed::nb_words(n);
+    const uint64_t nbk = (1ull << (2 * k)) + 1, nlut = (n >> SEQ_LUT_SHIFT) + 1;
+    GN_REQUIRE(hdr[8] == npk && hdr[9] == nnb && hdr[10] == nbk && hdr[11] == nlut, GN_EINVAL,
+               "index file: section sizes do not match the header");
+    GN_CUDA(cudaGetDevice(&ix->device));
+    configure_mempool(ix->device);
+    ix->k = k;
+    ix->t = t;
+    ix->n_seqs = (uint32_t)ns;
+    ix->n_bases = n;
+    ix->n_postings = np;
+    ix->max_seq_len = (uint32_t)hdr[7];
+    ix->seq_start_h.resize(ns + 1);
+    read_all(f, ix->seq_start_h.data(), sizeof(uint64_t) * (ns + 1));
+    GN_REQUIRE(ix->seq_start_h[0] == 0 && ix->seq_start_h[ns] == n, GN_EINVAL, "index file: bad sequence starts");
+    for (uint64_t i = 0; i < ns; ++i)
+        GN_REQUIRE(ix->seq_start_h[i + 1] >= ix->seq_start_h[i], GN_EINVAL, "index file: bad sequence starts");
+    uint64_t bytes = 0;
+    GN_CUDA(cudaMalloc(&ix->seq_start_d, sizeof(uint64_t) * (ns + 1)));
+    GN_CUDA(cudaMalloc(&ix->bank.pk, 4 * npk));
+    GN_CUDA(cudaMalloc(&ix->bank.nb, 4 * nnb));
+    GN_CUDA(cudaMalloc(&ix->off_d, 8 * nbk));
+    GN_CUDA(cudaMalloc(&ix->post_d, 4 * std::max<uint64_t>(np, 1)));
+    GN_CUDA(cudaMalloc(&ix->seq_lut_d, 4 * nlut));
+    ix->bank.n = n;
+    bytes += 8 * (ns + 1) + 4 * (npk + nnb) + 8 * nbk + 4 * np + 4 * nlut;
+    GN_CUDA(cudaMemcpy(ix->seq_start_d, ix->seq_start_h.data(), 8 * (ns + 1), cudaMemcpyHostToDevice));
+    std::vector<uint8_t> buf(IX_CHUNK);
+    read_device(f, ix->bank.pk, 4 * npk, buf);
+    read_device(f, ix->bank.nb, 4 * nnb, buf);
+    read_device(f, ix->off_d, 8 * nbk, buf);
+    read_device(f, ix->post_d, 4 * np, buf);
+    read_device(f, ix->seq_lut_d, 4 * nlut, buf);
+    uint64_t last = 0;
+    GN_CUDA(cudaMemcpy(&last, ix->off_d + (nbk - 1), 8, cudaMemcpyDeviceToHost));
+    GN_REQUIRE(last == np, GN_EINVAL, "index file: bucket starts do not end at the occurrence count");
+    ix->device_bytes = bytes;
 }
 
 }  // namespace gn

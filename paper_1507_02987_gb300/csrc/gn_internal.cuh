@@ -255,6 +255,8 @@ namespace gn {
 void index_build(const gn_bank *db, int k, int stride, cudaStream_t s, gn_index *ix);
 void index_free(gn_index *ix);
 void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos);
+void index_save(const gn_index *ix, const char *path);
+void index_load(const char *path, gn_index *ix);
 
 inline SeqMap seq_map(const gn_index *ix) { return SeqMap{ix->seq_start_d, ix->seq_lut_d, ix->n_seqs}; }
 struct SearchOptions {
