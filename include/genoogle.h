@@ -95,6 +95,12 @@ typedef struct {
 #define GN_FLAG_KEEP_STAGES 1u  /* keep every phase's output in the results (tests, debugging) */
 #define GN_FLAG_KEEP_HITS 2u    /* also keep the sorted hit list (small inputs only) */
 #define GN_FLAG_TIME_KERNELS 4u /* bracket every kernel launch with CUDA events (gn_last_kernel_times) */
+/* Both strands (the paper searches the query as given; BLAST-style tools also search
+ * its reverse complement): query i of the call is searched as result query 2i (as
+ * given) and result query 2i + 1, its reverse complement (A <-> T, C <-> G, U -> A,
+ * other bytes unchanged).  Ranges of query 2i + 1 are on the reverse complement;
+ * its e-values use the same query length.  At most 32,768 queries per call. */
+#define GN_FLAG_BOTH_STRANDS 8u
 
 /* One reported alignment. */
 typedef struct {
@@ -221,7 +227,8 @@ GN_API uint64_t gn_kernel_launch_count(void);
  * times 24 bytes, plus 64 bytes per base, 16 KiB of hit buckets and the
  * records of its selected HSPs; each micro-batch also counts 16 MiB of fixed
  * device memory.  Each query's result is identical to a gn_search of that
- * query alone.  mem_budget must exceed 16 MiB (GN_EINVAL otherwise). */
+ * query alone.  mem_budget must exceed 16 MiB (GN_EINVAL otherwise).  The server
+ * searches queries as given (GN_FLAG_BOTH_STRANDS and GN_FLAG_KEEP_* are ignored). */
 GN_API gn_status gn_serve_start(const gn_index *index, const gn_scoring *scoring, const gn_params *params,
                          uint64_t mem_budget, gn_server **out);
 /* Thread-safe; copies the query.  GN_ETOOBIG if the query alone exceeds the budget. */

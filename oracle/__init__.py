@@ -152,6 +152,7 @@ class Params:
     band_w: int = 16
     max_evalue: float = math.inf
     keep_hits: bool = False
+    both_strands: bool = False    # also search each query's reverse complement (result 2i + 1)
 
     def resolved(self) -> "Params":
         import dataclasses
@@ -241,6 +242,13 @@ class Index:
         if isinstance(queries, (list, tuple)):
             import synth
             queries = synth.queries_from_strings(queries)
+        if params.both_strands:
+            import synth
+            doubled = []
+            for i in range(queries.n):
+                q = queries.query(i)
+                doubled += [q, reverse_complement(q)]
+            queries = synth.queries_from_strings(doubled)
         n = queries.n
         qb = np.ascontiguousarray(queries.bases, dtype=np.uint8)
         qs = np.ascontiguousarray(queries.start, dtype=np.uint64)
@@ -254,6 +262,15 @@ class Index:
 
 
 # ---------------------------------------------------------------- pieces --
+_COMPLEMENT = bytes.maketrans(b"ACGTUacgtu", b"TGCAAtgcaa")
+
+
+def reverse_complement(seq) -> bytes:
+    """The other strand read 5' to 3': bases reversed, A <-> T and C <-> G (either case),
+    U read as T (so it pairs with A); any other byte (a non-base) is kept."""
+    return bytes(seq).translate(_COMPLEMENT)[::-1]
+
+
 def _b(s) -> np.ndarray:
     return np.frombuffer(s.encode() if isinstance(s, str) else bytes(s), dtype=np.uint8)
 

@@ -24,7 +24,7 @@ __all__ = ["GnError", "load", "Index", "search", "HIT_DTYPE", "HSP_DTYPE"]
 
 GN_OK, GN_EINVAL, GN_ENOMEM, GN_ECUDA, GN_ETIMEOUT, GN_EBUSY, GN_ETOOBIG, GN_EINTERNAL = range(8)
 GN_MEM_HOST, GN_MEM_DEVICE = 0, 1
-GN_FLAG_KEEP_STAGES, GN_FLAG_KEEP_HITS, GN_FLAG_TIME_KERNELS = 1, 2, 4
+GN_FLAG_KEEP_STAGES, GN_FLAG_KEEP_HITS, GN_FLAG_TIME_KERNELS, GN_FLAG_BOTH_STRANDS = 1, 2, 4, 8
 GN_STAGE_HSP, GN_STAGE_EXT, GN_STAGE_MERGED, GN_STAGE_SELECTED, GN_STAGE_ALIGNED, GN_STAGE_HITS, \
     GN_STAGE_HIT_COUNTS = range(7)
 STATUS_NAMES = {0: "GN_OK", 1: "GN_EINVAL", 2: "GN_ENOMEM", 3: "GN_ECUDA", 4: "GN_ETIMEOUT", 5: "GN_EBUSY",

@@ -316,6 +316,12 @@ gn_status gn_search(const gn_index *ix, const gn_queries *q, const gn_scoring *s
             GN_CUDA(cudaMemcpyAsync(tmp, q->bases, M, cudaMemcpyHostToDevice, s));
             qd = tmp;
         }
+        if (o.p.flags & GN_FLAG_BOTH_STRANDS) {
+            GN_REQUIRE(2ull * q->n <= MAX_QUERIES, GN_ETOOBIG, "more than 32,768 queries with both strands");
+            std::vector<uint64_t> qstart2;
+            both_strands(qd, qstart, arena, s, &qd, qstart2);
+            qstart.swap(qstart2);
+        }
         search(const_cast<gn_index *>(ix), qd, qstart, o, s, res);
         arena.release();
     });
@@ -399,7 +405,7 @@ gn_status gn_serve_start(const gn_index *ix, const gn_scoring *sc, const gn_para
     if (!sv) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
     gn_status st = guarded([&] {
         resolve(ix, sc, p, sv->opt);
-        sv->opt.p.flags &= ~(GN_FLAG_KEEP_STAGES | GN_FLAG_KEEP_HITS);
+        sv->opt.p.flags &= ~(GN_FLAG_KEEP_STAGES | GN_FLAG_KEEP_HITS | GN_FLAG_BOTH_STRANDS);
         GN_REQUIRE(mem_budget > BATCH_FIXED_BYTES, GN_EINVAL, "mem_budget must exceed 16 MiB");
         sv->ix = ix;
         sv->budget = mem_budget;

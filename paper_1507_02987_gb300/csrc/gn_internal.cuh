@@ -264,6 +264,9 @@ struct SearchOptions {
     gn_params p;           // resolved (no zero defaults left)
     uint64_t mem_cap = 0;  // device bytes the hit storage of one query chunk may take (0: 55 % of free)
 };
+// Query i -> queries 2i (as given) and 2i + 1 (reverse complement) in device memory from arena.
+void both_strands(const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart_h, DeviceArena &arena,
+                  cudaStream_t s, const uint8_t **out_bases, std::vector<uint64_t> &out_start);
 // Device-resident query set: bases (ASCII) on the device, starts on the host.
 void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart, const SearchOptions &o,
             cudaStream_t s, gn_results *res);

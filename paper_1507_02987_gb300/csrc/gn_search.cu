@@ -1655,6 +1655,46 @@ void allow_max_smem(int device) {
 }
 }  // namespace
 
+// Both strands: query i of the input becomes query 2i (the bases as given) and query
+// 2i + 1 (its reverse complement) of the output, back to back.  Complement: A <-> T,
+// C <-> G in either case, U (read as T) -> A; any other byte is a non-base and stays.
+__device__ __forceinline__ uint8_t dev_complement(uint8_t c) {
+    switch (c) {
+        case 'A': return 'T'; case 'T': return 'A'; case 'U': return 'A';
+        case 'C': return 'G'; case 'G': return 'C';
+        case 'a': return 't'; case 't': return 'a'; case 'u': return 'a';
+        case 'c': return 'g'; case 'g': return 'c';
+        default: return c;
+    }
+}
+__global__ void k_both_strands(const uint8_t *__restrict__ in, const uint64_t *__restrict__ qstart, uint32_t nq,
+                               uint64_t M, uint8_t *__restrict__ out) {
+    const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= M) return;
+    const uint32_t i = dev_upper_index(qstart, nq + 1, x);
+    const uint64_t s0 = qstart[i], m = qstart[i + 1] - s0, p = x - s0;
+    const uint8_t c = in[x];
+    out[2 * s0 + p] = c;
+    out[2 * s0 + m + (m - 1 - p)] = dev_complement(c);
+}
+
+void both_strands(const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart_h, DeviceArena &arena,
+                  cudaStream_t s, const uint8_t **out_bases, std::vector<uint64_t> &out_start) {
+    const uint32_t nq = (uint32_t)(qstart_h.size() - 1);
+    const uint64_t M = qstart_h[nq];
+    out_start.assign(2ull * nq + 1, 0);
+    for (uint32_t i = 0; i < nq; ++i) {
+        const uint64_t m = qstart_h[i + 1] - qstart_h[i];
+        out_start[2 * i + 1] = 2 * qstart_h[i] + m;
+        out_start[2 * i + 2] = 2 * qstart_h[i] + 2 * m;
+    }
+    uint8_t *d = arena.alloc_n<uint8_t>(2 * M);
+    uint64_t *qs = arena.alloc_n<uint64_t>(nq + 1);
+    GN_CUDA(cudaMemcpyAsync(qs, qstart_h.data(), 8ull * (nq + 1), cudaMemcpyHostToDevice, s));
+    if (M) GN_LAUNCH("k_both_strands", M, s, k_both_strands<<<blocks_for(M), 256, 0, s>>>(qbases_dev, qs, nq, M, d));
+    *out_bases = d;
+}
+
 void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart_h, const SearchOptions &o,
             cudaStream_t s, gn_results *res) {
     const uint32_t nq = (uint32_t)(qstart_h.size() - 1);

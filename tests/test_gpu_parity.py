@@ -171,6 +171,26 @@ def test_search_stages_mid_small_stride(gn, mid_small, stride, env, monkeypatch)
     ix.close()
 
 
+def test_both_strands_mid_small(gn, mid_small):
+    """GN_FLAG_BOTH_STRANDS: result 2i is query i as given, 2i + 1 its reverse complement."""
+    bank, qs, ix, ox = mid_small
+    # every third query, plus the reverse complements of two bank stretches (found on strand 2i + 1)
+    picked = [qs.query(i) for i in range(0, qs.n, 3)]
+    picked += [oracle.reverse_complement(bank.seq(5)[:600]), oracle.reverse_complement(bank.seq(77)[100:900])]
+    sub = synth.queries_from_strings(picked)
+    res = gn.search(ix, sub.start, sub.bases, params=gn.make_params(flags=gn.GN_FLAG_BOTH_STRANDS))
+    assert res.n_queries == 2 * sub.n
+    ref = ox.search(sub, oracle.Params(both_strands=True), threads=os.cpu_count() or 1)
+    for i in range(2 * sub.n):
+        assert_ranked_equal(res.query(i), ref[i].ranked, f"both strands, result {i}")
+    plain = gn.search(ix, sub.start, sub.bases)
+    for i in range(sub.n):
+        a, b = plain.query(i), res.query(2 * i)
+        assert np.array_equal(b["query"], np.full(len(b), 2 * i, dtype=b["query"].dtype))
+        assert all(np.array_equal(a[f], b[f]) for f in a.dtype.names if f != "query")
+    assert sum(len(res.query(2 * i + 1)) for i in range(sub.n)) > 0
+
+
 def test_batched_equals_plain(gn, mid_small):
     bank, qs, ix, ox = mid_small
     allq = gn.search(ix, qs.start, qs.bases)

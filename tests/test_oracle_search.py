@@ -400,3 +400,40 @@ def test_max_alignments_and_empty_query(tiny):
     assert r.n_hits == 0 and len(r.ranked) == 0
     r = ix.search_one(b"ACGTACG", P)           # shorter than k
     assert r.n_hits == 0
+
+
+# ---------------------------------------------------------- both strands --
+def test_reverse_complement_definition():
+    rc = oracle.reverse_complement
+    assert rc(b"") == b""
+    assert rc(b"A") == b"T" and rc(b"C") == b"G" and rc(b"G") == b"C" and rc(b"T") == b"A"
+    assert rc(b"U") == b"A" and rc(b"u") == b"a" and rc(b"acgt") == b"acgt"
+    assert rc(b"AACGN") == b"NCGTT"          # reversed, complemented, non-base kept
+    assert rc(b"ACGT") == b"ACGT"            # a reverse palindrome
+    assert rc(b"GATTACA") == b"TGTAATC"
+    import random
+    r = random.Random(7)
+    for _ in range(50):
+        s = bytes(r.choice(b"ACGTNacgt") for _ in range(r.randint(0, 40)))
+        assert rc(rc(s)) == s
+        assert len(rc(s)) == len(s)
+
+
+def test_both_strands_finds_reverse_complement_homolog():
+    bank = synth.make_bank("tiny", n_seqs=300)
+    src = bank.seq(42)[100:500]
+    q_fwd, q_rev = src, oracle.reverse_complement(src)
+    ox = oracle.Index(bank)
+    res = ox.search([q_fwd, q_rev], oracle.Params(both_strands=True))
+    assert len(res) == 4
+    # forward copy: found on its own strand (result 0); its reverse complement on result 3
+    for j in (0, 3):
+        top = res[j].ranked[0]
+        assert int(top["seq"]) == 42 and int(top["score"]) == 400, j
+    # the reverse-complemented query is not found as given (result 2), and result 1 is the same
+    # search as result 2's complement pair
+    assert all(int(a["seq"]) != 42 or int(a["score"]) < 100 for a in res[2].ranked)
+    assert [tuple(a) for a in res[1].ranked] == [tuple(a) for a in ox.search([q_rev], oracle.Params())[0].ranked]
+    # plain search is the even half of the both-strand search
+    plain = ox.search([q_fwd, q_rev], oracle.Params())
+    assert [tuple(a) for a in plain[1].ranked] == [tuple(a) for a in res[2].ranked]
