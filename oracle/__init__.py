@@ -92,6 +92,8 @@ def _load():
             vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
             lib.or_index_build.restype = vp
             lib.or_index_build.argtypes = [vp, vp, u32, ctypes.c_int, ctypes.c_int]
+            lib.or_index_build_masked.restype = vp
+            lib.or_index_build_masked.argtypes = [vp, vp, u32, ctypes.c_char_p, ctypes.c_int]
             lib.or_index_free.argtypes = [vp]
             lib.or_index_n_postings.restype = u64
             lib.or_index_n_postings.argtypes = [vp]
@@ -198,14 +200,21 @@ def _convert(r: _Result) -> QueryResult:
 class Index:
     """The oracle's inverted index: 4^k buckets of (sequence id, position) pairs."""
 
-    def __init__(self, bank, k: int = 11, stride: int = 11):
+    def __init__(self, bank, k: int = 11, stride: int = 11, mask: str | None = None):
+        """k-base windows, or with ``mask`` (e.g. "111010010100110111") windows of the mask's
+        length indexed under their kept bases ("Methods"); k is then the mask's weight."""
         self._lib = _load()
         self.bank = bank
         self._bases = np.ascontiguousarray(bank.bases, dtype=np.uint8)
         self._start = np.ascontiguousarray(bank.seq_start, dtype=np.uint64)
-        self.k, self.stride = k, stride
-        self._h = self._lib.or_index_build(self._bases.ctypes.data, self._start.ctypes.data, bank.n_seqs, k,
-                                           stride)
+        if mask is not None:
+            k = mask.count("1")
+            self._h = self._lib.or_index_build_masked(self._bases.ctypes.data, self._start.ctypes.data, bank.n_seqs,
+                                                      mask.encode(), stride)
+        else:
+            self._h = self._lib.or_index_build(self._bases.ctypes.data, self._start.ctypes.data, bank.n_seqs, k,
+                                               stride)
+        self.k, self.stride, self.mask = k, stride, mask
         if not self._h:
             raise ValueError("invalid k or stride")
 

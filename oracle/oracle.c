@@ -42,10 +42,14 @@ static int base_code(uint8_t b) {
     }
 }
 
-/* code of the k bases at s[0..k), or -1 if one of them is not a base */
-static int64_t window_code(const uint8_t *s, int k) {
+/* "Methods" (masks): a seed is `span` consecutive bases of which the mask keeps
+ * some (mask[i] == '1'); its code is the kept bases in order, first one most
+ * significant.  -1 if a kept base is not a base.  A plain k-base window is the
+ * mask of k ones. */
+static int64_t seed_code(const uint8_t *s, const char *mask, int span) {
     int64_t code = 0;
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < span; ++i) {
+        if (mask[i] != '1') continue;
         int c = base_code(s[i]);
         if (c < 0) return -1;
         code = code * 4 + c;
@@ -55,7 +59,9 @@ static int64_t window_code(const uint8_t *s, int k) {
 
 /* ------------------------------------------------------- inverted index --- */
 typedef struct {
-    int32_t k, t;
+    int32_t k, t;                /* k: kept bases of a seed (its code has 2k bits) */
+    int32_t span;                /* bases a seed covers (the mask length; k without a mask) */
+    char mask[33];               /* '1' = kept, '0' = removed */
     uint32_t n_seqs;
     const uint64_t *seq_start;   /* borrowed, n_seqs + 1 */
     const uint8_t *bases;        /* borrowed */
@@ -68,20 +74,31 @@ typedef struct {
 
 /* "Inverted Indexes": one bucket per possible sub-sequence; the bank is cut into
  * non-overlapping windows at offsets 0, t, 2t, ... of every sequence (a partial
- * tail is dropped, windows never cross sequences, windows holding a non-base are
- * not indexed).  Occurrences in a bucket are in ascending (sequence, position). */
-or_index *or_index_build(const uint8_t *bases, const uint64_t *seq_start, uint32_t n_seqs, int k, int t) {
-    if (k < 1 || k > 16 || t < 1) return NULL;
+ * tail is dropped, windows never cross sequences, windows holding a non-base at a
+ * kept position are not indexed).  With a mask ("Methods"; the paper's example
+ * keeps 11 of 18 bases) a window covers the mask's length and is indexed under the
+ * code of its kept bases.  Occurrences in a bucket are in ascending (sequence,
+ * position). */
+or_index *or_index_build_masked(const uint8_t *bases, const uint64_t *seq_start, uint32_t n_seqs, const char *mask,
+                                int t) {
+    int span = (int)strlen(mask), k = 0;
+    if (span < 1 || span > 32 || t < 1) return NULL;
+    for (int i = 0; i < span; ++i) {
+        if (mask[i] == '1') ++k;
+        else if (mask[i] != '0') return NULL;
+    }
+    if (k < 1 || k > 16) return NULL;
     or_index *ix = (or_index *)calloc(1, sizeof(or_index));
-    ix->k = k; ix->t = t; ix->n_seqs = n_seqs; ix->seq_start = seq_start; ix->bases = bases;
+    ix->k = k; ix->t = t; ix->span = span; ix->n_seqs = n_seqs; ix->seq_start = seq_start; ix->bases = bases;
+    memcpy(ix->mask, mask, (size_t)span + 1);
     ix->n_buckets = (uint64_t)1 << (2 * k);
     ix->bucket_start = (uint64_t *)calloc(ix->n_buckets + 1, sizeof(uint64_t));
     /* pass 1: occurrences per bucket */
     for (uint32_t s = 0; s < n_seqs; ++s) {
         uint64_t L = seq_start[s + 1] - seq_start[s];
         const uint8_t *seq = bases + seq_start[s];
-        for (uint64_t pos = 0; pos + (uint64_t)k <= L; pos += (uint64_t)t) {
-            int64_t c = window_code(seq + pos, k);
+        for (uint64_t pos = 0; pos + (uint64_t)span <= L; pos += (uint64_t)t) {
+            int64_t c = seed_code(seq + pos, ix->mask, span);
             if (c >= 0) ix->bucket_start[c + 1]++;
         }
     }
@@ -95,8 +112,8 @@ or_index *or_index_build(const uint8_t *bases, const uint64_t *seq_start, uint32
     for (uint32_t s = 0; s < n_seqs; ++s) {
         uint64_t L = seq_start[s + 1] - seq_start[s];
         const uint8_t *seq = bases + seq_start[s];
-        for (uint64_t pos = 0; pos + (uint64_t)k <= L; pos += (uint64_t)t) {
-            int64_t c = window_code(seq + pos, k);
+        for (uint64_t pos = 0; pos + (uint64_t)span <= L; pos += (uint64_t)t) {
+            int64_t c = seed_code(seq + pos, ix->mask, span);
             if (c < 0) continue;
             uint64_t at = cursor[c]++;
             ix->post_seq[at] = s;
@@ -105,6 +122,15 @@ or_index *or_index_build(const uint8_t *bases, const uint64_t *seq_start, uint32
     }
     free(cursor);
     return ix;
+}
+
+/* plain k-base windows: the mask of k ones */
+or_index *or_index_build(const uint8_t *bases, const uint64_t *seq_start, uint32_t n_seqs, int k, int t) {
+    if (k < 1 || k > 16) return NULL;
+    char mask[33];
+    memset(mask, '1', (size_t)k);
+    mask[k] = 0;
+    return or_index_build_masked(bases, seq_start, n_seqs, mask, t);
 }
 
 void or_index_free(or_index *ix) {
@@ -170,14 +196,15 @@ static int cmp_hit(const void *a, const void *b) {
 /* "Searching process", phase 2: every encoded query window is looked up; the
  * occurrences are grouped per bank sequence (here: per sequence and diagonal),
  * occurrences closer than D along the query are merged into one area, and areas
- * shorter than the minimum HSP length are dropped.  HSP length is the smaller of
- * its query and bank spans. */
+ * shorter than the minimum HSP length are dropped.  An area runs from its first
+ * seed to the end of its last one (a seed covers `span` bases).  HSP length is
+ * the smaller of its query and bank spans. */
 static void find_hsps(const or_index *ix, const uint8_t *q, uint32_t m, const or_params *p, or_result *r) {
-    int k = ix->k;
+    int span = ix->span; /* a seed covers span bases (k without a mask) */
     uint64_t nh = 0, cap = 1024;
     or_hit *hits = (or_hit *)malloc(sizeof(or_hit) * cap);
-    for (uint32_t qpos = 0; qpos + (uint32_t)k <= m; ++qpos) {
-        int64_t c = window_code(q + qpos, k);
+    for (uint32_t qpos = 0; qpos + (uint32_t)span <= m; ++qpos) {
+        int64_t c = seed_code(q + qpos, ix->mask, span);
         if (c < 0) continue;
         for (uint64_t e = ix->bucket_start[c]; e < ix->bucket_start[c + 1]; ++e) {
             if (nh == cap) { cap *= 2; hits = (or_hit *)realloc(hits, sizeof(or_hit) * cap); }
@@ -197,8 +224,8 @@ static void find_hsps(const or_index *ix, const uint8_t *q, uint32_t m, const or
                (int64_t)hits[j + 1].pos - hits[j + 1].qpos == (int64_t)hits[i].pos - hits[i].qpos &&
                hits[j + 1].qpos - hits[j].qpos <= p->max_hit_distance)
             ++j;
-        uint32_t qs = hits[i].qpos, qe = hits[j].qpos + (uint32_t)k;
-        uint32_t ds = hits[i].pos, de = hits[j].pos + (uint32_t)k;
+        uint32_t qs = hits[i].qpos, qe = hits[j].qpos + (uint32_t)span;
+        uint32_t ds = hits[i].pos, de = hits[j].pos + (uint32_t)span;
         uint32_t len = (qe - qs) < (de - ds) ? (qe - qs) : (de - ds);
         if (len >= p->min_hsp_len) {
             if (n == cap_h) { cap_h *= 2; out = (or_hsp *)realloc(out, sizeof(or_hsp) * cap_h); }

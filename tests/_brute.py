@@ -163,3 +163,37 @@ def kadane(scores) -> int:
         cur = max(0, cur + s)
         best = max(best, cur)
     return best
+
+
+def kept(w: str, mask: str) -> str:
+    """The bases of window w at the mask's '1' positions, normalised."""
+    return "".join(norm(c) for c, m in zip(w, mask) if m == "1")
+
+
+def masked_windows(seqs, mask, t):
+    """{kept-base string: [(seq, pos), ...]} over windows of len(mask) at pos = 0, t, 2t, ...;
+    a window with a non-base at a kept position is not indexed."""
+    span = len(mask)
+    d = {}
+    for s, seq in enumerate(seqs):
+        for pos in range(0, len(seq) - span + 1, t):
+            w = seq[pos:pos + span]
+            if all(is_base(c) for c, m in zip(w, mask) if m == "1"):
+                d.setdefault(kept(w, mask), []).append((s, pos))
+    return d
+
+
+def masked_hits(seqs, query, mask, t):
+    """Every (qpos, seq, pos) whose query window and bank window agree at the kept positions."""
+    span = len(mask)
+    out = []
+    for s, seq in enumerate(seqs):
+        for pos in range(0, len(seq) - span + 1, t):
+            w = seq[pos:pos + span]
+            if not all(is_base(c) for c, m in zip(w, mask) if m == "1"):
+                continue
+            for qpos in range(0, len(query) - span + 1):
+                v = query[qpos:qpos + span]
+                if all(is_base(c) for c, m in zip(v, mask) if m == "1") and kept(v, mask) == kept(w, mask):
+                    out.append((qpos, s, pos))
+    return out

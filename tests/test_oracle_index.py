@@ -99,3 +99,46 @@ def test_invalid_k_rejected():
         oracle.Index(bank, k=0, stride=1)
     with pytest.raises(ValueError):
         oracle.Index(bank, k=17, stride=1)
+
+
+# ------------------------------------------------------------ spaced seeds --
+@pytest.mark.parametrize("mask,t", [("1101", 4), ("1101", 1), ("10111", 3), ("110011", 6), ("1", 2)])
+def test_masked_buckets_equal_bruteforce_listing(mask, t):
+    """With a mask ("Methods": PatternHunter-style seeds) a window covers the mask's
+    length and is indexed under its kept bases; bucket i is the i-th kept-base string
+    in A<C<G<T order."""
+    rng = random.Random(77 + len(mask) + t)
+    seqs = _bank_with_oddities(rng)
+    bank = synth.bank_from_strings(seqs)
+    ix = oracle.Index(bank, stride=t, mask=mask)
+    k = mask.count("1")
+    assert ix.k == k
+    bs, ps, pp = ix.buckets()
+    brute = _brute.masked_windows(seqs, mask, t)
+    assert ix.n_postings == sum(len(v) for v in brute.values())
+    for i, kmer in enumerate(itertools.product("ACGT", repeat=k)):
+        w = "".join(kmer)
+        got = list(zip(ps[bs[i]:bs[i + 1]].tolist(), pp[bs[i]:bs[i + 1]].tolist()))
+        assert got == brute.get(w, []), (mask, i, w)
+
+
+def test_masked_paper_mask_window_rule():
+    """The paper's mask 111010010100110111 keeps 11 of 18 bases; at stride 18 the
+    posting count is sum(floor((len-18)/18)+1) on an all-ACGT bank, and a plain mask of
+    k ones is the plain index."""
+    bank = synth.make_bank("tiny")
+    mask = "111010010100110111"
+    ix = oracle.Index(bank, stride=18, mask=mask)
+    assert ix.k == 11
+    L = np.diff(bank.seq_start.astype(np.int64))
+    assert ix.n_postings == int(np.sum(np.where(L >= 18, (L - 18) // 18 + 1, 0)))
+    a = oracle.Index(bank, k=7, stride=5).buckets()
+    b = oracle.Index(bank, stride=5, mask="1111111").buckets()
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_masked_rejects_bad_masks():
+    bank = synth.bank_from_strings(["ACGTACGT"])
+    for bad in ("", "0000", "1" * 17, "1" * 33, "1021"):
+        with pytest.raises(ValueError):
+            oracle.Index(bank, stride=1, mask=bad)

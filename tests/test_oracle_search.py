@@ -437,3 +437,42 @@ def test_both_strands_finds_reverse_complement_homolog():
     # plain search is the even half of the both-strand search
     plain = ox.search([q_fwd, q_rev], oracle.Params())
     assert [tuple(a) for a in plain[1].ranked] == [tuple(a) for a in res[2].ranked]
+
+
+# ------------------------------------------------------------ spaced seeds --
+@pytest.mark.parametrize("mask,t", [("1101101", 7), ("1101101", 1), ("110101", 6)])
+def test_masked_hits_and_hsps_equal_bruteforce(mask, t):
+    """Masked seeds: hits are the query windows at every offset that agree with a bank
+    window at the kept positions; an HSP runs from its first seed to the end of its last
+    (len(mask) bases)."""
+    rng = random.Random(5 + t)
+    bank = synth.make_bank("tiny", n_seqs=40 if t > 1 else 10)
+    seqs = [bank.seq(i).decode() for i in range(bank.n_seqs)]
+    src = seqs[3][50:350]
+    q = "".join(c if rng.random() > 0.08 else rng.choice("ACGT") for c in src)
+    ox = oracle.Index(bank, stride=t, mask=mask)
+    p = oracle.Params(stride=t, keep_hits=True)
+    r = ox.search([q.encode()], p)[0]
+    got = sorted((int(h["qpos"]), int(h["seq"]), int(h["pos"])) for h in r.hits)
+    assert got == sorted(_brute.masked_hits(seqs, q, mask, t))
+    pr = p.resolved()
+    span = len(mask)
+    brute_hsp = _brute.chains(got, span, pr.max_hit_distance, pr.min_hsp_len)
+    assert sorted(tuple(int(x[f]) for f in ("seq", "qs", "qe", "ds", "de", "len")) for x in r.hsp) == brute_hsp
+    assert len(r.ranked) >= 1 and int(r.ranked[0]["seq"]) == 3
+
+
+def test_spaced_seed_survives_mismatches_at_removed_positions():
+    """The point of the mask: a window with mismatches only where the mask removes bases
+    still hits."""
+    mask = "111010010100110111"
+    rng = random.Random(9)
+    w = "".join(rng.choice("ACGT") for _ in range(18))
+    v = "".join(("A" if c != "A" else "C") if m == "0" else c for c, m in zip(w, mask))
+    assert sum(a != b for a, b in zip(w, v)) == 7
+    bank = synth.bank_from_strings(["".join(rng.choice("ACGT") for _ in range(40)) + w + "GGGG"])
+    hits_masked = _brute.masked_hits([bank.seq(0).decode()], v, mask, 1)
+    ox = oracle.Index(bank, stride=1, mask=mask)
+    r = ox.search([v.encode()], oracle.Params(stride=1, keep_hits=True, min_hsp_len=18))[0]
+    got = sorted((int(h["qpos"]), int(h["seq"]), int(h["pos"])) for h in r.hits)
+    assert (0, 0, 40) in got and got == sorted(hits_masked)
