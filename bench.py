@@ -65,6 +65,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="large", choices=["tiny", "mid", "batched", "large"])
     ap.add_argument("--stride", type=int, default=11)
+    ap.add_argument("--mask", default=None, help="spaced-seed mask, e.g. 111010010100110111 (k = its ones)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-queries", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle time of the CPU baseline")
@@ -206,11 +207,11 @@ def workload(name: str, stride: int, rank: int, n_queries: int = 0):
     return bank, queries, f"{desc}; k=11, stride {stride}; one gn_search over all queries per step"
 
 
-def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0):
+def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0, mask=None):
     """Times the oracle on growing samples of the query set until one takes >= target_s/2; returns
     (kbp/s, seconds, sample description, sample indices, results)."""
     import oracle
-    ox = oracle.Index(bank, k=11, stride=stride)
+    ox = oracle.Index(bank, k=11, stride=stride, mask=mask)
     n = min(queries.n, 16)
     order = list(range(0, queries.n, max(1, queries.n // 997)))
     while True:
@@ -325,7 +326,7 @@ def run_reference(args, dist):
     bank, queries, desc = workload(args.workload, args.stride, 0, args.queries)
     import oracle
     threads = os.cpu_count() or 1
-    ox = oracle.Index(bank, k=11, stride=args.stride)
+    ox = oracle.Index(bank, k=11, stride=args.stride, mask=args.mask)
     # size one step to about cpu_seconds / 3 of oracle time
     per_step = 8
     while True:
@@ -380,7 +381,7 @@ def run_ours(args, dist):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ix = gn.Index(bank.seq_start, bank.bases, k=11, stride=args.stride, stream=sh)
+    ix = gn.Index(bank.seq_start, bank.bases, k=11, stride=args.stride, stream=sh, mask=args.mask)
     torch.cuda.synchronize()
     t_index = time.perf_counter() - t0
     info = ix.info()
@@ -513,7 +514,8 @@ def run_ours(args, dist):
     parity = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        kbps, dt, sample, idx, ref, ox = oracle_run(bank, queries, args.stride, threads, args.cpu_seconds)
+        kbps, dt, sample, idx, ref, ox = oracle_run(bank, queries, args.stride, threads, args.cpu_seconds,
+                                                    mask=args.mask)
         cpu = {"value": kbps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample, "seconds": dt}
         # the same oracle on one host thread, on an evenly spaced sample of about cpu_seconds / 4
         import oracle
@@ -545,6 +547,7 @@ def run_ours(args, dist):
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": desc, "bank_bases": bank.n_bases, "bank_seqs": bank.n_seqs,
                            "n_queries": queries.n, "query_bases_per_rank": M, "k": 11, "stride": args.stride,
+                           "mask": args.mask,
                            "hits_per_step": (kern.get("k_bucket_fill") or kern.get("k_seed_gather") or [0, 0, 0])[2]
                            / max(1, args.steps),
                            "parallelism": f"replicas x{dist.world}",

@@ -149,6 +149,17 @@ typedef struct {
 } gn_index_info;
 GN_API gn_status gn_index_get_info(const gn_index *index, gn_index_info *info);
 
+/* Builds an index of spaced seeds ("Methods": masks after PatternHunter).  mask
+ * is a NUL-terminated string of '1' (base kept) and '0' (base removed), 1..32
+ * characters with 1..16 ones, e.g. the paper's "111010010100110111".  The bank is
+ * cut into windows of strlen(mask) bases at offsets 0, stride, 2 stride, ...; a
+ * window is indexed under the code of its kept bases (k = number of ones) unless a
+ * kept base is a non-base.  Queries are coded the same way at every offset, and an
+ * HSP ends strlen(mask) bases after its last seed.  A mask of k ones is the plain
+ * k-mer index.  Errors as gn_index_build, GN_EINVAL for a malformed mask. */
+GN_API gn_status gn_index_build_masked(const gn_bank *bank, const char *mask, int stride, void *cuda_stream,
+                                       gn_index **out);
+
 /* Index persistence (the paper keeps its index on disk and loads it at start-up,
  * "Inverted Indexes" section).  gn_index_save writes the whole device-resident
  * index (sequence starts, packed bank, bucket starts, occurrences, sequence lookup

@@ -109,6 +109,8 @@ def load():
                                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32),
                                                     ctypes.POINTER(u64), ctypes.c_int]),
             "gn_kernel_launch_count": (u64, []),
+            "gn_index_build_masked": (st, [ctypes.POINTER(gn_bank), ctypes.c_char_p, ctypes.c_int, vp,
+                                           ctypes.POINTER(vp)]),
             "gn_index_save": (st, [vp, ctypes.c_char_p]),
             "gn_index_load": (st, [ctypes.c_char_p, ctypes.POINTER(vp)]),
             "gn_serve_start": (st, [vp, ctypes.POINTER(gn_scoring), ctypes.POINTER(gn_params), u64,
@@ -144,6 +146,13 @@ def gn_default_params():
 def gn_index_build(bank: gn_bank, k: int, stride: int, stream: int = 0) -> int:
     h = ctypes.c_void_p()
     _check(load().gn_index_build(ctypes.byref(bank), k, stride, ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def gn_index_build_masked(bank: gn_bank, mask: str, stride: int, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().gn_index_build_masked(ctypes.byref(bank), mask.encode(), stride, ctypes.c_void_p(stream),
+                                        ctypes.byref(h)))
     return h.value
 
 
@@ -327,18 +336,24 @@ def make_params(max_hit_distance=0, min_hsp_len=0, xdrop=20, max_alignments=100,
 class Index:
     """A device-resident index of a bank (sequences back to back + starts)."""
 
-    def __init__(self, seq_start, bases, k: int = 11, stride: int = 11, stream: int = 0):
+    def __init__(self, seq_start, bases, k: int = 11, stride: int = 11, stream: int = 0, mask: str | None = None):
+        """k-mer windows, or with ``mask`` (e.g. "111010010100110111") spaced seeds of the mask's
+        length keyed by their kept bases; k is then the mask's number of ones."""
         ss = np.ascontiguousarray(seq_start, dtype=np.uint64)
         ptr, mem, keep = _buffer(bases)
         self._keep = (ss, keep)
         bank = gn_bank(len(ss) - 1, ss.ctypes.data, ptr, mem)
-        self.handle = gn_index_build(bank, k, stride, stream)
+        if mask is not None:
+            self.handle = gn_index_build_masked(bank, mask, stride, stream)
+            k = mask.count("1")
+        else:
+            self.handle = gn_index_build(bank, k, stride, stream)
         self._keep = None
-        self.k, self.stride = k, stride
+        self.k, self.stride, self.mask = k, stride, mask
 
     @classmethod
-    def from_bank(cls, bank, k=11, stride=11, stream=0):
-        return cls(bank.seq_start, bank.bases, k, stride, stream)
+    def from_bank(cls, bank, k=11, stride=11, stream=0, mask=None):
+        return cls(bank.seq_start, bank.bases, k, stride, stream, mask)
 
     @classmethod
     def load(cls, path: str) -> "Index":
@@ -347,7 +362,7 @@ class Index:
         self._keep = None
         self.handle = gn_index_load(path)
         info = gn_index_get_info(self.handle)
-        self.k, self.stride = info.k, info.stride
+        self.k, self.stride, self.mask = info.k, info.stride, None
         return self
 
     def save(self, path: str):

@@ -112,16 +112,20 @@ static int host_base(char c) {
 // a chunk budgets per hit, its per-offset arrays, its smallest set of hit buckets (two of 1,024
 // entries), and the alignment records of its selected HSPs.
 static uint64_t footprint_of(const gn_server *sv, const char *bases, uint32_t len) {
-    const int k = sv->ix->k;
-    const uint32_t mask = (uint32_t)((1ull << (2 * k)) - 1ull);
+    // seed code of every query offset (kept positions of the index's seed shape)
+    const int span = sv->ix->span;
+    const uint32_t keep = sv->ix->keep;
     uint64_t hits = 0;
-    uint32_t code = 0;
-    int valid = 0;  // bases since the last non-base
-    for (uint32_t i = 0; i < len; ++i) {
-        const int b = host_base(bases[i]);
-        if (b < 0) { valid = 0; code = 0; continue; }
-        code = ((code << 2) | (uint32_t)b) & mask;
-        if (++valid >= k) hits += sv->off_h[code + 1] - sv->off_h[code];
+    for (uint32_t q = 0; q + (uint32_t)span <= len; ++q) {
+        uint32_t code = 0;
+        bool ok = true;
+        for (int p = 0; p < span && ok; ++p) {
+            if (!((keep >> p) & 1u)) continue;
+            const int b = host_base(bases[q + p]);
+            if (b < 0) ok = false;
+            else code = (code << 2) | (uint32_t)b;
+        }
+        if (ok) hits += sv->off_h[code + 1] - sv->off_h[code];
     }
     const uint64_t n_sel = sv->opt.p.max_alignments ? sv->opt.p.max_alignments : 4096;
     return hits * HIT_BYTES + (uint64_t)len * 64 + 2 * 1024 * 8 + n_sel * (64 + 16 * (2ull * sv->opt.p.band_w + 2));
@@ -237,6 +241,23 @@ gn_status gn_index_build(const gn_bank *db, int k, int stride, void *cuda_stream
     gn_index *ix = new (std::nothrow) gn_index();
     if (!ix) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
     gn_status st = guarded([&] { index_build(db, k, stride, (cudaStream_t)cuda_stream, ix); });
+    if (st != GN_OK) {
+        std::string msg = g_last_error;
+        index_free(ix);
+        delete ix;
+        g_last_error = msg;
+        return st;
+    }
+    *out = ix;
+    return GN_OK;
+}
+
+gn_status gn_index_build_masked(const gn_bank *db, const char *mask, int stride, void *cuda_stream, gn_index **out) {
+    if (!out) { g_last_error = "out is required"; return GN_EINVAL; }
+    *out = nullptr;
+    gn_index *ix = new (std::nothrow) gn_index();
+    if (!ix) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
+    gn_status st = guarded([&] { index_build_masked(db, mask, stride, (cudaStream_t)cuda_stream, ix); });
     if (st != GN_OK) {
         std::string msg = g_last_error;
         index_free(ix);

@@ -7,19 +7,20 @@
 #include <algorithm>
 
 #include <cstdio>
+#include <cstring>
 #include <string>
 
 #include "gn_internal.cuh"
 
 namespace gn {
 
-// windows per sequence: len >= k ? (len - k) / t + 1 : 0
-__global__ void k_window_counts(const uint64_t *__restrict__ seq_start, uint32_t n_seqs, int k, int t,
+// windows per sequence: len >= span ? (len - span) / t + 1 : 0 (span = k without a mask)
+__global__ void k_window_counts(const uint64_t *__restrict__ seq_start, uint32_t n_seqs, int span, int t,
                                 uint32_t *__restrict__ wcnt) {
     uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_seqs) return;
     uint64_t L = seq_start[s + 1] - seq_start[s];
-    wcnt[s] = L >= (uint64_t)k ? (uint32_t)((L - k) / t + 1) : 0u;
+    wcnt[s] = L >= (uint64_t)span ? (uint32_t)((L - span) / t + 1) : 0u;
 }
 
 constexpr int WIN_J = 8;  // windows per lane per warp chunk
@@ -29,7 +30,7 @@ constexpr int WIN_J = 8;  // windows per lane per warp chunk
 template <bool FLAGS>
 __global__ void k_bank_windows(const uint64_t *__restrict__ seq_start, const uint64_t *__restrict__ woff,
                                uint32_t n_seqs, uint64_t W, const uint32_t *__restrict__ pk,
-                               const uint32_t *__restrict__ nb, int k, int t, uint32_t *__restrict__ flags,
+                               const uint32_t *__restrict__ nb, SeedShape sh, int t, uint32_t *__restrict__ flags,
                                uint32_t *__restrict__ hist, const uint64_t *__restrict__ slot,
                                uint64_t *__restrict__ keys) {
     const int lane = threadIdx.x & 31;
@@ -45,8 +46,8 @@ __global__ void k_bank_windows(const uint64_t *__restrict__ seq_start, const uin
         if (w >= W) break;
         while (woff[s + 1] <= w) ++s;
         uint64_t g = seq_start[s] + (w - woff[s]) * (uint64_t)t;
-        bool bad = dev_has_nonbase(nb, g, k);
-        uint32_t code = dev_kmer(pk, g, k);
+        bool bad = dev_seed_has_nonbase(nb, g, sh);
+        uint32_t code = dev_seed_code(pk, g, sh);
         if (FLAGS) {
             flags[w] = bad ? 0u : 1u;
             if (!bad) atomicAdd(&hist[code], 1u);
@@ -71,9 +72,33 @@ __global__ void k_seq_lut(const uint64_t *__restrict__ start, uint32_t ns, uint6
     lut[j] = dev_upper_index(start, ns, x);  // over the ns starts: the result is < ns
 }
 
+// Seeds of `span` bases keeping the positions set in `keep` (k of them).
+static void index_build_shape(const gn_bank *db, int k, int span, uint32_t keep, int t, cudaStream_t s, gn_index *ix);
+
 void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) {
-    GN_REQUIRE(db && db->seq_start, GN_EINVAL, "bank and bank.seq_start are required");
     GN_REQUIRE(k >= 1 && k <= 16, GN_EINVAL, "k must be in 1..16");
+    index_build_shape(db, k, k, (uint32_t)((1ull << k) - 1ull), t, s, ix);
+}
+
+// "Methods": a mask such as 111010010100110111 ('1' = base kept, '0' = removed) over
+// windows of the mask's length.
+void index_build_masked(const gn_bank *db, const char *mask, int t, cudaStream_t s, gn_index *ix) {
+    GN_REQUIRE(mask, GN_EINVAL, "mask is required");
+    const size_t span = strlen(mask);
+    GN_REQUIRE(span >= 1 && span <= 32, GN_EINVAL, "a mask has 1..32 positions");
+    uint32_t keep = 0;
+    int k = 0;
+    for (size_t i = 0; i < span; ++i) {
+        GN_REQUIRE(mask[i] == '0' || mask[i] == '1', GN_EINVAL, "a mask holds only '0' and '1'");
+        if (mask[i] == '1') { keep |= 1u << i; ++k; }
+    }
+    GN_REQUIRE(k >= 1 && k <= 16, GN_EINVAL, "a mask keeps 1..16 positions");
+    index_build_shape(db, k, (int)span, keep, t, s, ix);
+}
+
+static void index_build_shape(const gn_bank *db, int k, int span, uint32_t keep, int t, cudaStream_t s,
+                              gn_index *ix) {
+    GN_REQUIRE(db && db->seq_start, GN_EINVAL, "bank and bank.seq_start are required");
     GN_REQUIRE(t >= 1, GN_EINVAL, "stride must be >= 1");
     const uint32_t ns = db->n_seqs;
     const uint64_t n = db->seq_start[ns] - db->seq_start[0];
@@ -89,10 +114,13 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     configure_mempool(ix->device);
     ix->k = k;
     ix->t = t;
+    ix->span = span;
+    ix->keep = keep;
     ix->n_seqs = ns;
     ix->n_bases = n;
     ix->max_seq_len = (uint32_t)maxlen;
     ix->seq_start_h.assign(db->seq_start, db->seq_start + ns + 1);
+    const SeedShape sh{k, span, keep};
 
     const uint64_t nbk = 1ull << (2 * k);
     uint64_t bytes = 0;
@@ -130,7 +158,7 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     uint64_t *woff = arena.alloc_n<uint64_t>(ns + 1);
     if (ns) {
         GN_LAUNCH("k_window_counts", ns, s,
-                  k_window_counts<<<(ns + 255) / 256, 256, 0, s>>>(ix->seq_start_d, ns, k, t, wcnt));
+                  k_window_counts<<<(ns + 255) / 256, 256, 0, s>>>(ix->seq_start_d, ns, span, t, wcnt));
     }
     void *scan_scr = arena.alloc(std::max(scan_scratch_bytes(ns), scan_scratch_bytes(nbk)));
     exclusive_scan_u32(wcnt, woff, ns, scan_scr, s);
@@ -147,7 +175,7 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     unsigned grid = (unsigned)std::max<uint64_t>(1, (warps * 32 + 255) / 256);
     if (W) {
         GN_LAUNCH("k_bank_windows_flags", W, s,
-                  k_bank_windows<true><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
+                  k_bank_windows<true><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, sh, t,
                                                   flags, hist, nullptr, nullptr));
     }
     // K3: bucket starts = exclusive scan of the histogram
@@ -164,7 +192,7 @@ void index_build(const gn_bank *db, int k, int t, cudaStream_t s, gn_index *ix) 
     uint64_t *keys_alt = arena.alloc_n<uint64_t>(P);
     if (W) {
         GN_LAUNCH("k_bank_windows_keys", W, s,
-                  k_bank_windows<false><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, k, t,
+                  k_bank_windows<false><<<grid, 256, 0, s>>>(ix->seq_start_d, woff, ns, W, ix->bank.pk, ix->bank.nb, sh, t,
                                                    nullptr, nullptr, slot, keys));
     }
     void *rs = arena.alloc(radix_scratch_bytes(P));
@@ -208,13 +236,13 @@ void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq
 
 // --------------------------------------------------------- persistence --
 // File layout (little-endian): a header of 16 uint64 (magic, version, k, stride,
-// n_seqs, n_bases, n_postings, max_seq_len, then word counts of the sections that
-// follow), then the sections in order: sequence starts (n_seqs + 1 uint64), packed
+// n_seqs, n_bases, n_postings, max_seq_len, word counts of the sections that
+// follow, seed span and kept-position mask), then the sections in order: sequence starts (n_seqs + 1 uint64), packed
 // bank words, non-base words, bucket starts (4^k + 1 uint64), occurrences
 // (n_postings uint32), sequence lookup table.  Device arrays move through a bounded
 // host buffer, so an index of any size needs only that much host memory.
 constexpr uint64_t IX_MAGIC = 0x31584449474F4E47ull;  // "GNOGIDX1"
-constexpr uint64_t IX_VERSION = 1;
+constexpr uint64_t IX_VERSION = 2;
 constexpr size_t IX_CHUNK = 64ull << 20;
 
 namespace {
@@ -253,7 +281,7 @@ void index_save(const gn_index *ix, const char *path) {
     const uint64_t npk = Packed::pk_words(ix->n_bases), nnb = Packed::nb_words(ix->n_bases);
     const uint64_t nbk = (1ull << (2 * ix->k)) + 1, nlut = (ix->n_bases >> SEQ_LUT_SHIFT) + 1;
     uint64_t hdr[16] = {IX_MAGIC, IX_VERSION, (uint64_t)ix->k, (uint64_t)ix->t, ix->n_seqs, ix->n_bases,
-                        ix->n_postings, ix->max_seq_len, npk, nnb, nbk, nlut, 0, 0, 0, 0};
+                        ix->n_postings, ix->max_seq_len, npk, nnb, nbk, nlut, (uint64_t)ix->span, ix->keep, 0, 0};
     write_all(f, hdr, sizeof(hdr));
     write_all(f, ix->seq_start_h.data(), sizeof(uint64_t) * (ix->n_seqs + 1));
     std::vector<uint8_t> buf(IX_CHUNK);
@@ -286,6 +314,11 @@ void index_load(const char *path, gn_index *ix) {
     configure_mempool(ix->device);
     ix->k = k;
     ix->t = t;
+    ix->span = (int)hdr[12];
+    ix->keep = (uint32_t)hdr[13];
+    GN_REQUIRE(ix->span >= k && ix->span <= 32 && __builtin_popcount(ix->keep) == k &&
+                   (ix->span == 32 || (ix->keep >> ix->span) == 0),
+               GN_EINVAL, "index file: bad seed shape");
     ix->n_seqs = (uint32_t)ns;
     ix->n_bases = n;
     ix->n_postings = np;

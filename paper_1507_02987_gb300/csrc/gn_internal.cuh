@@ -177,6 +177,36 @@ __device__ __forceinline__ bool dev_has_nonbase(const uint32_t *__restrict__ nb,
     return (v & ((1ull << k) - 1ull)) != 0ull;
 }
 
+// Seed shape: a seed covers `span` (<= 32) consecutive bases and keeps those whose bit
+// is set in `keep` (k of them, k <= 16); its code is the kept bases in order, first
+// most significant.  A plain k-mer is span = k with every bit kept.
+struct SeedShape {
+    int k, span;
+    uint32_t keep;
+};
+
+__device__ __forceinline__ uint32_t dev_seed_code(const uint32_t *__restrict__ pk, uint64_t g, const SeedShape &sh) {
+    if (sh.span == sh.k) return dev_kmer(pk, g, sh.k);
+    const uint64_t w = g >> 4;
+    const int off = (int)(g & 15);
+    const uint64_t hi = ((uint64_t)pk[w] << 32) | (uint64_t)pk[w + 1];
+    const uint64_t v = off ? (hi << (2 * off)) | ((uint64_t)pk[w + 2] >> (32 - 2 * off)) : hi;  // bases g .. g+31
+    uint32_t code = 0, m = sh.keep;
+    while (m) {
+        const int p = __ffs(m) - 1;
+        m &= m - 1;
+        code = (code << 2) | (uint32_t)((v >> (62 - 2 * p)) & 3u);
+    }
+    return code;
+}
+
+__device__ __forceinline__ bool dev_seed_has_nonbase(const uint32_t *__restrict__ nb, uint64_t g, const SeedShape &sh) {
+    const uint64_t w = g >> 5;
+    const int off = (int)(g & 31);
+    const uint64_t v = (((uint64_t)nb[w + 1] << 32) | (uint64_t)nb[w]) >> off;
+    return (v & (uint64_t)sh.keep) != 0ull;
+}
+
 // 2-bit code of base g, or 4 for a non-base
 __device__ __forceinline__ uint32_t dev_base(const uint32_t *__restrict__ pk, const uint32_t *__restrict__ nb,
                                              uint64_t g) {
@@ -216,6 +246,8 @@ __device__ __forceinline__ uint32_t dev_seq_of(const SeqMap &m, uint64_t x) {
 // --------------------------------------------------------------- handles --
 struct gn_index {
     int k = 0, t = 0;
+    int span = 0;        // bases a seed covers (k without a mask)
+    uint32_t keep = 0;   // kept positions of a seed (all k bits without a mask)
     int device = 0;
     uint32_t n_seqs = 0;
     uint64_t n_bases = 0;
@@ -253,12 +285,14 @@ struct gn_results {
 
 namespace gn {
 void index_build(const gn_bank *db, int k, int stride, cudaStream_t s, gn_index *ix);
+void index_build_masked(const gn_bank *db, const char *mask, int stride, cudaStream_t s, gn_index *ix);
 void index_free(gn_index *ix);
 void index_export(const gn_index *ix, uint64_t *bucket_start, uint32_t *post_seq, uint32_t *post_pos);
 void index_save(const gn_index *ix, const char *path);
 void index_load(const char *path, gn_index *ix);
 
 inline SeqMap seq_map(const gn_index *ix) { return SeqMap{ix->seq_start_d, ix->seq_lut_d, ix->n_seqs}; }
+inline SeedShape seed_shape(const gn_index *ix) { return SeedShape{ix->k, ix->span, ix->keep}; }
 struct SearchOptions {
     gn_scoring sc;
     gn_params p;           // resolved (no zero defaults left)

@@ -42,7 +42,7 @@ enum { A_QI = 0, A_SEQ = 1, A_QS = 2, A_QE = 3, A_DS = 4, A_DE = 5, A_SCORE = 6 
 // Per global query offset x: query id and offset (qinfo = qi << 16 | qpos),
 // k-mer code and the length of its occurrence list (0 for no window).
 __global__ void k_query_codes(const uint64_t *__restrict__ qstart, uint32_t nq, uint64_t M,
-                              const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb, int k,
+                              const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb, SeedShape sh,
                               const uint64_t *__restrict__ off, uint32_t *__restrict__ codes,
                               uint32_t *__restrict__ qinfo, uint32_t *__restrict__ cnt,
                               uint32_t *__restrict__ src) {
@@ -53,8 +53,8 @@ __global__ void k_query_codes(const uint64_t *__restrict__ qstart, uint32_t nq, 
     uint64_t m = qstart[qi + 1] - qstart[qi];
     uint32_t c = 0, n = 0;
     uint64_t o = 0;
-    if (qpos + (uint64_t)k <= m && !dev_has_nonbase(qnb, x, k)) {
-        c = dev_kmer(qpk, x, k);
+    if (qpos + (uint64_t)sh.span <= m && !dev_seed_has_nonbase(qnb, x, sh)) {
+        c = dev_seed_code(qpk, x, sh);
         o = off[c];
         n = (uint32_t)(off[c + 1] - o);
     }
@@ -1699,7 +1699,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
             cudaStream_t s, gn_results *res) {
     const uint32_t nq = (uint32_t)(qstart_h.size() - 1);
     const uint64_t M = qstart_h[nq];
-    const int k = ix->k;
+    const int k = ix->span;  // HSPs end k bases after their last seed (the seed's span)
     const gn_params &p = o.p;
     const gn_scoring &sc = o.sc;
     const bool keep = (p.flags & GN_FLAG_KEEP_STAGES) != 0;
@@ -1731,7 +1731,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     uint64_t *hoff = arena.alloc_n<uint64_t>(M + 1);
     if (M) {
         GN_LAUNCH("k_query_codes", M, s,
-                  k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, k, ix->off_d, codes, qinfo,
+                  k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, seed_shape(ix), ix->off_d, codes, qinfo,
                                                               cnt, src));
     }
     {

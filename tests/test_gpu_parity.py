@@ -117,6 +117,17 @@ def test_index_bitexact_odd_bank(gn):
         assert np.array_equal(bs, r[0]) and np.array_equal(ps, r[1]) and np.array_equal(pp, r[2])
 
 
+@pytest.mark.parametrize("mask,t", [("1101", 4), ("111010010100110111", 18), ("110011", 1), ("1" * 11, 11)])
+def test_masked_index_bitexact(gn, mask, t):
+    """Spaced seeds: windows of the mask's length keyed by their kept bases."""
+    bank = synth.make_bank("tiny", n_seqs=300)
+    ix = gn.Index.from_bank(bank, stride=t, mask=mask)
+    ref = oracle.Index(bank, stride=t, mask=mask)
+    assert ix.info().n_postings == ref.n_postings
+    got, exp = ix.export(), ref.buckets()
+    assert all(np.array_equal(a, b) for a, b in zip(got, exp))
+
+
 # --------------------------------------------------------------- search --
 @pytest.fixture(scope="module")
 def tiny(gn):
@@ -168,6 +179,20 @@ def test_search_stages_mid_small_stride(gn, mid_small, stride, env, monkeypatch)
     res = gn.search(ix, sub.start, sub.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
     ref = ox.search(sub, oracle.Params(stride=stride), threads=os.cpu_count() or 1)
     check_stages(gn, res, ref, sub.n, f"stride {stride}")
+    ix.close()
+
+
+@pytest.mark.parametrize("mask,t", [("111010010100110111", 18), ("111010010100110111", 6)])
+def test_search_stages_masked(gn, mid_small, mask, t):
+    """The paper's mask: every phase equals the oracle's with spaced seeds."""
+    bank, qs, _, _ = mid_small
+    sub = qs.subset(range(0, qs.n, 2))
+    ix = gn.Index.from_bank(bank, stride=t, mask=mask)
+    ox = oracle.Index(bank, stride=t, mask=mask)
+    res = gn.search(ix, sub.start, sub.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
+    ref = ox.search(sub, oracle.Params(stride=t), threads=os.cpu_count() or 1)
+    check_stages(gn, res, ref, sub.n, f"mask {mask} stride {t}")
+    assert sum(len(r.ranked) for r in ref) > 50
     ix.close()
 
 

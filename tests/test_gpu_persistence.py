@@ -26,11 +26,11 @@ def gn():
     return g
 
 
-@pytest.mark.parametrize("stride", [11, 1])
-def test_saved_index_searches_the_same(gn, tmp_path, stride):
+@pytest.mark.parametrize("stride,mask", [(11, None), (1, None), (18, "111010010100110111")])
+def test_saved_index_searches_the_same(gn, tmp_path, stride, mask):
     bank = synth.make_bank("mid", n_seqs=5000)
     qs = synth.make_queries("mid", bank, n=40)
-    ix = gn.Index.from_bank(bank, stride=stride)
+    ix = gn.Index.from_bank(bank, stride=stride, mask=mask)
     path = str(tmp_path / f"mid_s{stride}.gnidx")
     ix.save(path)
     assert os.path.getsize(path) > 0
