@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--workload", default="large", choices=["tiny", "mid", "batched", "large"])
     ap.add_argument("--stride", type=int, default=11)
     ap.add_argument("--mask", default=None, help="spaced-seed mask, e.g. 111010010100110111 (k = its ones)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the band width and kernel tuning on a 200-query calibration sample first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-queries", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle time of the CPU baseline")
@@ -207,7 +209,7 @@ def workload(name: str, stride: int, rank: int, n_queries: int = 0):
     return bank, queries, f"{desc}; k=11, stride {stride}; one gn_search over all queries per step"
 
 
-def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0, mask=None):
+def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0, mask=None, band_w=16):
     """Times the oracle on growing samples of the query set until one takes >= target_s/2; returns
     (kbp/s, seconds, sample description, sample indices, results)."""
     import oracle
@@ -218,7 +220,7 @@ def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0, mask=None):
         idx = order[:n] if n <= len(order) else list(range(min(n, queries.n)))
         sub = queries.subset(idx)
         t0 = time.perf_counter()
-        res = ox.search(sub, oracle.Params(stride=stride), threads=threads)
+        res = ox.search(sub, oracle.Params(stride=stride, band_w=band_w), threads=threads)
         dt = time.perf_counter() - t0
         if dt >= target_s / 2 or n >= queries.n:
             bases = int(sub.start[-1])
@@ -394,8 +396,18 @@ def run_ours(args, dist):
     M = int(qstart[-1])
     flags_t = gn.GN_FLAG_TIME_KERNELS
 
+    # optional autotuner on an evenly spaced calibration sample (before any timed work)
+    band_w, tuned = 16, None
+    if args.autotune:
+        t0 = time.perf_counter()
+        cal = queries.subset(list(range(0, queries.n, max(1, queries.n // 200)))[:200])
+        tp, tuning = gn.autotune(ix, cal.start, cal.bases, stream=sh)
+        band_w = int(tp.band_w)
+        tuned = {"band_w": band_w, **tuning, "calibration_queries": cal.n, "seconds": time.perf_counter() - t0}
+        log(f"autotuned: {tuned}")
+    sp = gn.make_params(band_w=band_w)
     for _ in range(args.warmup):
-        gn.search(ix, qstart, qd, stream=sh).close()
+        gn.search(ix, qstart, qd, params=sp, stream=sh).close()
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident queries, events on the launching stream around the K steps
@@ -408,7 +420,7 @@ def run_ours(args, dist):
     n_hits = 0
     e0.record(stream)
     for _ in range(args.steps):
-        r = gn.search(ix, qstart, qd, stream=sh)
+        r = gn.search(ix, qstart, qd, params=sp, stream=sh)
         n_hits = r.n_queries and gn.gn_results_count(r.handle)[1]
         r.close()
     e1.record(stream)
@@ -426,7 +438,7 @@ def run_ours(args, dist):
     kern = {}
     phases = {}
     for _ in range(args.steps):
-        r = gn.search(ix, qstart, qd, params=gn.make_params(flags=flags_t), stream=sh)
+        r = gn.search(ix, qstart, qd, params=gn.make_params(flags=flags_t, band_w=band_w), stream=sh)
         for name, (ms, la, un) in ix.kernel_times().items():
             a = kern.setdefault(name, [0.0, 0, 0])
             a[0] += ms; a[1] += la; a[2] += un
@@ -441,7 +453,7 @@ def run_ours(args, dist):
     t0 = time.perf_counter()
     d2h = 0
     for _ in range(args.steps):
-        r = gn.search(ix, qstart, qh, stream=sh)
+        r = gn.search(ix, qstart, qh, params=sp, stream=sh)
         nq, nh = gn.gn_results_count(r.handle)
         d2h = nh * gn.HIT_DTYPE.itemsize
         r.close()
@@ -459,11 +471,11 @@ def run_ours(args, dist):
                  torch.from_numpy(sub.bases[int(sub.start[i]):int(sub.start[i + 1])]).to(f"cuda:{dev}"))
                 for i in range(sub.n)]
         for st, b in subs[:3]:
-            gn.search(ix, st, b, stream=sh).close()
+            gn.search(ix, st, b, params=sp, stream=sh).close()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for st, b in subs:
-            gn.search(ix, st, b, stream=sh).close()
+            gn.search(ix, st, b, params=sp, stream=sh).close()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         batched_sub = gn.search(ix, sub.start, torch.from_numpy(sub.bases).to(f"cuda:{dev}"), stream=sh)
@@ -515,19 +527,19 @@ def run_ours(args, dist):
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         kbps, dt, sample, idx, ref, ox = oracle_run(bank, queries, args.stride, threads, args.cpu_seconds,
-                                                    mask=args.mask)
+                                                    mask=args.mask, band_w=band_w)
         cpu = {"value": kbps, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample, "seconds": dt}
         # the same oracle on one host thread, on an evenly spaced sample of about cpu_seconds / 4
         import oracle
         one = list(range(0, queries.n, max(1, queries.n // 64)))[:64]
         sub1 = queries.subset(one)
         t0 = time.perf_counter()
-        ox.search(sub1, oracle.Params(stride=args.stride), threads=1)
+        ox.search(sub1, oracle.Params(stride=args.stride, band_w=band_w), threads=1)
         dt1 = time.perf_counter() - t0
         cpu["single_thread"] = {"value": int(sub1.start[-1]) / 1e3 / dt1, "unit": UNIT, "cores": 1,
                                 "sample": f"{sub1.n} evenly spaced queries, {int(sub1.start[-1])} bases",
                                 "seconds": dt1}
-        full = gn.search(ix, qstart, qd, stream=sh)
+        full = gn.search(ix, qstart, qd, params=sp, stream=sh)
         mism = 0
         for j, qi in enumerate(idx):
             got = full.query(qi)
@@ -547,7 +559,7 @@ def run_ours(args, dist):
                 "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": desc, "bank_bases": bank.n_bases, "bank_seqs": bank.n_seqs,
                            "n_queries": queries.n, "query_bases_per_rank": M, "k": 11, "stride": args.stride,
-                           "mask": args.mask,
+                           "mask": args.mask, "band_w": band_w, "autotune": tuned,
                            "hits_per_step": (kern.get("k_bucket_fill") or kern.get("k_seed_gather") or [0, 0, 0])[2]
                            / max(1, args.steps),
                            "parallelism": f"replicas x{dist.world}",

@@ -149,6 +149,34 @@ typedef struct {
 } gn_index_info;
 GN_API gn_status gn_index_get_info(const gn_index *index, gn_index_info *info);
 
+/* Execution settings that never change results (0 = the library's default): the
+ * fill kernel's tile size in hits (default 50,000) and threads per tile (512 or
+ * 256), and the raw hits planned per hit bucket (default 2,048 with the repeat
+ * filter).  They belong to an index (they depend on its occurrence lists). */
+typedef struct {
+    uint32_t tile_hits;
+    uint32_t fill_threads;
+    uint32_t bucket_target;
+    uint32_t reserved;
+} gn_tuning;
+GN_API gn_status gn_index_set_tuning(gn_index *index, const gn_tuning *tuning);
+GN_API gn_status gn_index_get_tuning(const gn_index *index, gn_tuning *tuning);
+
+/* Autotuner (no counterpart in the paper; it picks what the paper leaves open on a
+ * calibration sample of queries, before a run).  With GN_TUNE_BAND it sets
+ * params->band_w to the smallest w of 16, 32, 64, 128 for which a band of 2w
+ * raises the sample's total alignment score by at most 0.5 % (128 if none does):
+ * wider bands recover alignments whose indels drift off the seed diagonal, at a
+ * cost that grows with the band.  w changes results, so the caller passes the
+ * chosen params to every later search (and to any reference it compares with).  With GN_TUNE_KERNELS it times
+ * the search of the sample with several gn_tuning candidates and installs the
+ * fastest on the index (and copies it to *tuning if not NULL).  Not to be run
+ * concurrently with other searches on the same index.  Errors as gn_search. */
+#define GN_TUNE_BAND 1u
+#define GN_TUNE_KERNELS 2u
+GN_API gn_status gn_autotune(gn_index *index, const gn_queries *sample, const gn_scoring *scoring, gn_params *params,
+                             uint32_t what, void *cuda_stream, gn_tuning *tuning);
+
 /* Builds an index of spaced seeds ("Methods": masks after PatternHunter).  mask
  * is a NUL-terminated string of '1' (base kept) and '0' (base removed), 1..32
  * characters with 1..16 ones, e.g. the paper's "111010010100110111".  The bank is

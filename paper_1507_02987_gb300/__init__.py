@@ -25,6 +25,7 @@ __all__ = ["GnError", "load", "Index", "search", "HIT_DTYPE", "HSP_DTYPE"]
 GN_OK, GN_EINVAL, GN_ENOMEM, GN_ECUDA, GN_ETIMEOUT, GN_EBUSY, GN_ETOOBIG, GN_EINTERNAL = range(8)
 GN_MEM_HOST, GN_MEM_DEVICE = 0, 1
 GN_FLAG_KEEP_STAGES, GN_FLAG_KEEP_HITS, GN_FLAG_TIME_KERNELS, GN_FLAG_BOTH_STRANDS = 1, 2, 4, 8
+GN_TUNE_BAND, GN_TUNE_KERNELS = 1, 2
 GN_STAGE_HSP, GN_STAGE_EXT, GN_STAGE_MERGED, GN_STAGE_SELECTED, GN_STAGE_ALIGNED, GN_STAGE_HITS, \
     GN_STAGE_HIT_COUNTS = range(7)
 STATUS_NAMES = {0: "GN_OK", 1: "GN_EINVAL", 2: "GN_ENOMEM", 3: "GN_ECUDA", 4: "GN_ETIMEOUT", 5: "GN_EBUSY",
@@ -56,6 +57,10 @@ class gn_params(ctypes.Structure):
     _fields_ = [("max_hit_distance", ctypes.c_uint32), ("min_hsp_len", ctypes.c_uint32),
                 ("xdrop", ctypes.c_int32), ("max_alignments", ctypes.c_uint32), ("band_w", ctypes.c_uint32),
                 ("max_evalue", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+class gn_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("tile_hits", "fill_threads", "bucket_target", "reserved")]
 
 
 class gn_serve_stats(ctypes.Structure):
@@ -112,6 +117,10 @@ def load():
             "gn_index_build_masked": (st, [ctypes.POINTER(gn_bank), ctypes.c_char_p, ctypes.c_int, vp,
                                            ctypes.POINTER(vp)]),
             "gn_index_save": (st, [vp, ctypes.c_char_p]),
+            "gn_index_set_tuning": (st, [vp, ctypes.POINTER(gn_tuning)]),
+            "gn_index_get_tuning": (st, [vp, ctypes.POINTER(gn_tuning)]),
+            "gn_autotune": (st, [vp, ctypes.POINTER(gn_queries), ctypes.POINTER(gn_scoring), ctypes.POINTER(gn_params),
+                                 u32, vp, ctypes.POINTER(gn_tuning)]),
             "gn_index_load": (st, [ctypes.c_char_p, ctypes.POINTER(vp)]),
             "gn_serve_start": (st, [vp, ctypes.POINTER(gn_scoring), ctypes.POINTER(gn_params), u64,
                                     ctypes.POINTER(vp)]),
@@ -462,6 +471,34 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+def set_tuning(index: Index, tile_hits=0, fill_threads=0, bucket_target=0):
+    _check(load().gn_index_set_tuning(ctypes.c_void_p(index.handle),
+                                      ctypes.byref(gn_tuning(tile_hits, fill_threads, bucket_target, 0))))
+
+
+def get_tuning(index: Index) -> dict:
+    t = gn_tuning()
+    _check(load().gn_index_get_tuning(ctypes.c_void_p(index.handle), ctypes.byref(t)))
+    return {n: int(getattr(t, n)) for n, _ in gn_tuning._fields_ if n != "reserved"}
+
+
+def autotune(index: Index, start, bases, scoring: gn_scoring | None = None, params: gn_params | None = None,
+             what: int = GN_TUNE_BAND | GN_TUNE_KERNELS, stream: int = 0):
+    """Runs the autotuner on a calibration sample; returns (params with the chosen band_w, tuning dict).
+    The kernel tuning is installed on the index."""
+    st = np.ascontiguousarray(start, dtype=np.uint64)
+    ptr, mem, keep = _buffer(bases)
+    q = gn_queries(len(st) - 1, st.ctypes.data, ptr, mem)
+    sc = scoring if scoring is not None else make_scoring()
+    p = params if params is not None else make_params()
+    p = gn_params.from_buffer_copy(p)
+    t = gn_tuning()
+    _check(load().gn_autotune(ctypes.c_void_p(index.handle), ctypes.byref(q), ctypes.byref(sc), ctypes.byref(p),
+                              what, ctypes.c_void_p(stream), ctypes.byref(t)))
+    del keep
+    return p, {n: int(getattr(t, n)) for n, _ in gn_tuning._fields_ if n != "reserved"}
 
 
 def search(index: Index, start, bases, scoring: gn_scoring | None = None, params: gn_params | None = None,

@@ -269,6 +269,102 @@ gn_status gn_index_build_masked(const gn_bank *db, const char *mask, int stride,
     return GN_OK;
 }
 
+gn_status gn_index_set_tuning(gn_index *ix, const gn_tuning *t) {
+    if (!ix || !t) { g_last_error = "index and tuning are required"; return GN_EINVAL; }
+    if (t->fill_threads != 0 && t->fill_threads != 256 && t->fill_threads != 512) {
+        g_last_error = "fill_threads is 0, 256 or 512";
+        return GN_EINVAL;
+    }
+    ix->tuning = *t;
+    return GN_OK;
+}
+
+gn_status gn_index_get_tuning(const gn_index *ix, gn_tuning *t) {
+    if (!ix || !t) { g_last_error = "index and tuning are required"; return GN_EINVAL; }
+    *t = ix->tuning;
+    return GN_OK;
+}
+
+gn_status gn_autotune(gn_index *ix, const gn_queries *q, const gn_scoring *sc, gn_params *p, uint32_t what,
+                      void *cuda_stream, gn_tuning *tuning) {
+    if (!ix || !q || !p) { g_last_error = "index, sample and params are required"; return GN_EINVAL; }
+    return guarded([&] {
+        check_queries(q);
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        std::vector<uint64_t> qstart(q->start, q->start + q->n + 1);
+        const uint64_t M = qstart[q->n];
+        DeviceArena arena(s);
+        const uint8_t *qd = reinterpret_cast<const uint8_t *>(q->bases);
+        if (q->bases_mem == GN_MEM_HOST && M > 0) {
+            uint8_t *tmp = arena.alloc_n<uint8_t>(M);
+            GN_CUDA(cudaMemcpyAsync(tmp, q->bases, M, cudaMemcpyHostToDevice, s));
+            qd = tmp;
+        }
+        auto run = [&](const gn_params &pp, gn_results &res) {
+            SearchOptions o;
+            gn_params p2 = pp;
+            p2.flags &= ~(GN_FLAG_KEEP_STAGES | GN_FLAG_KEEP_HITS | GN_FLAG_BOTH_STRANDS | GN_FLAG_TIME_KERNELS);
+            resolve(ix, sc, &p2, o);
+            search(ix, qd, qstart, o, s, &res);
+        };
+        auto total = [](const gn_results &a) {
+            double t = 0.0;
+            for (const gn_hit &h : a.hits) t += (double)h.score;
+            return t;
+        };
+        if (what & GN_TUNE_BAND) {
+            // the smallest band that a band twice as wide improves by at most 0.5 % of the sample's total
+            // alignment score (a wider band recovers alignments whose indels drift off the seed diagonal)
+            const uint32_t ws[] = {16, 32, 64, 128};
+            gn_params pp = *p;
+            uint32_t chosen = 128;
+            gn_results prev;
+            pp.band_w = ws[0];
+            run(pp, prev);
+            for (int i = 0; i + 1 < 4; ++i) {
+                gn_results next;
+                pp.band_w = ws[i + 1];
+                run(pp, next);
+                const double a = total(prev), b = total(next);
+                if (b - a <= 0.005 * std::max(a, 1.0)) { chosen = ws[i]; break; }
+                prev = std::move(next);
+            }
+            p->band_w = chosen;
+        }
+        if (what & GN_TUNE_KERNELS) {
+            // fastest of a few result-invariant settings, by CUDA-event time on the caller's stream
+            const gn_tuning saved = ix->tuning;
+            gn_tuning best = saved;
+            float best_ms = 0.f;
+            bool have = false;
+            cudaEvent_t e0, e1;
+            GN_CUDA(cudaEventCreate(&e0));
+            GN_CUDA(cudaEventCreate(&e1));
+            for (uint32_t th : {512u, 256u}) {
+                for (uint32_t hits : {25000u, 50000u, 100000u}) {
+                    gn_tuning cand{hits, th, 0, 0};
+                    ix->tuning = cand;
+                    float ms = 0.f;
+                    for (int rep = 0; rep < 2; ++rep) {  // the first run warms pools and caches
+                        gn_results r;
+                        GN_CUDA(cudaEventRecord(e0, s));
+                        run(*p, r);
+                        GN_CUDA(cudaEventRecord(e1, s));
+                        GN_CUDA(cudaEventSynchronize(e1));
+                        GN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    }
+                    if (!have || ms < best_ms) { best = cand; best_ms = ms; have = true; }
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            ix->tuning = best;
+        }
+        if (tuning) *tuning = ix->tuning;
+        arena.release();
+    });
+}
+
 gn_status gn_index_save(const gn_index *ix, const char *path) {
     if (!ix) { g_last_error = "index is required"; return GN_EINVAL; }
     return guarded([&] { index_save(ix, path); });

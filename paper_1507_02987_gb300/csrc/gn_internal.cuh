@@ -247,6 +247,7 @@ __device__ __forceinline__ uint32_t dev_seq_of(const SeqMap &m, uint64_t x) {
 struct gn_index {
     int k = 0, t = 0;
     int span = 0;        // bases a seed covers (k without a mask)
+    gn_tuning tuning{};  // result-invariant execution settings (0 = defaults)
     uint32_t keep = 0;   // kept positions of a seed (all k bits without a mask)
     int device = 0;
     uint32_t n_seqs = 0;

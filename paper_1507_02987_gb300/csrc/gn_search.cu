@@ -1854,15 +1854,18 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 // a 4 Gbp bank), fewer where lists are long (small strides), up to 1,024 where they are
                 // short; 2^19-bit "seen" and 2^17-bit "seen twice" bitmaps (two tiles per SM)
                 const double per_offset = (double)Hc / (double)std::max<uint64_t>(1, xb - xa);
+                const double tile_hits = ix->tuning.tile_hits ? (double)ix->tuning.tile_hits : 50000.0;
                 int tpos = 32;
-                while (tpos < 1024 && tpos * 2 * per_offset <= 50000.0 * 1.5) tpos *= 2;
-                int fbits = 19, fbits2 = 17, fthreads = 512;
+                while (tpos < 1024 && tpos * 2 * per_offset <= tile_hits * 1.5) tpos *= 2;
+                int fthreads = ix->tuning.fill_threads == 256 ? 256 : 512;
                 if (const char *e = getenv("GN_FILL_THREADS")) fthreads = atoi(e) >= 512 ? 512 : 256;
+                // two 512-thread tiles or four 256-thread tiles per SM
+                int fbits = fthreads == 512 ? 19 : 18, fbits2 = fthreads == 512 ? 17 : 16;
                 if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS2")) fbits2 = std::max(12, std::min(19, atoi(e)));
                 // the filter keeps about a fifth of the hits; capacity has ~2x slack over the expected fill
-                uint32_t target = filter ? 2048 : 512, bcap = 1024;
+                uint32_t target = filter ? (ix->tuning.bucket_target ? ix->tuning.bucket_target : 2048) : 512, bcap = 1024;
                 if (const char *e = getenv("GN_BUCKET_TARGET")) target = std::max(64, std::min(65536, atoi(e)));
                 if (const char *e = getenv("GN_BUCKET_CAP")) {  // small buckets (exercises the spill path)
                     bcap = (uint32_t)std::max(8ul, std::min(65536ul, strtoul(e, nullptr, 10)));

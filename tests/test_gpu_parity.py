@@ -292,3 +292,33 @@ def test_too_long_query_rejected(gn, tiny):
     with pytest.raises(gn.GnError) as e:
         gn.search(ix, q.start, q.bases)
     assert e.value.status == gn.GN_ETOOBIG
+
+
+def test_autotune(gn, mid_small):
+    """The autotuner picks a band width from the calibration sample and a result-invariant
+    kernel tuning; results with the tuning installed equal the untuned ones, and results with
+    the chosen band equal the oracle's with that band."""
+    bank, qs, _, ox = mid_small
+    ix = gn.Index.from_bank(bank)
+    sub = qs.subset(range(0, qs.n, 4))
+    before = gn.search(ix, sub.start, sub.bases).all()
+    p, tuning = gn.autotune(ix, sub.start, sub.bases)
+    assert p.band_w in (16, 32, 64, 128)
+    assert tuning["fill_threads"] in (256, 512) and tuning["tile_hits"] in (25000, 50000, 100000)
+    assert gn.get_tuning(ix) == tuning
+    after = gn.search(ix, sub.start, sub.bases).all()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    res = gn.search(ix, sub.start, sub.bases, params=p)
+    ref = ox.search(sub, oracle.Params(band_w=p.band_w), threads=os.cpu_count() or 1)
+    for i in range(sub.n):
+        assert_ranked_equal(res.query(i), ref[i].ranked, f"autotuned band {p.band_w} query {i}")
+    # twice the chosen band raises the sample's total score by at most 0.5 % (unless it is the widest)
+    if p.band_w < 128:
+        wide = gn.search(ix, sub.start, sub.bases, params=gn.make_params(band_w=2 * p.band_w)).all()
+        a = sum(int(x["score"].sum()) for x in res.all())
+        b = sum(int(x["score"].sum()) for x in wide)
+        assert b - a <= 0.005 * max(a, 1)
+    gn.set_tuning(ix)
+    assert gn.get_tuning(ix) == {"tile_hits": 0, "fill_threads": 0, "bucket_target": 0}
+    ix.close()
