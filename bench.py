@@ -52,7 +52,7 @@ BYTES_PER_UNIT = {
 }
 # integer-ALU kernels: units = DP cells of the band area; 8 algorithmic integer operations per
 # cell (E and F: add + max each; H: substitution select, add, three-way max with 0)
-ALU_KERNELS = {"k_banded_sw"}
+ALU_KERNELS = {"k_banded_sw", "k_banded_sw_wide"}
 ALU_OPS_PER_UNIT = 8.0
 INT_LANES_PER_SM = 128   # 32-bit integer lanes per SM (4 partitions x 32)
 

@@ -1088,8 +1088,15 @@ __device__ __forceinline__ void sw_rows_pair(int64_t I0, int64_t I1, int64_t J0,
 }
 
 
-// One HSP aligned by a whole warp: the pair path for bands of at most 64 diagonals,
-// else the strip path (the band in chunks of 32 offsets, previous row in scratch).
+// Band width (diagonals) of an HSP's alignment: the spread of its end diagonals plus 2w + 1.
+__device__ __forceinline__ int64_t dev_band(const DevHsp &h, int32_t w) {
+    const int64_t d_s = (int64_t)h.ds - h.qs, d_e = (int64_t)h.de - h.qe;
+    return max(d_s, d_e) - min(d_s, d_e) + 2 * (int64_t)w + 1;
+}
+
+// One HSP aligned by a whole warp: the pair path (bands of at most 64 diagonals), or
+// with STRIP the strip path (the band in chunks of 32 offsets, previous row in scratch).
+template <bool STRIP>
 __device__ void sw_task_warp(const DevHsp *__restrict__ sel, uint32_t task, const uint64_t *__restrict__ strip_off,
                              SwCell *__restrict__ strips, const uint32_t *__restrict__ qpk,
                              const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
@@ -1116,7 +1123,7 @@ __device__ void sw_task_warp(const DevHsp *__restrict__ sel, uint32_t task, cons
     int64_t bi = INT64_MAX, bj = INT64_MAX;
     uint32_t bs = 0;
     const int32_t goe = go + ge;
-    if (B <= 64) {
+    if (!STRIP) {  // bands of at most 64 diagonals (the caller routes wider ones elsewhere)
         sw_rows_pair(I0, I1, J0, J1, dlo, B, qb, sb, qpk, qnb, bpk, bnb, match, mismatch, goe, ge, lane, best, bi,
                      bj, bs);
     } else
@@ -1363,6 +1370,7 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
                                                    const uint64_t *__restrict__ seq_start, int32_t match,
                                                    int32_t mismatch, int32_t go, int32_t ge, int32_t w,
                                                    uint32_t *__restrict__ next_task, const uint64_t *__restrict__ order,
+                                                   uint32_t *__restrict__ wide, uint32_t *__restrict__ wide_count,
                                                    DevAln *__restrict__ out, uint32_t *__restrict__ status) {
     const int lane = threadIdx.x & 31, seg = lane / SWG_G;
     constexpr int NG = 32 / SWG_G;
@@ -1385,10 +1393,52 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
         while (rest) {
             const int src = __ffs(rest) - 1;
             rest &= rest - 1;
-            sw_task_warp(sel, (uint32_t)order[base + (uint32_t)(src / SWG_G)], strip_off, strips, qpk, qnb, qstart,
-                         bpk, bnb, seq_start, match, mismatch, go, ge, w, out, status);
+            const uint32_t t2 = (uint32_t)order[base + (uint32_t)(src / SWG_G)];
+            if (dev_band(sel[t2], w) > 64) {  // wide bands: k_banded_sw_wide
+                if (lane == 0) wide[atomicAdd(wide_count, 1u)] = t2;
+                continue;
+            }
+            sw_task_warp<false>(sel, t2, strip_off, strips, qpk, qnb, qstart, bpk, bnb, seq_start, match, mismatch, go,
+                                ge, w, out, status);
             __syncwarp();
         }
+    }
+}
+
+// Bands wider than 64 diagonals, one HSP per warp: up to 32 x SWW_K offsets with the
+// row states in registers (the grouped path over the whole warp), wider ones on the
+// strip path.  A kernel of its own, so that its registers do not limit the main
+// alignment kernel.
+constexpr int SWW_K = 9;
+__global__ void __launch_bounds__(128) k_banded_sw_wide(const DevHsp *__restrict__ sel, const uint32_t *__restrict__ wide,
+                                                        const uint32_t *__restrict__ wide_count,
+                                                        uint32_t *__restrict__ next, const uint64_t *__restrict__ strip_off,
+                                                        SwCell *__restrict__ strips, const uint32_t *__restrict__ qpk,
+                                                        const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
+                                                        const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                                                        const uint64_t *__restrict__ seq_start, int32_t match,
+                                                        int32_t mismatch, int32_t go, int32_t ge, int32_t w,
+                                                        DevAln *__restrict__ out, uint32_t *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = *wide_count;
+    for (;;) {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(next, 1u);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= n) return;
+        const uint32_t task = wide[j];
+        const DevHsp h = sel[task];
+        bool handled = false;
+        DevAln res;
+        sw_group<32, SWW_K>(true, h, qpk, qnb, qstart, bpk, bnb, seq_start, match, mismatch, go + ge, ge, w, handled,
+                            res);
+        if (handled) {
+            if (lane == 0) out[task] = res;
+        } else {
+            sw_task_warp<true>(sel, task, strip_off, strips, qpk, qnb, qstart, bpk, bnb, seq_start, match, mismatch,
+                               go, ge, w, out, status);
+        }
+        __syncwarp();
     }
 }
 
@@ -1406,7 +1456,8 @@ __global__ void k_sw_order_keys(const DevHsp *__restrict__ h, uint32_t n, int32_
 }
 
 // Strip length of each HSP's band (B + 1), and the band area (DP-window rows x B, the
-// cells the alignment kernel evaluates) summed into *cells.
+// cells the alignment kernels evaluate) summed into cells[0] (bands of at most 64
+// diagonals) or cells[1] (wider bands).
 __global__ void k_band_width(const DevHsp *__restrict__ h, uint32_t n, int32_t w, const uint64_t *__restrict__ qstart,
                              uint32_t *__restrict__ B, unsigned long long *__restrict__ cells) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1416,7 +1467,7 @@ __global__ void k_band_width(const DevHsp *__restrict__ h, uint32_t n, int32_t w
     B[i] = (uint32_t)min(b + 1, (int64_t)65537);  // +1: the strip is read at b + 1
     const int64_t m = (int64_t)(qstart[h[i].qi + 1] - qstart[h[i].qi]);
     const int64_t rows = min(m, (int64_t)h[i].qe + w) - max((int64_t)0, (int64_t)h[i].qs - w);
-    if (rows > 0) atomicAdd(cells, (unsigned long long)(rows * b));
+    if (rows > 0) atomicAdd(cells + (b > 64 ? 1 : 0), (unsigned long long)(rows * b));
 }
 
 // ------------------------------------------------------ a13: ranking --
@@ -2161,16 +2212,16 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     if (n_sel) {
         uint32_t *B = arena.alloc_n<uint32_t>(n_sel);
         uint64_t *soff = arena.alloc_n<uint64_t>(n_sel + 1);
-        unsigned long long *dp_cells = reinterpret_cast<unsigned long long *>(arena.alloc_n<uint64_t>(1));
-        GN_CUDA(cudaMemsetAsync(dp_cells, 0, 8, s));
+        unsigned long long *dp_cells = reinterpret_cast<unsigned long long *>(arena.alloc_n<uint64_t>(2));
+        GN_CUDA(cudaMemsetAsync(dp_cells, 0, 16, s));
         GN_LAUNCH("k_band_width", n_sel, s,
                   k_band_width<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, B,
                                                                   dp_cells));
         void *scr = arena.alloc(scan_scratch_bytes(n_sel));
         exclusive_scan_u32(B, soff, n_sel, scr, s);
-        uint64_t cells = 0, area = 0;
+        uint64_t cells = 0, area[2] = {0, 0};
         GN_CUDA(cudaMemcpyAsync(&cells, soff + n_sel, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        GN_CUDA(cudaMemcpyAsync(&area, dp_cells, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        GN_CUDA(cudaMemcpyAsync(area, dp_cells, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         GN_CUDA(cudaStreamSynchronize(s));
         SwCell *strips = arena.alloc_n<SwCell>(cells);
         uint64_t *okeys = arena.alloc_n<uint64_t>(n_sel), *okeys_alt = arena.alloc_n<uint64_t>(n_sel);
@@ -2179,13 +2230,20 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         void *rs = arena.alloc(radix_scratch_bytes(n_sel));
         const uint64_t *order = radix_sort(okeys, okeys_alt, nullptr, nullptr, n_sel, 32, 48, rs, s, TAG_RECORD_SORT)
                                     ? okeys_alt : okeys;
-        GN_CUDA(cudaMemsetAsync(counter, 0, 4, s));
+        GN_CUDA(cudaMemsetAsync(counter, 0, 12, s));
+        uint32_t *wide = arena.alloc_n<uint32_t>(n_sel);
         unsigned warps = (unsigned)std::min<uint64_t>((n_sel + 3) / 4, (uint64_t)num_sms() * 32);
-        GN_LAUNCH("k_banded_sw", area, s,
+        GN_LAUNCH("k_banded_sw", area[0], s,
                   k_banded_sw<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
                                                             ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
                                                             sc.mismatch, sc.gap_open, sc.gap_extend,
-                                                            (int32_t)p.band_w, counter, order, aln, status));
+                                                            (int32_t)p.band_w, counter, order, wide, counter + 1,
+                                                            aln, status));
+        GN_LAUNCH("k_banded_sw_wide", area[1], s,
+                  k_banded_sw_wide<<<num_sms() * 4, 128, 0, s>>>(sel, wide, counter + 1, counter + 2, soff, strips, qp.pk,
+                                                                qp.nb, qstart_d, ix->bank.pk, ix->bank.nb,
+                                                                ix->seq_start_d, sc.match, sc.mismatch, sc.gap_open,
+                                                                sc.gap_extend, (int32_t)p.band_w, aln, status));
     }
     timer.mark("banded_sw");
     if (keep) {

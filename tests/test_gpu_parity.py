@@ -259,7 +259,8 @@ def test_device_queries_equal_host_queries(gn, mid_small):
 
 
 @pytest.mark.parametrize("kw", [dict(max_alignments=0), dict(max_alignments=1), dict(band_w=0),
-                                dict(band_w=64), dict(xdrop=5), dict(max_hit_distance=11, min_hsp_len=33),
+                                dict(band_w=20), dict(band_w=64), dict(band_w=128), dict(band_w=150),
+                                dict(xdrop=5), dict(max_hit_distance=11, min_hsp_len=33),
                                 dict(min_hsp_len=11), dict(min_hsp_len=5)])
 def test_parameters_mid_small(gn, mid_small, kw):
     bank, qs, ix, ox = mid_small
