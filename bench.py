@@ -77,6 +77,9 @@ def parse_args():
                          "at once, a saturation run of all requests); empty to skip it")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
     ap.add_argument("--serve-budget-gib", type=float, default=16.0, help="server memory budget")
+    ap.add_argument("--sweep", action="store_true",
+                    help="sensitivity sweep instead of the benchmark: planted-homolog recovery and time per "
+                         "step for a grid of minimum HSP length, hit distance and drop-off around the defaults")
     return ap.parse_args()
 
 
@@ -581,12 +584,72 @@ def run_ours(args, dist):
     return 0
 
 
+# minimum HSP length, maximum hit distance (0: 3 x stride) and drop-off of each sweep point;
+# the first is the default.  With stride 11 any two hits of a chain span >= 22 query
+# bases, so lengths 12..22 select the same HSPs: 11 (single hits) is the next step down.
+SWEEP_GRID = [(0, 0, 20), (11, 0, 20), (33, 0, 20), (44, 0, 20), (0, 11, 20), (0, 22, 20), (0, 66, 20),
+              (0, 0, 10), (0, 0, 40)]
+
+
+def run_sweep(args, dist):
+    """Sensitivity sweep (the paper's minimum-HSP-length experiment, section "Results
+    quality"): for each parameter point, the time per step of the whole query set and the
+    planted homologs recovered, by divergence and E-value threshold."""
+    import torch
+
+    import paper_1507_02987_gb300 as gn
+    from paper_1507_02987_gb300.sensitivity import recovery_table
+
+    if dist.rank:
+        return 0
+    dev = dist.local if torch.cuda.device_count() > dist.local else 0
+    torch.cuda.set_device(dev)
+    gn.load()
+    bank, queries, desc = workload(args.workload, args.stride, 0, args.queries)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ix = gn.Index(bank.seq_start, bank.bases, k=11, stride=args.stride, stream=sh, mask=args.mask)
+    qd = torch.from_numpy(queries.bases).to(f"cuda:{dev}")
+    M = int(queries.start[-1])
+    points = []
+    for min_len, dist_max, xdrop in SWEEP_GRID:
+        sp = gn.make_params(max_hit_distance=dist_max, min_hsp_len=min_len, xdrop=xdrop)
+        for _ in range(max(1, args.warmup)):
+            gn.search(ix, queries.start, qd, params=sp, stream=sh).close()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            gn.search(ix, queries.start, qd, params=sp, stream=sh).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        r = gn.search(ix, queries.start, qd, params=sp, stream=sh)
+        res = r.all()
+        r.close()
+        k = ix.k
+        points.append({"min_hsp_len": min_len or 2 * k, "max_hit_distance": dist_max or 3 * args.stride,
+                       "xdrop": xdrop, "ms_per_step": ms, "value": M / 1e3 / (ms / 1e3),
+                       "alignments": int(sum(len(a) for a in res)),
+                       "recovery": recovery_table(queries.meta, res)})
+        print(f"[sweep] {points[-1]['min_hsp_len']:3d} {points[-1]['max_hit_distance']:3d} {xdrop:3d}: "
+              f"{ms:8.2f} ms, found {points[-1]['recovery']['found']} of {points[-1]['recovery']['planted']}",
+              file=sys.stderr, flush=True)
+    ix.close()
+    print(json.dumps({"mode": "sensitivity_sweep", "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+                      "config": {"workload": desc, "mask": args.mask, "band_w": 16},
+                      "data": "synthetic", "sweep": points}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     dist = Dist()
     try:
         if args.impl == "reference":
             return run_reference(args, dist)
+        if args.sweep:
+            return run_sweep(args, dist)
         return run_ours(args, dist)
     finally:
         dist.close()

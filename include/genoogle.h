@@ -213,8 +213,20 @@ GN_API gn_status gn_index_export(const gn_index *index, uint64_t *bucket_start, 
  * banded affine-gap Smith-Waterman of each selected HSP; ranking by score with
  * e-value and bit score.  Queries are independent: results do not depend on
  * how queries are grouped into calls.  Results are host memory owned by the
- * library (gn_results_free).  Errors: GN_EINVAL, GN_ETOOBIG (a query >= 65,536
- * bases or > 65,536 queries), GN_ENOMEM, GN_ECUDA. */
+ * library (gn_results_free).
+ *
+ * Queries of up to 2^24 - 1 bases are taken (the paper's query sets reach 1 Mbp).
+ * The seed phases handle at most 65,535 bases at a time: a longer query is cut
+ * into segments of 65,535 bases that overlap by 8,192, and the chains found in
+ * the segments are joined before extension, which gives exactly the result on
+ * the whole query.  Such calls need max_hit_distance + seed span <= 8,192, no
+ * GN_FLAG_KEEP_STAGES / GN_FLAG_KEEP_HITS, at most 65,536 segments in all, and
+ * bank sequences shorter than 2^32 - 2^24 bases (GN_EINVAL / GN_ETOOBIG
+ * otherwise).  The request loop (gn_serve_submit) takes queries of one segment.
+ *
+ * Errors: GN_EINVAL, GN_ETOOBIG (a query of 2^24 bases or more, more than 65,536
+ * queries, an alignment band over 65,535 diagonals or a DP window of 2^32 cells),
+ * GN_ENOMEM, GN_ECUDA. */
 GN_API gn_status gn_search(const gn_index *index, const gn_queries *queries, const gn_scoring *scoring,
                     const gn_params *params, void *cuda_stream, gn_results **out);
 GN_API void gn_results_free(gn_results *results);

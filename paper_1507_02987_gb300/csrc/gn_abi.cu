@@ -54,13 +54,14 @@ static void resolve(const gn_index *ix, const gn_scoring *sc, const gn_params *p
     GN_REQUIRE(o.sc.K > 0 && o.sc.lambda > 0, GN_EINVAL, "lambda and K must be > 0");
 }
 
-static void check_queries(const gn_queries *q) {
+static void check_queries(const gn_queries *q, uint64_t max_len = MAX_QUERY_LEN) {
     GN_REQUIRE(q && q->start, GN_EINVAL, "queries and queries.start are required");
     GN_REQUIRE(q->n <= MAX_QUERIES, GN_ETOOBIG, "at most 65,536 queries per call");
     GN_REQUIRE(q->start[0] == 0, GN_EINVAL, "queries.start[0] must be 0");
     for (uint32_t i = 0; i < q->n; ++i) {
         GN_REQUIRE(q->start[i + 1] >= q->start[i], GN_EINVAL, "queries.start must be non-decreasing");
-        GN_REQUIRE(q->start[i + 1] - q->start[i] <= MAX_QUERY_LEN, GN_ETOOBIG, "a query holds 65,536 bases or more");
+        GN_REQUIRE(q->start[i + 1] - q->start[i] <= max_len, GN_ETOOBIG,
+                   max_len == MAX_QUERY_LEN ? "a query holds 65,536 bases or more" : "a query holds 2^24 bases or more");
     }
     GN_REQUIRE(q->start[q->n] == 0 || q->bases, GN_EINVAL, "queries.bases is required");
 }
@@ -417,7 +418,7 @@ gn_status gn_search(const gn_index *ix, const gn_queries *q, const gn_scoring *s
     gn_results *res = new (std::nothrow) gn_results();
     if (!res) { g_last_error = "host allocation failed"; return GN_ENOMEM; }
     gn_status st = guarded([&] {
-        check_queries(q);
+        check_queries(q, MAX_LONG_QUERY_LEN);
         SearchOptions o;
         resolve(ix, sc, p, o);
         int dev = 0;

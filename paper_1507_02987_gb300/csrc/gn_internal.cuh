@@ -83,7 +83,10 @@ enum : uint32_t {
 
 // ------------------------------------------------------------- constants --
 constexpr uint32_t QBIAS = 65536;          // > any query offset: diagonal key = gpos - qpos + QBIAS > 0
-constexpr uint32_t MAX_QUERY_LEN = 65535;
+constexpr uint32_t MAX_QUERY_LEN = 65535;   // longest query (segment) the seed phases take
+constexpr uint64_t MAX_LONG_QUERY_LEN = (1ull << 24) - 1;  // longest query gn_search takes (in segments)
+constexpr uint32_t SEG_OVERLAP = 8192;      // bases shared by neighbouring segments of a long query
+constexpr uint32_t SEG_STEP = MAX_QUERY_LEN - SEG_OVERLAP;
 constexpr uint32_t MAX_QUERIES = 65536;
 constexpr uint64_t HIT_BYTES = 24;  // device bytes budgeted per raw hit of a query chunk
 

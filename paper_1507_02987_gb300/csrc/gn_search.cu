@@ -815,6 +815,61 @@ __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__re
     }
 }
 
+// ------------------------------------------- long queries: segments, join --
+// Bases of each segment (block v): len bytes from offset off[v] of query parent[v].
+__global__ void k_segment_bases(const uint8_t *__restrict__ qbases, const uint64_t *__restrict__ qstart,
+                                const uint32_t *__restrict__ parent, const uint64_t *__restrict__ off,
+                                const uint64_t *__restrict__ vstart, uint8_t *__restrict__ out) {
+    const uint32_t v = blockIdx.x;
+    const uint64_t from = qstart[parent[v]] + off[v], to = vstart[v], len = vstart[v + 1] - to;
+    for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) out[to + i] = qbases[from + i];
+}
+
+// Chain pieces of the segments onto their queries; the len word carries the diagonal
+// (ds - qs mod 2^32, distinct for distinct diagonals when sequences are shorter than
+// 2^32 - 2^24 bases) for the join's sort.
+__global__ void k_segment_map(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__restrict__ parent,
+                              const uint64_t *__restrict__ off) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    DevHsp r = h[i];
+    const uint32_t o = (uint32_t)off[r.qi];
+    r.qi = parent[r.qi];
+    r.qs += o;
+    r.qe += o;
+    r.len = r.ds - r.qs;
+    h[i] = r;
+}
+
+// Pieces sorted by (qi, seq, diagonal, qs).  Two pieces of one chain share a hit, so
+// a piece joins the current chain when its first hit starts no later than the chain's
+// last hit (qs + span <= qe); pieces of different chains on one diagonal are more than
+// D >= 0 offsets apart and never do.  The first piece of each (qi, seq, diagonal) run
+// walks the run.  A chain is written at the index of its first piece and kept (flag)
+// when it is at least min_len long.
+__global__ void k_stitch_sweep(const DevHsp *__restrict__ in, uint32_t n, uint32_t span, uint32_t min_len,
+                               DevHsp *__restrict__ out, uint32_t *__restrict__ flag) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    auto same = [&](uint32_t a, uint32_t b) {
+        return in[a].qi == in[b].qi && in[a].seq == in[b].seq && in[a].len == in[b].len;
+    };
+    if (i > 0 && same(i - 1, i)) return;
+    uint32_t j = i;
+    while (j < n && same(j, i)) {
+        DevHsp c = in[j];
+        const uint32_t head = j++;
+        while (j < n && same(j, i) && in[j].qs + span <= c.qe) {
+            c.qe = max(c.qe, in[j].qe);
+            flag[j++] = 0;
+        }
+        c.len = c.qe - c.qs;
+        c.de = c.ds + c.len;
+        out[head] = c;
+        flag[head] = c.len >= min_len ? 1u : 0u;
+    }
+}
+
 // -------------------------------------------------- a10: overlap merging --
 // Records sorted by (qi, seq, qs, ds, qe, de).  The first record of each
 // (qi, seq) run sweeps the run: each record joins the current box when both its
@@ -982,7 +1037,7 @@ __global__ void k_select_flags(const DevHsp *__restrict__ h, uint32_t n, const u
 // when the scan keeps the later of equal values.
 struct SwCell {
     int32_t H, E;
-    uint32_t SH, SE;  // start cells: (row - I0) << 16 | band offset
+    uint32_t SH, SE;  // start cells: (row - I0) * B + band offset
 };
 
 constexpr int32_t SW_NEG = -(1 << 29);
@@ -1016,6 +1071,7 @@ __device__ __forceinline__ void sw_rows_pair(int64_t I0, int64_t I1, int64_t J0,
     const int32_t b0 = 2 * lane, b1 = 2 * lane + 1;
     BaseCursor cq(qpk, qnb), cd(bpk, bnb);
     const int32_t irows = (int32_t)(I1 - I0);
+    const uint32_t Bu = (uint32_t)B;  // start cells: row * B + band offset
     const int32_t jlo = (int32_t)(J0 - I0 - dlo), jhi = (int32_t)(J1 - 1 - I0 - dlo);  // band offset limits at row I0
     for (int32_t r = 0; r < irows; ++r) {
         // row i = I0 + r: band offsets with J0 <= i + dlo + b <= J1 - 1
@@ -1042,7 +1098,7 @@ __device__ __forceinline__ void sw_rows_pair(int64_t I0, int64_t I1, int64_t J0,
         }
         const bool okd0 = act0 && prow && b0 >= pblo && b0 <= pbhi;
         const int32_t Hd0 = okd0 ? pH0 : 0;
-        const uint32_t SD0 = (Hd0 > 0) ? pSH0 : ((uint32_t)r << 16) | (uint32_t)b0;
+        const uint32_t SD0 = (Hd0 > 0) ? pSH0 : (uint32_t)r * Bu + (uint32_t)b0;
         const int32_t Dg0 = Hd0 + dev_pair(qc, d0, match, mismatch);
         int32_t c0v; uint32_t c0s;
         if (Dg0 >= E0) { c0v = Dg0; c0s = SD0; } else { c0v = E0; c0s = SE0; }
@@ -1056,7 +1112,7 @@ __device__ __forceinline__ void sw_rows_pair(int64_t I0, int64_t I1, int64_t J0,
         }
         const bool okd1 = act1 && prow && b1 >= pblo && b1 <= pbhi;
         const int32_t Hd1 = okd1 ? pH1 : 0;
-        const uint32_t SD1 = (Hd1 > 0) ? pSH1 : ((uint32_t)r << 16) | (uint32_t)b1;
+        const uint32_t SD1 = (Hd1 > 0) ? pSH1 : (uint32_t)r * Bu + (uint32_t)b1;
         const int32_t Dg1 = Hd1 + dev_pair(qc, d1, match, mismatch);
         int32_t c1v; uint32_t c1s;
         if (Dg1 >= E1) { c1v = Dg1; c1s = SD1; } else { c1v = E1; c1s = SE1; }
@@ -1114,7 +1170,8 @@ __device__ void sw_task_warp(const DevHsp *__restrict__ sel, uint32_t task, cons
     const int64_t B = dhi - dlo + 1;
     DevAln res;
     res.qi = h.qi; res.seq = h.seq; res.qs = res.qe = res.ds = res.de = 0; res.score = 0; res.pad = 0;
-    if (B > 65535 || I1 - I0 > 65535) {
+    // start cells are (row - I0) * B + offset in 32 bits; strips hold up to 65,536 entries
+    if (B > 65535 || (uint64_t)max(I1 - I0, (int64_t)0) * (uint64_t)B >= (1ull << 32)) {
         if (lane == 0) { atomicOr(status, DEV_ERR_BAND_TOO_WIDE); out[task] = res; }
         return;
     }
@@ -1151,7 +1208,7 @@ __device__ void sw_task_warp(const DevHsp *__restrict__ sel, uint32_t task, cons
                 if (eo >= ee) { E = eo; SE = pu.SH; } else { E = ee; SE = pu.SE; }
             }
             const int32_t Hd = ok_d ? pd.H : 0;
-            const uint32_t SD = (Hd > 0) ? pd.SH : ((uint32_t)(i - I0) << 16) | (uint32_t)b;
+            const uint32_t SD = (Hd > 0) ? pd.SH : (uint32_t)(i - I0) * (uint32_t)B + (uint32_t)b;
             const int64_t j = i + dlo + b;
             int32_t sigma = mismatch;
             if (act) sigma = dev_pair(qc, dev_base(bpk, bnb, sb + (uint64_t)j), match, mismatch);
@@ -1199,8 +1256,8 @@ __device__ void sw_task_warp(const DevHsp *__restrict__ sel, uint32_t task, cons
     }
     if (lane == 0) {
         if (best > 0) {
-            int64_t i0 = I0 + (int64_t)(bs >> 16);
-            int64_t j0 = i0 + dlo + (int64_t)(bs & 0xFFFFu);
+            int64_t i0 = I0 + (int64_t)(bs / (uint32_t)B);
+            int64_t j0 = i0 + dlo + (int64_t)(bs % (uint32_t)B);
             res.qs = (uint32_t)i0; res.qe = (uint32_t)(bi + 1);
             res.ds = (uint32_t)j0; res.de = (uint32_t)(bj + 1);
             res.score = best;
@@ -1775,29 +1832,86 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     pack_bases(qbases_dev, M, qp, s);
     uint64_t *qstart_d = arena.alloc_n<uint64_t>(nq + 1);
     GN_CUDA(cudaMemcpyAsync(qstart_d, qstart_h.data(), sizeof(uint64_t) * (nq + 1), cudaMemcpyHostToDevice, s));
-    uint32_t *codes = arena.alloc_n<uint32_t>(M);
-    uint32_t *qinfo = arena.alloc_n<uint32_t>(M);
-    uint32_t *cnt = arena.alloc_n<uint32_t>(M);
-    uint32_t *src = arena.alloc_n<uint32_t>(M);
-    uint64_t *hoff = arena.alloc_n<uint64_t>(M + 1);
-    if (M) {
-        GN_LAUNCH("k_query_codes", M, s,
-                  k_query_codes<<<blocks_for(M), 256, 0, s>>>(qstart_d, nq, M, qp.pk, qp.nb, seed_shape(ix), ix->off_d, codes, qinfo,
+
+    // The seed phases (a5-a8) run on the queries themselves, or, when a query is longer
+    // than MAX_QUERY_LEN, on segments: every query of at most MAX_QUERY_LEN bases is one
+    // segment, a longer one is cut into segments of MAX_QUERY_LEN bases SEG_STEP apart
+    // (neighbours share SEG_OVERLAP bases; the last one ends with the query).  Every
+    // chain of hits at most D offsets apart then has each pair of consecutive hits inside
+    // one segment (D + span <= SEG_OVERLAP), so the chain is the union of its pieces in
+    // the segments, and pieces of one chain share a hit.  The pieces are emitted whatever
+    // their length, mapped back onto the query and joined after a8 (k_stitch_sweep),
+    // which then applies min_hsp_len.
+    std::vector<uint64_t> seg_start{0}, seg_off;  // per segment: start in the segment batch, offset in its query
+    std::vector<uint32_t> seg_parent;
+    bool segmented = false;
+    uint64_t max_qlen = 0;
+    for (uint32_t i = 0; i < nq; ++i) {
+        const uint64_t m = qstart_h[i + 1] - qstart_h[i];
+        max_qlen = std::max(max_qlen, m);
+        for (uint64_t o = 0;; o += SEG_STEP) {
+            const uint64_t len = std::min<uint64_t>(MAX_QUERY_LEN, m - o);
+            seg_parent.push_back(i);
+            seg_off.push_back(o);
+            seg_start.push_back(seg_start.back() + len);
+            if (o + MAX_QUERY_LEN >= m) break;
+            segmented = true;
+        }
+    }
+    GN_REQUIRE(seg_parent.size() <= MAX_QUERIES, GN_ETOOBIG, "more than 65,536 query segments in one call");
+    if (segmented) {
+        GN_REQUIRE(p.max_hit_distance + (uint32_t)k <= SEG_OVERLAP, GN_EINVAL,
+                   "queries over 65,535 bases need max_hit_distance + seed span <= 8,192");
+        GN_REQUIRE(!(p.flags & (GN_FLAG_KEEP_STAGES | GN_FLAG_KEEP_HITS)), GN_EINVAL,
+                   "stage outputs are not kept for queries over 65,535 bases");
+        GN_REQUIRE(ix->max_seq_len < (1ull << 32) - (1ull << 24), GN_ETOOBIG,
+                   "queries over 65,535 bases need bank sequences shorter than 2^32 - 2^24 bases");
+    }
+    const uint32_t hnq = segmented ? (uint32_t)seg_parent.size() : nq;
+    const std::vector<uint64_t> &hstart_h = segmented ? seg_start : qstart_h;
+    const uint64_t HM = hstart_h[hnq];
+    const uint32_t hit_min_len = segmented ? 1u : p.min_hsp_len;
+    Packed hqp = qp;
+    uint64_t *hstart_d = qstart_d;
+    uint32_t *seg_parent_d = nullptr;
+    uint64_t *seg_off_d = nullptr;
+    if (segmented) {
+        hstart_d = arena.alloc_n<uint64_t>(hnq + 1);
+        seg_off_d = arena.alloc_n<uint64_t>(hnq);
+        seg_parent_d = arena.alloc_n<uint32_t>(hnq);
+        GN_CUDA(cudaMemcpyAsync(hstart_d, seg_start.data(), sizeof(uint64_t) * (hnq + 1), cudaMemcpyHostToDevice, s));
+        GN_CUDA(cudaMemcpyAsync(seg_off_d, seg_off.data(), sizeof(uint64_t) * hnq, cudaMemcpyHostToDevice, s));
+        GN_CUDA(cudaMemcpyAsync(seg_parent_d, seg_parent.data(), sizeof(uint32_t) * hnq, cudaMemcpyHostToDevice, s));
+        uint8_t *sb = arena.alloc_n<uint8_t>(HM);
+        GN_LAUNCH("k_segment_bases", HM, s,
+                  k_segment_bases<<<hnq, 256, 0, s>>>(qbases_dev, qstart_d, seg_parent_d, seg_off_d, hstart_d, sb));
+        hqp.pk = arena.alloc_n<uint32_t>(Packed::pk_words(HM));
+        hqp.nb = arena.alloc_n<uint32_t>(Packed::nb_words(HM));
+        pack_bases(sb, HM, hqp, s);
+    }
+    uint32_t *codes = arena.alloc_n<uint32_t>(HM);
+    uint32_t *qinfo = arena.alloc_n<uint32_t>(HM);
+    uint32_t *cnt = arena.alloc_n<uint32_t>(HM);
+    uint32_t *src = arena.alloc_n<uint32_t>(HM);
+    uint64_t *hoff = arena.alloc_n<uint64_t>(HM + 1);
+    if (HM) {
+        GN_LAUNCH("k_query_codes", HM, s,
+                  k_query_codes<<<blocks_for(HM), 256, 0, s>>>(hstart_d, hnq, HM, hqp.pk, hqp.nb, seed_shape(ix), ix->off_d, codes, qinfo,
                                                               cnt, src));
     }
     {
-        void *scr = arena.alloc(scan_scratch_bytes(M));
-        exclusive_scan_u32(cnt, hoff, M, scr, s);
+        void *scr = arena.alloc(scan_scratch_bytes(HM));
+        exclusive_scan_u32(cnt, hoff, HM, scr, s);
     }
     // hit offsets at query boundaries -> per-query hit counts (chunk plan)
-    uint64_t *hq_d = arena.alloc_n<uint64_t>(nq + 1);
-    GN_LAUNCH("k_gather_u64", nq + 1, s,
-              k_gather_u64<<<blocks_for(nq + 1), 256, 0, s>>>(hoff, qstart_d, nq + 1, hq_d));
-    std::vector<uint64_t> hq = to_host(hq_d, nq + 1, s);
+    uint64_t *hq_d = arena.alloc_n<uint64_t>(hnq + 1);
+    GN_LAUNCH("k_gather_u64", hnq + 1, s,
+              k_gather_u64<<<blocks_for(hnq + 1), 256, 0, s>>>(hoff, hstart_d, hnq + 1, hq_d));
+    std::vector<uint64_t> hq = to_host(hq_d, hnq + 1, s);
     timer.mark("query_codes");
     if (keep) {
-        res->st_hit_counts.resize(nq);
-        for (uint32_t i = 0; i < nq; ++i) res->st_hit_counts[i] = hq[i + 1] - hq[i];
+        res->st_hit_counts.resize(hnq);
+        for (uint32_t i = 0; i < hnq; ++i) res->st_hit_counts[i] = hq[i + 1] - hq[i];
     }
 
     // a6-a8 per chunk of queries whose hits fit the budget
@@ -1816,7 +1930,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     const uint64_t gbits_max = (uint64_t)bits_for(ix->n_bases + QBIAS);
     const uint32_t max_chunk_q = (uint32_t)std::min<uint64_t>(MAX_QUERIES, 1ull << std::min<uint64_t>(48 - gbits_max, 31));
 
-    uint32_t hsp_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(1u << 16, hq[nq] / 128));
+    uint32_t hsp_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFFFull, std::max<uint64_t>(1u << 16, hq[hnq] / 128));
     DevHsp *hsp = arena.alloc_n<DevHsp>(hsp_cap);
     uint32_t n_hsp = 0;
     uint32_t *counter = arena.alloc_n<uint32_t>(4);
@@ -1825,10 +1939,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     std::vector<uint32_t> hits_q;
 
     uint32_t qa = 0;
-    while (qa < nq) {
+    while (qa < hnq) {
         uint32_t qb = qa + 1;
-        while (qb < nq && qb - qa < max_chunk_q && hq[qb + 1] - hq[qa] <= hit_budget) ++qb;
-        const uint64_t xa = qstart_h[qa], xb = qstart_h[qb];
+        while (qb < hnq && qb - qa < max_chunk_q && hq[qb + 1] - hq[qa] <= hit_budget) ++qb;
+        const uint64_t xa = hstart_h[qa], xb = hstart_h[qb];
         const uint64_t ha = hq[qa], Hc = hq[qb] - hq[qa];
         GN_REQUIRE(Hc < (1ull << 32), GN_ETOOBIG, "a query has 2^32 seed hits or more");
         if (Hc > 0) {
@@ -1870,7 +1984,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     uint64_t threads = std::min<uint64_t>(n, (uint64_t)num_sms() * 2048);
                     GN_LAUNCH("k_hit_merge", n, s,
                               k_hit_merge<<<blocks_for(threads), 256, 0, s>>>(sorted, n, qbits, qa, k,
-                                                                             p.max_hit_distance, p.min_hsp_len,
+                                                                             p.max_hit_distance, hit_min_len,
                                                                              seq_map(ix), o, counter, room, status));
                 });
                 return sorted;
@@ -2075,7 +2189,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                         GN_CUDA(cudaMemsetAsync(big_count, 0, 4, s));
                         GN_LAUNCH("k_bucket_group", n_kept, s,
                                   k_bucket_group_warp<<<ggrid, BGW_WARPS * 32, smem, s>>>(
-                                      bkeys, bcount, bcap, NB, bq, qa, qbits, k, p.max_hit_distance, p.min_hsp_len,
+                                      bkeys, bcount, bcap, NB, bq, qa, qbits, k, p.max_hit_distance, hit_min_len,
                                       singles, seq_map(ix), o, counter, room, gsp + spilled_fill,
                                       (unsigned long long)group_room, ovf_count, status, counter + 1, big,
                                       big_count));
@@ -2097,7 +2211,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 if (n_big) emit([&](DevHsp *o, uint32_t room) {
                     GN_LAUNCH("k_bucket_group_block", n_big, s,
                               k_bucket_group_block<<<num_sms() * 4, 256, 0, s>>>(
-                                  bkeys, bcount, bcap, bq, big, big_count, qa, k, p.max_hit_distance, p.min_hsp_len,
+                                  bkeys, bcount, bcap, bq, big, big_count, qa, k, p.max_hit_distance, hit_min_len,
                                   singles, seq_map(ix), o, counter, room, status));
                 });
                 timer.mark("bucket_group");
@@ -2107,6 +2221,32 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
             timer.mark("hit_merge");
         }
         qa = qb;
+    }
+    const int qib = bits_for(nq ? nq - 1 : 0);
+    const int seqb = bits_for(ix->n_seqs ? ix->n_seqs - 1 : 0);
+    const int posb = bits_for(ix->max_seq_len);
+    const int qposb = std::max(16, bits_for(max_qlen));
+    if (segmented && n_hsp) {
+        // pieces onto their queries, then one chain per run of pieces sharing seeds
+        GN_LAUNCH("k_segment_map", n_hsp, s,
+                  k_segment_map<<<blocks_for(n_hsp), 256, 0, s>>>(hsp, n_hsp, seg_parent_d, seg_off_d));
+        uint32_t *perm = arena.alloc_n<uint32_t>(n_hsp);
+        sort_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, n_hsp,
+                     {{W_QI, qib, false}, {W_SEQ, seqb, false}, {W_LEN, 32, false}, {W_QS, qposb, false}},
+                     perm, arena, s);
+        DevHsp *srt = arena.alloc_n<DevHsp>(n_hsp);
+        gather_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, perm, n_hsp,
+                       reinterpret_cast<uint32_t *>(srt), s);
+        DevHsp *chains = arena.alloc_n<DevHsp>(n_hsp);
+        uint32_t *flag = arena.alloc_n<uint32_t>(n_hsp);
+        GN_LAUNCH("k_stitch_sweep", n_hsp, s,
+                  k_stitch_sweep<<<blocks_for(n_hsp), 256, 0, s>>>(srt, n_hsp, (uint32_t)k, p.min_hsp_len, chains,
+                                                                  flag));
+        DevHsp *joined = arena.alloc_n<DevHsp>(n_hsp);
+        n_hsp = compact_records(reinterpret_cast<const uint32_t *>(chains), HSP_WORDS, flag, n_hsp,
+                                reinterpret_cast<uint32_t *>(joined), arena, s);
+        hsp = joined;
+        timer.mark("stitch");
     }
     if (keep_hits) res->st_hits.swap(hits_q);
     if (keep) {
@@ -2129,11 +2269,6 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         res->st_ext.resize(n_hsp);
         if (n_hsp) memcpy(res->st_ext.data(), v.data(), sizeof(DevHsp) * n_hsp);
     }
-
-    const int qib = bits_for(nq ? nq - 1 : 0);
-    const int seqb = bits_for(ix->n_seqs ? ix->n_seqs - 1 : 0);
-    const int posb = bits_for(ix->max_seq_len);
-    const int qposb = 16;
 
     // a10: merge overlapped HSPs
     uint32_t n_mg = 0;
@@ -2167,7 +2302,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     uint32_t *first = arena.alloc_n<uint32_t>(nq);
     const char *senv = getenv("GN_SELECT_PATH");
     const bool per_query_select = p.max_alignments > 0 && p.max_alignments <= (uint32_t)SQ_CAP &&
-                                  !(senv && strcmp(senv, "sort") == 0);
+                                  max_qlen <= 65535 && !(senv && strcmp(senv, "sort") == 0);
     if (n_mg && per_query_select) {
         uint32_t *qb = arena.alloc_n<uint32_t>(nq + 1);
         GN_LAUNCH("k_query_bounds", nq + 1, s, k_query_bounds<<<blocks_for(nq + 1), 256, 0, s>>>(merged, n_mg, nq, qb));
@@ -2282,7 +2417,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         GN_LAUNCH("k_gather_ranked", n_out, s,
                   k_gather_ranked<<<rgrid, 256, 0, s>>>(hits, qrange, qoff, nq, fin));
     } else if (n_sel) {
-        const int scb = std::min(31, bits_for((uint64_t)65535 * (uint64_t)std::max(1, sc.match)));
+        const int scb = std::min(31, bits_for(std::max<uint64_t>(65535, max_qlen) * (uint64_t)std::max(1, sc.match)));
         uint32_t *perm = arena.alloc_n<uint32_t>(n_sel);
         sort_records(reinterpret_cast<const uint32_t *>(aln), ALN_WORDS, n_sel,
                      {{A_QI, qib, false}, {A_SEQ, seqb, false}, {A_QS, qposb, false}, {A_QE, qposb, false},
@@ -2322,7 +2457,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     GN_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
     res->hits = to_host(fin, n_out, s);
     GN_REQUIRE((st & (DEV_ERR_BAND_TOO_WIDE | DEV_ERR_BOUNDS)) == 0, GN_ETOOBIG,
-               "an alignment band or window exceeded 65,535 cells in one dimension");
+               "an alignment band exceeded 65,535 diagonals or its window 2^32 cells");
     res->qoff.assign(nq + 1, 0);
     for (uint32_t i = 0; i < n_out; ++i) res->qoff[res->hits[i].query + 1]++;
     for (uint32_t i = 0; i < nq; ++i) res->qoff[i + 1] += res->qoff[i];

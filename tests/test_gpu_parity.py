@@ -290,9 +290,12 @@ def test_edge_queries(gn, tiny):
 def test_too_long_query_rejected(gn, tiny):
     bank, qs, ix, ox = tiny
     q = synth.queries_from_strings([b"A" * 70000])
-    with pytest.raises(gn.GnError) as e:
-        gn.search(ix, q.start, q.bases)
+    srv = gn.Server(ix, 1 << 30)
+    with pytest.raises(gn.GnError) as e:  # the request loop takes queries of one segment
+        srv.submit(q.query(0))
     assert e.value.status == gn.GN_ETOOBIG
+    srv.stop()
+    assert gn.search(ix, q.start, q.bases).n_queries == 1  # gn_search takes it in segments
 
 
 def test_autotune(gn, mid_small):
@@ -323,3 +326,14 @@ def test_autotune(gn, mid_small):
     gn.set_tuning(ix)
     assert gn.get_tuning(ix) == {"tile_hits": 0, "fill_threads": 0, "bucket_target": 0}
     ix.close()
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(min_hsp_len=11), dict(max_hit_distance=66, xdrop=40)])
+def test_sensitivity_recovery_matches_oracle(gn, mid_small, kw):
+    from paper_1507_02987_gb300.sensitivity import recovery_table
+    bank, _, ix, ox = mid_small
+    qs = synth.make_queries("mid", bank, n=60)
+    res = gn.search(ix, qs.start, qs.bases, params=gn.make_params(**kw)).all()
+    ref = [r.ranked for r in ox.search(qs, oracle.Params(**kw), threads=os.cpu_count() or 1)]
+    got, exp = recovery_table(qs.meta, res), recovery_table(qs.meta, ref)
+    assert got == exp and got["planted"] == qs.n and got["found"] > qs.n // 2
