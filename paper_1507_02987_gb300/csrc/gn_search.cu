@@ -1285,6 +1285,55 @@ struct BaseWin {
     }
 };
 
+// 64 consecutive bases [p0, p0 + 64) of a packed sequence (p0 a multiple of 16) that
+// slide forward 16 at a time, with the next 16 bases loaded one slide ahead, so a
+// warp walking rows rarely waits on memory.  All lanes of a segment hold the same
+// window.  Words at or past `end` (the sequence's end) are never read.
+struct SegWin {
+    uint64_t p0 = 0, hi = 0, lo = 0, bad = 0;  // codes of p0..p0+31 (hi) and p0+32..p0+63 (lo); non-base bits
+    uint32_t nxt_pk = 0, nxt_nb = 0;            // the 16 bases after the window (code word, non-base word)
+    __device__ __forceinline__ static uint32_t pk_at(const uint32_t *__restrict__ pk, uint64_t x, uint64_t end) {
+        return x < end ? pk[x >> 4] : 0u;
+    }
+    __device__ __forceinline__ static uint32_t nb_at(const uint32_t *__restrict__ nb, uint64_t x, uint64_t end) {
+        return x < end ? nb[x >> 5] : 0u;
+    }
+    __device__ __forceinline__ void prefetch(const uint32_t *__restrict__ pk, const uint32_t *__restrict__ nb,
+                                             uint64_t end) {
+        nxt_pk = pk_at(pk, p0 + 64, end);
+        nxt_nb = nb_at(nb, p0 + 64, end);
+    }
+    __device__ __forceinline__ void init(const uint32_t *__restrict__ pk, const uint32_t *__restrict__ nb, uint64_t p,
+                                         uint64_t end) {
+        p0 = p & ~15ull;
+        hi = ((uint64_t)pk_at(pk, p0, end) << 32) | pk_at(pk, p0 + 16, end);
+        lo = ((uint64_t)pk_at(pk, p0 + 32, end) << 32) | pk_at(pk, p0 + 48, end);
+        // bit o = base p0 + o; words of 32 bases hold p0 at bit 0 or at bit 16
+        if (p0 & 16) {
+            bad = ((uint64_t)nb_at(nb, p0, end) >> 16) | ((uint64_t)nb_at(nb, p0 + 16, end) << 16) |
+                  ((uint64_t)nb_at(nb, p0 + 48, end) << 48);
+        } else {
+            bad = (uint64_t)nb_at(nb, p0, end) | ((uint64_t)nb_at(nb, p0 + 32, end) << 32);
+        }
+        prefetch(pk, nb, end);
+    }
+    __device__ __forceinline__ void advance(const uint32_t *__restrict__ pk, const uint32_t *__restrict__ nb,
+                                            uint64_t end) {
+        const uint64_t q = p0 + 64;
+        hi = (hi << 32) | (lo >> 32);
+        lo = (lo << 32) | nxt_pk;
+        bad = (bad >> 16) | ((uint64_t)((nxt_nb >> (q & 16)) & 0xFFFFu) << 48);
+        p0 += 16;
+        prefetch(pk, nb, end);
+    }
+    // code of base p (p0 <= p < p0 + 64), 4 for a non-base
+    __device__ __forceinline__ uint32_t at(uint64_t p) const {
+        const uint32_t o = (uint32_t)(p - p0);
+        const uint32_t c = (uint32_t)((o < 32 ? hi : lo) >> (62 - 2 * (o & 31))) & 3u;
+        return ((bad >> o) & 1ull) ? 4u : c;
+    }
+};
+
 // 32 / G HSPs per warp: segment s (lanes sG .. sG + G - 1) aligns its own HSP, lane l of
 // the segment owns band offsets K l .. K l + K - 1 and keeps their previous-row states
 // in registers.  All segments step through rows together.  The vertical-gap input of
@@ -1299,11 +1348,13 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
                                          int32_t goe, int32_t ge, int32_t w, bool &handled, DevAln &res) {
     const int lane = threadIdx.x & 31, sl = lane % G;
     int64_t I0 = 0, I1 = 0, J0 = 0, J1 = 0, dlo = 0, B = 0;
-    uint64_t qb = 0, sb = 0;
+    uint64_t qb = 0, sb = 0, qend = 0, send = 0;
     if (valid) {
         qb = qstart[h.qi];
         sb = seq_start[h.seq];
-        const int64_t m = (int64_t)(qstart[h.qi + 1] - qb), L = (int64_t)(seq_start[h.seq + 1] - sb);
+        qend = qstart[h.qi + 1];
+        send = seq_start[h.seq + 1];
+        const int64_t m = (int64_t)(qend - qb), L = (int64_t)(send - sb);
         const int64_t d_s = (int64_t)h.ds - h.qs, d_e = (int64_t)h.de - h.qe;
         dlo = min(d_s, d_e) - w;
         B = max(d_s, d_e) + w - dlo + 1;
@@ -1323,7 +1374,15 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
     for (int k = 0; k < K; ++k) { pH[k] = 0; pE[k] = SW_NEG; pSH[k] = 0; pSE[k] = 0; }
     int32_t best = 0, br = INT32_MAX, bb = INT32_MAX;
     uint32_t bs = 0;
+    // bases: one 64-base window per segment (bands of up to 49 diagonals), else a
+    // 32-base window per lane
+    constexpr bool SEG = G * K <= 49;
     BaseWin wq, wd;
+    SegWin sq, sd;
+    if (SEG && handled) {
+        sq.init(qpk, qnb, qb + (uint64_t)I0, qend);
+        sd.init(bpk, bnb, sb + (uint64_t)max(I0 + dlo, J0), send);
+    }
     for (int32_t r = 0; r < max_rows; ++r) {
         const bool seg_on = r < rows;
         const int32_t blo = max(0, jlo - r), bhi = min(Bm1, jhi - r);
@@ -1338,7 +1397,14 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
         uint32_t qc = 4u;
         const uint64_t i = (uint64_t)(I0 + r);
         const uint64_t jb = sb + (uint64_t)((int64_t)i + dlo + b0);  // bank position of offset b0
-        if (lane_on) {
+        if (SEG) {
+            if (seg_on) {  // the same in every lane of the segment
+                if (qb + i >= sq.p0 + 64) sq.advance(qpk, qnb, qend);
+                const uint64_t jhi_pos = sb + (uint64_t)min((int64_t)i + dlo + B - 1, J1 - 1);
+                if (jhi_pos >= sd.p0 + 64) sd.advance(bpk, bnb, send);
+                if (lane_on) qc = sq.at(qb + i);
+            }
+        } else if (lane_on) {
             if (i + qb < wq.p0 || i + qb >= wq.p0 + 32) wq.load(qpk, qnb, qb + i);
             qc = wq.at(qb + i);
             const uint64_t jfirst = jb + (uint64_t)max(0, blo - b0), jlast = jb + (uint64_t)min(K - 1, bhi - b0);
@@ -1362,7 +1428,7 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
             const bool okd = act && prow && b >= pblo && b <= pbhi;
             const int32_t Hd = okd ? pH[k] : 0;
             const uint32_t SD = (Hd > 0) ? pSH[k] : ((uint32_t)r << 16) | (uint32_t)b;
-            const uint32_t d = act ? wd.at(jb + k) : 4u;
+            const uint32_t d = act ? (SEG ? sd.at(jb + k) : wd.at(jb + k)) : 4u;
             const int32_t Dg = Hd + dev_pair(qc, d, match, mismatch);
             int32_t cv;
             if (Dg >= E[k]) { cv = Dg; C[k] = SD; } else { cv = E[k]; C[k] = SE[k]; }
@@ -1415,6 +1481,131 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
     }
 }
 
+// One HSP with a band of at most 64 diagonals on anti-diagonal wavefronts, for the
+// longest alignments, whose row-by-row chains would otherwise bound the kernel's time.
+// Cell (r, b) (row I0 + r, band offset b) lies on wavefront t = 2r + b; its diagonal
+// input (r - 1, b) is on t - 2, its vertical input (r - 1, b + 1) and horizontal input
+// (r, b - 1) on t - 1.  Lane l owns offsets 2l and 2l + 1 and computes one of them per
+// wavefront (offset 2l on even t, 2l + 1 on odd t), so each wavefront takes one
+// shuffle step and a short chain of operations instead of a row's scan.  Each cell
+// follows the sequential recurrence with its tie rules: E and F open on ties, the
+// diagonal beats E, H0 beats F; F extends from the left cell's H0 (as the row scan
+// does).  The best cell is the highest score, then the smallest row, then the
+// smallest offset.  Start cells are (row - I0) * B + offset.
+struct WaveCell {
+    int32_t H, E, H0, F;
+    uint32_t SH, SE, C, SF;
+};
+
+__device__ __forceinline__ void sw_wave(const DevHsp &h, const uint32_t *__restrict__ qpk,
+                                        const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
+                                        const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                                        const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch,
+                                        int32_t goe, int32_t ge, int32_t w, DevAln &res) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t qb = qstart[h.qi], sb = seq_start[h.seq], qend = qstart[h.qi + 1], send = seq_start[h.seq + 1];
+    const int64_t m = (int64_t)(qend - qb), L = (int64_t)(send - sb);
+    const int64_t d_s = (int64_t)h.ds - h.qs, d_e = (int64_t)h.de - h.qe;
+    const int64_t dlo = min(d_s, d_e) - w;
+    const int32_t B = (int32_t)(max(d_s, d_e) + w - dlo + 1);
+    const int64_t I0 = max((int64_t)0, (int64_t)h.qs - w), I1 = min(m, (int64_t)h.qe + w);
+    const int64_t J0 = max((int64_t)0, (int64_t)h.ds - w), J1 = min(L, (int64_t)h.de + w);
+    const int32_t rows = (int32_t)max(I1 - I0, (int64_t)0);
+    const int32_t jlo = (int32_t)(J0 - I0 - dlo), jhi = (int32_t)(J1 - 1 - I0 - dlo);
+    auto valid = [&](int32_t r, int32_t b) {
+        return r >= 0 && r < rows && b >= 0 && b < B && b >= jlo - r && b <= jhi - r;
+    };
+    WaveCell c0, c1;  // the lane's last cells at offsets 2l and 2l + 1
+    c0.H = c1.H = 0; c0.E = c1.E = SW_NEG; c0.H0 = c1.H0 = 0; c0.F = c1.F = SW_NEG;
+    c0.SH = c1.SH = c0.SE = c1.SE = c0.C = c1.C = c0.SF = c1.SF = 0;
+    int32_t best = 0, br = INT32_MAX, bb = INT32_MAX;
+    uint32_t bs = 0;
+    SegWin sq, sd;
+    sq.init(qpk, qnb, qb + (uint64_t)I0, qend);
+    sd.init(bpk, bnb, sb + (uint64_t)max(I0 + dlo, J0), send);
+    // one cell: left, up-right and diagonal inputs (valid or not), the bases, the cell
+    auto step = [&](int32_t r, int32_t b, const WaveCell &lf, const WaveCell &ur, const WaveCell &dg, WaveCell &out) {
+        const bool cv = valid(r, b);
+        int32_t E = SW_NEG;
+        uint32_t SE = 0;
+        if (cv && valid(r - 1, b + 1)) {
+            const int32_t eo = ur.H + goe, ee = ur.E + ge;
+            if (eo >= ee) { E = eo; SE = ur.SH; } else { E = ee; SE = ur.SE; }
+        }
+        const int32_t Hd = (cv && valid(r - 1, b)) ? dg.H : 0;
+        const uint32_t SD = Hd > 0 ? dg.SH : (uint32_t)r * (uint32_t)B + (uint32_t)b;
+        int32_t sc = mismatch;
+        if (cv) {
+            const uint64_t i = qb + (uint64_t)(I0 + r), j = sb + (uint64_t)(I0 + r + dlo + b);
+            sc = dev_pair(sq.at(i), sd.at(j), match, mismatch);
+        }
+        const int32_t Dg = Hd + sc;
+        int32_t cand;
+        uint32_t C;
+        if (Dg >= E) { cand = Dg; C = SD; } else { cand = E; C = SE; }
+        const int32_t H0 = cand > 0 ? cand : 0;
+        int32_t F = SW_NEG;
+        uint32_t SF = 0;
+        if (cv && valid(r, b - 1)) {
+            const int32_t fo = lf.H0 + goe, fe = lf.F + ge;
+            if (fo >= fe) { F = fo; SF = lf.C; } else { F = fe; SF = lf.SF; }
+        }
+        int32_t H;
+        uint32_t SH;
+        if (H0 >= F) { H = H0; SH = C; } else { H = F; SH = SF; }
+        if (cv && H > 0 && (H > best || (H == best && (r < br || (r == br && b < bb))))) {
+            best = H; br = r; bb = b; bs = SH;
+        }
+        out.H = H; out.E = E; out.H0 = H0; out.F = F; out.SH = SH; out.SE = SE; out.C = C; out.SF = SF;
+    };
+    const int32_t T = rows > 0 ? 2 * rows + B - 2 : 0;  // wavefronts 0 .. T - 1
+    const int32_t b0 = 2 * lane, b1 = 2 * lane + 1;
+    for (int32_t t = 0; t < T; t += 2) {
+        // windows: query rows up to t / 2, bank positions up to offset B - 1 of wavefront t + 1
+        if (qb + (uint64_t)(I0 + t / 2) >= sq.p0 + 64) sq.advance(qpk, qnb, qend);
+        const uint64_t jmax = sb + (uint64_t)min(I0 + dlo + (int64_t)((t + B) / 2), J1 - 1);
+        if (jmax >= sd.p0 + 64) sd.advance(bpk, bnb, send);
+        // even wavefront t: offset 2l; left is lane l - 1's offset 2l - 1 (from wavefront t - 1)
+        {
+            WaveCell lf;
+            lf.H0 = __shfl_up_sync(0xffffffffu, c1.H0, 1);
+            lf.F = __shfl_up_sync(0xffffffffu, c1.F, 1);
+            lf.C = __shfl_up_sync(0xffffffffu, c1.C, 1);
+            lf.SF = __shfl_up_sync(0xffffffffu, c1.SF, 1);
+            WaveCell nc;
+            step((t - b0) >> 1, b0, lf, c1, c0, nc);  // up-right: own offset 2l + 1; diagonal: own 2l
+            c0 = nc;
+        }
+        // odd wavefront t + 1: offset 2l + 1; up-right is lane l + 1's offset 2l + 2 (wavefront t)
+        {
+            WaveCell ur;
+            ur.H = __shfl_down_sync(0xffffffffu, c0.H, 1);
+            ur.E = __shfl_down_sync(0xffffffffu, c0.E, 1);
+            ur.SH = __shfl_down_sync(0xffffffffu, c0.SH, 1);
+            ur.SE = __shfl_down_sync(0xffffffffu, c0.SE, 1);
+            WaveCell nc;
+            step((t + 1 - b1) >> 1, b1, c0, ur, c1, nc);  // left: own offset 2l (this row)
+            c1 = nc;
+        }
+    }
+    // highest score, then smallest row, then smallest offset
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int32_t ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int32_t orr = __shfl_down_sync(0xffffffffu, br, o), obb = __shfl_down_sync(0xffffffffu, bb, o);
+        const uint32_t os = __shfl_down_sync(0xffffffffu, bs, o);
+        if (ob > best || (ob == best && (orr < br || (orr == br && obb < bb)))) { best = ob; br = orr; bb = obb; bs = os; }
+    }
+    res.qi = h.qi; res.seq = h.seq; res.qs = res.qe = res.ds = res.de = 0; res.score = 0; res.pad = 0;
+    if (best > 0) {
+        const int64_t bi = I0 + br, bj = bi + dlo + bb;
+        const int64_t i0 = I0 + (int64_t)(bs / (uint32_t)B), j0 = i0 + dlo + (int64_t)(bs % (uint32_t)B);
+        res.qs = (uint32_t)i0; res.qe = (uint32_t)(bi + 1);
+        res.ds = (uint32_t)j0; res.de = (uint32_t)(bj + 1);
+        res.score = best;
+    }
+}
+
 // Warps take 32 / SWG_G selected HSPs at a time; each segment of SWG_G lanes aligns one
 // whose band fits SWG_G x SWG_K offsets, and the whole warp then aligns the others one by
 // one (pair or strip path).
@@ -1428,13 +1619,31 @@ __global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ se
                                                    int32_t mismatch, int32_t go, int32_t ge, int32_t w,
                                                    uint32_t *__restrict__ next_task, const uint64_t *__restrict__ order,
                                                    uint32_t *__restrict__ wide, uint32_t *__restrict__ wide_count,
+                                                   const uint32_t *__restrict__ n_long, uint32_t *__restrict__ next_long,
                                                    DevAln *__restrict__ out, uint32_t *__restrict__ status) {
     const int lane = threadIdx.x & 31, seg = lane / SWG_G;
     constexpr int NG = 32 / SWG_G;
+    // the first n_long tasks of the order (the longest alignments): one warp each on wavefronts
+    const uint32_t nl = *n_long;
+    for (;;) {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(next_long, 1u);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= nl) break;
+        const uint32_t task = (uint32_t)order[j];
+        const DevHsp h = sel[task];
+        if (dev_band(h, w) > 64) {
+            if (lane == 0) wide[atomicAdd(wide_count, 1u)] = task;
+            continue;
+        }
+        DevAln res;
+        sw_wave(h, qpk, qnb, qstart, bpk, bnb, seq_start, match, mismatch, go + ge, ge, w, res);
+        if (lane == 0) out[task] = res;
+    }
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(next_task, (uint32_t)NG);
-        base = __shfl_sync(0xffffffffu, base, 0);
+        base = __shfl_sync(0xffffffffu, base, 0) + nl;
         if (base >= n) return;
         const bool valid = base + seg < n;
         const uint32_t task = valid ? (uint32_t)order[base + seg] : 0u;  // longest alignments first
@@ -1502,14 +1711,21 @@ __global__ void __launch_bounds__(128) k_banded_sw_wide(const DevHsp *__restrict
 // Alignment order: key = (65535 - DP-window rows) << 32 | task, so that an ascending
 // sort on bits 32..47 hands out the longest alignments first (they bound the kernel's
 // time) and groups alignments of similar length.
+// Alignments of at least long_rows rows are counted in *n_long (they sort first).
 __global__ void k_sw_order_keys(const DevHsp *__restrict__ h, uint32_t n, int32_t w,
-                                const uint64_t *__restrict__ qstart, uint64_t *__restrict__ keys) {
+                                const uint64_t *__restrict__ qstart, uint32_t long_rows, uint64_t *__restrict__ keys,
+                                uint32_t *__restrict__ n_long) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t m = (int64_t)(qstart[h[i].qi + 1] - qstart[h[i].qi]);
-    const int64_t rows = min(m, (int64_t)h[i].qe + w) - max((int64_t)0, (int64_t)h[i].qs - w);
-    const int64_t r = rows < 0 ? 0 : (rows > 65535 ? 65535 : rows);
-    keys[i] = ((uint64_t)(65535 - (uint32_t)r) << 32) | i;
+    const bool in = i < n;
+    int64_t rows = 0;
+    if (in) {
+        const int64_t m = (int64_t)(qstart[h[i].qi + 1] - qstart[h[i].qi]);
+        rows = min(m, (int64_t)h[i].qe + w) - max((int64_t)0, (int64_t)h[i].qs - w);
+        const int64_t r = rows < 0 ? 0 : (rows > 65535 ? 65535 : rows);
+        keys[i] = ((uint64_t)(65535 - (uint32_t)r) << 32) | i;
+    }
+    const uint32_t lng = __ballot_sync(0xffffffffu, in && rows >= (int64_t)min(long_rows, 65535u));
+    if ((threadIdx.x & 31) == 0 && lng) atomicAdd(n_long, (uint32_t)__popc(lng));
 }
 
 // Strip length of each HSP's band (B + 1), and the band area (DP-window rows x B, the
@@ -2360,8 +2576,15 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         GN_CUDA(cudaStreamSynchronize(s));
         SwCell *strips = arena.alloc_n<SwCell>(cells);
         uint64_t *okeys = arena.alloc_n<uint64_t>(n_sel), *okeys_alt = arena.alloc_n<uint64_t>(n_sel);
+        // alignments of at least sw_long rows go to the wavefront path (their rows would
+        // bound the kernel's time on the grouped path)
+        uint32_t sw_long = 768;
+        if (const char *e = getenv("GN_SW_LONG_ROWS")) sw_long = (uint32_t)std::max(1l, strtol(e, nullptr, 10));
+        uint32_t *n_long = arena.alloc_n<uint32_t>(2);
+        GN_CUDA(cudaMemsetAsync(n_long, 0, 8, s));
         GN_LAUNCH("k_sw_order_keys", n_sel, s,
-                  k_sw_order_keys<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, okeys));
+                  k_sw_order_keys<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, sw_long,
+                                                                    okeys, n_long));
         void *rs = arena.alloc(radix_scratch_bytes(n_sel));
         const uint64_t *order = radix_sort(okeys, okeys_alt, nullptr, nullptr, n_sel, 32, 48, rs, s, TAG_RECORD_SORT)
                                     ? okeys_alt : okeys;
@@ -2373,7 +2596,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                                             ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
                                                             sc.mismatch, sc.gap_open, sc.gap_extend,
                                                             (int32_t)p.band_w, counter, order, wide, counter + 1,
-                                                            aln, status));
+                                                            n_long, n_long + 1, aln, status));
         GN_LAUNCH("k_banded_sw_wide", area[1], s,
                   k_banded_sw_wide<<<num_sms() * 4, 128, 0, s>>>(sel, wide, counter + 1, counter + 2, soff, strips, qp.pk,
                                                                 qp.nb, qstart_d, ix->bank.pk, ix->bank.nb,

@@ -238,7 +238,8 @@ def test_chunked_equals_unchunked(gn, mid_small, monkeypatch):
 @pytest.mark.parametrize("env", [{"GN_HIT_GROUPING": "sort"}, {"GN_BUCKET_CAP": "64"}, {"GN_TILE_FILTER": "0"},
                                  {"GN_RANK_PATH": "sort"}, {"GN_TILE_POS": "64"}, {"GN_SELECT_PATH": "sort"},
                                  {"GN_BUCKET_CAP": "64", "GN_MAX_CHUNK_HITS": "30000"},
-                                 {"GN_BUCKET_CAP": "64", "GN_SPILL_ROOM": "16"}])
+                                 {"GN_BUCKET_CAP": "64", "GN_SPILL_ROOM": "16"}, {"GN_SW_LONG_ROWS": "1"},
+                                 {"GN_SW_LONG_ROWS": "100"}])
 def test_hit_grouping_paths_agree_with_oracle(gn, mid_small, monkeypatch, env):
     """The global sort path, the bucketed path and its overflow fallback give the oracle's HSPs."""
     bank, qs, ix, ox = mid_small
@@ -337,3 +338,15 @@ def test_sensitivity_recovery_matches_oracle(gn, mid_small, kw):
     ref = [r.ranked for r in ox.search(qs, oracle.Params(**kw), threads=os.cpu_count() or 1)]
     got, exp = recovery_table(qs.meta, res), recovery_table(qs.meta, ref)
     assert got == exp and got["planted"] == qs.n and got["found"] > qs.n // 2
+
+
+@pytest.mark.parametrize("band_w", [0, 1, 16, 20, 24])
+def test_wavefront_alignment_path(gn, mid_small, band_w, monkeypatch):
+    """Every alignment through the anti-diagonal path (bands up to 64 diagonals) gives the oracle's."""
+    bank, qs, ix, ox = mid_small
+    monkeypatch.setenv("GN_SW_LONG_ROWS", "1")
+    sub = qs.subset(range(0, qs.n, 2))
+    res = gn.search(ix, sub.start, sub.bases, params=gn.make_params(band_w=band_w))
+    ref = ox.search(sub, oracle.Params(band_w=band_w), threads=os.cpu_count() or 1)
+    for i in range(sub.n):
+        assert_ranked_equal(res.query(i), ref[i].ranked, f"band {band_w} query {i}")
