@@ -1334,6 +1334,28 @@ struct SegWin {
     }
 };
 
+// Codes of the bases at offsets o, o + 1, ... of a window from the top of a 64-bit
+// word (2 bits each; -31 <= o < 64, offsets outside the window read as 0), and their
+// non-base bits from bit 0.
+__device__ __forceinline__ uint64_t segwin_codes(const SegWin &wn, int32_t o) {
+    if (o < 0) return wn.hi >> (2 * -o);
+    if (o == 0) return wn.hi;
+    if (o < 32) return (wn.hi << (2 * o)) | (wn.lo >> (64 - 2 * o));
+    return wn.lo << (2 * (o - 32));
+}
+__device__ __forceinline__ uint32_t segwin_bad(const SegWin &wn, int32_t o) {
+    return o < 0 ? (uint32_t)(wn.bad << -o) : (uint32_t)(wn.bad >> o);
+}
+
+// Code of the base at offset o (0 <= o < 64) of a window, 4 for a non-base.
+__device__ __forceinline__ uint32_t segwin_code(const SegWin &wn, uint32_t o) {
+    const uint32_t word = o < 32 ? (o < 16 ? (uint32_t)(wn.hi >> 32) : (uint32_t)wn.hi)
+                                 : (o < 48 ? (uint32_t)(wn.lo >> 32) : (uint32_t)wn.lo);
+    const uint32_t c = (word >> (30 - 2 * (o & 15))) & 3u;
+    const uint32_t badw = o < 32 ? (uint32_t)wn.bad : (uint32_t)(wn.bad >> 32);
+    return ((badw >> (o & 31)) & 1u) ? 4u : c;
+}
+
 // 32 / G HSPs per warp: segment s (lanes sG .. sG + G - 1) aligns its own HSP, lane l of
 // the segment owns band offsets K l .. K l + K - 1 and keeps their previous-row states
 // in registers.  All segments step through rows together.  The vertical-gap input of
@@ -1410,6 +1432,14 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
             const uint64_t jfirst = jb + (uint64_t)max(0, blo - b0), jlast = jb + (uint64_t)min(K - 1, bhi - b0);
             if (jfirst < wd.p0 || jlast >= wd.p0 + 32) wd.load(bpk, bnb, jfirst);
         }
+        // the lane's K bank bases (window offsets o0 .. o0 + K - 1; o0 >= -(K - 1))
+        uint64_t dcodes = 0;
+        uint32_t dbad = 0;
+        if (SEG && lane_on) {
+            const int32_t o0 = (int32_t)((int64_t)jb - (int64_t)sd.p0);
+            dcodes = segwin_codes(sd, o0);
+            dbad = segwin_bad(sd, o0);
+        }
         int32_t H0[K], E[K], X[K];
         uint32_t C[K], SE[K];
 #pragma unroll
@@ -1428,7 +1458,9 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
             const bool okd = act && prow && b >= pblo && b <= pbhi;
             const int32_t Hd = okd ? pH[k] : 0;
             const uint32_t SD = (Hd > 0) ? pSH[k] : ((uint32_t)r << 16) | (uint32_t)b;
-            const uint32_t d = act ? (SEG ? sd.at(jb + k) : wd.at(jb + k)) : 4u;
+            const uint32_t d = act ? (SEG ? (((dbad >> k) & 1u) ? 4u : (uint32_t)(dcodes >> (62 - 2 * k)) & 3u)
+                                          : wd.at(jb + k))
+                                   : 4u;
             const int32_t Dg = Hd + dev_pair(qc, d, match, mismatch);
             int32_t cv;
             if (Dg >= E[k]) { cv = Dg; C[k] = SD; } else { cv = E[k]; C[k] = SE[k]; }
@@ -1512,80 +1544,100 @@ __device__ __forceinline__ void sw_wave(const DevHsp &h, const uint32_t *__restr
     const int64_t J0 = max((int64_t)0, (int64_t)h.ds - w), J1 = min(L, (int64_t)h.de + w);
     const int32_t rows = (int32_t)max(I1 - I0, (int64_t)0);
     const int32_t jlo = (int32_t)(J0 - I0 - dlo), jhi = (int32_t)(J1 - 1 - I0 - dlo);
-    auto valid = [&](int32_t r, int32_t b) {
-        return r >= 0 && r < rows && b >= 0 && b < B && b >= jlo - r && b <= jhi - r;
-    };
+    // rows r where offset e is a cell of the window: max(0, jlo - e) <= r <= min(rows - 1, jhi - e)
+    const int32_t b0 = 2 * lane, b1 = 2 * lane + 1;
+    auto lo_of = [&](int32_t e) { return (e >= 0 && e < B) ? max(0, jlo - e) : INT32_MAX; };
+    auto hi_of = [&](int32_t e) { return (e >= 0 && e < B) ? min(rows - 1, jhi - e) : -1; };
+    const int32_t lo_m = lo_of(b0 - 1), hi_m = hi_of(b0 - 1), lo_0 = lo_of(b0), hi_0 = hi_of(b0);
+    const int32_t lo_1 = lo_of(b1), hi_1 = hi_of(b1), lo_2 = lo_of(b1 + 1), hi_2 = hi_of(b1 + 1);
     WaveCell c0, c1;  // the lane's last cells at offsets 2l and 2l + 1
     c0.H = c1.H = 0; c0.E = c1.E = SW_NEG; c0.H0 = c1.H0 = 0; c0.F = c1.F = SW_NEG;
     c0.SH = c1.SH = c0.SE = c1.SE = c0.C = c1.C = c0.SF = c1.SF = 0;
+    bool v0 = false, v1 = false;  // cells (r - 1, 2l) and (r - 1, 2l + 1) were in the window
     int32_t best = 0, br = INT32_MAX, bb = INT32_MAX;
     uint32_t bs = 0;
     SegWin sq, sd;
     sq.init(qpk, qnb, qb + (uint64_t)I0, qend);
     sd.init(bpk, bnb, sb + (uint64_t)max(I0 + dlo, J0), send);
-    // one cell: left, up-right and diagonal inputs (valid or not), the bases, the cell
-    auto step = [&](int32_t r, int32_t b, const WaveCell &lf, const WaveCell &ur, const WaveCell &dg, WaveCell &out) {
-        const bool cv = valid(r, b);
-        int32_t E = SW_NEG;
-        uint32_t SE = 0;
-        if (cv && valid(r - 1, b + 1)) {
-            const int32_t eo = ur.H + goe, ee = ur.E + ge;
-            if (eo >= ee) { E = eo; SE = ur.SH; } else { E = ee; SE = ur.SE; }
-        }
-        const int32_t Hd = (cv && valid(r - 1, b)) ? dg.H : 0;
-        const uint32_t SD = Hd > 0 ? dg.SH : (uint32_t)r * (uint32_t)B + (uint32_t)b;
-        int32_t sc = mismatch;
-        if (cv) {
-            const uint64_t i = qb + (uint64_t)(I0 + r), j = sb + (uint64_t)(I0 + r + dlo + b);
-            sc = dev_pair(sq.at(i), sd.at(j), match, mismatch);
-        }
-        const int32_t Dg = Hd + sc;
-        int32_t cand;
-        uint32_t C;
-        if (Dg >= E) { cand = Dg; C = SD; } else { cand = E; C = SE; }
-        const int32_t H0 = cand > 0 ? cand : 0;
-        int32_t F = SW_NEG;
-        uint32_t SF = 0;
-        if (cv && valid(r, b - 1)) {
-            const int32_t fo = lf.H0 + goe, fe = lf.F + ge;
-            if (fo >= fe) { F = fo; SF = lf.C; } else { F = fe; SF = lf.SF; }
-        }
-        int32_t H;
-        uint32_t SH;
-        if (H0 >= F) { H = H0; SH = C; } else { H = F; SH = SF; }
-        if (cv && H > 0 && (H > best || (H == best && (r < br || (r == br && b < bb))))) {
-            best = H; br = r; bb = b; bs = SH;
-        }
-        out.H = H; out.E = E; out.H0 = H0; out.F = F; out.SH = SH; out.SE = SE; out.C = C; out.SF = SF;
-    };
+    // window offsets of this lane's bases at iteration k = t / 2 (row r = k - l): query
+    // base I0 + r, bank base I0 + dlo + r + 2l (offset 2l; 2l + 1 is the next one)
+    int32_t oq = (int32_t)((int64_t)(qb + (uint64_t)I0) - (int64_t)sq.p0) - lane;
+    int32_t od = (int32_t)((int64_t)sb + I0 + dlo - (int64_t)sd.p0) + lane;
+    int32_t qmax = (int32_t)((int64_t)(qb + (uint64_t)I0) - (int64_t)sq.p0);  // lane 0's query offset
+    // last bank offset the wavefront pair t, t + 1 reads: I0 + dlo + (t + B) / 2, at most J1 - 1
+    const int64_t dmax0 = (int64_t)sb + I0 + dlo - (int64_t)sd.p0;
+    const int64_t dcap = (int64_t)sb + J1 - 1 - (int64_t)sd.p0;
+    int32_t dshift = 0;  // 16 x the bank window's advances
+    uint32_t rB = (uint32_t)(-lane) * (uint32_t)B;  // r * B (start cells)
     const int32_t T = rows > 0 ? 2 * rows + B - 2 : 0;  // wavefronts 0 .. T - 1
-    const int32_t b0 = 2 * lane, b1 = 2 * lane + 1;
-    for (int32_t t = 0; t < T; t += 2) {
-        // windows: query rows up to t / 2, bank positions up to offset B - 1 of wavefront t + 1
-        if (qb + (uint64_t)(I0 + t / 2) >= sq.p0 + 64) sq.advance(qpk, qnb, qend);
-        const uint64_t jmax = sb + (uint64_t)min(I0 + dlo + (int64_t)((t + B) / 2), J1 - 1);
-        if (jmax >= sd.p0 + 64) sd.advance(bpk, bnb, send);
-        // even wavefront t: offset 2l; left is lane l - 1's offset 2l - 1 (from wavefront t - 1)
+    for (int32_t t = 0, r = -lane; t < T; t += 2, ++r, ++oq, ++od, ++qmax, rB += (uint32_t)B) {
+        if (qmax >= 64) { sq.advance(qpk, qnb, qend); oq -= 16; qmax -= 16; }
+        if (min(dmax0 + (t + B) / 2, dcap) - dshift >= 64) { sd.advance(bpk, bnb, send); od -= 16; dshift += 16; }
+        const uint32_t qc = (r >= 0 && r < rows) ? segwin_code(sq, (uint32_t)oq) : 4u;
+        // even wavefront t: cell (r, 2l); left (r, 2l - 1) is lane l - 1's, from wavefront t - 1
         {
-            WaveCell lf;
-            lf.H0 = __shfl_up_sync(0xffffffffu, c1.H0, 1);
-            lf.F = __shfl_up_sync(0xffffffffu, c1.F, 1);
-            lf.C = __shfl_up_sync(0xffffffffu, c1.C, 1);
-            lf.SF = __shfl_up_sync(0xffffffffu, c1.SF, 1);
-            WaveCell nc;
-            step((t - b0) >> 1, b0, lf, c1, c0, nc);  // up-right: own offset 2l + 1; diagonal: own 2l
-            c0 = nc;
+            const int32_t lH0 = __shfl_up_sync(0xffffffffu, c1.H0, 1), lF = __shfl_up_sync(0xffffffffu, c1.F, 1);
+            const uint32_t lC = __shfl_up_sync(0xffffffffu, c1.C, 1), lSF = __shfl_up_sync(0xffffffffu, c1.SF, 1);
+            const bool cv = r >= lo_0 && r <= hi_0;
+            int32_t E = SW_NEG;
+            uint32_t SE = 0;
+            if (cv && v1) {  // up-right (r - 1, 2l + 1): own, from wavefront t - 1
+                const int32_t eo = c1.H + goe, ee = c1.E + ge;
+                if (eo >= ee) { E = eo; SE = c1.SH; } else { E = ee; SE = c1.SE; }
+            }
+            const int32_t Hd = (cv && v0) ? c0.H : 0;
+            const uint32_t SD = Hd > 0 ? c0.SH : rB + (uint32_t)b0;
+            const int32_t sc = cv ? dev_pair(qc, segwin_code(sd, (uint32_t)od), match, mismatch) : mismatch;
+            const int32_t Dg = Hd + sc;
+            int32_t cand;
+            uint32_t C;
+            if (Dg >= E) { cand = Dg; C = SD; } else { cand = E; C = SE; }
+            const int32_t H0 = cand > 0 ? cand : 0;
+            int32_t F = SW_NEG;
+            uint32_t SF = 0;
+            if (cv && r >= lo_m && r <= hi_m) {
+                const int32_t fo = lH0 + goe, fe = lF + ge;
+                if (fo >= fe) { F = fo; SF = lC; } else { F = fe; SF = lSF; }
+            }
+            int32_t H;
+            uint32_t SH;
+            if (H0 >= F) { H = H0; SH = C; } else { H = F; SH = SF; }
+            // cells of one lane come in row-major order: the first maximum wins
+            if (cv && H > best) { best = H; br = r; bb = b0; bs = SH; }
+            c0.H = H; c0.E = E; c0.H0 = H0; c0.F = F; c0.SH = SH; c0.SE = SE; c0.C = C; c0.SF = SF;
+            v0 = cv;
         }
-        // odd wavefront t + 1: offset 2l + 1; up-right is lane l + 1's offset 2l + 2 (wavefront t)
+        // odd wavefront t + 1: cell (r, 2l + 1); up-right (r - 1, 2l + 2) is lane l + 1's, from wavefront t
         {
-            WaveCell ur;
-            ur.H = __shfl_down_sync(0xffffffffu, c0.H, 1);
-            ur.E = __shfl_down_sync(0xffffffffu, c0.E, 1);
-            ur.SH = __shfl_down_sync(0xffffffffu, c0.SH, 1);
-            ur.SE = __shfl_down_sync(0xffffffffu, c0.SE, 1);
-            WaveCell nc;
-            step((t + 1 - b1) >> 1, b1, c0, ur, c1, nc);  // left: own offset 2l (this row)
-            c1 = nc;
+            const int32_t uH = __shfl_down_sync(0xffffffffu, c0.H, 1), uE = __shfl_down_sync(0xffffffffu, c0.E, 1);
+            const uint32_t uSH = __shfl_down_sync(0xffffffffu, c0.SH, 1), uSE = __shfl_down_sync(0xffffffffu, c0.SE, 1);
+            const bool cv = r >= lo_1 && r <= hi_1;
+            int32_t E = SW_NEG;
+            uint32_t SE = 0;
+            if (cv && r - 1 >= lo_2 && r - 1 <= hi_2) {
+                const int32_t eo = uH + goe, ee = uE + ge;
+                if (eo >= ee) { E = eo; SE = uSH; } else { E = ee; SE = uSE; }
+            }
+            const int32_t Hd = (cv && v1) ? c1.H : 0;
+            const uint32_t SD = Hd > 0 ? c1.SH : rB + (uint32_t)b1;
+            const int32_t sc = cv ? dev_pair(qc, segwin_code(sd, (uint32_t)od + 1u), match, mismatch) : mismatch;
+            const int32_t Dg = Hd + sc;
+            int32_t cand;
+            uint32_t C;
+            if (Dg >= E) { cand = Dg; C = SD; } else { cand = E; C = SE; }
+            const int32_t H0 = cand > 0 ? cand : 0;
+            int32_t F = SW_NEG;
+            uint32_t SF = 0;
+            if (cv && v0) {  // left (r, 2l): own, just computed
+                const int32_t fo = c0.H0 + goe, fe = c0.F + ge;
+                if (fo >= fe) { F = fo; SF = c0.C; } else { F = fe; SF = c0.SF; }
+            }
+            int32_t H;
+            uint32_t SH;
+            if (H0 >= F) { H = H0; SH = C; } else { H = F; SH = SF; }
+            if (cv && H > best) { best = H; br = r; bb = b1; bs = SH; }
+            c1.H = H; c1.E = E; c1.H0 = H0; c1.F = F; c1.SH = SH; c1.SE = SE; c1.C = C; c1.SF = SF;
+            v1 = cv;
         }
     }
     // highest score, then smallest row, then smallest offset
@@ -2578,7 +2630,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         uint64_t *okeys = arena.alloc_n<uint64_t>(n_sel), *okeys_alt = arena.alloc_n<uint64_t>(n_sel);
         // alignments of at least sw_long rows go to the wavefront path (their rows would
         // bound the kernel's time on the grouped path)
-        uint32_t sw_long = 768;
+        uint32_t sw_long = 512;
         if (const char *e = getenv("GN_SW_LONG_ROWS")) sw_long = (uint32_t)std::max(1l, strtol(e, nullptr, 10));
         uint32_t *n_long = arena.alloc_n<uint32_t>(2);
         GN_CUDA(cudaMemsetAsync(n_long, 0, 8, s));
