@@ -169,9 +169,13 @@ def measured_peaks() -> dict:
 
 
 def csrc_digest() -> str:
+    """Digest of the device-code sources (every csrc file but the host-only C ABI file,
+    which holds no kernel): committed ncu traffic counts are valid while it is unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1507_02987_gb300", "csrc")
     for f in sorted(os.listdir(d)):
+        if f == "gn_abi.cu":
+            continue
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -243,6 +247,7 @@ def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
     srv = gn.Server(ix, budget)
     n = len(reqs)
     done_at = {}
+    held = []  # results are freed after the run: the collector does as little as it can
 
     def collector():
         end = time.perf_counter() + timeout_s
@@ -250,9 +255,8 @@ def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
             got = srv.poll_any(200)
             if got is None:
                 continue
-            t, res = got
-            done_at[t] = time.perf_counter()
-            res.close()
+            done_at[got[0]] = time.perf_counter()
+            held.append(got[1])
 
     th = threading.Thread(target=collector, daemon=True)
     th.start()
@@ -263,14 +267,18 @@ def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
         if wait > 0:
             time.sleep(wait)
         tickets.append(srv.submit(reqs[i]))
+    submit_s = time.perf_counter() - t0
     th.join(timeout_s)
+    for res in held:
+        res.close()
     stats = srv.stats()
     srv.stop()
     lat = [1e3 * (done_at[t] - (t0 + float(arrivals[i]))) for i, t in enumerate(tickets) if t in done_at]
     wall = (max(done_at.values()) - t0) if done_at else float("nan")
     return {"requests": n, "completed": len(lat), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
             "kbp_s": sum(len(r) for r in reqs) / 1e3 / wall, "batches": stats["batches"],
-            "max_batch": stats["max_batch"], "max_concurrent_batches": stats["max_concurrent"]}
+            "max_batch": stats["max_batch"], "max_concurrent_batches": stats["max_concurrent"],
+            "submit_ms": 1e3 * submit_s}
 
 
 def plain_leg(gn, ix, reqs, arrivals, stream):

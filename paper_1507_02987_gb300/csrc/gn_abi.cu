@@ -117,16 +117,29 @@ static uint64_t footprint_of(const gn_server *sv, const char *bases, uint32_t le
     const int span = sv->ix->span;
     const uint32_t keep = sv->ix->keep;
     uint64_t hits = 0;
-    for (uint32_t q = 0; q + (uint32_t)span <= len; ++q) {
+    if (keep == (span >= 32 ? 0xFFFFFFFFu : (1u << span) - 1u)) {
+        // contiguous seeds: rolling code, and the offset of the last non-base
+        const uint32_t mask = span >= 16 ? 0xFFFFFFFFu : (1u << (2 * span)) - 1u;
         uint32_t code = 0;
-        bool ok = true;
-        for (int p = 0; p < span && ok; ++p) {
-            if (!((keep >> p) & 1u)) continue;
-            const int b = host_base(bases[q + p]);
-            if (b < 0) ok = false;
-            else code = (code << 2) | (uint32_t)b;
+        int64_t last_bad = -1;
+        for (uint32_t x = 0; x < len; ++x) {
+            const int b = host_base(bases[x]);
+            if (b < 0) last_bad = x;
+            code = ((code << 2) | (uint32_t)(b < 0 ? 0 : b)) & mask;
+            if (x + 1 >= (uint32_t)span && last_bad < (int64_t)(x + 1 - span)) hits += sv->off_h[code + 1] - sv->off_h[code];
         }
-        if (ok) hits += sv->off_h[code + 1] - sv->off_h[code];
+    } else {
+        for (uint32_t q = 0; q + (uint32_t)span <= len; ++q) {
+            uint32_t code = 0;
+            bool ok = true;
+            for (int p = 0; p < span && ok; ++p) {
+                if (!((keep >> p) & 1u)) continue;
+                const int b = host_base(bases[q + p]);
+                if (b < 0) ok = false;
+                else code = (code << 2) | (uint32_t)b;
+            }
+            if (ok) hits += sv->off_h[code + 1] - sv->off_h[code];
+        }
     }
     const uint64_t n_sel = sv->opt.p.max_alignments ? sv->opt.p.max_alignments : 4096;
     return hits * HIT_BYTES + (uint64_t)len * 64 + 2 * 1024 * 8 + n_sel * (64 + 16 * (2ull * sv->opt.p.band_w + 2));
