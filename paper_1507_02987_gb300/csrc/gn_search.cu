@@ -2525,7 +2525,11 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
 
     // a9: extension
     if (n_hsp) {
-        const uint64_t xwarps = std::min<uint64_t>(n_hsp, (uint64_t)num_sms() * 64);
+        // resident warps only: each walks a fixed stride of the HSPs, so warps that would wait
+        // for a second wave would finish late
+        int xocc = 0;
+        GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xocc, k_xdrop, 256, 0));
+        const uint64_t xwarps = std::min<uint64_t>(n_hsp, (uint64_t)num_sms() * std::max(xocc, 1) * 8);
         GN_LAUNCH("k_xdrop", n_hsp, s,
                   k_xdrop<<<blocks_for(xwarps * 32, 256), 256, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d,
                                                                       ix->bank.pk, ix->bank.nb, ix->seq_start_d,
@@ -2543,9 +2547,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     DevHsp *merged = arena.alloc_n<DevHsp>(n_hsp);
     if (n_hsp) {
         uint32_t *perm = arena.alloc_n<uint32_t>(n_hsp);
+        // (qi, seq, qs, ds, qe, de) order: de = ds + qe - qs for the ungapped HSPs, so it is not keyed
         sort_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, n_hsp,
                      {{W_QI, qib, false}, {W_SEQ, seqb, false}, {W_QS, qposb, false}, {W_DS, posb, false},
-                      {W_QE, qposb, false}, {W_DE, posb, false}},
+                      {W_QE, qposb, false}},
                      perm, arena, s);
         DevHsp *srt = arena.alloc_n<DevHsp>(n_hsp);
         gather_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, perm, n_hsp,
