@@ -3,12 +3,13 @@ the console with the results written out), over the C ABI.
 
     python -m paper_1507_02987_gb300 format BANK.fa BANK.gnb
     python -m paper_1507_02987_gb300 index BANK.gnb BANK.gnx [--k 11] [--stride 11] [--mask M]
+    python -m paper_1507_02987_gb300 serve BANK.gnb [--index BANK.gnx] [--port 8080] [--budget-gib 16]
     python -m paper_1507_02987_gb300 search BANK.gnb QUERIES.fa [--index BANK.gnx | --k/--stride/--mask]
                                          [--out FILE] [--format tsv|xml] [--both-strands]
                                          [--max-alignments N] [--max-evalue E] [--band-w W] ...
 
-``format`` runs on the host. ``index`` and ``search`` need the CUDA library and a
-GPU; there is no CPU fallback. ``search`` sends the queries in calls of at most
+``format`` runs on the host. ``index``, ``search`` and ``serve`` (the HTTP service
+of ``service.py``) need the CUDA library and a GPU; there is no CPU fallback. ``search`` sends the queries in calls of at most
 ``--batch`` queries and writes one line (tsv) or element (xml) per alignment in
 rank order: query name, strand, bank sequence name, score, bit score, e-value and
 1-based inclusive ranges (on the reverse complement of the query for the minus
@@ -96,11 +97,16 @@ def main(argv=None, gn=None) -> int:
     f = sub.add_parser("format", help="FASTA bank -> formatted bank file")
     f.add_argument("fasta")
     f.add_argument("out")
-    for name in ("index", "search"):
+    for name in ("index", "search", "serve"):
         p = sub.add_parser(name)
         p.add_argument("bank", help="formatted bank file")
         if name == "index":
             p.add_argument("out", help="index file to write")
+        elif name == "serve":
+            p.add_argument("--index", help="a saved index of this bank (else one is built)")
+            p.add_argument("--host", default="127.0.0.1")
+            p.add_argument("--port", type=int, default=8080)
+            p.add_argument("--budget-gib", type=float, default=16.0, help="request loop memory budget")
         else:
             p.add_argument("queries", help="query FASTA")
             p.add_argument("--index", help="a saved index of this bank (else one is built)")
@@ -130,6 +136,25 @@ def main(argv=None, gn=None) -> int:
         ix = _build_index(gn, bankmod.BankFile(args.bank), args)
         ix.save(args.out)
         ix.close()
+        return 0
+    if args.cmd == "serve":
+        import os
+        import time
+
+        from . import service
+        bf = bankmod.BankFile(args.bank)
+        ix = gn.Index.load(args.index) if args.index else _build_index(gn, bf, args)
+        name = os.path.splitext(os.path.basename(args.bank))[0]
+        svc = service.BankService(gn, name, bf, int(args.budget_gib * 2**30), index=ix, k=args.k,
+                                  stride=args.stride, mask=args.mask)
+        httpd, _ = service.serve({name: svc}, args.host, args.port)
+        print(f"serving bank {name!r} on http://{args.host}:{httpd.server_address[1]}", file=sys.stderr)
+        try:
+            while True:
+                time.sleep(3600)
+        except KeyboardInterrupt:
+            httpd.shutdown()
+            svc.close()
         return 0
     text = run_search(gn, args)
     if args.out:

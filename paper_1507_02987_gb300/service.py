@@ -1,0 +1,121 @@
+"""HTTP service over the request loop: the paper's web services ("Interfaces": run
+queries, set parameters and list the banks from scripts), with the Python standard
+library only.
+
+    GET  /banks                   -> [{"name", "sequences", "bases", "k", "stride", "mask"}]
+    POST /search?bank=NAME
+         body: FASTA text, or JSON {"queries": [{"name", "sequence"}...]}
+                                -> {"bank", "queries": [{"name", "length",
+                                     "alignments": [{"rank", "subject", "subject_id", "score",
+                                                     "bits", "evalue", "q_start", "q_end",
+                                                     "s_start", "s_end"}]}]}
+
+Each bank has one request loop (``Server``: continuous batching over the resident
+index, admission by memory footprint); every query of a request is submitted to it
+and the results are collected by ticket, so concurrent requests share micro-batches.
+Search parameters are fixed per bank when the service starts (the request loop's
+parameters); queries are searched on the strand given (``gn_search`` with
+``GN_FLAG_BOTH_STRANDS``, or the command line's ``--both-strands``, searches both).
+Ranges are 0-based and end-exclusive, as in the library's results.
+"""
+from __future__ import annotations
+
+import json
+import threading
+from http.server import BaseHTTPRequestHandler, ThreadingHTTPServer
+from urllib.parse import parse_qs, urlparse
+
+from . import bank as bankmod
+
+
+class BankService:
+    """One served bank: its metadata, its index and its request loop."""
+
+    def __init__(self, gn, name, bank_file, mem_budget, index=None, k=11, stride=11, mask=None, params=None):
+        self.gn, self.name = gn, name
+        self.bf = bank_file if isinstance(bank_file, bankmod.BankFile) else bankmod.BankFile(bank_file)
+        if index is None:
+            start, bases = self.bf.arrays()
+            index = gn.Index(start, bases, k=k, stride=stride, mask=mask)
+        self.index = index
+        self.k, self.stride, self.mask = k, stride, mask
+        self.server = gn.Server(index, mem_budget, params=params)
+
+    def describe(self) -> dict:
+        return {"name": self.name, "sequences": self.bf.n_seqs, "bases": self.bf.n_bases, "k": self.k,
+                "stride": self.stride, "mask": self.mask}
+
+    def search(self, queries, timeout_ms=600000) -> dict:
+        """queries: [(name, sequence bytes)]; one result entry per query, in order."""
+        srv = self.server
+        jobs = [(name, seq, srv.submit(seq)) for name, seq in queries]
+        out = []
+        for name, seq, ticket in jobs:
+            res = srv.poll(ticket, timeout_ms)
+            if res is None:
+                raise TimeoutError(f"query {name} did not finish")
+            hits = res.query(0)
+            res.close()
+            out.append({"name": name, "length": len(seq), "alignments": [
+                {"rank": int(h["rank"]) + 1, "subject": self.bf.names[int(h["seq"])], "subject_id": int(h["seq"]),
+                 "score": int(h["score"]), "bits": float(h["bits"]), "evalue": float(h["evalue"]),
+                 "q_start": int(h["q_start"]), "q_end": int(h["q_end"]), "s_start": int(h["db_start"]),
+                 "s_end": int(h["db_end"])} for h in hits]})
+        return {"bank": self.name, "queries": out}
+
+    def close(self):
+        self.server.stop()
+
+
+def parse_queries(body: bytes, content_type: str):
+    """[(name, sequence)] from a FASTA body or a JSON {"queries": [...]} body."""
+    if content_type.startswith("application/json") or body.lstrip()[:1] == b"{":
+        doc = json.loads(body)
+        return [(str(q.get("name", f"q{i}")), str(q["sequence"]).encode()) for i, q in enumerate(doc["queries"])]
+    return [(r.name, r.sequence) for r in bankmod.read_fasta(body.decode("utf-8", "replace").splitlines())]
+
+
+def make_handler(banks: dict):
+    class Handler(BaseHTTPRequestHandler):
+        def _send(self, code, doc):
+            data = json.dumps(doc).encode()
+            self.send_response(code)
+            self.send_header("Content-Type", "application/json")
+            self.send_header("Content-Length", str(len(data)))
+            self.end_headers()
+            self.wfile.write(data)
+
+        def log_message(self, fmt, *args):  # quiet
+            pass
+
+        def do_GET(self):
+            if urlparse(self.path).path == "/banks":
+                return self._send(200, [b.describe() for b in banks.values()])
+            return self._send(404, {"error": "unknown path"})
+
+        def do_POST(self):
+            url = urlparse(self.path)
+            if url.path != "/search":
+                return self._send(404, {"error": "unknown path"})
+            qs = parse_qs(url.query)
+            name = qs.get("bank", [next(iter(banks), "")])[0]
+            if name not in banks:
+                return self._send(404, {"error": f"no bank {name!r}"})
+            try:
+                body = self.rfile.read(int(self.headers.get("Content-Length", "0")))
+                queries = parse_queries(body, self.headers.get("Content-Type", ""))
+                return self._send(200, banks[name].search(queries))
+            except (ValueError, KeyError, json.JSONDecodeError) as e:
+                return self._send(400, {"error": str(e)})
+            except Exception as e:  # a library error: the status and message of the call
+                return self._send(500, {"error": str(e)})
+
+    return Handler
+
+
+def serve(banks: dict, host="127.0.0.1", port=8080):
+    """Starts the HTTP service on a background thread; returns (server, thread). server.shutdown() stops it."""
+    httpd = ThreadingHTTPServer((host, port), make_handler(banks))
+    th = threading.Thread(target=httpd.serve_forever, daemon=True)
+    th.start()
+    return httpd, th
