@@ -3,8 +3,8 @@ queries, set parameters and list the banks from scripts), with the Python standa
 library only.
 
     GET  /banks                   -> [{"name", "sequences", "bases", "k", "stride", "mask"}]
-    POST /search?bank=NAME
-         body: FASTA text, or JSON {"queries": [{"name", "sequence"}...]}
+    POST /search?bank=NAME[&max_alignments=N&max_evalue=E&min_hsp_len=L&...]
+         body: FASTA text, or JSON {"queries": [{"name", "sequence"}...], "params": {...}}
                                 -> {"bank", "queries": [{"name", "length",
                                      "alignments": [{"rank", "subject", "subject_id", "score",
                                                      "bits", "evalue", "q_start", "q_end",
@@ -13,9 +13,12 @@ library only.
 Each bank has one request loop (``Server``: continuous batching over the resident
 index, admission by memory footprint); every query of a request is submitted to it
 and the results are collected by ticket, so concurrent requests share micro-batches.
-Search parameters are fixed per bank when the service starts (the request loop's
-parameters); queries are searched on the strand given (``gn_search`` with
-``GN_FLAG_BOTH_STRANDS``, or the command line's ``--both-strands``, searches both).
+Search parameters (``PARAMS``: hit distance, minimum HSP length, drop-off, number of
+alignments, band half-width, e-value cut) may be set per request, in the query
+string or the JSON body; each distinct set gets a request loop of its own, at most
+``max_param_sets`` per bank (each with the bank's memory budget). Queries are
+searched on the strand given (``gn_search`` with ``GN_FLAG_BOTH_STRANDS``, or the
+command line's ``--both-strands``, searches both).
 Ranges are 0-based and end-exclusive, as in the library's results.
 """
 from __future__ import annotations
@@ -28,10 +31,16 @@ from urllib.parse import parse_qs, urlparse
 from . import bank as bankmod
 
 
-class BankService:
-    """One served bank: its metadata, its index and its request loop."""
+# per-request search parameters: name -> type (defaults are the library's)
+PARAMS = {"max_hit_distance": int, "min_hsp_len": int, "xdrop": int, "max_alignments": int, "band_w": int,
+          "max_evalue": float}
 
-    def __init__(self, gn, name, bank_file, mem_budget, index=None, k=11, stride=11, mask=None, params=None):
+
+class BankService:
+    """One served bank: its metadata, its index and a request loop per parameter set."""
+
+    def __init__(self, gn, name, bank_file, mem_budget, index=None, k=11, stride=11, mask=None,
+                 max_param_sets=4):
         self.gn, self.name = gn, name
         self.bf = bank_file if isinstance(bank_file, bankmod.BankFile) else bankmod.BankFile(bank_file)
         if index is None:
@@ -39,15 +48,32 @@ class BankService:
             index = gn.Index(start, bases, k=k, stride=stride, mask=mask)
         self.index = index
         self.k, self.stride, self.mask = k, stride, mask
-        self.server = gn.Server(index, mem_budget, params=params)
+        self.mem_budget, self.max_param_sets = mem_budget, max_param_sets
+        self.servers = {(): gn.Server(index, mem_budget)}
+        self.lock = threading.Lock()
+
+    def server_for(self, params: dict):
+        """The request loop of a parameter set (created on first use)."""
+        unknown = set(params) - set(PARAMS)
+        if unknown:
+            raise ValueError(f"unknown parameters {sorted(unknown)}")
+        key = tuple(sorted((k, PARAMS[k](v)) for k, v in params.items()))
+        with self.lock:
+            srv = self.servers.get(key)
+            if srv is None:
+                if len(self.servers) >= self.max_param_sets:
+                    raise ValueError(f"at most {self.max_param_sets} parameter sets per bank")
+                srv = self.gn.Server(self.index, self.mem_budget, params=self.gn.make_params(**dict(key)))
+                self.servers[key] = srv
+            return srv
 
     def describe(self) -> dict:
         return {"name": self.name, "sequences": self.bf.n_seqs, "bases": self.bf.n_bases, "k": self.k,
                 "stride": self.stride, "mask": self.mask}
 
-    def search(self, queries, timeout_ms=600000) -> dict:
+    def search(self, queries, params=None, timeout_ms=600000) -> dict:
         """queries: [(name, sequence bytes)]; one result entry per query, in order."""
-        srv = self.server
+        srv = self.server_for(params or {})
         jobs = [(name, seq, srv.submit(seq)) for name, seq in queries]
         out = []
         for name, seq, ticket in jobs:
@@ -64,15 +90,17 @@ class BankService:
         return {"bank": self.name, "queries": out}
 
     def close(self):
-        self.server.stop()
+        for srv in self.servers.values():
+            srv.stop()
 
 
 def parse_queries(body: bytes, content_type: str):
-    """[(name, sequence)] from a FASTA body or a JSON {"queries": [...]} body."""
+    """([(name, sequence)], params) from a FASTA body or a JSON {"queries": [...], "params": {...}} body."""
     if content_type.startswith("application/json") or body.lstrip()[:1] == b"{":
         doc = json.loads(body)
-        return [(str(q.get("name", f"q{i}")), str(q["sequence"]).encode()) for i, q in enumerate(doc["queries"])]
-    return [(r.name, r.sequence) for r in bankmod.read_fasta(body.decode("utf-8", "replace").splitlines())]
+        qs = [(str(q.get("name", f"q{i}")), str(q["sequence"]).encode()) for i, q in enumerate(doc["queries"])]
+        return qs, dict(doc.get("params", {}))
+    return [(r.name, r.sequence) for r in bankmod.read_fasta(body.decode("utf-8", "replace").splitlines())], {}
 
 
 def make_handler(banks: dict):
@@ -103,8 +131,9 @@ def make_handler(banks: dict):
                 return self._send(404, {"error": f"no bank {name!r}"})
             try:
                 body = self.rfile.read(int(self.headers.get("Content-Length", "0")))
-                queries = parse_queries(body, self.headers.get("Content-Type", ""))
-                return self._send(200, banks[name].search(queries))
+                queries, params = parse_queries(body, self.headers.get("Content-Type", ""))
+                params.update({k: v[0] for k, v in qs.items() if k != "bank"})
+                return self._send(200, banks[name].search(queries, params))
             except (ValueError, KeyError, json.JSONDecodeError) as e:
                 return self._send(400, {"error": str(e)})
             except Exception as e:  # a library error: the status and message of the call

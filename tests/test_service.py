@@ -38,12 +38,17 @@ class OracleLoop:
             self.ox = oracle.Index(synth.Bank(np.asarray(start, np.uint64), np.asarray(bases, np.uint8),
                                               synth.BANKS["tiny"]), k=k, stride=stride, mask=mask)
 
+    @staticmethod
+    def make_params(**kw):
+        return kw
+
     class Server:
         def __init__(self, index, budget, params=None):
             self.index, self.done, self.lock, self.next = index, {}, threading.Lock(), 0
+            self.params = params or {}
 
         def submit(self, seq):
-            r = self.index.ox.search([bytes(seq)], oracle.Params())[0].ranked
+            r = self.index.ox.search([bytes(seq)], oracle.Params(**self.params))[0].ranked
             a = np.zeros(len(r), dtype=[("seq", "<u4"), ("q_start", "<u4"), ("q_end", "<u4"), ("db_start", "<u4"),
                                         ("db_end", "<u4"), ("score", "<i4"), ("rank", "<u4"), ("evalue", "<f8"),
                                         ("bits", "<f8")])
@@ -131,3 +136,25 @@ def test_concurrent_requests_and_errors(running):
         with pytest.raises(urllib.error.HTTPError) as e:
             _post(url + path, body, "text/plain")
         assert e.value.code == code
+
+
+def test_parameters_per_request(running):
+    b0, qs, url = running
+    fasta = "".join(f">q{i}\n{qs.query(i).decode()}\n" for i in range(qs.n)).encode()
+    doc = _post(url + "/search?max_alignments=2&xdrop=10", fasta, "text/plain")
+    ref = oracle.Index(b0).search(qs, oracle.Params(max_alignments=2, xdrop=10), threads=os.cpu_count() or 1)
+    for i, q in enumerate(doc["queries"]):
+        assert len(q["alignments"]) == len(ref[i].ranked) <= 2
+        assert [a["score"] for a in q["alignments"]] == [int(h["score"]) for h in ref[i].ranked]
+    body = json.dumps({"queries": [{"name": "a", "sequence": qs.query(0).decode()}],
+                       "params": {"max_alignments": 1}}).encode()
+    assert len(_post(url + "/search", body, "application/json")["queries"][0]["alignments"]) <= 1
+    for path in ("/search?no_such=1", "/search?max_alignments=x"):
+        with pytest.raises(urllib.error.HTTPError) as e:
+            _post(url + path, fasta, "text/plain")
+        assert e.value.code == 400
+    # the default set and three more fill the pool of four: a fifth set is refused
+    _post(url + "/search?max_alignments=3", fasta, "text/plain")
+    with pytest.raises(urllib.error.HTTPError) as e:
+        _post(url + "/search?max_alignments=4", fasta, "text/plain")
+    assert e.value.code == 400
