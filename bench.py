@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="large", choices=["tiny", "mid", "batched", "large"])
+    ap.add_argument("--workload", default="large", choices=["tiny", "mid", "batched", "large", "long"])
     ap.add_argument("--stride", type=int, default=11)
     ap.add_argument("--mask", default=None, help="spaced-seed mask, e.g. 111010010100110111 (k = its ones)")
     ap.add_argument("--autotune", action="store_true",
@@ -212,6 +212,7 @@ def workload(name: str, stride: int, rank: int, n_queries: int = 0):
         "mid": "mid bank (200,000 log-normal sequences, ~400 Mbp, GC 0.35-0.65, 20% repeats), 1,000 homolog queries 80-10,000 bp",
         "batched": "mid bank (~400 Mbp), 10,000 queries 50-5,000 bp, half planted homologs",
         "large": "large bank (2.5 M log-normal sequences, ~4.0 Gbp, GC 0.35-0.65, 20% repeats), 2,000 queries 200-20,000 bp, half planted homologs",
+        "long": "large bank (~4.0 Gbp), 40 queries 65,536 bp - 1 Mbp (searched in overlapping segments), half planted homologs",
     }[name]
     return bank, queries, f"{desc}; k=11, stride {stride}; one gn_search over all queries per step"
 

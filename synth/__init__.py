@@ -23,6 +23,10 @@ Recipes (one per workload; base seed 0x6E000000 + workload index):
              queries, log-uniform 200-20,000 bp, half planted homologs at 2-25 %.
 * serving  - the large bank; requests log-uniform 50-20,000 bp, 30 % homologs,
              open-loop Poisson arrivals.
+* long     - the large bank; 40 queries log-uniform 65,536 bp - 1 Mbp (the size
+             range of the paper's longest query sets), half planted homologs at
+             2-25 % divergence (a homolog is at most as long as the longest bank
+             sequence, 200,000 bp).
 """
 from __future__ import annotations
 
@@ -140,7 +144,7 @@ BANKS = {
     "large": BankSpec(BASE_SEED + 3, 2_500_000, 1, 1200.0, _SIGMA, 100, 200_000, 0.35, 0.65, 500, 300, 6000,
                       0.01, 0.10, 0.20),
 }
-BANK_OF = {"tiny": "tiny", "mid": "mid", "batched": "mid", "large": "large", "serving": "large"}
+BANK_OF = {"tiny": "tiny", "mid": "mid", "batched": "mid", "large": "large", "serving": "large", "long": "large"}
 
 QUERIES = {
     "tiny": QuerySpec(BASE_SEED + 0, 10, 0, 300, 1000, 1.0, p_sub=0.05, p_indel=0.01),
@@ -148,6 +152,7 @@ QUERIES = {
     "batched": QuerySpec(BASE_SEED + 2, 10_000, 1, 50, 5_000, 0.5, 0.0, 0.30),
     "large": QuerySpec(BASE_SEED + 3, 2000, 1, 200, 20_000, 0.5, 0.02, 0.25),
     "serving": QuerySpec(BASE_SEED + 4, 4000, 1, 50, 20_000, 0.3, 0.02, 0.25),
+    "long": QuerySpec(BASE_SEED + 5, 40, 1, 65_536, 1_000_000, 0.5, 0.02, 0.25),
 }
 
 

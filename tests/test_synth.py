@@ -40,3 +40,18 @@ def test_poisson_arrivals():
     t = synth.poisson_arrivals(200.0, 4000)
     gaps = np.diff(np.concatenate([[0.0], t]))
     assert (gaps > 0).all() and abs(gaps.mean() - 1 / 200.0) < 0.1 / 200.0
+
+
+def test_long_query_recipe():
+    """Random queries of the long recipe span 65,536 bp - 1 Mbp; planted homologs are clipped to the
+    longest bank sequence (here the tiny bank's)."""
+    bank = synth.make_bank("tiny")
+    qs = synth.make_queries("long", bank)
+    lens = np.diff(qs.start).astype(np.int64)
+    planted = qs.meta[:, 0] != 0
+    assert qs.n == 40 and 0 < planted.sum() < 40
+    assert ((lens[~planted] >= 65_536) & (lens[~planted] <= 1_000_000)).all()
+    longest = int(np.diff(bank.seq_start).max())
+    assert (qs.meta[planted, 3] <= longest).all()
+    again = synth.make_queries("long", bank)
+    assert np.array_equal(again.bases, qs.bases)
