@@ -70,7 +70,7 @@ def read_fasta(source):
     is an error (ValueError)."""
     if isinstance(source, (str, os.PathLike)):
         with open(source, "rb") as f:
-            yield from read_fasta(f)
+            yield from _read_fasta_bytes(f.read())
         return
     name = desc = None
     parts: list[bytes] = []
@@ -92,6 +92,40 @@ def read_fasta(source):
         parts.append(b"".join(line.split()))
     if name is not None:
         yield Record(name, desc, b"".join(parts))
+
+
+_WS = b" \t\r\n\v\f"
+
+
+def _read_fasta_bytes(data: bytes):
+    """read_fasta over a whole file's bytes: records split at header lines, whitespace
+    removed with byte operations (the same records as the line-by-line reader)."""
+    if b";" in data:  # comment lines: the line-by-line reader handles them
+        yield from read_fasta(data.splitlines(keepends=True))
+        return
+    n = len(data)
+    # the first header line; text before it must be whitespace only
+    if data.startswith(b">"):
+        pos = 0
+    else:
+        nl = data.find(b"\n>")
+        if nl < 0:
+            if data.translate(None, _WS):
+                raise ValueError("FASTA sequence text before the first header")
+            return
+        pos = nl + 1
+        if data[:pos].translate(None, _WS):
+            raise ValueError("FASTA sequence text before the first header")
+    while pos < n:
+        eol = data.find(b"\n", pos)
+        eol = n if eol < 0 else eol
+        head = data[pos + 1:eol].strip().split(None, 1)
+        nxt = data.find(b"\n>", eol)
+        end = n if nxt < 0 else nxt + 1
+        name = head[0].decode("utf-8", "replace") if head else ""
+        desc = head[1].decode("utf-8", "replace") if len(head) > 1 else ""
+        yield Record(name, desc, data[eol:end].translate(None, _WS))
+        pos = end
 
 
 def _nonbase_runs(codes: np.ndarray) -> np.ndarray:

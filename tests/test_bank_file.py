@@ -98,3 +98,31 @@ def test_search_over_decoded_bank_equals_original(tmp_path):
     assert sum(len(r.ranked) for r in r1) > 0
     for a, b in zip(r1, r2):
         assert np.array_equal(a.ranked, b.ranked)
+
+
+def test_file_reader_equals_line_reader(tmp_path):
+    """FASTA files are read as whole bytes; the records equal those of the line-by-line reader."""
+    rng = random.Random(17)
+    p = tmp_path / "x.fa"
+    for trial in range(300):
+        parts = []
+        if rng.random() < 0.3:
+            parts.append(rng.choice(["\n", "  \n", "\r\n", "ACG\n"]))
+        for r in range(rng.randint(0, 5)):
+            parts.append(">" + rng.choice(["", " ", "name", "n1 desc here", "  spaced  name  x ", "a>b"]) + "\n")
+            for line in range(rng.randint(0, 4)):
+                parts.append("".join(rng.choice("ACGTacgtN \t>") for _ in range(rng.randint(0, 20)))
+                             + rng.choice(["\n", "\r\n"]))
+        text = "".join(parts)
+        if rng.random() < 0.2:
+            text = text.rstrip("\n")
+        p.write_text(text)
+        try:
+            by_line = list(bank.read_fasta(text.splitlines(keepends=True)))
+        except ValueError:
+            by_line = "error"
+        try:
+            whole = list(bank.read_fasta(p))
+        except ValueError:
+            whole = "error"
+        assert by_line == whole, repr(text)
