@@ -269,6 +269,42 @@ def test_sw_hand_cases():
     assert oracle.banded_sw("ACG", "ACGTTTTTACG", (0, 3, 0, 11), wide) == (3, 0, 3, 0, 3)
 
 
+def test_sw_start_tie_rules_hand_cases():
+    """Where two alignments of equal score meet in one cell, the reading's tie order decides
+    which start is reported: H takes the diagonal over E over F, and E and F take a gap opened
+    from H over one extended.  Each pair below has two best alignments with different starts
+    that merge at a single tie of one kind; the expected start is the one the rule picks.
+    Cells are (query row i, bank column j), 0-based; scores +1/-3, a gap of g costs 5 + 2g."""
+    wide = oracle.Params(band_w=64)
+
+    # Diagonal over E.  b is a with one of the two Cs at a[7:9] deleted.  Alignment 1 starts at
+    # (0,0): a[0:8] = b[0:8] (8), a[8] against a gap (-7), a[9:17] = b[8:16] (8): 9.
+    # Alignment 2 starts at (8,7): a[8:17] = b[7:16] (9 matches): 9.  At cell (8,7) the fresh
+    # diagonal step C/C (0 + 1) ties with E = H(7,7) - 7 = 8 - 7 = 1; the diagonal wins.
+    a, b = "ATAGTTACCGATCAATT", "ATAGTTACGATCAATT"
+    assert oracle.banded_sw(a, b, _full_box(a, b), wide) == (9, 8, 17, 7, 16)
+
+    # E over F.  a = (CA)^5 + s, b = (AC)^5 + s with s = ACTCGCACC.  On diagonal +1,
+    # a[0:9] = b[1:10] (9 matches from (0,1)); on diagonal -1, a[1:10] = b[0:9] (9 matches
+    # from (1,0)).  At cell (9,9) the vertical gap after the first, E = 9 - 7 = 2, ties with
+    # the horizontal gap after the second, F = 9 - 7 = 2, and the diagonal step is below them
+    # (H(8,8) = 1, A/C: -2).  Both continue over s on diagonal 0: 2 + 9 = 11.  E wins: (0,1).
+    a, b = "CACACACACAACTCGCACC", "ACACACACACACTCGCACC"
+    assert oracle.banded_sw(a, b, _full_box(a, b), wide) == (11, 0, 19, 1, 19)
+
+    # E: open over extend.  a = (AC)^6 + CCA + s, b = (AC)^6 + s, s = GATGTTAGATAA (12).
+    # Alignment 1 from (0,0): (AC)^6 on both (12), a[12:15] against a gap of 3 (-11), s (12): 13.
+    # Alignment 2 from (2,0): a[2:12] = b[0:10] (10), C/A (-3), C/C (+1), so H(13,11) = 8; a[14]
+    # against a gap of 1 (-7); s (12): 13.  At cell (14,11) E can extend alignment 1's gap a
+    # third time (E(13,11) - 2 = 3 - 2 = 1) or open from H(13,11) (8 - 7 = 1); the open wins.
+    a, b = "ACACACACACACCCAGATGTTAGATAA", "ACACACACACACGATGTTAGATAA"
+    assert oracle.banded_sw(a, b, _full_box(a, b), wide) == (13, 2, 27, 0, 24)
+
+    # F: open over extend, the mirror image (query and bank swapped, so the gaps are horizontal):
+    # at cell (11,14) F can extend the three-base gap (1) or open from H(11,13) = 8 (1).
+    assert oracle.banded_sw(b, a, _full_box(b, a), wide) == (13, 0, 24, 2, 27)
+
+
 def test_sw_band_zero_is_best_ungapped_segment():
     """w = 0 on an HSP of diagonal 0 leaves only the main diagonal: the score is the best
     ungapped segment (Kadane's maximum subarray over match/mismatch scores)."""
