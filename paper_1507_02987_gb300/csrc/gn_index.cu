@@ -197,7 +197,7 @@ static void index_build_shape(const gn_bank *db, int k, int span, uint32_t keep,
     }
     void *rs = arena.alloc(radix_scratch_bytes(P));
     bool flipped = radix_sort(keys, keys_alt, nullptr, nullptr, P, 32, 32 + 2 * k, rs, s, TAG_INDEX_SORT);
-    GN_CUDA(cudaMalloc(&ix->post_d, sizeof(uint32_t) * (P ? P : 1)));
+    GN_CUDA(cudaMalloc(&ix->post_d, sizeof(uint32_t) * post_alloc_entries(P)));
     bytes += sizeof(uint32_t) * P;
     if (P) {
         GN_LAUNCH("k_low_words", P, s,
@@ -333,7 +333,7 @@ void index_load(const char *path, gn_index *ix) {
     GN_CUDA(cudaMalloc(&ix->bank.pk, 4 * npk));
     GN_CUDA(cudaMalloc(&ix->bank.nb, 4 * nnb));
     GN_CUDA(cudaMalloc(&ix->off_d, 8 * nbk));
-    GN_CUDA(cudaMalloc(&ix->post_d, 4 * std::max<uint64_t>(np, 1)));
+    GN_CUDA(cudaMalloc(&ix->post_d, 4 * post_alloc_entries(np)));
     GN_CUDA(cudaMalloc(&ix->seq_lut_d, 4 * nlut));
     ix->bank.n = n;
     bytes += 8 * (ns + 1) + 4 * (npk + nnb) + 8 * nbk + 4 * np + 4 * nlut;

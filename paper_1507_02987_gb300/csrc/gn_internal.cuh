@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -231,6 +232,10 @@ __device__ __forceinline__ uint32_t dev_upper_index(const uint64_t *__restrict__
 // Sequence lookup: lut[j] is the sequence holding bank position j << SEQ_LUT_SHIFT, so
 // the sequence of position x is found by a short forward walk from lut[x >> shift]
 // (sequences of >= 1 base; a block of 2^SEQ_LUT_SHIFT bases starts few of them).
+// Entries allocated for n occurrences: whole quads (16 bytes), so that the search may read
+// any list in aligned 16-byte loads; the entries past n are never used.
+inline uint64_t post_alloc_entries(uint64_t n) { return std::max<uint64_t>(4, (n + 3) & ~3ull); }
+
 constexpr int SEQ_LUT_SHIFT = 10;
 struct SeqMap {
     const uint64_t *start;  // n_seqs + 1 sequence starts (start[n_seqs] = bank length)
@@ -262,7 +267,7 @@ struct gn_index {
     uint32_t *seq_lut_d = nullptr;    // (n_bases >> SEQ_LUT_SHIFT) + 1 entries, see SeqMap
     gn::Packed bank;                  // packed bank + non-base bitmap
     uint64_t *off_d = nullptr;        // 4^k + 1 bucket starts
-    uint32_t *post_d = nullptr;       // occurrences: global base offset of the window
+    uint32_t *post_d = nullptr;       // occurrences: global base offset of the window (post_alloc_entries)
     uint64_t device_bytes = 0;
     // per-phase device times of the most recent search through this handle
     std::vector<std::pair<const char *, float>> last_phases;

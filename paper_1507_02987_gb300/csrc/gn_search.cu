@@ -182,95 +182,111 @@ __global__ void k_hit_merge(const uint64_t *__restrict__ keys, uint64_t n, int q
 
 // Tile-level bucketing: a CTA takes tpos consecutive query offsets (the core).
 // With the repeat filter on (min_hsp_len > k and D <= BT_MAX_D), every hit of the
-// core and of the D offsets on either side (the halo) is first hashed by its
-// (query, diagonal) into two shared-memory bitmaps, "seen" and "seen twice".  A
-// core hit can only be part of a chain of two or more hits if another hit lies
-// on its diagonal within D query offsets, and all those offsets are inside core
-// + halo; so a core hit whose hash was not seen twice cannot reach min_hsp_len
-// and is dropped here (a hash collision only keeps an extra hit).
+// core and of the D offsets on either side (the halo) is first entered, by its
+// (query, diagonal), into a shared-memory Bloom filter "seen" (three bits of one
+// 32-bit word per key); a hit that finds all its bits set already enters its key
+// into a second one, "seen twice" (two bits of one word).  A core hit can only be
+// part of a chain of two or more hits if another hit lies on its diagonal within D
+// query offsets, and all those offsets are inside core + halo; the later of two
+// hits with one key always finds that key's "seen" bits set.  A Bloom filter has
+// no false negatives, so a core hit whose "seen twice" bits are not all set cannot
+// reach min_hsp_len and is dropped here; a false positive only keeps an extra hit.
 constexpr int BT_MAX_D = 256;  // largest hit distance the tile filter supports
-constexpr int BF_CHUNK = 128;  // hits a warp takes at a time (four per lane)
 
-// Two hashes of (query, diagonal), into the "seen" and the "seen twice" bitmaps:
-// multiplicative (Fibonacci) hashing with two constants keeps nearby diagonals apart,
-// and a key that collides with another in "seen" marks a "seen twice" slot of its own
-// rather than the other key's.
-__device__ __forceinline__ uint32_t tile_key(uint32_t ql, uint64_t gk) { return (uint32_t)gk ^ (ql * 0x85EBCA77u); }
-__device__ __forceinline__ uint32_t tile_h1(uint32_t key, int fbits) { return (key * 0x9E3779B1u) >> (32 - fbits); }
-__device__ __forceinline__ uint32_t tile_h2(uint32_t key, int fbits2) { return (key * 0xC2B2AE35u) >> (32 - fbits2); }
+// The tile's occurrence lists are read in aligned quads of four entries (16-byte
+// loads): the list of offset i, occurrences [beg_i, end_i), covers quads beg_i / 4
+// to (end_i - 1) / 4 of the occurrence array, and the quads of all the tile's lists
+// form one index space.  Warps take chunks of BF_QCHUNK quads from a shared counter
+// (lane l holds quads c * BF_QCHUNK + 32 v + l, v < BF_QV), whatever lists they fall
+// in, so every lane has work and a long list is shared by many warps.  A quad lies
+// in one list; entries of a neighbouring list that share its 16 bytes are masked.
+constexpr int BF_QV = 2;
+constexpr int BF_QCHUNK = 32 * BF_QV;
+constexpr int BF_CMAX = 512;  // chunks whose first list is tabulated (later ones are searched)
 
-// Shared-memory table of a tile's query offsets lo + i, i in [0, span): hit prefix
-// relative to the tile's first hit (span + 1 entries), occurrence-list start,
+// Key of a hit for the filters: the low 32 bits of its diagonal key G' mixed with its
+// query (kadd = QBIAS - query offset, kx = query in chunk times an odd constant).
+__device__ __forceinline__ uint32_t bf_key(uint32_t ent, uint32_t kadd, uint32_t kx) { return (ent + kadd) ^ kx; }
+// Positions of a key in the two filters: the word of each from the top bits of one
+// multiplicative (Fibonacci) hash, which spreads the keys of nearby diagonals over the
+// words; the bits inside the word from 5-bit fields of the key itself, which differ
+// between nearby diagonals.
+__device__ __forceinline__ uint32_t bf_hash(uint32_t key) { return key * 0x9E3779B1u; }
+__device__ __forceinline__ uint32_t bf_mask(uint32_t key) {  // "seen": three bits
+    return (1u << (key & 31u)) | (1u << ((key >> 5) & 31u)) | (1u << ((key >> 10) & 31u));
+}
+__device__ __forceinline__ uint32_t bf2_mask(uint32_t key) {  // "seen twice": two bits
+    return (1u << ((key >> 15) & 31u)) | (1u << ((key >> 20) & 31u));
+}
+
+// Shared-memory table of a tile's query offsets lo + i, i in [0, span): quad prefix
+// relative to the tile's first quad (span + 1 entries), occurrence range [beg, end),
 // (query in chunk << 16 | query offset), and the query's bucket base and shift;
-// cs[c] is the offset holding hit c * BF_CHUNK for the first BF_CMAX chunks.
-// Tile-relative hit indices fit 32 bits: a query chunk holds < 2^32 hits.
-constexpr int BF_CMAX = 512;
+// cs[c] is the offset holding quad c * BF_QCHUNK for the first BF_CMAX chunks.
+// Tile-relative quad indices fit 32 bits: a query chunk holds < 2^32 hits.
 struct TileTable {
-    uint32_t *hs, *src, *qq, *bb, *cs;
+    uint32_t *qp, *beg, *end, *qq, *bb, *cs;
     uint8_t *bs;
     uint32_t span, nchunks;
 };
 
-// Last table index i in [i_lo, i_hi] with hs[i] <= h: the offset whose list holds hit h.
-__device__ __forceinline__ uint32_t tile_find(const uint32_t *hs, uint32_t i_lo, uint32_t i_hi, uint32_t h) {
+// Last table index i in [i_lo, i_hi] with qp[i] <= e: the offset whose list holds quad e.
+__device__ __forceinline__ uint32_t tile_find(const uint32_t *qp, uint32_t i_lo, uint32_t i_hi, uint32_t e) {
     while (i_lo < i_hi) {
         const uint32_t mid = (i_lo + i_hi + 1) >> 1;
-        if (hs[mid] <= h) i_lo = mid;
+        if (qp[mid] <= e) i_lo = mid;
         else i_hi = mid - 1;
     }
     return i_lo;
 }
 
-__device__ __forceinline__ uint32_t tile_chunk_offset(const TileTable &t, uint32_t c) {
-    return c < BF_CMAX ? t.cs[c] : tile_find(t.hs, 0, t.span - 1, c * BF_CHUNK);
+__device__ __forceinline__ uint32_t tile_chunk_list(const TileTable &t, uint32_t c) {
+    return c < BF_CMAX ? t.cs[c] : tile_find(t.qp, 0, t.span - 1, c * BF_QCHUNK);
 }
 
-// The four hits a lane holds of one chunk: occurrence entries (loads in flight until
-// used), table index of each, and which are inside the pass's hit range.
-struct ChunkLoad {
-    uint32_t ent[4], idx[4];
-    bool ok[4];
+// The BF_QV quads a lane holds of one chunk: entries (loads in flight until used),
+// table index, occurrence index of the first entry, and whether the quad is inside
+// the pass's quad range.
+struct QuadLoad {
+    uint4 ent[BF_QV];
+    uint32_t idx[BF_QV], occ[BF_QV];
+    bool ok[BF_QV];
 };
 
-// Issues the loads of chunk c, masked to the hit range [r0, r1).  Lane l takes the
-// four consecutive hits c * BF_CHUNK + 4l + v, which nearly always lie in one list:
-// one search per lane, then a boundary check per hit.
-__device__ __forceinline__ void tile_chunk_load(const TileTable &t, uint32_t c, uint32_t r0, uint32_t r1,
-                                                const uint32_t *__restrict__ post, ChunkLoad &L) {
+// Issues the loads of chunk c, masked to the quad range [r0, r1): one search per lane
+// for its first quad's list, then a boundary check per quad.
+__device__ __forceinline__ void tile_quad_load(const TileTable &t, uint32_t c, uint32_t r0, uint32_t r1,
+                                               const uint4 *__restrict__ post4, QuadLoad &L) {
     const int lane = threadIdx.x & 31;
-    const uint32_t hl = c * BF_CHUNK + 4 * lane;
-    const uint32_t i0 = tile_chunk_offset(t, c);
-    const uint32_t i1 = c + 1 < t.nchunks ? tile_chunk_offset(t, c + 1) : t.span - 1;
-    uint32_t i = tile_find(t.hs, i0, i1, max(hl, t.hs[i0]));
-    uint32_t hb = t.hs[i], he = t.hs[i + 1];
-    uint64_t base = (uint64_t)t.src[i] - hb;
+    const uint32_t e0 = c * BF_QCHUNK + lane;
+    const uint32_t i0 = tile_chunk_list(t, c);
+    const uint32_t i1 = c + 1 < t.nchunks ? tile_chunk_list(t, c + 1) : t.span - 1;
+    uint32_t i = tile_find(t.qp, i0, i1, e0);
+    uint32_t nx = t.qp[i + 1];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const uint32_t h = hl + v;
-        L.ok[v] = h >= r0 && h < r1;
-        while (h >= he && i < i1) {  // the next non-empty list
+    for (int v = 0; v < BF_QV; ++v) {
+        const uint32_t e = e0 + 32u * v;
+        while (e >= nx && i < i1) {  // the next non-empty list
             ++i;
-            hb = he;
-            he = t.hs[i + 1];
-            base = (uint64_t)t.src[i] - hb;
+            nx = t.qp[i + 1];
         }
         L.idx[v] = i;
-        L.ent[v] = L.ok[v] ? post[base + h] : 0u;
+        L.ok[v] = e >= r0 && e < r1;
+        const uint32_t q = (t.beg[i] >> 2) + (e - t.qp[i]);
+        L.occ[v] = q << 2;
+        L.ent[v] = L.ok[v] ? __ldg(&post4[q]) : make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
-// Calls f(idx[4], entry[4], ok[4]) for every hit of [r0, r1) (tile-relative hit
-// indices).  The tile's hits form one index space cut into BF_CHUNK-hit chunks; warps
-// take the chunks that meet [r0, r1) from a shared counter, whatever lists they fall
-// in, so every lane has work and a long list is shared by many warps.  A warp issues
-// the loads of its next chunk before it processes the current one.  Lane l holds hits
-// c * BF_CHUNK + 4l + v (v < 4); all lanes of a warp call f together.
+// Calls f(L) for every chunk of quads meeting [r0, r1) (tile-relative quad indices);
+// all lanes of a warp call f together.  A warp issues the loads of its next chunk
+// before it processes the current one.
 template <class F>
-__device__ __forceinline__ void for_tile_chunks(const TileTable &t, uint32_t r0, uint32_t r1, uint32_t *ctr,
-                                                const uint32_t *__restrict__ post, F &&f) {
+__device__ __forceinline__ void for_tile_quads(const TileTable &t, uint32_t r0, uint32_t r1, uint32_t *ctr,
+                                               const uint4 *__restrict__ post4, F &&f) {
     const int lane = threadIdx.x & 31;
     if (r0 >= r1) return;
-    const uint32_t c0 = r0 / BF_CHUNK, nc = (r1 + BF_CHUNK - 1) / BF_CHUNK - c0;
+    const uint32_t c0 = r0 / BF_QCHUNK, nc = (r1 + BF_QCHUNK - 1) / BF_QCHUNK - c0;
     auto claim = [&]() {
         uint32_t c = 0;
         if (lane == 0) c = atomicAdd(ctr, 1u);
@@ -278,24 +294,58 @@ __device__ __forceinline__ void for_tile_chunks(const TileTable &t, uint32_t r0,
     };
     uint32_t c = claim();
     if (c >= nc) return;
-    ChunkLoad cur, nxt;
-    tile_chunk_load(t, c0 + c, r0, r1, post, cur);
+    QuadLoad cur, nxt;
+    tile_quad_load(t, c0 + c, r0, r1, post4, cur);
     for (;;) {
         const uint32_t cn = claim();
         const bool more = cn < nc;
-        if (more) tile_chunk_load(t, c0 + cn, r0, r1, post, nxt);
-        f(cur.idx, cur.ent, cur.ok);
+        if (more) tile_quad_load(t, c0 + cn, r0, r1, post4, nxt);
+        f(cur);
         if (!more) break;
         cur = nxt;
     }
 }
 
-// Bucket fill: one kernel per query chunk.  Each tile (tpos core offsets) hashes the
-// hits of core + halo into the "seen" / "seen twice" bitmaps (repeat filter), then
+__device__ __forceinline__ uint32_t quad_word(const uint4 &q, int u) {
+    return u == 0 ? q.x : u == 1 ? q.y : u == 2 ? q.z : q.w;
+}
+
+// Exclusive scan of one value per thread over the block (blockDim.x a multiple of 32,
+// at most 1,024); wtot holds 32 words of shared memory.
+__device__ __forceinline__ uint32_t bf_block_scan(uint32_t v, uint32_t *wtot, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? wtot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) wtot[lane] = w;
+    }
+    __syncthreads();
+    total = wtot[nw - 1];
+    const uint32_t before = warp ? wtot[warp - 1] : 0u;
+    __syncthreads();  // wtot is reused by the next call
+    return before + x - v;
+}
+
+// Bucket fill: one kernel per query chunk.  Each tile (tpos core offsets) enters the
+// hits of core + halo into the "seen" / "seen twice" filters (repeat filter), then
 // places every kept core hit: one global atomic reserves its slot in its bucket.
 // Buckets have a fixed capacity bcap; hits past it go to the spill list in global
-// hit-key format, which the global sort path handles.
-__global__ void __launch_bounds__(512) k_bucket_fill(
+// hit-key format, which the global sort path handles.  count_only: no placement,
+// kept_total[0] counts the kept core hits and kept_total[1] all core hits of the
+// tiles visited (tiles 0, tile_step, 2 tile_step, ...).
+__global__ void __launch_bounds__(512, 2) k_bucket_fill(
     const uint32_t *__restrict__ qinfo, const uint32_t *__restrict__ src, const uint64_t *__restrict__ hoff,
     uint64_t xa, uint64_t xb, const uint32_t *__restrict__ post, uint32_t qa, const uint32_t *__restrict__ bbase,
     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount, uint64_t *__restrict__ bkeys, uint32_t bcap,
@@ -305,66 +355,84 @@ __global__ void __launch_bounds__(512) k_bucket_fill(
     extern __shared__ __align__(16) unsigned char bf_smem[];
     const uint32_t halo = filter ? D : 0u;
     const uint32_t span_max = (uint32_t)tpos + 2u * halo;
-    const uint32_t nwords = filter ? (1u << fbits) / 32 : 0u, nwords2 = filter ? (1u << fbits2) / 32 : 0u;
+    const int wbits = fbits - 5, wbits2 = fbits2 - 5;
+    const uint32_t nwords = filter ? 1u << wbits : 0u, nwords2 = filter ? 1u << wbits2 : 0u;
+    const uint4 *__restrict__ post4 = reinterpret_cast<const uint4 *>(post);
+    uint32_t *seen = reinterpret_cast<uint32_t *>(bf_smem);
+    uint32_t *seen2 = seen + nwords;
     TileTable t;
-    t.hs = reinterpret_cast<uint32_t *>(bf_smem);
-    t.src = t.hs + span_max + 1;
-    t.qq = t.src + span_max;
+    t.qp = seen2 + nwords2;
+    t.beg = t.qp + span_max + 1;
+    t.end = t.beg + span_max;
+    t.qq = t.end + span_max;
     t.bb = t.qq + span_max;
     t.cs = t.bb + span_max;
-    uint32_t *seen = t.cs + BF_CMAX;
-    uint32_t *seen2 = seen + nwords;
-    t.bs = reinterpret_cast<uint8_t *>(seen2 + nwords2);
+    t.bs = reinterpret_cast<uint8_t *>(t.cs + BF_CMAX);
     __shared__ uint32_t ctr;
+    __shared__ uint32_t wtot[32];
     uint32_t my_kept = 0;
-    uint32_t my_core = 0;  // core hits seen (count-only runs)
-    // tiles 0, tile_step, 2 tile_step, ... (every tile unless sampling)
+    unsigned long long my_core = 0;  // core hits of the visited tiles (count-only runs)
     for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tile_step * tpos; t0 < xb;
          t0 += (uint64_t)gridDim.x * tile_step * tpos) {
         const uint64_t t1 = min(xb, t0 + (uint64_t)tpos);
         const uint64_t lo = t0 - xa > halo ? t0 - halo : xa, hi = min(xb, t1 + halo);
         const uint32_t span = (uint32_t)(hi - lo);
-        const uint64_t hbase = hoff[lo];
-        for (uint32_t i = threadIdx.x; i <= span; i += blockDim.x) {
+        // per-offset table; quad counts first, then their exclusive scan in place
+        for (uint32_t i = threadIdx.x; i < span; i += blockDim.x) {
             const uint64_t x = lo + i;
-            t.hs[i] = (uint32_t)(hoff[x] - hbase);
-            if (i < span) {
-                t.src[i] = src[x];
-                const uint32_t qinf = qinfo[x];
-                const uint32_t ql = (qinf >> 16) - qa;
-                t.qq[i] = (ql << 16) | (qinf & 0xFFFFu);
-                t.bb[i] = bbase[ql];
-                t.bs[i] = (uint8_t)bshift[ql];
-            }
+            const uint32_t b = src[x], n = (uint32_t)(hoff[x + 1] - hoff[x]);
+            t.beg[i] = b;
+            t.end[i] = b + n;
+            t.qp[i] = n ? ((b + n + 3u) >> 2) - (b >> 2) : 0u;
+            const uint32_t qinf = qinfo[x];
+            const uint32_t ql = (qinf >> 16) - qa;
+            t.qq[i] = (ql << 16) | (qinf & 0xFFFFu);
+            t.bb[i] = bbase[ql];
+            t.bs[i] = (uint8_t)bshift[ql];
         }
         for (uint32_t i = threadIdx.x; i < nwords + nwords2; i += blockDim.x) seen[i] = 0u;
         if (threadIdx.x == 0) ctr = 0;
+        if (count_only && threadIdx.x == 0) my_core += hoff[t1] - hoff[t0];
+        __syncthreads();
+        {
+            const uint32_t per = (span + blockDim.x - 1) / blockDim.x;
+            const uint32_t a = min(span, threadIdx.x * per), b = min(span, a + per);
+            uint32_t sum = 0;
+            for (uint32_t i = a; i < b; ++i) sum += t.qp[i];
+            uint32_t total = 0;
+            uint32_t run = bf_block_scan(sum, wtot, total);
+            for (uint32_t i = a; i < b; ++i) {
+                const uint32_t nq = t.qp[i];
+                t.qp[i] = run;
+                run += nq;
+            }
+            if (threadIdx.x == 0) t.qp[span] = total;
+        }
         __syncthreads();
         t.span = span;
-        t.nchunks = (t.hs[span] + BF_CHUNK - 1) / BF_CHUNK;
-        // chunk -> offset of its first hit
+        t.nchunks = (t.qp[span] + BF_QCHUNK - 1) / BF_QCHUNK;
+        // chunk -> offset of its first quad
         for (uint32_t i = threadIdx.x; i < span; i += blockDim.x) {
-            const uint32_t ca = (t.hs[i] + BF_CHUNK - 1) / BF_CHUNK;
-            const uint32_t cb = min((t.hs[i + 1] + BF_CHUNK - 1) / BF_CHUNK, (uint32_t)BF_CMAX);
+            const uint32_t ca = (t.qp[i] + BF_QCHUNK - 1) / BF_QCHUNK;
+            const uint32_t cb = min((t.qp[i + 1] + BF_QCHUNK - 1) / BF_QCHUNK, (uint32_t)BF_CMAX);
             for (uint32_t c = ca; c < cb; ++c) t.cs[c] = i;
         }
         __syncthreads();
         if (filter) {
-            for_tile_chunks(t, 0, t.hs[span], &ctr, post, [&](const uint32_t *idx, const uint32_t *ent,
-                                                              const bool *ok) {
-                uint32_t qq = t.qq[idx[0]];
+            for_tile_quads(t, 0, t.qp[span], &ctr, post4, [&](const QuadLoad &L) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (u && idx[u] != idx[u - 1]) qq = t.qq[idx[u]];
-                    if (!ok[u]) continue;
-                    const uint64_t gk = (uint64_t)ent[u] + QBIAS - (qq & 0xFFFFu);
-                    const uint32_t key = tile_key(qq >> 16, gk);
-                    const uint32_t h = tile_h1(key, fbits);
-                    const uint32_t bit = 1u << (h & 31);
-                    const uint32_t old = atomicOr(&seen[h >> 5], bit);
-                    if (old & bit) {
-                        const uint32_t h2 = tile_h2(key, fbits2);
-                        atomicOr(&seen2[h2 >> 5], 1u << (h2 & 31));
+                for (int v = 0; v < BF_QV; ++v) {
+                    if (!L.ok[v]) continue;
+                    const uint32_t qq = t.qq[L.idx[v]];
+                    const uint32_t kadd = QBIAS - (qq & 0xFFFFu), kx = (qq >> 16) * 0x85EBCA77u;
+                    // entries of a neighbouring list that share the quad are entered too: an
+                    // extra key can only add false positives
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t key = bf_key(quad_word(L.ent[v], u), kadd, kx);
+                        const uint32_t h = bf_hash(key), m = bf_mask(key);
+                        const uint32_t old = atomicOr(&seen[h >> (32 - wbits)], m);
+                        if ((old & m) == m) atomicOr(&seen2[h >> (32 - wbits2)], bf2_mask(key));
                     }
                 }
             });
@@ -373,53 +441,54 @@ __global__ void __launch_bounds__(512) k_bucket_fill(
             __syncthreads();
         }
         // place the kept core hits (count them only, when sampling the keep rate)
-        if (count_only && threadIdx.x == 0) my_core += t.hs[t1 - lo] - t.hs[t0 - lo];
-        for_tile_chunks(t, t.hs[t0 - lo], t.hs[t1 - lo], &ctr, post, [&](const uint32_t *idx, const uint32_t *ent,
-                                                                            const bool *ok) {
-            uint64_t key[4];
-            uint32_t b[4], slot[4];
-            bool kk[4];
-            uint32_t qq = t.qq[idx[0]], bb = t.bb[idx[0]], bs = t.bs[idx[0]];
+        for_tile_quads(t, t.qp[t0 - lo], t.qp[t1 - lo], &ctr, post4, [&](const QuadLoad &L) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (u && idx[u] != idx[u - 1]) { qq = t.qq[idx[u]]; bb = t.bb[idx[u]]; bs = t.bs[idx[u]]; }
-                const uint64_t gk = (uint64_t)ent[u] + QBIAS - (qq & 0xFFFFu);
-                kk[u] = ok[u];
-                if (filter && kk[u]) {
-                    const uint32_t h2 = tile_h2(tile_key(qq >> 16, gk), fbits2);
-                    kk[u] = ((seen2[h2 >> 5] >> (h2 & 31)) & 1u) != 0u;
+            for (int v = 0; v < BF_QV; ++v) {
+                if (!L.ok[v]) continue;
+                const uint32_t i = L.idx[v], qq = t.qq[i], beg = t.beg[i], end = t.end[i], occ = L.occ[v];
+                // entries of this list in the quad: from beg - occ (first quad) to end - occ (last)
+                const uint32_t first = occ < beg ? beg - occ : 0u, last = end - occ < 4u ? end - occ : 4u;
+                uint32_t keep = (0xFu >> (4u - last)) & (0xFu << first);  // bit u: entry u is a kept hit
+                if (filter) {
+                    const uint32_t kadd = QBIAS - (qq & 0xFFFFu), kx = (qq >> 16) * 0x85EBCA77u;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t key = bf_key(quad_word(L.ent[v], u), kadd, kx);
+                        const uint32_t m2 = bf2_mask(key);
+                        if ((seen2[bf_hash(key) >> (32 - wbits2)] & m2) != m2) keep &= ~(1u << u);
+                    }
                 }
-                my_kept += kk[u] ? 1u : 0u;
-                b[u] = bb + (uint32_t)(gk >> bs);
-                key[u] = (gk << 16) | (qq & 0xFFFFu);
-            }
-            if (count_only) return;
-            // the global slot reservations first, then the dependent stores
+                if (!keep) continue;
+                my_kept += __popc(keep);
+                if (count_only) continue;
+                const uint32_t bb = t.bb[i], bs = t.bs[i];
+                // kept hits are few: each reserves its slot and is stored in turn
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (kk[u]) slot[u] = atomicAdd(&bcount[b[u]], 1u);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (!kk[u]) continue;
-                if (slot[u] < bcap) {
-                    bkeys[(uint64_t)b[u] * bcap + slot[u]] = key[u];
-                } else {
-                    const unsigned long long at = atomicAdd(spill_count, 1ull);
-                    const uint64_t gk = key[u] >> 16, qq = t.qq[idx[u]];
-                    if (at < spill_cap) spill[at] = (gk << (16 + qbits)) | ((qq >> 16) << 16) | (qq & 0xFFFFu);
+                for (int u = 0; u < 4; ++u) {
+                    if (!(keep >> u & 1u)) continue;
+                    const uint64_t gk = (uint64_t)quad_word(L.ent[v], u) + QBIAS - (qq & 0xFFFFu);
+                    const uint32_t b = bb + (uint32_t)(gk >> bs);
+                    const uint32_t slot = atomicAdd(&bcount[b], 1u);
+                    if (slot < bcap) {
+                        bkeys[(uint64_t)b * bcap + slot] = (gk << 16) | (qq & 0xFFFFu);
+                    } else {
+                        const unsigned long long at = atomicAdd(spill_count, 1ull);
+                        if (at < spill_cap)
+                            spill[at] = (gk << (16 + qbits)) | ((uint64_t)(qq >> 16) << 16) | (qq & 0xFFFFu);
+                    }
                 }
             }
         });
-        __syncthreads();  // the table and bitmaps are rebuilt for the next tile
+        __syncthreads();  // the table and filters are rebuilt for the next tile
     }
     if (my_kept) atomicAdd(kept_total, (unsigned long long)my_kept);
-    if (my_core) atomicAdd(kept_total + 1, (unsigned long long)my_core);
+    if (my_core) atomicAdd(kept_total + 1, my_core);
 }
 
-// Dynamic shared memory of k_bucket_fill.
+// Dynamic shared memory of k_bucket_fill: filters, then the offset table.
 static size_t bucket_fill_smem(int tpos, uint32_t halo, int filter, int fbits, int fbits2) {
     const size_t span_max = (size_t)tpos + 2 * halo;
-    return (span_max + 1) * 4 + span_max * 13 + 4 * BF_CMAX + (filter ? ((1u << fbits) + (1u << fbits2)) / 8 : 0);
+    return (filter ? ((1u << fbits) + (1u << fbits2)) / 8 : 0) + (span_max + 1) * 4 + span_max * 17 + 4 * BF_CMAX;
 }
 
 __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc, uint32_t NB,
