@@ -203,6 +203,11 @@ constexpr int BT_MAX_D = 256;  // largest hit distance the tile filter supports
 constexpr int BF_QV = 2;
 constexpr int BF_QCHUNK = 32 * BF_QV;
 constexpr int BF_CMAX = 512;  // chunks whose first list is tabulated (later ones are searched)
+// Kept hits of a tile are staged in shared memory (stage_cap of them, the room the
+// launch leaves) and placed in their buckets after the tile's placement pass, all
+// threads at once, so that their global atomics overlap instead of stalling each warp's
+// pass; hits past the stage's room are placed directly.
+constexpr int BF_STAGE_BYTES = 14;  // per staged hit: key, bucket, query
 
 // Key of a hit for the filters: the low 32 bits of its diagonal key G' mixed with its
 // query (kadd = QBIAS - query offset, kx = query in chunk times an odd constant).
@@ -338,6 +343,22 @@ __device__ __forceinline__ uint32_t bf_block_scan(uint32_t v, uint32_t *wtot, ui
     return before + x - v;
 }
 
+// Places one kept hit (key = G' << 16 | query offset, ql = query in chunk) in bucket b:
+// a global atomic reserves its slot; past the bucket's capacity it goes to the spill
+// list in global hit-key format.
+__device__ __forceinline__ void bucket_place(uint32_t b, uint64_t key, uint32_t ql, uint32_t *__restrict__ bcount,
+                                             uint64_t *__restrict__ bkeys, uint32_t bcap, uint64_t *__restrict__ spill,
+                                             unsigned long long *__restrict__ spill_count,
+                                             unsigned long long spill_cap, int qbits) {
+    const uint32_t slot = atomicAdd(&bcount[b], 1u);
+    if (slot < bcap) {
+        bkeys[(uint64_t)b * bcap + slot] = key;
+    } else {
+        const unsigned long long at = atomicAdd(spill_count, 1ull);
+        if (at < spill_cap) spill[at] = ((key >> 16) << (16 + qbits)) | ((uint64_t)ql << 16) | (key & 0xFFFFu);
+    }
+}
+
 // Bucket fill: one kernel per query chunk.  Each tile (tpos core offsets) enters the
 // hits of core + halo into the "seen" / "seen twice" filters (repeat filter), then
 // places every kept core hit: one global atomic reserves its slot in its bucket.
@@ -351,14 +372,15 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount, uint64_t *__restrict__ bkeys, uint32_t bcap,
     uint64_t *__restrict__ spill, unsigned long long *__restrict__ spill_count, unsigned long long spill_cap,
     int qbits, int filter, uint32_t D, int tpos, int fbits, int fbits2, unsigned long long *__restrict__ kept_total,
-    uint32_t tile_step, int count_only) {
+    uint32_t tile_step, int count_only, uint32_t stage_cap) {
     extern __shared__ __align__(16) unsigned char bf_smem[];
     const uint32_t halo = filter ? D : 0u;
     const uint32_t span_max = (uint32_t)tpos + 2u * halo;
     const int wbits = fbits - 5, wbits2 = fbits2 - 5;
     const uint32_t nwords = filter ? 1u << wbits : 0u, nwords2 = filter ? 1u << wbits2 : 0u;
     const uint4 *__restrict__ post4 = reinterpret_cast<const uint4 *>(post);
-    uint32_t *seen = reinterpret_cast<uint32_t *>(bf_smem);
+    uint64_t *stage_key = reinterpret_cast<uint64_t *>(bf_smem);  // G' << 16 | query offset
+    uint32_t *seen = reinterpret_cast<uint32_t *>(stage_key + stage_cap);
     uint32_t *seen2 = seen + nwords;
     TileTable t;
     t.qp = seen2 + nwords2;
@@ -367,8 +389,10 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     t.qq = t.end + span_max;
     t.bb = t.qq + span_max;
     t.cs = t.bb + span_max;
-    t.bs = reinterpret_cast<uint8_t *>(t.cs + BF_CMAX);
-    __shared__ uint32_t ctr;
+    uint32_t *stage_b = t.cs + BF_CMAX;                                 // bucket
+    uint16_t *stage_q = reinterpret_cast<uint16_t *>(stage_b + stage_cap);  // query in chunk
+    t.bs = reinterpret_cast<uint8_t *>(stage_q + stage_cap);
+    __shared__ uint32_t ctr, nstage;
     __shared__ uint32_t wtot[32];
     uint32_t my_kept = 0;
     unsigned long long my_core = 0;  // core hits of the visited tiles (count-only runs)
@@ -391,7 +415,7 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
             t.bs[i] = (uint8_t)bshift[ql];
         }
         for (uint32_t i = threadIdx.x; i < nwords + nwords2; i += blockDim.x) seen[i] = 0u;
-        if (threadIdx.x == 0) ctr = 0;
+        if (threadIdx.x == 0) ctr = nstage = 0;
         if (count_only && threadIdx.x == 0) my_core += hoff[t1] - hoff[t0];
         __syncthreads();
         {
@@ -462,33 +486,41 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
                 my_kept += __popc(keep);
                 if (count_only) continue;
                 const uint32_t bb = t.bb[i], bs = t.bs[i];
-                // kept hits are few: each reserves its slot and is stored in turn
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (!(keep >> u & 1u)) continue;
                     const uint64_t gk = (uint64_t)quad_word(L.ent[v], u) + QBIAS - (qq & 0xFFFFu);
                     const uint32_t b = bb + (uint32_t)(gk >> bs);
-                    const uint32_t slot = atomicAdd(&bcount[b], 1u);
-                    if (slot < bcap) {
-                        bkeys[(uint64_t)b * bcap + slot] = (gk << 16) | (qq & 0xFFFFu);
+                    const uint64_t key = (gk << 16) | (qq & 0xFFFFu);
+                    const uint32_t at = atomicAdd(&nstage, 1u);
+                    if (at < stage_cap) {
+                        stage_key[at] = key;
+                        stage_b[at] = b;
+                        stage_q[at] = (uint16_t)(qq >> 16);
                     } else {
-                        const unsigned long long at = atomicAdd(spill_count, 1ull);
-                        if (at < spill_cap)
-                            spill[at] = (gk << (16 + qbits)) | ((uint64_t)(qq >> 16) << 16) | (qq & 0xFFFFu);
+                        bucket_place(b, key, qq >> 16, bcount, bkeys, bcap, spill, spill_count, spill_cap, qbits);
                     }
                 }
             }
         });
+        if (!count_only) {
+            __syncthreads();
+            const uint32_t ns = min(nstage, stage_cap);
+            for (uint32_t j = threadIdx.x; j < ns; j += blockDim.x)
+                bucket_place(stage_b[j], stage_key[j], stage_q[j], bcount, bkeys, bcap, spill, spill_count, spill_cap,
+                             qbits);
+        }
         __syncthreads();  // the table and filters are rebuilt for the next tile
     }
     if (my_kept) atomicAdd(kept_total, (unsigned long long)my_kept);
     if (my_core) atomicAdd(kept_total + 1, my_core);
 }
 
-// Dynamic shared memory of k_bucket_fill: filters, then the offset table.
-static size_t bucket_fill_smem(int tpos, uint32_t halo, int filter, int fbits, int fbits2) {
+// Dynamic shared memory of k_bucket_fill: staged kept hits, filters, offset table.
+static size_t bucket_fill_smem(int tpos, uint32_t halo, int filter, int fbits, int fbits2, uint32_t stage_cap) {
     const size_t span_max = (size_t)tpos + 2 * halo;
-    return (filter ? ((1u << fbits) + (1u << fbits2)) / 8 : 0) + (span_max + 1) * 4 + span_max * 17 + 4 * BF_CMAX;
+    return (size_t)stage_cap * BF_STAGE_BYTES + (filter ? ((1u << fbits) + (1u << fbits2)) / 8 : 0) +
+           (span_max + 1) * 4 + span_max * 17 + 4 * BF_CMAX;
 }
 
 __global__ void k_bucket_query(const uint32_t *__restrict__ bbase, uint32_t nqc, uint32_t NB,
@@ -2414,7 +2446,21 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 if (min_room) spill_room = min_room;
                 uint64_t *spill = carena.alloc_n<uint64_t>(spill_room);
                 const uint64_t tiles = (xb - xa + tpos - 1) / tpos;
-                const size_t bf_smem = bucket_fill_smem(tpos, filter ? p.max_hit_distance : 0u, filter, fbits, fbits2);
+                // the kept-hit stage gets what the SM's shared memory leaves for two 512-thread (or four
+                // 256-thread) tiles per SM after the filters and the table, at least 256 hits
+                uint32_t stage_cap = 256;
+                {
+                    const uint32_t halo = filter ? p.max_hit_distance : 0u;
+                    int per_sm = 0, reserved = 0;
+                    GN_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ix->device));
+                    GN_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ix->device));
+                    const int64_t room = (int64_t)per_sm / (fthreads == 512 ? 2 : 4) - reserved - 512 -
+                                         (int64_t)bucket_fill_smem(tpos, halo, filter, fbits, fbits2, 0);
+                    if (room > 256 * BF_STAGE_BYTES)
+                        stage_cap = (uint32_t)std::min<int64_t>(8192, room / BF_STAGE_BYTES) & ~31u;
+                }
+                const size_t bf_smem = bucket_fill_smem(tpos, filter ? p.max_hit_distance : 0u, filter, fbits, fbits2,
+                                                        stage_cap);
                 auto fill_kernel = k_bucket_fill;
                 allow_max_smem(ix->device);
                 int focc = 0;
@@ -2448,7 +2494,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                             bf_smem, s>>>(
                                   qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, nullptr, nullptr, bcap,
                                   nullptr, nullptr, 0ull, qbits, filter, p.max_hit_distance, tpos, fbits, fbits2,
-                                  kept_total, tile_step, 1));
+                                  kept_total, tile_step, 1, stage_cap));
                     GN_CUDA(cudaMemcpyAsync(got, kept_total, 16, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
                     if (got[1]) {
@@ -2474,7 +2520,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                   fill_kernel<<<fgrid, fthreads, bf_smem, s>>>(
                                       qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
                                       spill, spill_count, (unsigned long long)spill_room, qbits, filter,
-                                      p.max_hit_distance, tpos, fbits, fbits2, kept_total, 1u, 0));
+                                      p.max_hit_distance, tpos, fbits, fbits2, kept_total, 1u, 0, stage_cap));
                         GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
                         GN_CUDA(cudaMemcpyAsync(&n_kept, kept_total, 8, cudaMemcpyDeviceToHost, s));
                         GN_CUDA(cudaStreamSynchronize(s));
