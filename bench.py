@@ -242,13 +242,27 @@ def percentile(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
+def same_result(a, b):
+    """Two one-query results agree: integers identical, e-values within 1e-9 relative (both below
+    1e-300 counts as equal)."""
+    import numpy as np
+    if a is None or b is None or len(a) != len(b):
+        return False
+    for f in ("seq", "q_start", "q_end", "db_start", "db_end", "score", "rank"):
+        if not np.array_equal(a[f], b[f]):
+            return False
+    tiny = (np.abs(a["evalue"]) < 1e-300) & (np.abs(b["evalue"]) < 1e-300)
+    return bool((tiny | np.isclose(a["evalue"], b["evalue"], rtol=1e-9, atol=0)).all())
+
+
 def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
     """Open-loop run of the request loop: submits reqs[i] at t0 + arrivals[i], collects results from
-    the completion queue on another thread.  Latency = result on the host - scheduled arrival."""
+    the completion queue on another thread.  Latency = result on the host - scheduled arrival.
+    Returns the leg's figures and each request's result (read after the run)."""
     srv = gn.Server(ix, budget)
     n = len(reqs)
     done_at = {}
-    held = []  # results are freed after the run: the collector does as little as it can
+    held = {}  # ticket -> result, read and freed after the run: the collector does as little as it can
 
     def collector():
         end = time.perf_counter() + timeout_s
@@ -257,7 +271,7 @@ def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
             if got is None:
                 continue
             done_at[got[0]] = time.perf_counter()
-            held.append(got[1])
+            held[got[0]] = got[1]
 
     th = threading.Thread(target=collector, daemon=True)
     th.start()
@@ -270,7 +284,8 @@ def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
         tickets.append(srv.submit(reqs[i]))
     submit_s = time.perf_counter() - t0
     th.join(timeout_s)
-    for res in held:
+    results = [held[t].query(0).copy() if t in held else None for t in tickets]
+    for res in held.values():
         res.close()
     stats = srv.stats()
     srv.stop()
@@ -279,25 +294,27 @@ def serve_leg(gn, ix, reqs, arrivals, budget, timeout_s=120.0):
     return {"requests": n, "completed": len(lat), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
             "kbp_s": sum(len(r) for r in reqs) / 1e3 / wall, "batches": stats["batches"],
             "max_batch": stats["max_batch"], "max_concurrent_batches": stats["max_concurrent"],
-            "submit_ms": 1e3 * submit_s}
+            "submit_ms": 1e3 * submit_s}, results
 
 
 def plain_leg(gn, ix, reqs, arrivals, stream):
     """The same arrivals served by the plain path: one gn_search per query, in arrival order, with host
-    queries and host results."""
+    queries and host results.  Returns the leg's figures and each request's result."""
     import numpy as np
     t0 = time.perf_counter()
-    lat = []
+    lat, results = [], []
     for i, q in enumerate(reqs):
         wait = t0 + float(arrivals[i]) - time.perf_counter()
         if wait > 0:
             time.sleep(wait)
         st = np.array([0, len(q)], dtype=np.uint64)
-        gn.search(ix, st, np.frombuffer(q, dtype=np.uint8), stream=stream).close()
+        res = gn.search(ix, st, np.frombuffer(q, dtype=np.uint8), stream=stream)
+        results.append(res.query(0).copy())
+        res.close()
         lat.append(1e3 * (time.perf_counter() - (t0 + float(arrivals[i]))))
     wall = time.perf_counter() - t0
     return {"requests": len(reqs), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
-            "kbp_s": sum(len(r) for r in reqs) / 1e3 / wall}
+            "kbp_s": sum(len(r) for r in reqs) / 1e3 / wall}, results
 
 
 def serving(args, gn, ix, bank, stream, log):
@@ -322,12 +339,15 @@ def serving(args, gn, ix, bank, stream, log):
             rate = float(r)
             n = int(min(len(reqs), max(50, rate * args.serve_seconds)))
             arr = synth.poisson_arrivals(rate, n, seed=spec.seed + int(rate))
-        served = serve_leg(gn, ix, reqs[:n], arr, budget)
+        served, served_res = serve_leg(gn, ix, reqs[:n], arr, budget)
         n_plain = min(n, 1000)
-        plain = plain_leg(gn, ix, reqs[:n_plain], arr[:n_plain], stream)
+        plain, plain_res = plain_leg(gn, ix, reqs[:n_plain], arr[:n_plain], stream)
+        # identical results: each request served in the mix against the same request on the plain path
+        served["compared_with_plain"] = n_plain
+        served["mismatches"] = sum(0 if same_result(a, b) else 1 for a, b in zip(served_res, plain_res))
         log(f"serving at {r} q/s: served {served['kbp_s']:.0f} kbp/s p50 {served['p50_ms']:.1f} ms "
             f"p99 {served['p99_ms']:.1f} ms; plain {plain['kbp_s']:.0f} kbp/s p50 {plain['p50_ms']:.1f} ms "
-            f"p99 {plain['p99_ms']:.1f} ms")
+            f"p99 {plain['p99_ms']:.1f} ms; mismatches {served['mismatches']} of {n_plain}")
         out["rates"].append({"rate_qps": rate if rate is not None else "max (all at t=0)",
                              "served": served, "plain": plain})
     return out

@@ -94,6 +94,9 @@ def _load():
             lib.or_index_build.argtypes = [vp, vp, u32, ctypes.c_int, ctypes.c_int]
             lib.or_index_build_masked.restype = vp
             lib.or_index_build_masked.argtypes = [vp, vp, u32, ctypes.c_char_p, ctypes.c_int]
+            lib.or_index_build_restricted.restype = vp
+            lib.or_index_build_restricted.argtypes = [vp, vp, u32, ctypes.c_char_p, ctypes.c_int, vp, ctypes.c_int]
+            lib.or_mark_query_codes.argtypes = [vp, u32, ctypes.c_char_p, vp]
             lib.or_index_free.argtypes = [vp]
             lib.or_index_n_postings.restype = u64
             lib.or_index_n_postings.argtypes = [vp]
@@ -200,14 +203,30 @@ def _convert(r: _Result) -> QueryResult:
 class Index:
     """The oracle's inverted index: 4^k buckets of (sequence id, position) pairs."""
 
-    def __init__(self, bank, k: int = 11, stride: int = 11, mask: str | None = None):
+    def __init__(self, bank, k: int = 11, stride: int = 11, mask: str | None = None, restrict_to=None,
+                 threads: int = 1):
         """k-base windows, or with ``mask`` (e.g. "111010010100110111") windows of the mask's
-        length indexed under their kept bases ("Methods"); k is then the mask's weight."""
+        length indexed under their kept bases ("Methods"); k is then the mask's weight.
+
+        ``restrict_to`` (a query set) keeps only the buckets of those queries' seed codes, each
+        exactly as in the full index, so that searching those queries gives the full index's
+        results; the bank is then scanned by ``threads`` threads.  For banks whose full index
+        would not fit the host."""
         self._lib = _load()
         self.bank = bank
         self._bases = np.ascontiguousarray(bank.bases, dtype=np.uint8)
         self._start = np.ascontiguousarray(bank.seq_start, dtype=np.uint64)
-        if mask is not None:
+        if restrict_to is not None:
+            m = mask if mask is not None else "1" * k
+            k = m.count("1")
+            keep = np.zeros(1 << (2 * k), dtype=np.uint8)
+            for i in range(restrict_to.n):
+                q = np.frombuffer(restrict_to.query(i), dtype=np.uint8)
+                self._lib.or_mark_query_codes(q.ctypes.data, len(q), m.encode(), keep.ctypes.data)
+            self._h = self._lib.or_index_build_restricted(self._bases.ctypes.data, self._start.ctypes.data,
+                                                          bank.n_seqs, m.encode(), stride, keep.ctypes.data,
+                                                          max(1, int(threads)))
+        elif mask is not None:
             k = mask.count("1")
             self._h = self._lib.or_index_build_masked(self._bases.ctypes.data, self._start.ctypes.data, bank.n_seqs,
                                                       mask.encode(), stride)

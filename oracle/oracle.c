@@ -124,6 +124,96 @@ or_index *or_index_build_masked(const uint8_t *bases, const uint64_t *seq_start,
     return ix;
 }
 
+/* Marks in keep[] (4^k bytes) the code of every seed of a query (offsets 0 .. m - span,
+ * seeds holding a non-base at a kept position excepted), as the search looks them up. */
+void or_mark_query_codes(const uint8_t *q, uint32_t m, const char *mask, uint8_t *keep) {
+    int span = (int)strlen(mask);
+    for (uint64_t x = 0; x + (uint64_t)span <= m; ++x) {
+        int64_t c = seed_code(q + x, mask, span);
+        if (c >= 0) keep[c] = 1;
+    }
+}
+
+typedef struct {
+    const uint8_t *bases;
+    const uint64_t *seq_start;
+    uint32_t s_lo, s_hi;
+    const char *mask;
+    int span, t;
+    const uint8_t *keep;
+    uint64_t n, cap;
+    uint64_t *code;
+    uint32_t *seq, *pos;
+} restrict_scan;
+
+static void *restrict_scan_run(void *arg) {
+    restrict_scan *r = (restrict_scan *)arg;
+    for (uint32_t s = r->s_lo; s < r->s_hi; ++s) {
+        uint64_t L = r->seq_start[s + 1] - r->seq_start[s];
+        const uint8_t *seq = r->bases + r->seq_start[s];
+        for (uint64_t pos = 0; pos + (uint64_t)r->span <= L; pos += (uint64_t)r->t) {
+            int64_t c = seed_code(seq + pos, r->mask, r->span);
+            if (c < 0 || !r->keep[c]) continue;
+            if (r->n == r->cap) {
+                r->cap = r->cap ? 2 * r->cap : 1024;
+                r->code = (uint64_t *)realloc(r->code, sizeof(uint64_t) * r->cap);
+                r->seq = (uint32_t *)realloc(r->seq, sizeof(uint32_t) * r->cap);
+                r->pos = (uint32_t *)realloc(r->pos, sizeof(uint32_t) * r->cap);
+            }
+            r->code[r->n] = (uint64_t)c; r->seq[r->n] = s; r->pos[r->n] = (uint32_t)pos;
+            ++r->n;
+        }
+    }
+    return NULL;
+}
+
+/* The index restricted to the buckets whose code has keep[code] != 0: each of them holds
+ * exactly the occurrences of the full index in the same (sequence, position) order, the
+ * others are empty.  A query whose seed codes are all kept is therefore searched exactly
+ * as against the full index.  It serves tests on banks whose full index would not fit
+ * the host.  The bank is scanned by `threads` threads over consecutive sequence ranges;
+ * their occurrences, taken range by range, are in bank order. */
+or_index *or_index_build_restricted(const uint8_t *bases, const uint64_t *seq_start, uint32_t n_seqs,
+                                    const char *mask, int t, const uint8_t *keep, int threads) {
+    or_index *ix = or_index_build_masked(bases, seq_start, 0, mask, t);  /* validated, empty */
+    if (!ix) return NULL;
+    ix->n_seqs = n_seqs;
+    if (threads < 1) threads = 1;
+    if ((uint32_t)threads > n_seqs) threads = n_seqs ? (int)n_seqs : 1;
+    restrict_scan *rs = (restrict_scan *)calloc((size_t)threads, sizeof(restrict_scan));
+    pthread_t *th = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    for (int i = 0; i < threads; ++i) {
+        rs[i].bases = bases; rs[i].seq_start = seq_start; rs[i].mask = ix->mask; rs[i].span = ix->span;
+        rs[i].t = t; rs[i].keep = keep;
+        rs[i].s_lo = (uint32_t)((uint64_t)n_seqs * i / threads);
+        rs[i].s_hi = (uint32_t)((uint64_t)n_seqs * (i + 1) / threads);
+        pthread_create(&th[i], NULL, restrict_scan_run, &rs[i]);
+    }
+    for (int i = 0; i < threads; ++i) pthread_join(th[i], NULL);
+    uint64_t total = 0;
+    for (int i = 0; i < threads; ++i) {
+        total += rs[i].n;
+        for (uint64_t j = 0; j < rs[i].n; ++j) ix->bucket_start[rs[i].code[j] + 1]++;
+    }
+    for (uint64_t c = 0; c < ix->n_buckets; ++c) ix->bucket_start[c + 1] += ix->bucket_start[c];
+    ix->n_postings = total;
+    free(ix->post_seq); free(ix->post_pos);
+    ix->post_seq = (uint32_t *)malloc(sizeof(uint32_t) * (total ? total : 1));
+    ix->post_pos = (uint32_t *)malloc(sizeof(uint32_t) * (total ? total : 1));
+    uint64_t *cursor = (uint64_t *)malloc(sizeof(uint64_t) * ix->n_buckets);
+    memcpy(cursor, ix->bucket_start, sizeof(uint64_t) * ix->n_buckets);
+    for (int i = 0; i < threads; ++i) {
+        for (uint64_t j = 0; j < rs[i].n; ++j) {
+            uint64_t at = cursor[rs[i].code[j]]++;
+            ix->post_seq[at] = rs[i].seq[j];
+            ix->post_pos[at] = rs[i].pos[j];
+        }
+        free(rs[i].code); free(rs[i].seq); free(rs[i].pos);
+    }
+    free(cursor); free(rs); free(th);
+    return ix;
+}
+
 /* plain k-base windows: the mask of k ones */
 or_index *or_index_build(const uint8_t *bases, const uint64_t *seq_start, uint32_t n_seqs, int k, int t) {
     if (k < 1 || k > 16) return NULL;

@@ -142,3 +142,42 @@ def test_masked_rejects_bad_masks():
     for bad in ("", "0000", "1" * 17, "1" * 33, "1021"):
         with pytest.raises(ValueError):
             oracle.Index(bank, stride=1, mask=bad)
+
+
+@pytest.mark.parametrize("stride,mask", [(11, None), (1, None), (6, "111010010100110111")])
+def test_restricted_index_equals_full_on_kept_buckets(stride, mask):
+    """The index restricted to some queries' seed codes holds, for every such code, the full
+    index's bucket (same occurrences, same order) and nothing else; searching those queries
+    gives the full index's results.  Several scan threads give the same index as one."""
+    bank = synth.make_bank("mid", n_seqs=3000)
+    qs = synth.make_queries("mid", bank, n=6)
+    full = oracle.Index(bank, k=11, stride=stride, mask=mask)
+    bs, ps, pp = full.buckets()
+    keep = set()
+    span = len(mask) if mask else 11
+    for i in range(qs.n):
+        q = qs.query(i)
+        for x in range(len(q) - span + 1):
+            w = q[x:x + span].decode()
+            kept = _brute.kept(w, mask) if mask else "".join(_brute.norm(c) for c in w)
+            if all(_brute.is_base(c) for c in kept):
+                keep.add(kept)
+    kept_codes = set()
+    for s in keep:
+        c = 0
+        for ch in s:
+            c = 4 * c + "ACGT".index(ch)
+        kept_codes.add(c)
+    for threads in (1, 5):
+        r = oracle.Index(bank, k=11, stride=stride, mask=mask, restrict_to=qs, threads=threads)
+        rbs, rps, rpp = r.buckets()
+        counts = np.diff(rbs)
+        assert set(np.nonzero(counts)[0].tolist()) <= kept_codes
+        for c in kept_codes:
+            a, b = int(bs[c]), int(bs[c + 1])
+            ra, rb = int(rbs[c]), int(rbs[c + 1])
+            assert np.array_equal(ps[a:b], rps[ra:rb]) and np.array_equal(pp[a:b], rpp[ra:rb]), c
+        p = oracle.Params(stride=stride)
+        got, exp = r.search(qs, p), full.search(qs, p)
+        for g, e in zip(got, exp):
+            assert np.array_equal(g.ranked, e.ranked)
