@@ -77,6 +77,8 @@ def parse_args():
                          "at once, a saturation run of all requests); empty to skip it")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window per serving rate")
     ap.add_argument("--serve-budget-gib", type=float, default=16.0, help="server memory budget")
+    ap.add_argument("--no-sub-legs", action="store_true",
+                    help="skip the batched (10,000 queries on the mid bank) and long-query sub-legs")
     ap.add_argument("--sweep", action="store_true",
                     help="sensitivity sweep instead of the benchmark: planted-homolog recovery and time per "
                          "step for a grid of minimum HSP length, hit distance and drop-off around the defaults")
@@ -192,6 +194,17 @@ def ncu_traffic(kernel: str):
     return k.get("dram_bytes_per_unit") if k else None
 
 
+def workload_desc(name: str, stride: int) -> str:
+    desc = {
+        "tiny": "tiny bank (1,000 uniform sequences, ~1.25 Mbp), 10 mutated-copy queries",
+        "mid": "mid bank (200,000 log-normal sequences, ~400 Mbp, GC 0.35-0.65, 20% repeats), 1,000 homolog queries 80-10,000 bp",
+        "batched": "mid bank (~400 Mbp), 10,000 queries 50-5,000 bp, half planted homologs",
+        "large": "large bank (2.5 M log-normal sequences, ~4.0 Gbp, GC 0.35-0.65, 20% repeats), 2,000 queries 200-20,000 bp, half planted homologs",
+        "long": "large bank (~4.0 Gbp), 40 queries 65,536 bp - 1 Mbp (searched in overlapping segments), half planted homologs",
+    }[name]
+    return f"{desc}; k=11, stride {stride}; one gn_search over all queries per step"
+
+
 def workload(name: str, stride: int, rank: int, n_queries: int = 0):
     import dataclasses
 
@@ -207,14 +220,7 @@ def workload(name: str, stride: int, rank: int, n_queries: int = 0):
     queries = synth.make_queries(spec, bank)
     if n_queries and n_queries < queries.n:
         queries = queries.subset(range(n_queries))
-    desc = {
-        "tiny": "tiny bank (1,000 uniform sequences, ~1.25 Mbp), 10 mutated-copy queries",
-        "mid": "mid bank (200,000 log-normal sequences, ~400 Mbp, GC 0.35-0.65, 20% repeats), 1,000 homolog queries 80-10,000 bp",
-        "batched": "mid bank (~400 Mbp), 10,000 queries 50-5,000 bp, half planted homologs",
-        "large": "large bank (2.5 M log-normal sequences, ~4.0 Gbp, GC 0.35-0.65, 20% repeats), 2,000 queries 200-20,000 bp, half planted homologs",
-        "long": "large bank (~4.0 Gbp), 40 queries 65,536 bp - 1 Mbp (searched in overlapping segments), half planted homologs",
-    }[name]
-    return bank, queries, f"{desc}; k=11, stride {stride}; one gn_search over all queries per step"
+    return bank, queries, workload_desc(name, stride)
 
 
 def oracle_run(bank, queries, stride, threads, target_s, rng_seed=0, mask=None, band_w=16):
@@ -350,6 +356,54 @@ def serving(args, gn, ix, bank, stream, log):
             f"p99 {plain['p99_ms']:.1f} ms; mismatches {served['mismatches']} of {n_plain}")
         out["rates"].append({"rate_qps": rate if rate is not None else "max (all at t=0)",
                              "served": served, "plain": plain})
+    return out
+
+
+def matches_oracle(got, exp):
+    """A GPU result (gn_hit records) against the oracle's ranked alignments of the same query."""
+    import numpy as np
+    if len(got) != len(exp):
+        return False
+    for a, b in (("seq", "seq"), ("q_start", "qs"), ("q_end", "qe"), ("db_start", "ds"), ("db_end", "de"),
+                 ("score", "score"), ("rank", "rank")):
+        if not np.array_equal(got[a].astype(np.int64), exp[b].astype(np.int64)):
+            return False
+    tiny = (np.abs(got["evalue"]) < 1e-300) & (np.abs(exp["evalue"]) < 1e-300)
+    return bool((tiny | np.isclose(got["evalue"], exp["evalue"], rtol=1e-9, atol=0)).all())
+
+
+def sub_leg(gn, ix, bank, queries, desc, steps, warmup, stream, dev, parity_idx, log):
+    """One gn_search over a whole query set per step (device-resident queries, CUDA events around
+    the steps, as the main leg), then the sampled queries parity_idx against the oracle (an index
+    restricted to their seed codes, which searches them as the full one does)."""
+    import oracle
+    import torch
+    sh = stream.cuda_stream
+    qd = torch.from_numpy(queries.bases).to(f"cuda:{dev}")
+    M = int(queries.start[-1])
+    for _ in range(warmup):
+        gn.search(ix, queries.start, qd, stream=sh).close()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        gn.search(ix, queries.start, qd, stream=sh).close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    res = gn.search(ix, queries.start, qd, stream=sh)
+    got = [res.query(i).copy() for i in parity_idx]
+    res.close()
+    sub = queries.subset(parity_idx)
+    threads = os.cpu_count() or 1
+    ox = oracle.Index(bank, k=11, stride=ix.stride, restrict_to=sub, threads=threads)
+    ref = ox.search(sub, oracle.Params(stride=ix.stride), threads=threads)
+    mism = sum(0 if matches_oracle(g, r.ranked) else 1 for g, r in zip(got, ref))
+    out = {"workload": desc, "queries": queries.n, "query_bases": M, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms, "value": M / 1e3 / (ms / 1e3), "unit": UNIT,
+           "oracle_parity": {"queries_compared": len(parity_idx), "mismatches": mism}}
+    log(f"sub-leg {desc[:40]}...: {out['value']:.0f} kbp/s, {ms:.2f} ms per step, "
+        f"oracle mismatches {mism} of {len(parity_idx)}")
     return out
 
 
@@ -518,6 +572,23 @@ def run_ours(args, dist):
     # ---- serving: Poisson arrivals through the request loop and through the plain path
     serve = serving(args, gn, ix, bank, sh, log) if dist.rank == 0 else None
 
+    # ---- sub-legs (rank 0, large workload only): the batched workload (10,000 queries on the mid
+    # bank) and the long-query workload (40 queries of 65,536 bp - 1 Mbp on this bank and index)
+    legs = None
+    if dist.rank == 0 and args.workload == "large" and not args.no_sub_legs and not args.queries and not args.mask:
+        import synth
+        legs = {}
+        lq = synth.make_queries("long", bank)
+        order = sorted(range(lq.n), key=lambda i: int(lq.start[i + 1] - lq.start[i]))
+        legs["long"] = sub_leg(gn, ix, bank, lq, workload_desc("long", args.stride), 3, 3, stream, dev,
+                               sorted(order[:3]), log)
+        bb = synth.make_bank("batched")
+        bq = synth.make_queries("batched", bb)
+        bix = gn.Index(bb.seq_start, bb.bases, k=11, stride=args.stride, stream=sh)
+        legs["batched"] = sub_leg(gn, bix, bb, bq, workload_desc("batched", args.stride), 5, 3, stream, dev,
+                                  list(range(0, bq.n, bq.n // 40))[:40] + [bq.n - 1], log)
+        bix.close()
+
     # ---- roofline of the dominant kernel (and of the next ones)
     peaks = measured_peaks()
     try:
@@ -599,7 +670,7 @@ def run_ours(args, dist):
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / max(1, args.steps), "roofline": roof,
                 "kernel_rooflines": roofs,
-                "cpu_baseline": cpu, "plain_per_query": plain, "serving": serve,
+                "cpu_baseline": cpu, "plain_per_query": plain, "serving": serve, "sub_legs": legs,
                 "oracle_parity_on_sample": parity,
                 "index_build": {"seconds": t_index, "bank_gbp_per_s": bank.n_bases / 1e9 / t_index,
                                 "postings": info.n_postings, "device_gib": info.device_bytes / 2**30,

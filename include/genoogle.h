@@ -19,8 +19,10 @@
  *    anything else (N, IUPAC codes) is a non-base: windows holding one are
  *    neither indexed nor looked up, and it scores as a mismatch against
  *    everything in extension and alignment.
- *  - Limits: bank < 2^32 bases in total; query length < 65,536 bases; at most
- *    65,536 queries per gn_search call; k in 1..16; stride >= 1.
+ *  - Limits: bank < 2^32 bases in total; query length < 2^24 bases for gn_search
+ *    (over 65,535 in overlapping segments) and < 65,536 for the request loop; at
+ *    most 65,536 queries (or query segments) per gn_search call; k in 1..16;
+ *    stride >= 1.
  */
 #ifndef GENOOGLE_H
 #define GENOOGLE_H
@@ -206,8 +208,10 @@ GN_API gn_status gn_index_export(const gn_index *index, uint64_t *bucket_start, 
 
 /* Searches every query against the index ("Searching process", seven phases):
  * rolling k-mer codes of every query offset; lookup of each code's
- * occurrences (hits); grouping of the hits by (sequence, diagonal) with a radix
- * sort and merging of hits at most D query offsets apart into HSPs of length >=
+ * occurrences (hits); grouping of the hits by (query, diagonal) in per-query
+ * diagonal buckets (a repeat filter first drops hits alone on their diagonal;
+ * overflowing buckets go through a radix sort) and merging of hits at most D
+ * query offsets apart on one (sequence, diagonal) into HSPs of length >=
  * min_hsp_len; X-drop ungapped extension of both HSP ends; merging of
  * overlapped HSPs; selection of the longest max_alignments HSPs per query;
  * banded affine-gap Smith-Waterman of each selected HSP; ranking by score with
@@ -231,8 +235,10 @@ GN_API gn_status gn_search(const gn_index *index, const gn_queries *queries, con
                     const gn_params *params, void *cuda_stream, gn_results **out);
 GN_API void gn_results_free(gn_results *results);
 
-/* Ranked alignments of one query (rank order).  *hits stays valid until
- * gn_results_free. */
+/* Ranked alignments of one query ("Searching process", last phase: the alignments
+ * sorted by score with e-value and normalized score), in rank order.  *hits stays
+ * valid until gn_results_free.  Errors: GN_EINVAL (missing pointer, query index out
+ * of range). */
 GN_API gn_status gn_results_get(const gn_results *results, uint32_t query, const gn_hit **hits, uint32_t *n);
 GN_API gn_status gn_results_count(const gn_results *results, uint32_t *n_queries, uint64_t *n_hits);
 
@@ -274,23 +280,31 @@ GN_API uint64_t gn_kernel_launch_count(void);
  * order while their footprint fits mem_budget, run them as one micro-batch
  * (a gn_search on that worker's stream) while other micro-batches still run,
  * and make each result available to gn_serve_poll / gn_serve_poll_any.
- * A query's footprint is its exact hit count (from the index's bucket starts)
- * times 24 bytes, plus 64 bytes per base, 16 KiB of hit buckets and the
- * records of its selected HSPs; each micro-batch also counts 16 MiB of fixed
- * device memory.  Each query's result is identical to a gn_search of that
+ * A query's footprint is its exact seed-hit count times 24 bytes, plus 64
+ * bytes per base, 16 KiB of hit buckets and the records of its selected HSPs;
+ * each micro-batch also counts 16 MiB of fixed device memory.  The workers
+ * count the hits of waiting queries on the device, in arrival order and many at
+ * a time, before admitting them; when nothing runs, the oldest query starts at
+ * once, alone, with the whole budget (its hit storage capped to what the budget
+ * leaves), without waiting for its count.  Each query's result is identical to a gn_search of that
  * query alone.  mem_budget must exceed 16 MiB (GN_EINVAL otherwise).  The server
  * searches queries as given (GN_FLAG_BOTH_STRANDS and GN_FLAG_KEEP_* are ignored). */
 GN_API gn_status gn_serve_start(const gn_index *index, const gn_scoring *scoring, const gn_params *params,
                          uint64_t mem_budget, gn_server **out);
-/* Thread-safe; copies the query.  GN_ETOOBIG if the query alone exceeds the budget. */
+/* Thread-safe; copies the query and queues it (no other work on the caller's thread).
+ * GN_ETOOBIG for a query of 65,536 bases or more; a query whose footprint alone exceeds
+ * the budget fails later, at poll, with GN_ETOOBIG. */
 GN_API gn_status gn_serve_submit(gn_server *server, const char *bases, uint32_t len, uint64_t *ticket);
 /* Waits up to timeout_ms for the given ticket; GN_ETIMEOUT if not done yet.  On
  * GN_OK *out holds a one-query result owned by the caller (gn_results_free).  A
- * failed micro-batch returns GN_ECUDA for each of its tickets. */
+ * ticket that failed returns its error: GN_ETOOBIG (the query alone exceeds the
+ * budget), or the error of its micro-batch (GN_ENOMEM, GN_ECUDA, ...) for each of
+ * the batch's tickets; the server keeps serving. */
 GN_API gn_status gn_serve_poll(gn_server *server, uint64_t ticket, uint32_t timeout_ms, gn_results **out);
 /* Completion queue: waits up to timeout_ms for any finished ticket and returns
  * the oldest one in *ticket (GN_ETIMEOUT and *ticket = 0 if none finished).  On
- * GN_OK *out holds its one-query result; on GN_ECUDA that ticket failed. */
+ * GN_OK *out holds its one-query result; any other status is that ticket's error
+ * (as gn_serve_poll). */
 GN_API gn_status gn_serve_poll_any(gn_server *server, uint32_t timeout_ms, uint64_t *ticket, gn_results **out);
 /* Counters of a server since its start (for monitoring and tests). */
 typedef struct {
@@ -335,6 +349,18 @@ GN_API gn_status gn_serve_stop(gn_server *server);
 GN_API gn_status gn_align_hsps_static(const gn_index *index, const char *query_bases, const uint64_t *query_start,
                                       uint32_t n_queries, const gn_hsp *hsps, uint32_t n_hsps,
                                       const gn_scoring *scoring, uint32_t band_w, gn_hit *out, void *cuda_stream);
+
+/* ----------------------------------------------------- fault injection ---
+ * For tests of the error paths (the paper has no counterpart).  gn_debug_fail_alloc(n)
+ * makes the n-th device allocation that a search (gn_search, or a micro-batch of the
+ * request loop) makes from now on fail as if the device were out of memory: the call
+ * then returns GN_ENOMEM (a micro-batch fails its tickets with GN_ENOMEM) after freeing
+ * what it held.  n = 0 disables it.  gn_debug_alloc_count is the number of such
+ * allocations made so far in the process, gn_debug_live_allocs the number held now
+ * (0 between calls). */
+GN_API void gn_debug_fail_alloc(uint64_t nth);
+GN_API uint64_t gn_debug_alloc_count(void);
+GN_API int64_t gn_debug_live_allocs(void);
 
 /* Message of the last failing call on this thread ("" if none). */
 GN_API const char *gn_last_error(void);

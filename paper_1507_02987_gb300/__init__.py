@@ -130,6 +130,9 @@ def load():
             "gn_serve_get_stats": (st, [vp, ctypes.POINTER(gn_serve_stats)]),
             "gn_serve_stop": (st, [vp]),
             "gn_align_hsps_static": (st, [vp, vp, vp, u32, vp, u32, ctypes.POINTER(gn_scoring), u32, vp, vp]),
+            "gn_debug_fail_alloc": (None, [u64]),
+            "gn_debug_alloc_count": (u64, []),
+            "gn_debug_live_allocs": (ctypes.c_int64, []),
             "gn_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -146,6 +149,19 @@ def _check(status: int):
 
 
 # ------------------------------------------------------------ raw ABI --
+def gn_debug_fail_alloc(nth: int):
+    """The nth device allocation of a search from now on fails (GN_ENOMEM); 0 disables."""
+    load().gn_debug_fail_alloc(nth)
+
+
+def gn_debug_alloc_count() -> int:
+    return int(load().gn_debug_alloc_count())
+
+
+def gn_debug_live_allocs() -> int:
+    return int(load().gn_debug_live_allocs())
+
+
 def gn_default_params():
     sc, p = gn_scoring(), gn_params()
     _check(load().gn_default_params(ctypes.byref(sc), ctypes.byref(p)))

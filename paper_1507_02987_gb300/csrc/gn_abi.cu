@@ -67,10 +67,18 @@ static void check_queries(const gn_queries *q, uint64_t max_len = MAX_QUERY_LEN)
 }
 
 // ------------------------------------------------------------ serving --
+constexpr uint64_t FOOTPRINT_UNKNOWN = ~0ull;
+
+// A submitted query.  Its footprint is unknown until a worker has counted its seed hits
+// on the device (`counting` while one does); a request whose count failed carries the
+// error and fails when it reaches the head of the queue.
 struct Request {
     uint64_t ticket;
     std::string bases;
-    uint64_t footprint;
+    uint64_t footprint = FOOTPRINT_UNKNOWN;
+    bool counting = false;
+    gn_status status = GN_OK;
+    std::string err;
 };
 
 }  // namespace gn
@@ -85,10 +93,10 @@ struct gn_server {
     std::condition_variable cv_work, cv_done;
     std::deque<gn::Request> queue;
     std::map<uint64_t, gn_results *> done;
-    std::map<uint64_t, std::string> failed;
+    std::map<uint64_t, std::pair<gn_status, std::string>> failed;
     uint64_t next_ticket = 1;
+    uint64_t count_from = 1;  // requests with smaller tickets are counted, or being counted
     std::vector<std::thread> workers;
-    std::vector<uint64_t> off_h;  // host copy of the bucket starts: exact hit counts for admission
     int device = 0;
     gn_serve_stats stats{};
     uint64_t running = 0;  // micro-batches on the device now
@@ -99,84 +107,152 @@ namespace gn {
 // buffers, counters, scan scratch).
 constexpr uint64_t BATCH_FIXED_BYTES = 16ull << 20;
 
-static int host_base(char c) {
-    switch (c) {
-        case 'A': case 'a': return 0;
-        case 'C': case 'c': return 1;
-        case 'G': case 'g': return 2;
-        case 'T': case 't': case 'U': case 'u': return 3;
-        default: return -1;
-    }
+// Admission footprint of one query: its exact seed-hit count times the bytes a chunk
+// budgets per hit, its per-offset arrays, its smallest set of hit buckets (two of 1,024
+// entries), and the alignment records of its selected HSPs.
+static uint64_t footprint_of(const gn_server *sv, uint64_t hits, uint64_t len) {
+    const uint64_t n_sel = sv->opt.p.max_alignments ? sv->opt.p.max_alignments : 4096;
+    return hits * HIT_BYTES + len * 64 + 2 * 1024 * 8 + n_sel * (64 + 16 * (2ull * sv->opt.p.band_w + 2));
 }
 
-// Admission footprint of one query: its exact hit count (from the bucket starts) times the bytes
-// a chunk budgets per hit, its per-offset arrays, its smallest set of hit buckets (two of 1,024
-// entries), and the alignment records of its selected HSPs.
-static uint64_t footprint_of(const gn_server *sv, const char *bases, uint32_t len) {
-    // seed code of every query offset (kept positions of the index's seed shape)
-    const int span = sv->ix->span;
-    const uint32_t keep = sv->ix->keep;
-    uint64_t hits = 0;
-    if (keep == (span >= 32 ? 0xFFFFFFFFu : (1u << span) - 1u)) {
-        // contiguous seeds: rolling code, and the offset of the last non-base
-        const uint32_t mask = span >= 16 ? 0xFFFFFFFFu : (1u << (2 * span)) - 1u;
-        uint32_t code = 0;
-        int64_t last_bad = -1;
-        for (uint32_t x = 0; x < len; ++x) {
-            const int b = host_base(bases[x]);
-            if (b < 0) last_bad = x;
-            code = ((code << 2) | (uint32_t)(b < 0 ? 0 : b)) & mask;
-            if (x + 1 >= (uint32_t)span && last_bad < (int64_t)(x + 1 - span)) hits += sv->off_h[code + 1] - sv->off_h[code];
+// Requests a worker counts in one launch.
+constexpr size_t COUNT_MAX_REQUESTS = 4096;
+constexpr uint64_t COUNT_MAX_BASES = 16ull << 20;
+
+// Device buffer that only grows (one per worker and purpose).
+struct GrowBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    void *get(size_t bytes) {
+        if (bytes > cap) {
+            if (p) cudaFree(p);
+            p = nullptr;
+            cap = std::max<size_t>(bytes, 1 << 20);
+            GN_CUDA(cudaMalloc(&p, cap));
         }
-    } else {
-        for (uint32_t q = 0; q + (uint32_t)span <= len; ++q) {
-            uint32_t code = 0;
-            bool ok = true;
-            for (int p = 0; p < span && ok; ++p) {
-                if (!((keep >> p) & 1u)) continue;
-                const int b = host_base(bases[q + p]);
-                if (b < 0) ok = false;
-                else code = (code << 2) | (uint32_t)b;
-            }
-            if (ok) hits += sv->off_h[code + 1] - sv->off_h[code];
-        }
+        return p;
     }
-    const uint64_t n_sel = sv->opt.p.max_alignments ? sv->opt.p.max_alignments : 4096;
-    return hits * HIT_BYTES + (uint64_t)len * 64 + 2 * 1024 * 8 + n_sel * (64 + 16 * (2ull * sv->opt.p.band_w + 2));
-}
+    ~GrowBuf() {
+        if (p) cudaFree(p);
+    }
+};
 
 static void serve_worker(gn_server *sv) {
     cudaSetDevice(sv->device);
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
-    uint8_t *dbuf = nullptr;
-    size_t dcap = 0;
+    GrowBuf dbases, dstart, dhits;
+    auto first_uncounted = [&]() -> size_t {  // position of the first request not yet claimed for counting
+        auto it = std::lower_bound(sv->queue.begin(), sv->queue.end(), sv->count_from,
+                                   [](const Request &r, uint64_t t) { return r.ticket < t; });
+        return (size_t)(it - sv->queue.begin());
+    };
     for (;;) {
         std::vector<Request> batch;
+        std::vector<Request *> tocount;
         uint64_t taken = 0;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv_work.wait(lk, [&] {
-                return (sv->stopping && sv->queue.empty()) ||
-                       (!sv->queue.empty() &&
-                        sv->in_use + BATCH_FIXED_BYTES + sv->queue.front().footprint <= sv->budget);
+                if (sv->queue.empty()) return sv->stopping;
+                if (first_uncounted() < sv->queue.size()) return true;
+                const Request &f = sv->queue.front();
+                if (f.footprint == FOOTPRINT_UNKNOWN) return false;
+                return f.status != GN_OK || f.footprint + BATCH_FIXED_BYTES > sv->budget ||
+                       sv->in_use + BATCH_FIXED_BYTES + f.footprint <= sv->budget;
             });
             if (sv->queue.empty()) break;
-            // admit arrivals in order while they fit the memory budget (continuous batching)
-            taken = BATCH_FIXED_BYTES;
-            while (!sv->queue.empty() && batch.size() < MAX_QUERIES &&
-                   sv->in_use + taken + sv->queue.front().footprint <= sv->budget) {
-                taken += sv->queue.front().footprint;
+            const size_t k = first_uncounted();
+            const uint64_t rest = sv->budget - BATCH_FIXED_BYTES;
+            if (k == 0 && sv->running == 0 && sv->in_use == 0 &&
+                footprint_of(sv, 0, sv->queue.front().bases.size()) < rest) {
+                // nothing runs: the head request runs at once, alone, with the whole budget (its hit
+                // storage capped to what the budget leaves), without waiting for its count
+                taken = sv->budget;
+                sv->count_from = sv->queue.front().ticket + 1;
                 batch.push_back(std::move(sv->queue.front()));
                 sv->queue.pop_front();
+                sv->in_use += taken;
+                sv->stats.batches += 1;
+                sv->stats.requests += 1;
+                sv->stats.max_batch = std::max<uint64_t>(sv->stats.max_batch, 1);
+                sv->running += 1;
+                sv->stats.max_concurrent = std::max(sv->stats.max_concurrent, sv->running);
+                sv->stats.peak_in_use = std::max(sv->stats.peak_in_use, sv->in_use);
+            } else if (k < sv->queue.size()) {
+                // claim the next arrivals for counting (in arrival order)
+                uint64_t nb = 0;
+                for (size_t i = k; i < sv->queue.size() && tocount.size() < COUNT_MAX_REQUESTS && nb < COUNT_MAX_BASES;
+                     ++i) {
+                    Request &r = sv->queue[i];
+                    r.counting = true;
+                    tocount.push_back(&r);
+                    nb += r.bases.size();
+                }
+                sv->count_from = tocount.back()->ticket + 1;
+            } else {
+                Request &f = sv->queue.front();
+                if (f.status != GN_OK || f.footprint + BATCH_FIXED_BYTES > sv->budget) {
+                    // a request that cannot run: its count failed, or it alone exceeds the budget
+                    if (f.status != GN_OK) sv->failed[f.ticket] = {f.status, f.err};
+                    else sv->failed[f.ticket] = {GN_ETOOBIG, "the query alone exceeds the server's memory budget"};
+                    sv->queue.pop_front();
+                    lk.unlock();
+                    sv->cv_done.notify_all();
+                    continue;
+                }
+                // admit counted arrivals in order while they fit the memory budget (continuous batching)
+                taken = BATCH_FIXED_BYTES;
+                while (!sv->queue.empty() && batch.size() < MAX_QUERIES) {
+                    const Request &r = sv->queue.front();
+                    if (r.footprint == FOOTPRINT_UNKNOWN || r.status != GN_OK ||
+                        sv->in_use + taken + r.footprint > sv->budget)
+                        break;
+                    taken += r.footprint;
+                    batch.push_back(std::move(sv->queue.front()));
+                    sv->queue.pop_front();
+                }
+                sv->in_use += taken;
+                sv->stats.batches += 1;
+                sv->stats.requests += batch.size();
+                sv->stats.max_batch = std::max<uint64_t>(sv->stats.max_batch, batch.size());
+                sv->running += 1;
+                sv->stats.max_concurrent = std::max(sv->stats.max_concurrent, sv->running);
+                sv->stats.peak_in_use = std::max(sv->stats.peak_in_use, sv->in_use);
             }
-            sv->in_use += taken;
-            sv->stats.batches += 1;
-            sv->stats.requests += batch.size();
-            sv->stats.max_batch = std::max<uint64_t>(sv->stats.max_batch, batch.size());
-            sv->running += 1;
-            sv->stats.max_concurrent = std::max(sv->stats.max_concurrent, sv->running);
-            sv->stats.peak_in_use = std::max(sv->stats.peak_in_use, sv->in_use);
+        }
+        if (!tocount.empty()) {
+            // seed hits of the claimed requests, counted on the device (the requests stay in the
+            // queue: only the head is ever removed, and not while a request is being counted)
+            const uint32_t n = (uint32_t)tocount.size();
+            std::vector<uint64_t> start(n + 1, 0);
+            for (uint32_t i = 0; i < n; ++i) start[i + 1] = start[i] + tocount[i]->bases.size();
+            std::vector<unsigned long long> hits(n, 0);
+            gn_status st = guarded([&] {
+                std::string host;
+                host.reserve(start[n]);
+                for (auto *r : tocount) host += r->bases;
+                uint8_t *b = static_cast<uint8_t *>(dbases.get(std::max<uint64_t>(start[n], 1)));
+                uint64_t *st_d = static_cast<uint64_t *>(dstart.get(8 * (n + 1)));
+                unsigned long long *h_d = static_cast<unsigned long long *>(dhits.get(8 * n));
+                if (start[n]) GN_CUDA(cudaMemcpyAsync(b, host.data(), start[n], cudaMemcpyHostToDevice, s));
+                GN_CUDA(cudaMemcpyAsync(st_d, start.data(), 8 * (n + 1), cudaMemcpyHostToDevice, s));
+                count_request_hits(sv->ix, b, st_d, n, h_d, s);
+                GN_CUDA(cudaMemcpyAsync(hits.data(), h_d, 8 * n, cudaMemcpyDeviceToHost, s));
+                GN_CUDA(cudaStreamSynchronize(s));
+            });
+            const std::string err = st != GN_OK ? g_last_error : std::string();
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                for (uint32_t i = 0; i < n; ++i) {
+                    Request *r = tocount[i];
+                    r->counting = false;
+                    r->footprint = footprint_of(sv, hits[i], r->bases.size());
+                    if (st != GN_OK) { r->status = st; r->err = err; }
+                }
+            }
+            sv->cv_work.notify_all();
+            continue;
         }
         std::vector<uint64_t> qstart(batch.size() + 1, 0);
         for (size_t i = 0; i < batch.size(); ++i) qstart[i + 1] = qstart[i] + batch[i].bases.size();
@@ -184,26 +260,27 @@ static void serve_worker(gn_server *sv) {
         gn_results all;
         gn_status st = guarded([&] {
             uint64_t M = qstart.back();
-            if (M > dcap) {
-                if (dbuf) cudaFree(dbuf);
-                dbuf = nullptr;
-                dcap = std::max<uint64_t>(M, 1 << 20);
-                GN_CUDA(cudaMalloc(&dbuf, dcap));
-            }
+            uint8_t *b = static_cast<uint8_t *>(dbases.get(std::max<uint64_t>(M, 1)));
             std::string host;
             host.reserve(M);
             for (auto &r : batch) host += r.bases;
-            if (M) GN_CUDA(cudaMemcpyAsync(dbuf, host.data(), M, cudaMemcpyHostToDevice, s));
+            if (M) GN_CUDA(cudaMemcpyAsync(b, host.data(), M, cudaMemcpyHostToDevice, s));
             SearchOptions o = sv->opt;
-            o.mem_cap = taken - BATCH_FIXED_BYTES;  // the hit storage stays inside what was admitted
-            search(const_cast<gn_index *>(sv->ix), dbuf, qstart, o, s, &all);
+            // the hit storage stays inside what was admitted (a lone request admitted before its
+            // count: the budget less its other arrays)
+            o.mem_cap = taken - BATCH_FIXED_BYTES;
+            if (batch.size() == 1 && batch[0].footprint == FOOTPRINT_UNKNOWN) {
+                o.mem_cap -= footprint_of(sv, 0, batch[0].bases.size());
+                o.max_hit_bytes = o.mem_cap;  // as admission would: GN_ETOOBIG if it cannot fit even alone
+            }
+            search(const_cast<gn_index *>(sv->ix), b, qstart, o, s, &all);
         });
         if (st != GN_OK) err = g_last_error;
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             for (size_t i = 0; i < batch.size(); ++i) {
                 if (st != GN_OK) {
-                    sv->failed[batch[i].ticket] = err;
+                    sv->failed[batch[i].ticket] = {st, err};
                     continue;
                 }
                 gn_results *r = new gn_results();
@@ -219,7 +296,6 @@ static void serve_worker(gn_server *sv) {
         sv->cv_done.notify_all();
         sv->cv_work.notify_all();
     }
-    if (dbuf) cudaFree(dbuf);
     cudaStreamDestroy(s);
 }
 }  // namespace gn
@@ -542,8 +618,6 @@ gn_status gn_serve_start(const gn_index *ix, const gn_scoring *sc, const gn_para
         sv->budget = mem_budget;
         sv->device = ix->device;
         GN_CUDA(cudaSetDevice(ix->device));
-        sv->off_h.resize((1ull << (2 * ix->k)) + 1);
-        GN_CUDA(cudaMemcpy(sv->off_h.data(), ix->off_d, 8 * sv->off_h.size(), cudaMemcpyDeviceToHost));
         for (int w = 0; w < 3; ++w) sv->workers.emplace_back(serve_worker, sv);
     });
     if (st != GN_OK) { delete sv; return st; }
@@ -554,18 +628,12 @@ gn_status gn_serve_start(const gn_index *ix, const gn_scoring *sc, const gn_para
 gn_status gn_serve_submit(gn_server *sv, const char *bases, uint32_t len, uint64_t *ticket) {
     if (!sv || !ticket || (len && !bases)) { g_last_error = "server, bases and ticket are required"; return GN_EINVAL; }
     if (len > MAX_QUERY_LEN) { g_last_error = "a query holds 65,536 bases or more"; return GN_ETOOBIG; }
-    const uint64_t fp = footprint_of(sv, bases, len);
-    if (fp + BATCH_FIXED_BYTES > sv->budget) {
-        g_last_error = "the query alone exceeds the server's memory budget";
-        return GN_ETOOBIG;
-    }
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stopping) { g_last_error = "server is stopping"; return GN_EBUSY; }
         Request r;
         r.ticket = sv->next_ticket++;
         r.bases.assign(bases ? bases : "", len);
-        r.footprint = fp;
         *ticket = r.ticket;
         sv->queue.push_back(std::move(r));
     }
@@ -585,9 +653,10 @@ gn_status gn_serve_poll(gn_server *sv, uint64_t ticket, uint32_t timeout_ms, gn_
     }
     auto f = sv->failed.find(ticket);
     if (f != sv->failed.end()) {
-        g_last_error = f->second;
+        const gn_status st = f->second.first;
+        g_last_error = f->second.second;
         sv->failed.erase(f);
-        return GN_ECUDA;
+        return st;
     }
     auto it = sv->done.find(ticket);
     *out = it->second;
@@ -612,9 +681,10 @@ gn_status gn_serve_poll_any(gn_server *sv, uint32_t timeout_ms, uint64_t *ticket
     if (take_failed) {
         auto f = sv->failed.begin();
         *ticket = f->first;
-        g_last_error = f->second;
+        const gn_status st = f->second.first;
+        g_last_error = f->second.second;
         sv->failed.erase(f);
-        return GN_ECUDA;
+        return st;
     }
     auto it = sv->done.begin();
     *ticket = it->first;
@@ -654,6 +724,10 @@ gn_status gn_align_hsps_static(const gn_index *ix, const char *query_bases, cons
                           (cudaStream_t)cuda_stream);
     });
 }
+
+void gn_debug_fail_alloc(uint64_t nth) { debug_fail_alloc(nth); }
+uint64_t gn_debug_alloc_count(void) { return debug_alloc_count(); }
+int64_t gn_debug_live_allocs(void) { return debug_live_allocs(); }
 
 const char *gn_last_error(void) { return g_last_error.c_str(); }
 

@@ -109,6 +109,11 @@ private:
 
 void configure_mempool(int device);
 
+// Allocation fault injection and counters (tests): see gn_debug_fail_alloc.
+void debug_fail_alloc(uint64_t nth);
+uint64_t debug_alloc_count();
+int64_t debug_live_allocs();
+
 // ------------------------------------------------------------ packed DNA --
 // 16 bases per uint32 word, first base in the two most significant bits;
 // a parallel bitmap marks non-bases (bit g & 31 of word g >> 5).  One extra
@@ -302,10 +307,16 @@ void index_load(const char *path, gn_index *ix);
 
 inline SeqMap seq_map(const gn_index *ix) { return SeqMap{ix->seq_start_d, ix->seq_lut_d, ix->n_seqs}; }
 inline SeedShape seed_shape(const gn_index *ix) { return SeedShape{ix->k, ix->span, ix->keep}; }
+
+// Seed hits of each of n queries (ASCII bases and starts in device memory): hits[q] is the
+// sum of the occurrence-list lengths of query q's seed codes (request admission).
+void count_request_hits(const gn_index *ix, const uint8_t *bases, const uint64_t *start, uint32_t n,
+                        unsigned long long *hits, cudaStream_t s);
 struct SearchOptions {
     gn_scoring sc;
     gn_params p;           // resolved (no zero defaults left)
     uint64_t mem_cap = 0;  // device bytes the hit storage of one query chunk may take (0: 55 % of free)
+    uint64_t max_hit_bytes = 0;  // GN_ETOOBIG if the call's hits need more (HIT_BYTES each; 0: no limit)
 };
 // Query i -> queries 2i (as given) and 2i + 1 (reverse complement) in device memory from arena.
 void both_strands(const uint8_t *qbases_dev, const std::vector<uint64_t> &qstart_h, DeviceArena &arena,

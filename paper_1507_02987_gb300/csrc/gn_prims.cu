@@ -41,7 +41,21 @@ void configure_mempool(int device) {
     done[device] = true;
 }
 
+// Allocation fault injection (tests): the n-th next arena allocation fails as if the device
+// were out of memory.  Counters of arena allocations made and held.
+static std::atomic<uint64_t> g_fail_alloc_in{0};
+static std::atomic<uint64_t> g_alloc_count{0};
+static std::atomic<int64_t> g_live_allocs{0};
+
+void debug_fail_alloc(uint64_t nth) { g_fail_alloc_in.store(nth); }
+uint64_t debug_alloc_count() { return g_alloc_count.load(); }
+int64_t debug_live_allocs() { return g_live_allocs.load(); }
+
 void *DeviceArena::alloc(size_t bytes) {
+    uint64_t v = g_fail_alloc_in.load();
+    while (v && !g_fail_alloc_in.compare_exchange_weak(v, v - 1)) {
+    }
+    if (v == 1) throw Error{GN_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)"};
     void *p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 1, stream_);
     if (e != cudaSuccess) {
@@ -50,11 +64,14 @@ void *DeviceArena::alloc(size_t bytes) {
                                    cudaGetErrorString(e)};
     }
     ptrs_.push_back(p);
+    g_alloc_count.fetch_add(1);
+    g_live_allocs.fetch_add(1);
     return p;
 }
 
 void DeviceArena::release() {
     for (void *p : ptrs_) cudaFreeAsync(p, stream_);
+    g_live_allocs.fetch_sub((int64_t)ptrs_.size());
     ptrs_.clear();
 }
 

@@ -64,6 +64,52 @@ __global__ void k_query_codes(const uint64_t *__restrict__ qstart, uint32_t nq, 
     src[x] = (uint32_t)o;  // occurrence indices fit 32 bits: the bank holds < 2^32 bases
 }
 
+// Seed hits of each query of a batch (request admission): one block per query sums the
+// occurrence-list lengths of the seed codes of its offsets, read from ASCII bases.
+__device__ __forceinline__ uint32_t ascii_base_code(uint8_t b) {
+    const uint32_t c = b & 0xDFu;
+    return c == 'A' ? 0u : c == 'C' ? 1u : c == 'G' ? 2u : (c == 'T' || c == 'U') ? 3u : 4u;
+}
+
+__global__ void __launch_bounds__(256) k_request_hits(const uint8_t *__restrict__ bases,
+                                                      const uint64_t *__restrict__ start, uint32_t n, SeedShape sh,
+                                                      const uint64_t *__restrict__ off,
+                                                      unsigned long long *__restrict__ hits) {
+    __shared__ unsigned long long part[8];
+    for (uint32_t q = blockIdx.x; q < n; q += gridDim.x) {
+        const uint64_t b0 = start[q], m = start[q + 1] - b0;
+        unsigned long long sum = 0;
+        for (uint64_t x = threadIdx.x; x + (uint64_t)sh.span <= m; x += blockDim.x) {
+            uint32_t code = 0;
+            bool ok = true;
+            for (int p = 0; p < sh.span; ++p) {
+                if (!((sh.keep >> p) & 1u)) continue;
+                const uint32_t c = ascii_base_code(bases[b0 + x + p]);
+                ok = ok && c < 4u;
+                code = (code << 2) | (c & 3u);
+            }
+            if (ok) sum += off[code + 1] - off[code];
+        }
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+            hits[q] = t;
+        }
+        __syncthreads();
+    }
+}
+
+void count_request_hits(const gn_index *ix, const uint8_t *bases, const uint64_t *start, uint32_t n,
+                        unsigned long long *hits, cudaStream_t s) {
+    if (!n) return;
+    GN_LAUNCH("k_request_hits", n, s,
+              k_request_hits<<<(unsigned)std::min<uint32_t>(n, (uint32_t)num_sms() * 8), 256, 0, s>>>(
+                  bases, start, n, seed_shape(ix), ix->off_d, hits));
+}
+
 __global__ void k_gather_u64(const uint64_t *__restrict__ src, const uint64_t *__restrict__ idx, uint32_t n,
                              uint64_t *__restrict__ out) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2277,6 +2323,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     GN_LAUNCH("k_gather_u64", hnq + 1, s,
               k_gather_u64<<<blocks_for(hnq + 1), 256, 0, s>>>(hoff, hstart_d, hnq + 1, hq_d));
     std::vector<uint64_t> hq = to_host(hq_d, hnq + 1, s);
+    GN_REQUIRE(!o.max_hit_bytes || hq[hnq] * HIT_BYTES <= o.max_hit_bytes, GN_ETOOBIG,
+               "the query alone exceeds the server's memory budget");
     timer.mark("query_codes");
     if (keep) {
         res->st_hit_counts.resize(hnq);
@@ -2851,7 +2899,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     uint32_t st = 0;
     GN_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
     res->hits = to_host(fin, n_out, s);
-    GN_REQUIRE((st & (DEV_ERR_BAND_TOO_WIDE | DEV_ERR_BOUNDS)) == 0, GN_ETOOBIG,
+    GN_REQUIRE((st & DEV_ERR_BOUNDS) == 0, GN_EINTERNAL, "a device-side bounds check failed");
+    GN_REQUIRE((st & DEV_ERR_BAND_TOO_WIDE) == 0, GN_ETOOBIG,
                "an alignment band exceeded 65,535 diagonals or its window 2^32 cells");
     res->qoff.assign(nq + 1, 0);
     for (uint32_t i = 0; i < n_out; ++i) res->qoff[res->hits[i].query + 1]++;

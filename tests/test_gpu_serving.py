@@ -129,8 +129,11 @@ def test_admission_limits(gn, served):
         gn.Server(ix, 16 << 20)
     assert e.value.status == gn.GN_EINVAL
     srv = gn.Server(ix, (16 << 20) + (1 << 20))
+    # 60,000 bases: 3.84 MB of per-offset arrays alone; submit only queues it, and the
+    # ticket fails with GN_ETOOBIG once its footprint is known
+    big = srv.submit(b"ACGT" * 15000)
     with pytest.raises(gn.GnError) as e:
-        srv.submit(b"ACGT" * 15000)  # 60,000 bases: 3.84 MB of per-offset arrays alone
+        srv.poll(big, 60000)
     assert e.value.status == gn.GN_ETOOBIG
     with pytest.raises(gn.GnError) as e:
         srv.submit(b"A" * 70000)
