@@ -54,7 +54,8 @@ BYTES_PER_UNIT = {
 # cell (E and F: add + max each; H: substitution select, add, three-way max with 0)
 ALU_KERNELS = {"k_banded_sw", "k_banded_sw_wide"}
 ALU_OPS_PER_UNIT = 8.0
-INT_LANES_PER_SM = 128   # 32-bit integer lanes per SM (4 partitions x 32)
+# their peak: integer operations per second measured in the same run by gn_measure_int_peaks
+# (DPX add-max, two operations per instruction, every SM filled)
 
 
 def parse_args():
@@ -591,6 +592,8 @@ def run_ours(args, dist):
 
     # ---- roofline of the dominant kernel (and of the next ones)
     peaks = measured_peaks()
+    int_peaks = gn.gn_measure_int_peaks(sh)
+    torch.cuda.synchronize()
     try:
         n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     except Exception:
@@ -599,11 +602,11 @@ def run_ours(args, dist):
     def roof_for(name):
         ms, la, un = kern[name]
         if name in ALU_KERNELS:
-            mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz")
-            peak = (n_sms * INT_LANES_PER_SM * mhz * 1e6 / 1e12) if (n_sms and mhz) else None
+            peak = int_peaks["dpx_addmax_ops"] / 1e12 if int_peaks else None
             achieved = un * ALU_OPS_PER_UNIT / (ms / 1e3) / 1e12
             return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                    "peak_source": "derived: SMs x 128 integer lanes x median SM clock under load" if peak else None,
+                    "peak_source": ("measured in this run: DPX add-max (__viaddmax_s32) throughput, 2 operations "
+                                    "per instruction, all SMs") if peak else None,
                     "frac": (achieved / peak) if peak else None, "traffic": None,
                     "gcups": un / (ms / 1e3) / 1e9, "avg_launch_ms": ms / la, "launches": la}
         bpu = BYTES_PER_UNIT.get(name)
@@ -670,6 +673,7 @@ def run_ours(args, dist):
                 "clocks": clk, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / max(1, args.steps), "roofline": roof,
                 "kernel_rooflines": roofs,
+                "int_peaks_tops": {k: (v / 1e12 if k != "sms" else v) for k, v in int_peaks.items()},
                 "cpu_baseline": cpu, "plain_per_query": plain, "serving": serve, "sub_legs": legs,
                 "oracle_parity_on_sample": parity,
                 "index_build": {"seconds": t_index, "bank_gbp_per_s": bank.n_bases / 1e9 / t_index,

@@ -350,6 +350,21 @@ GN_API gn_status gn_align_hsps_static(const gn_index *index, const char *query_b
                                       uint32_t n_queries, const gn_hsp *hsps, uint32_t n_hsps,
                                       const gn_scoring *scoring, uint32_t band_w, gn_hit *out, void *cuda_stream);
 
+/* ------------------------------------------------ integer-pipe peaks ---
+ * Measured throughput of this GPU's integer pipes (no counterpart in the paper: it
+ * is the denominator of the alignment kernel's roofline).  Each figure is operations
+ * per second over the whole device, with every SM filled: a three-input add (2
+ * operations), max(a + b, c) as plain C (2), the DPX add-max __viaddmax_s32 (2 in
+ * one instruction), the DPX three-way max __vimax3_s32 (2), and the DPX max with its
+ * predicate __vibmax_s32 after an add (2, plus a select by the predicate).  Runs for
+ * some milliseconds on cuda_stream and allocates 64 bytes of device memory.
+ * Errors: GN_EINVAL (out is NULL), GN_ENOMEM, GN_ECUDA. */
+typedef struct {
+    double add3_ops, addmax_plain_ops, dpx_addmax_ops, dpx_max3_ops, dpx_bmax_ops;
+    uint32_t sms;
+} gn_int_peaks;
+GN_API gn_status gn_measure_int_peaks(gn_int_peaks *out, void *cuda_stream);
+
 /* ----------------------------------------------------- fault injection ---
  * For tests of the error paths (the paper has no counterpart).  gn_debug_fail_alloc(n)
  * makes the n-th device allocation that a search (gn_search, or a micro-batch of the

@@ -68,6 +68,11 @@ class gn_serve_stats(ctypes.Structure):
                                                  "peak_in_use", "in_use", "queued")]
 
 
+class gn_int_peaks(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("add3_ops", "addmax_plain_ops", "dpx_addmax_ops", "dpx_max3_ops",
+                                                "dpx_bmax_ops")] + [("sms", ctypes.c_uint32)]
+
+
 class gn_index_info(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("stride", ctypes.c_int32), ("n_seqs", ctypes.c_uint32),
                 ("n_bases", ctypes.c_uint64), ("n_postings", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
@@ -130,6 +135,7 @@ def load():
             "gn_serve_get_stats": (st, [vp, ctypes.POINTER(gn_serve_stats)]),
             "gn_serve_stop": (st, [vp]),
             "gn_align_hsps_static": (st, [vp, vp, vp, u32, vp, u32, ctypes.POINTER(gn_scoring), u32, vp, vp]),
+            "gn_measure_int_peaks": (st, [ctypes.POINTER(gn_int_peaks), vp]),
             "gn_debug_fail_alloc": (None, [u64]),
             "gn_debug_alloc_count": (u64, []),
             "gn_debug_live_allocs": (ctypes.c_int64, []),
@@ -149,6 +155,13 @@ def _check(status: int):
 
 
 # ------------------------------------------------------------ raw ABI --
+def gn_measure_int_peaks(stream: int = 0) -> dict:
+    """Measured integer-pipe throughput of the current GPU (operations per second)."""
+    o = gn_int_peaks()
+    _check(load().gn_measure_int_peaks(ctypes.byref(o), ctypes.c_void_p(stream)))
+    return {n: getattr(o, n) for n, _ in gn_int_peaks._fields_}
+
+
 def gn_debug_fail_alloc(nth: int):
     """The nth device allocation of a search from now on fails (GN_ENOMEM); 0 disables."""
     load().gn_debug_fail_alloc(nth)

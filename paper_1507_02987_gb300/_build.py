@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgenoogle.so")
-SOURCES = ["gn_prims.cu", "gn_index.cu", "gn_search.cu", "gn_abi.cu", "gn_noalloc.cu"]
+SOURCES = ["gn_prims.cu", "gn_index.cu", "gn_search.cu", "gn_abi.cu", "gn_noalloc.cu", "gn_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

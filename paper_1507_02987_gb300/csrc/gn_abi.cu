@@ -725,6 +725,10 @@ gn_status gn_align_hsps_static(const gn_index *ix, const char *query_bases, cons
     });
 }
 
+gn_status gn_measure_int_peaks(gn_int_peaks *out, void *cuda_stream) {
+    return guarded([&] { measure_int_peaks(out, (cudaStream_t)cuda_stream); });
+}
+
 void gn_debug_fail_alloc(uint64_t nth) { debug_fail_alloc(nth); }
 uint64_t gn_debug_alloc_count(void) { return debug_alloc_count(); }
 int64_t gn_debug_live_allocs(void) { return debug_live_allocs(); }

@@ -109,6 +109,9 @@ private:
 
 void configure_mempool(int device);
 
+// Integer-pipe throughput (gn_measure_int_peaks).
+void measure_int_peaks(gn_int_peaks *out, cudaStream_t s);
+
 // Allocation fault injection and counters (tests): see gn_debug_fail_alloc.
 void debug_fail_alloc(uint64_t nth);
 uint64_t debug_alloc_count();

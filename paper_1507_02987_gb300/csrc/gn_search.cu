@@ -1508,7 +1508,14 @@ __device__ __forceinline__ uint32_t segwin_code(const SegWin &wn, uint32_t o) {
 // in registers.  All segments step through rows together.  The vertical-gap input of
 // offset b is offset b + 1 of the previous row (own state, or the next lane's first
 // offset); horizontal gaps come from a segmented warp max-scan as in the pair path.
-// Returns false (and computes nothing) for an HSP whose band exceeds G K offsets.
+// A cell outside the DP region keeps H = 0 and E = -inf as its state, so the next row
+// reads its neighbours without range checks: a neutral neighbour yields only E <= 0 and
+// a diagonal from H = 0, neither of which can raise a score (an alignment may begin at
+// any cell); a per-row bit mask of the lane's cells in the region masks the stored
+// state and the best cell.  Every tracked maximum is a DPX max with its predicate
+// (__vibmax_s32: the first operand wins ties), which also selects the start cell.
+// Returns with handled = false (and computes nothing) for an HSP whose band exceeds G K
+// offsets.
 template <int G, int K>
 __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint32_t *__restrict__ qpk,
                                          const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
@@ -1537,12 +1544,20 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
     const int32_t max_rows = __reduce_max_sync(0xffffffffu, (uint32_t)rows);
     const int32_t jlo = (int32_t)(J0 - I0 - dlo), jhi = (int32_t)(J1 - 1 - I0 - dlo);
     const int32_t Bm1 = (int32_t)B - 1;
+    const int32_t b0 = K * sl;
+    // per-offset constants: X(b) = H0(b) + cX[k], F(b) = max_{b' < b} X(b') + cF[k]
+    int32_t cX[K], cF[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        cX[k] = goe - ge * (b0 + k);
+        cF[k] = ge * (b0 + k - 1);
+    }
     int32_t pH[K], pE[K];
     uint32_t pSH[K], pSE[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) { pH[k] = 0; pE[k] = SW_NEG; pSH[k] = 0; pSE[k] = 0; }
-    int32_t best = 0, br = INT32_MAX, bb = INT32_MAX;
-    uint32_t bs = 0;
+    int32_t best = 0;
+    uint32_t bpos = 0xFFFFFFFFu, bs = 0;  // best cell: row << 16 | band offset, and its start cell
     // bases: one 64-base window per segment (bands of up to 49 diagonals), else a
     // 32-base window per lane
     constexpr bool SEG = G * K <= 49;
@@ -1555,14 +1570,16 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
     for (int32_t r = 0; r < max_rows; ++r) {
         const bool seg_on = r < rows;
         const int32_t blo = max(0, jlo - r), bhi = min(Bm1, jhi - r);
-        const int32_t pblo = max(0, jlo - r + 1), pbhi = min(Bm1, jhi - r + 1);
-        const bool prow = r > 0;
-        // previous-row state of offset K (sl + 1) (the next lane's first offset)
-        const int32_t uH = __shfl_down_sync(0xffffffffu, pH[0], 1, G), uE = __shfl_down_sync(0xffffffffu, pE[0], 1, G);
+        // the lane's offsets b0 + k inside [blo, bhi]
+        const int32_t klo = max(blo - b0, 0), khi = min(bhi - b0, K - 1);
+        const uint32_t amask = (seg_on && klo <= khi) ? ((2u << khi) - 1u) & ~((1u << klo) - 1u) : 0u;
+        const bool lane_on = amask != 0u;
+        // previous-row state of offset K (sl + 1) (the next lane's first offset); the last lane's
+        // is beyond the band
+        int32_t uH = __shfl_down_sync(0xffffffffu, pH[0], 1, G), uE = __shfl_down_sync(0xffffffffu, pE[0], 1, G);
         const uint32_t uSH = __shfl_down_sync(0xffffffffu, pSH[0], 1, G);
         const uint32_t uSE = __shfl_down_sync(0xffffffffu, pSE[0], 1, G);
-        const int32_t b0 = K * sl;
-        bool lane_on = seg_on && b0 <= bhi && b0 + K - 1 >= blo;
+        if (sl == G - 1) { uH = 0; uE = SW_NEG; }
         uint32_t qc = 4u;
         const uint64_t i = (uint64_t)(I0 + r);
         const uint64_t jb = sb + (uint64_t)((int64_t)i + dlo + b0);  // bank position of offset b0
@@ -1587,72 +1604,77 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
             dcodes = segwin_codes(sd, o0);
             dbad = segwin_bad(sd, o0);
         }
+        const uint32_t rowbase = (uint32_t)r << 16;
         int32_t H0[K], E[K], X[K];
         uint32_t C[K], SE[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const int32_t b = b0 + k;
-            const bool act = lane_on && b >= blo && b <= bhi;
-            // vertical gap from offset b + 1 of the previous row
+            // vertical gap from offset b + 1 of the previous row: open wins ties
             const int32_t vH = k + 1 < K ? pH[k + 1] : uH, vE = k + 1 < K ? pE[k + 1] : uE;
             const uint32_t vSH = k + 1 < K ? pSH[k + 1] : uSH, vSE = k + 1 < K ? pSE[k + 1] : uSE;
-            E[k] = SW_NEG;
-            SE[k] = 0;
-            if (act && prow && b + 1 >= pblo && b + 1 <= pbhi) {
-                const int32_t eo = vH + goe, ee = vE + ge;
-                if (eo >= ee) { E[k] = eo; SE[k] = vSH; } else { E[k] = ee; SE[k] = vSE; }
-            }
-            const bool okd = act && prow && b >= pblo && b <= pbhi;
-            const int32_t Hd = okd ? pH[k] : 0;
-            const uint32_t SD = (Hd > 0) ? pSH[k] : ((uint32_t)r << 16) | (uint32_t)b;
-            const uint32_t d = act ? (SEG ? (((dbad >> k) & 1u) ? 4u : (uint32_t)(dcodes >> (62 - 2 * k)) & 3u)
-                                          : wd.at(jb + k))
-                                   : 4u;
-            const int32_t Dg = Hd + dev_pair(qc, d, match, mismatch);
-            int32_t cv;
-            if (Dg >= E[k]) { cv = Dg; C[k] = SD; } else { cv = E[k]; C[k] = SE[k]; }
-            H0[k] = cv > 0 ? cv : 0;
-            X[k] = act ? H0[k] + goe - ge * b : SW_XNEG;
+            bool po;
+            E[k] = __vibmax_s32(vH + goe, vE + ge, &po);
+            SE[k] = po ? vSH : vSE;
+            // diagonal: from the previous row's H, or a start here
+            const int32_t Hd = pH[k];
+            const uint32_t SD = Hd > 0 ? pSH[k] : rowbase | (uint32_t)(b0 + k);
+            uint32_t d;
+            if (SEG) d = ((dbad >> k) & 1u) ? 4u : (uint32_t)(dcodes >> (62 - 2 * k)) & 3u;
+            else d = lane_on ? wd.at(jb + k) : 4u;
+            const int32_t Dg = Hd + ((qc < 4u && d == qc) ? match : mismatch);
+            // diagonal over E on ties
+            bool pd;
+            const int32_t cv = __vibmax_s32(Dg, E[k], &pd);
+            C[k] = pd ? SD : SE[k];
+            H0[k] = max(cv, 0);
+            X[k] = H0[k] + cX[k];
         }
         // lane aggregate of X (later offsets win ties), then the segmented scan over lanes
         int32_t xv = X[0];
         uint32_t xs = C[0];
 #pragma unroll
-        for (int k = 1; k < K; ++k)
-            if (X[k] >= xv) { xv = X[k]; xs = C[k]; }
+        for (int k = 1; k < K; ++k) {
+            bool p;
+            xv = __vibmax_s32(X[k], xv, &p);
+            xs = p ? C[k] : xs;
+        }
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) {
             const int32_t ov = __shfl_up_sync(0xffffffffu, xv, o, G);
             const uint32_t os = __shfl_up_sync(0xffffffffu, xs, o, G);
-            if (sl >= o && ov > xv) { xv = ov; xs = os; }
+            bool p;
+            xv = __vibmax_s32(xv, sl >= o ? ov : SW_XNEG, &p);
+            xs = p ? xs : os;
         }
         int32_t ev = __shfl_up_sync(0xffffffffu, xv, 1, G);
         uint32_t es = __shfl_up_sync(0xffffffffu, xs, 1, G);
         if (sl == 0) { ev = SW_XNEG; es = 0; }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const int32_t b = b0 + k;
-            const bool act = lane_on && b >= blo && b <= bhi;
-            const int32_t F = (ev > SW_XNEG) ? ev + ge * (b - 1) : SW_NEG;
-            int32_t Hv;
-            uint32_t S;
-            if (H0[k] >= F) { Hv = H0[k]; S = C[k]; } else { Hv = F; S = es; }
-            if (X[k] >= ev) { ev = X[k]; es = C[k]; }
-            if (act && Hv > best) { best = Hv; br = r; bb = b; bs = S; }
-            pH[k] = Hv; pE[k] = E[k]; pSH[k] = S; pSE[k] = SE[k];
+            // H0 over F on ties
+            bool ph;
+            const int32_t Hv = __vibmax_s32(H0[k], ev + cF[k], &ph);
+            const uint32_t S = ph ? C[k] : es;
+            bool px;
+            ev = __vibmax_s32(X[k], ev, &px);
+            es = px ? C[k] : es;
+            const bool act = (amask >> k) & 1u;
+            const int32_t Hm = act ? Hv : 0;
+            if (Hm > best) { best = Hm; bpos = rowbase | (uint32_t)(b0 + k); bs = S; }
+            pH[k] = Hm; pE[k] = act ? E[k] : SW_NEG; pSH[k] = S; pSE[k] = SE[k];
         }
     }
     // segment reduction: highest score, then smallest row, then smallest offset (smallest j)
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         const int32_t ob = __shfl_down_sync(0xffffffffu, best, o, G);
-        const int32_t orr = __shfl_down_sync(0xffffffffu, br, o, G), obb = __shfl_down_sync(0xffffffffu, bb, o, G);
+        const uint32_t op = __shfl_down_sync(0xffffffffu, bpos, o, G);
         const uint32_t os = __shfl_down_sync(0xffffffffu, bs, o, G);
-        if (ob > best || (ob == best && (orr < br || (orr == br && obb < bb)))) { best = ob; br = orr; bb = obb; bs = os; }
+        if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; bs = os; }
     }
     res.qi = h.qi; res.seq = h.seq; res.qs = res.qe = res.ds = res.de = 0; res.score = 0; res.pad = 0;
     if (handled && best > 0) {
-        const int64_t bi = I0 + br, bj = bi + dlo + bb;
+        const int64_t bi = I0 + (int64_t)(bpos >> 16), bj = bi + dlo + (int64_t)(bpos & 0xFFFFu);
         const int64_t i0 = I0 + (int64_t)(bs >> 16), j0 = i0 + dlo + (int64_t)(bs & 0xFFFFu);
         res.qs = (uint32_t)i0; res.qe = (uint32_t)(bi + 1);
         res.ds = (uint32_t)j0; res.de = (uint32_t)(bj + 1);
@@ -1809,7 +1831,7 @@ __device__ __forceinline__ void sw_wave(const DevHsp &h, const uint32_t *__restr
 // whose band fits SWG_G x SWG_K offsets, and the whole warp then aligns the others one by
 // one (pair or strip path).
 constexpr int SWG_G = 8, SWG_K = 5;
-__global__ void __launch_bounds__(128) k_banded_sw(const DevHsp *__restrict__ sel, uint32_t n,
+__global__ void __launch_bounds__(128, 1) k_banded_sw(const DevHsp *__restrict__ sel, uint32_t n,
                                                    const uint64_t *__restrict__ strip_off, SwCell *__restrict__ strips,
                                                    const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
                                                    const uint64_t *__restrict__ qstart,
