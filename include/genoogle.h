@@ -45,7 +45,7 @@ typedef enum {
     GN_EINVAL = 1,    /* invalid argument (k, stride, lengths, null pointers, ...) */
     GN_ENOMEM = 2,    /* device or host allocation failed */
     GN_ECUDA = 3,     /* a CUDA call or a kernel-side check failed */
-    GN_ETIMEOUT = 4,  /* a bounded wait ran out (serving poll, device waits) */
+    GN_ETIMEOUT = 4,  /* a bounded wait ran out (serving poll, device-side waits of a scan) */
     GN_EBUSY = 5,     /* the server is stopping or its queue is full */
     GN_ETOOBIG = 6,   /* the request exceeds a documented limit or the memory budget */
     GN_EINTERNAL = 7  /* broken internal invariant (a bug) */
@@ -374,6 +374,15 @@ GN_API gn_status gn_measure_int_peaks(gn_int_peaks *out, void *cuda_stream);
  * allocations made so far in the process, gn_debug_live_allocs the number held now
  * (0 between calls). */
 GN_API void gn_debug_fail_alloc(uint64_t nth);
+/* The library's single-pass scan (decoupled look-back: each block of the launch waits for
+ * the blocks before it to publish their sums), for tests of its bounded wait:
+ * out[i] = in[0] + ... + in[i-1] and out[n] = the total; in (n uint32) and out (n + 1
+ * uint64) are device memory.  wait_cycles bounds each block's wait (SM clock cycles;
+ * 0 = the library's default, about a second); drop_first = 1 keeps the first tile of
+ * 2,048 elements from publishing its sum, so that the waits behind it run out.  Returns
+ * GN_ETIMEOUT if a wait ran out (out is then wrong), after the stream has finished. */
+GN_API gn_status gn_debug_scan(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t wait_cycles, int drop_first,
+                               void *cuda_stream);
 GN_API uint64_t gn_debug_alloc_count(void);
 GN_API int64_t gn_debug_live_allocs(void);
 

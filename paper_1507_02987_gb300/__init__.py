@@ -137,6 +137,7 @@ def load():
             "gn_align_hsps_static": (st, [vp, vp, vp, u32, vp, u32, ctypes.POINTER(gn_scoring), u32, vp, vp]),
             "gn_measure_int_peaks": (st, [ctypes.POINTER(gn_int_peaks), vp]),
             "gn_debug_fail_alloc": (None, [u64]),
+            "gn_debug_scan": (st, [vp, vp, u64, u64, ctypes.c_int, vp]),
             "gn_debug_alloc_count": (u64, []),
             "gn_debug_live_allocs": (ctypes.c_int64, []),
             "gn_last_error": (ctypes.c_char_p, []),
@@ -165,6 +166,13 @@ def gn_measure_int_peaks(stream: int = 0) -> dict:
 def gn_debug_fail_alloc(nth: int):
     """The nth device allocation of a search from now on fails (GN_ENOMEM); 0 disables."""
     load().gn_debug_fail_alloc(nth)
+
+
+def gn_debug_scan(in_ptr: int, out_ptr: int, n: int, wait_cycles: int = 0, drop_first: bool = False,
+                  stream: int = 0):
+    """The library's single-pass scan on device buffers (tests of its bounded wait)."""
+    _check(load().gn_debug_scan(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), n, wait_cycles,
+                                1 if drop_first else 0, ctypes.c_void_p(stream)))
 
 
 def gn_debug_alloc_count() -> int:

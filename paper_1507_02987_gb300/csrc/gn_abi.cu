@@ -730,6 +730,16 @@ gn_status gn_measure_int_peaks(gn_int_peaks *out, void *cuda_stream) {
 }
 
 void gn_debug_fail_alloc(uint64_t nth) { debug_fail_alloc(nth); }
+
+gn_status gn_debug_scan(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t wait_cycles, int drop_first,
+                        void *cuda_stream) {
+    return guarded([&] {
+        GN_REQUIRE(out && (n == 0 || in), GN_EINVAL, "in and out are required");
+        const long long budget = wait_cycles ? (long long)std::min<uint64_t>(wait_cycles, 1ull << 40) : (1ll << 31);
+        const bool ran_out = debug_scan(in, out, n, budget, drop_first ? 1 : 0, (cudaStream_t)cuda_stream);
+        GN_REQUIRE(!ran_out, GN_ETIMEOUT, "a device-side wait ran out (scan look-back)");
+    });
+}
 uint64_t gn_debug_alloc_count(void) { return debug_alloc_count(); }
 int64_t gn_debug_live_allocs(void) { return debug_live_allocs(); }
 

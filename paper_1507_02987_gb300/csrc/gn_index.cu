@@ -144,6 +144,9 @@ static void index_build_shape(const gn_bank *db, int k, int span, uint32_t keep,
         GN_CUDA(cudaMemsetAsync(ix->seq_lut_d, 0, sizeof(uint32_t) * nlut, s));
 
     DeviceArena arena(s);
+    uint32_t *wait_status = arena.alloc_n<uint32_t>(1);  // bounded waits of the scans
+    GN_CUDA(cudaMemsetAsync(wait_status, 0, 4, s));
+    WaitStatusScope wscope(wait_status);
     // K1: 2-bit packing of the bank
     const uint8_t *bases_d = reinterpret_cast<const uint8_t *>(db->bases);
     if (db->bases_mem == GN_MEM_HOST && n > 0) {
@@ -203,8 +206,11 @@ static void index_build_shape(const gn_bank *db, int k, int span, uint32_t keep,
         GN_LAUNCH("k_low_words", P, s,
                   k_low_words<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(flipped ? keys_alt : keys, P, ix->post_d));
     }
+    uint32_t wst = 0;
+    GN_CUDA(cudaMemcpyAsync(&wst, wait_status, 4, cudaMemcpyDeviceToHost, s));
     arena.release();
     GN_CUDA(cudaStreamSynchronize(s));
+    GN_REQUIRE((wst & DEV_ERR_TIMEOUT) == 0, GN_ETIMEOUT, "a device-side wait ran out (scan look-back)");
     ix->device_bytes = bytes;
 }
 

@@ -80,6 +80,7 @@ enum : uint32_t {
     DEV_ERR_BAND_TOO_WIDE = 1u,   // alignment band wider than the start encoding allows
     DEV_ERR_CAPACITY = 2u,        // an output buffer was too small (caller retries with more room)
     DEV_ERR_BOUNDS = 4u,          // an index fell outside its buffer
+    DEV_ERR_TIMEOUT = 8u,         // a bounded device-side wait ran out
 };
 
 // ------------------------------------------------------------- constants --
@@ -132,9 +133,19 @@ struct Packed {
 void pack_bases(const uint8_t *ascii_dev, uint64_t n, Packed &out, cudaStream_t s);
 
 // --------------------------------------------------------------- scans --
-// out[i] = sum(in[0..i)), out[n] = total; out has n + 1 entries.
+// out[i] = sum(in[0..i)), out[n] = total; out has n + 1 entries.  One pass over the data
+// (decoupled look-back); a wait that runs out records DEV_ERR_TIMEOUT in *g_wait_status
+// (the calling thread's current search or index build) when it is set.
 size_t scan_scratch_bytes(uint64_t n);
 void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scratch, cudaStream_t s);
+extern thread_local uint32_t *g_wait_status;
+bool debug_scan(const uint32_t *in, uint64_t *out, uint64_t n, long long budget, int drop_first, cudaStream_t s);
+// Sets g_wait_status for the scope (a device word the caller checks for DEV_ERR_TIMEOUT).
+struct WaitStatusScope {
+    uint32_t *prev;
+    explicit WaitStatusScope(uint32_t *w) : prev(g_wait_status) { g_wait_status = w; }
+    ~WaitStatusScope() { g_wait_status = prev; }
+};
 
 // ----------------------------------------------------------- radix sort --
 // Stable LSD radix sort of 64-bit keys (optionally carrying 32-bit values) on

@@ -124,9 +124,6 @@ void pack_bases(const uint8_t *ascii_dev, uint64_t n, Packed &out, cudaStream_t 
 }
 
 // ----------------------------------------------------------------- scans --
-constexpr int SC_THREADS = 256;
-constexpr int SC_ITEMS = 16;
-constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
 
 template <class T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
@@ -158,66 +155,97 @@ __device__ __forceinline__ T block_excl_scan(T v, T *warp_sums, T *total) {
     return r;
 }
 
-__global__ void k_scan_reduce(const uint32_t *__restrict__ in, uint64_t n, uint64_t *__restrict__ sums) {
-    __shared__ uint64_t ws[SC_THREADS / 32];
-    __shared__ uint64_t tot;
-    uint64_t base = (uint64_t)blockIdx.x * SC_TILE;
-    uint64_t s = 0;
-#pragma unroll 4
-    for (int j = 0; j < SC_ITEMS; ++j) {
-        uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
-        if (i < n) s += in[i];
-    }
-    block_excl_scan<uint64_t, SC_THREADS>(s, ws, &tot);
-    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
+// Single-pass scan with decoupled look-back.  A block takes the next tile from a ticket
+// counter (so every tile it waits on belongs to a block that is already running), sums
+// it, publishes the sum in the tile's state word, then its first warp reads the states of
+// the preceding tiles 32 at a time, adding sums until it meets a tile whose inclusive
+// prefix is published; the block then publishes its own inclusive prefix and writes its
+// outputs.  A state word holds a flag in its top two bits (0: nothing yet, 1: the tile's
+// sum, 2: its inclusive prefix) and the value below.  The wait for a predecessor's state
+// is bounded: after `budget` SM clock cycles the block records DEV_ERR_TIMEOUT in
+// *status, takes the prefix found so far and goes on (its outputs are then wrong, and
+// the caller reports the error).
+constexpr int SP_THREADS = 256, SP_ITEMS = 8, SP_TILE = SP_THREADS * SP_ITEMS;
+constexpr uint64_t SP_AGG = 1ull << 62, SP_PRE = 2ull << 62, SP_VAL = (1ull << 62) - 1;
 
-// Single block: exclusive scan of nb 64-bit block sums in place; total to *total_out.
-__global__ void k_scan_sums(uint64_t *sums, uint64_t nb, uint64_t *total_out) {
-    constexpr int T = 1024;
-    __shared__ uint64_t ws[T / 32];
-    __shared__ uint64_t tot;
-    uint64_t per = (nb + T - 1) / T;
-    uint64_t b = threadIdx.x * per, e = min(nb, b + per);
-    uint64_t s = 0;
-    for (uint64_t i = b; i < e; ++i) s += sums[i];
-    uint64_t off = block_excl_scan<uint64_t, T>(s, ws, &tot);
-    for (uint64_t i = b; i < e; ++i) {
-        uint64_t v = sums[i];
-        sums[i] = off;
-        off += v;
-    }
-    if (threadIdx.x == 0) *total_out = tot;
-}
-
-__global__ void k_scan_down(const uint32_t *__restrict__ in, uint64_t n, const uint64_t *__restrict__ sums,
-                            uint64_t *__restrict__ out) {
-    __shared__ uint64_t tile[SC_TILE];
-    __shared__ uint64_t ws[SC_THREADS / 32];
-    __shared__ uint64_t tot;
-    uint64_t base = (uint64_t)blockIdx.x * SC_TILE;
-    for (int j = 0; j < SC_ITEMS; ++j) {
-        int li = j * SC_THREADS + threadIdx.x;
-        uint64_t i = base + li;
-        tile[li] = (i < n) ? in[i] : 0;
+__global__ void __launch_bounds__(SP_THREADS) k_scan_onepass(const uint32_t *__restrict__ in, uint64_t n,
+                                                             uint64_t *__restrict__ out, uint32_t *ticket,
+                                                             unsigned long long *state, uint32_t *status,
+                                                             long long budget, int drop_first) {
+    __shared__ uint32_t tin[SP_TILE + SP_TILE / 32];  // one pad word per 32: conflict-free runs
+    __shared__ uint64_t tout[SP_TILE + SP_TILE / 32];
+    __shared__ uint64_t ws[SP_THREADS / 32];
+    __shared__ uint64_t s_tot, s_prefix;
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    const uint64_t base = (uint64_t)t * SP_TILE;
+#pragma unroll
+    for (int j = 0; j < SP_ITEMS; ++j) {
+        const int li = j * SP_THREADS + tid;
+        tin[li + (li >> 5)] = base + li < n ? in[base + li] : 0u;
     }
     __syncthreads();
-    uint64_t loc[SC_ITEMS];
-    uint64_t s = 0;
+    uint64_t loc[SP_ITEMS];
+    uint64_t sum = 0;
 #pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) {
-        loc[j] = s;
-        s += tile[threadIdx.x * SC_ITEMS + j];
+    for (int j = 0; j < SP_ITEMS; ++j) {
+        const int li = tid * SP_ITEMS + j;
+        loc[j] = sum;
+        sum += tin[li + (li >> 5)];
     }
-    uint64_t off = block_excl_scan<uint64_t, SC_THREADS>(s, ws, &tot) + sums[blockIdx.x];
+    const uint64_t off = block_excl_scan<uint64_t, SP_THREADS>(sum, ws, &s_tot);
+    if (tid < 32) {
+        const uint64_t agg = s_tot;
+        uint64_t excl = 0;
+        if (t == 0) {
+            if (lane == 0 && !drop_first) atomicExch(&state[0], SP_PRE | agg);
+        } else {
+            if (lane == 0) atomicExch(&state[t], SP_AGG | agg);
+            int64_t j = (int64_t)t - 1;
+            const long long t0 = clock64();
+            for (;;) {
+                const int64_t q = j - lane;
+                const uint64_t st = q >= 0 ? *(volatile unsigned long long *)&state[q] : SP_PRE;
+                // lanes up to the nearest published prefix must all hold a state
+                const uint32_t pre = __ballot_sync(0xffffffffu, (st >> 62) == 2ull);
+                const uint32_t none = __ballot_sync(0xffffffffu, (st >> 62) == 0ull);
+                const int stop = pre ? __ffs(pre) - 1 : 31;
+                const uint32_t need = stop == 31 ? 0xffffffffu : (2u << stop) - 1u;
+                if (none & need) {
+                    if (clock64() - t0 > budget) {
+                        if (lane == 0) atomicOr(status, DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                uint64_t v = lane <= stop ? (st & SP_VAL) : 0ull;
 #pragma unroll
-    for (int j = 0; j < SC_ITEMS; ++j) tile[threadIdx.x * SC_ITEMS + j] = loc[j] + off;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                excl += __shfl_sync(0xffffffffu, v, 0);
+                if (pre) break;
+                j -= 32;
+            }
+            if (lane == 0) atomicExch(&state[t], SP_PRE | (excl + agg));
+        }
+        if (lane == 0) s_prefix = excl;
+    }
     __syncthreads();
-    for (int j = 0; j < SC_ITEMS; ++j) {
-        int li = j * SC_THREADS + threadIdx.x;
-        uint64_t i = base + li;
-        if (i < n) out[i] = tile[li];
+    const uint64_t pre = s_prefix + off;
+#pragma unroll
+    for (int j = 0; j < SP_ITEMS; ++j) {
+        const int li = tid * SP_ITEMS + j;
+        tout[li + (li >> 5)] = pre + loc[j];
     }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < SP_ITEMS; ++j) {
+        const int li = j * SP_THREADS + tid;
+        if (base + li < n) out[base + li] = tout[li + (li >> 5)];
+    }
+    if (base + SP_TILE >= n && tid == 0) out[n] = s_prefix + s_tot;  // the last tile: the total
 }
 
 // One block scans up to SC_SMALL elements: each thread sums a contiguous run, the block
@@ -242,11 +270,26 @@ __global__ void __launch_bounds__(1024) k_scan_small(const uint32_t *__restrict_
     if (threadIdx.x == 0) out[n] = tot;
 }
 
-size_t scan_scratch_bytes(uint64_t n) { return sizeof(uint64_t) * ((n + SC_TILE - 1) / SC_TILE + 1); }
+// Scratch of one scan: ticket counter, status word, tile states.
+size_t scan_scratch_bytes(uint64_t n) { return 16 + sizeof(uint64_t) * ((n + SP_TILE - 1) / SP_TILE + 1); }
+
+// Bound of the scan's wait for a preceding tile, in SM clock cycles: about a second.
+constexpr long long SCAN_WAIT_BUDGET = 1ll << 31;
+thread_local uint32_t *g_wait_status = nullptr;
+
+static void scan_onepass(const uint32_t *in, uint64_t *out, uint64_t n, void *scratch, uint32_t *status,
+                         long long budget, int drop_first, cudaStream_t s) {
+    const uint64_t nb = (n + SP_TILE - 1) / SP_TILE;
+    uint32_t *head = static_cast<uint32_t *>(scratch);
+    unsigned long long *state = reinterpret_cast<unsigned long long *>(head + 4);
+    GN_CUDA(cudaMemsetAsync(scratch, 0, 16 + 8 * nb, s));
+    GN_LAUNCH("k_scan_onepass", n, s,
+              k_scan_onepass<<<(unsigned)nb, SP_THREADS, 0, s>>>(in, n, out, head, state,
+                                                               status ? status : head + 1, budget, drop_first));
+}
 
 void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scratch, cudaStream_t s) {
-    uint64_t nb = (n + SC_TILE - 1) / SC_TILE;
-    if (nb == 0) {
+    if (n == 0) {
         GN_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), s));
         return;
     }
@@ -254,13 +297,22 @@ void exclusive_scan_u32(const uint32_t *in, uint64_t *out, uint64_t n, void *scr
         GN_LAUNCH("k_scan_small", n, s, k_scan_small<<<1, 1024, 0, s>>>(in, n, out));
         return;
     }
-    uint64_t *sums = static_cast<uint64_t *>(scratch);
-    GN_LAUNCH("k_scan_reduce", n, s,
-              k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums));
-    GN_LAUNCH("k_scan_sums", nb, s,
-              k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, out + n));
-    GN_LAUNCH("k_scan_down", n, s,
-              k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(in, n, sums, out));
+    scan_onepass(in, out, n, scratch, g_wait_status, SCAN_WAIT_BUDGET, 0, s);
+}
+
+// Scan of caller buffers with a given wait budget; drop_first keeps the first tile from
+// publishing its state, so that the next tiles' waits run out.  Returns whether a wait ran out.
+bool debug_scan(const uint32_t *in, uint64_t *out, uint64_t n, long long budget, int drop_first, cudaStream_t s) {
+    DeviceArena arena(s);
+    void *scr = arena.alloc(scan_scratch_bytes(n));
+    uint32_t *st = arena.alloc_n<uint32_t>(1);
+    GN_CUDA(cudaMemsetAsync(st, 0, 4, s));
+    if (n == 0) GN_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), s));
+    else scan_onepass(in, out, n, scr, st, budget, drop_first, s);
+    uint32_t h = 0;
+    GN_CUDA(cudaMemcpyAsync(&h, st, 4, cudaMemcpyDeviceToHost, s));
+    GN_CUDA(cudaStreamSynchronize(s));
+    return (h & DEV_ERR_TIMEOUT) != 0;
 }
 
 // ------------------------------------------------------------ radix sort --

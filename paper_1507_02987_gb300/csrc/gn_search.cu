@@ -2261,6 +2261,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     };
     TimerScope tscope((p.flags & GN_FLAG_TIME_KERNELS) ? &ktimer : nullptr);
     DeviceArena arena(s);
+    // bounded device-side waits (the scans' look-back) record a timeout here
+    uint32_t *wait_status = arena.alloc_n<uint32_t>(1);
+    GN_CUDA(cudaMemsetAsync(wait_status, 0, 4, s));
+    WaitStatusScope wscope(wait_status);
 
     // a5: pack queries, code every offset, list lengths
     Packed qp;
@@ -2918,9 +2922,11 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         }
     }
     timer.mark("rank");
-    uint32_t st = 0;
+    uint32_t st = 0, wst = 0;
     GN_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
+    GN_CUDA(cudaMemcpyAsync(&wst, wait_status, 4, cudaMemcpyDeviceToHost, s));
     res->hits = to_host(fin, n_out, s);
+    GN_REQUIRE((wst & DEV_ERR_TIMEOUT) == 0, GN_ETIMEOUT, "a device-side wait ran out (scan look-back)");
     GN_REQUIRE((st & DEV_ERR_BOUNDS) == 0, GN_EINTERNAL, "a device-side bounds check failed");
     GN_REQUIRE((st & DEV_ERR_BAND_TOO_WIDE) == 0, GN_ETOOBIG,
                "an alignment band exceeded 65,535 diagonals or its window 2^32 cells");

@@ -96,3 +96,36 @@ def test_serving_batch_allocation_failure(env):
         r.close()
     srv.stop()
     assert gn.gn_debug_live_allocs() == 0
+
+
+@pytest.mark.parametrize("n", [1, 4096, 4097, 2048 * 5 + 3, 1_000_003])
+def test_single_pass_scan(env, n):
+    """The single-pass scan (decoupled look-back) against numpy's cumulative sum."""
+    gn, ix, qs = env
+    import torch
+    rng = np.random.default_rng(n)
+    a = rng.integers(0, 1 << 20, n, dtype=np.uint32)
+    din = torch.from_numpy(a.view(np.int32)).cuda()
+    dout = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
+    gn.gn_debug_scan(din.data_ptr(), dout.data_ptr(), n, stream=torch.cuda.current_stream().cuda_stream)
+    exp = np.concatenate([[0], np.cumsum(a, dtype=np.uint64)])
+    assert np.array_equal(dout.cpu().numpy().view(np.uint64), exp)
+
+
+def test_scan_wait_runs_out_and_the_device_stays_usable(env):
+    """A wait that nothing ends (the first tile never publishes its sum) runs out after its
+    bound: GN_ETIMEOUT, and the next scan and search work."""
+    gn, ix, qs = env
+    import torch
+    n = 2048 * 64
+    a = np.ones(n, dtype=np.uint32)
+    din = torch.from_numpy(a.view(np.int32)).cuda()
+    dout = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    sh = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(gn.GnError) as e:
+        gn.gn_debug_scan(din.data_ptr(), dout.data_ptr(), n, wait_cycles=2_000_000, drop_first=True, stream=sh)
+    assert e.value.status == gn.GN_ETIMEOUT
+    gn.gn_debug_scan(din.data_ptr(), dout.data_ptr(), n, stream=sh)
+    assert np.array_equal(dout.cpu().numpy(), np.arange(n + 1))
+    ref = _all(gn.search(ix, qs.start, qs.bases))
+    assert len(ref) == qs.n
