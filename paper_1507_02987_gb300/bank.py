@@ -97,11 +97,22 @@ def read_fasta(source):
 _WS = b" \t\r\n\v\f"
 
 
+def _line_spans(data: bytes):
+    """(start, end) of each line of data, end at its \\n (or the last byte), as file iteration splits them."""
+    pos, n = 0, len(data)
+    while pos < n:
+        nl = data.find(b"\n", pos)
+        end = n - 1 if nl < 0 else nl
+        yield pos, end
+        pos = end + 1
+
+
 def _read_fasta_bytes(data: bytes):
     """read_fasta over a whole file's bytes: records split at header lines, whitespace
     removed with byte operations (the same records as the line-by-line reader)."""
-    if b";" in data:  # comment lines: the line-by-line reader handles them
-        yield from read_fasta(data.splitlines(keepends=True))
+    if data.startswith(b";") or b"\n;" in data:  # comment lines: the line-by-line reader handles them
+        # lines as iterating over the file gives them (split at \n only)
+        yield from read_fasta(data[i:j + 1] for i, j in _line_spans(data))
         return
     n = len(data)
     # the first header line; text before it must be whitespace only

@@ -126,3 +126,20 @@ def test_file_reader_equals_line_reader(tmp_path):
         except ValueError:
             whole = "error"
         assert by_line == whole, repr(text)
+
+
+def test_fasta_comment_fallback_matches_line_reader(tmp_path):
+    """A ';' inside a header does not switch readers; a comment line does, and both readers
+    split lines at \\n only (a lone \\r stays inside its line)."""
+    text = b">s1 desc;with semicolon\nACGT\rAC\n>s2\nGG\n"
+    p = tmp_path / "a.fa"
+    p.write_bytes(text)
+    with open(p, "rb") as f:
+        by_lines = list(bank.read_fasta(f))
+    assert list(bank._read_fasta_bytes(text)) == by_lines
+    text2 = b";comment\n>s1 d\nAC\r\nGT\n;another\n>s2\nTT\n"
+    p.write_bytes(text2)
+    with open(p, "rb") as f:
+        by_lines = list(bank.read_fasta(f))
+    assert list(bank._read_fasta_bytes(text2)) == by_lines
+    assert [r.sequence for r in by_lines] == [b"ACGT", b"TT"]

@@ -153,8 +153,41 @@ def test_parameters_per_request(running):
         with pytest.raises(urllib.error.HTTPError) as e:
             _post(url + path, fasta, "text/plain")
         assert e.value.code == 400
-    # the default set and three more fill the pool of four: a fifth set is refused
+    # the default set and three more fill the pool of four: a fifth set replaces the least
+    # recently used idle one, and its results are still right
     _post(url + "/search?max_alignments=3", fasta, "text/plain")
-    with pytest.raises(urllib.error.HTTPError) as e:
-        _post(url + "/search?max_alignments=4", fasta, "text/plain")
-    assert e.value.code == 400
+    doc = _post(url + "/search?max_alignments=4", fasta, "text/plain")
+    ref = oracle.Index(b0).search(qs, oracle.Params(max_alignments=4), threads=os.cpu_count() or 1)
+    assert [len(q["alignments"]) for q in doc["queries"]] == [len(r.ranked) for r in ref]
+
+
+def test_parameter_sets_share_loops_and_are_checked(tmp_path):
+    b0 = synth.make_bank("tiny", n_seqs=60)
+    gnb = tmp_path / "t.gnb"
+    bank.write_bank(gnb, [(f"chr{i}", "d", b0.seq(i)) for i in range(b0.n_seqs)])
+    svc = service.BankService(OracleLoop(), "t", str(gnb), 1 << 30, max_param_sets=2)
+    q = [("a", synth.make_queries("tiny", b0, n=1).query(0))]
+    # the library's default values, named or left out, are one set: the default loop
+    for params in ({}, {"band_w": 16}, {"max_alignments": 100, "xdrop": "20"}, {"max_hit_distance": 33},
+                   {"min_hsp_len": 22}, {"max_evalue": "inf"}, {"band_w": 16.0}):
+        svc.search(q, params)
+        assert len(svc.servers) == 1, params
+    # each loop gets an even share of the bank's budget
+    assert svc.loop_budget() == (1 << 30) // 2
+    # out of range, negative, fractional or non-numeric values are refused
+    for params in ({"max_alignments": -1}, {"min_hsp_len": -5}, {"max_alignments": 2.7}, {"band_w": 16385},
+                   {"xdrop": "x"}, {"max_evalue": -1}, {"max_hit_distance": 70000}, {"band_w": True},
+                   {"max_evalue": "nan"}):
+        with pytest.raises(ValueError):
+            svc.search(q, params)
+    # a second set takes the second loop; a third replaces it (least recently used, idle)
+    svc.search(q, {"max_alignments": 5})
+    svc.search(q, {"max_alignments": 6})
+    assert len(svc.servers) == 2 and svc.default_key in svc.servers
+    # with every non-default loop busy, a new set is refused
+    key, _ = svc.acquire({"max_alignments": 6})
+    with pytest.raises(service.Busy):
+        svc.search(q, {"max_alignments": 7})
+    svc.release(key)
+    svc.search(q, {"max_alignments": 7})
+    svc.close()
