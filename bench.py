@@ -373,7 +373,7 @@ def matches_oracle(got, exp):
     return bool((tiny | np.isclose(got["evalue"], exp["evalue"], rtol=1e-9, atol=0)).all())
 
 
-def sub_leg(gn, ix, bank, queries, desc, steps, warmup, stream, dev, parity_idx, log):
+def sub_leg(gn, ix, bank, queries, desc, steps, warmup, stream, dev, parity_idx, log, band_w=16, tuned=None):
     """One gn_search over a whole query set per step (device-resident queries, CUDA events around
     the steps, as the main leg), then the sampled queries parity_idx against the oracle (an index
     restricted to their seed codes, which searches them as the full one does)."""
@@ -382,26 +382,27 @@ def sub_leg(gn, ix, bank, queries, desc, steps, warmup, stream, dev, parity_idx,
     sh = stream.cuda_stream
     qd = torch.from_numpy(queries.bases).to(f"cuda:{dev}")
     M = int(queries.start[-1])
+    sp = gn.make_params(band_w=band_w)
     for _ in range(warmup):
-        gn.search(ix, queries.start, qd, stream=sh).close()
+        gn.search(ix, queries.start, qd, params=sp, stream=sh).close()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
-        gn.search(ix, queries.start, qd, stream=sh).close()
+        gn.search(ix, queries.start, qd, params=sp, stream=sh).close()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    res = gn.search(ix, queries.start, qd, stream=sh)
+    res = gn.search(ix, queries.start, qd, params=sp, stream=sh)
     got = [res.query(i).copy() for i in parity_idx]
     res.close()
     sub = queries.subset(parity_idx)
     threads = os.cpu_count() or 1
     ox = oracle.Index(bank, k=11, stride=ix.stride, restrict_to=sub, threads=threads)
-    ref = ox.search(sub, oracle.Params(stride=ix.stride), threads=threads)
+    ref = ox.search(sub, oracle.Params(stride=ix.stride, band_w=band_w), threads=threads)
     mism = sum(0 if matches_oracle(g, r.ranked) else 1 for g, r in zip(got, ref))
     out = {"workload": desc, "queries": queries.n, "query_bases": M, "steps": steps, "warmup": warmup,
-           "ms_per_step": ms, "value": M / 1e3 / (ms / 1e3), "unit": UNIT,
+           "ms_per_step": ms, "value": M / 1e3 / (ms / 1e3), "unit": UNIT, "band_w": band_w, "autotune": tuned,
            "oracle_parity": {"queries_compared": len(parity_idx), "mismatches": mism}}
     log(f"sub-leg {desc[:40]}...: {out['value']:.0f} kbp/s, {ms:.2f} ms per step, "
         f"oracle mismatches {mism} of {len(parity_idx)}")
@@ -586,8 +587,20 @@ def run_ours(args, dist):
         bb = synth.make_bank("batched")
         bq = synth.make_queries("batched", bb)
         bix = gn.Index(bb.seq_start, bb.bases, k=11, stride=args.stride, stream=sh)
+        # the batched workload's band width and kernel settings from the autotuner, on an evenly
+        # spaced 200-query calibration sample, before the timed steps
+        t0 = time.perf_counter()
+        cal = bq.subset(list(range(0, bq.n, bq.n // 200))[:200])
+        tp, tuning = gn.autotune(bix, cal.start, cal.bases, stream=sh)
+        tuned = {"band_w": int(tp.band_w), **tuning, "calibration_queries": cal.n,
+                 "seconds": time.perf_counter() - t0}
+        log(f"batched sub-leg autotuned: {tuned}")
+        pidx = list(range(0, bq.n, bq.n // 40))[:40] + [bq.n - 1]
         legs["batched"] = sub_leg(gn, bix, bb, bq, workload_desc("batched", args.stride), 5, 3, stream, dev,
-                                  list(range(0, bq.n, bq.n // 40))[:40] + [bq.n - 1], log)
+                                  pidx, log, band_w=int(tp.band_w), tuned=tuned)
+        if int(tp.band_w) != 16:  # the same workload at the default band, with the tuned kernel settings
+            legs["batched_default_band"] = sub_leg(gn, bix, bb, bq, workload_desc("batched", args.stride), 5, 3,
+                                                   stream, dev, pidx, log, band_w=16, tuned=tuned)
         bix.close()
 
     # ---- roofline of the dominant kernel (and of the next ones)

@@ -153,12 +153,18 @@ GN_API gn_status gn_index_get_info(const gn_index *index, gn_index_info *info);
 
 /* Execution settings that never change results (0 = the library's default): the
  * fill kernel's tile size in hits (default 50,000) and threads per tile (512 or
- * 256), and the raw hits planned per hit bucket (default 2,048 with the repeat
- * filter).  They belong to an index (they depend on its occurrence lists). */
+ * 256), the raw hits planned per hit bucket (default 4,096 with the repeat
+ * filter), the lanes that align one HSP in the alignment kernel's grouped path
+ * (8, 16 or 32: four, two or one HSP per warp, for bands of up to 40, 48 or 64
+ * diagonals; default 8) and the DP-window rows from which an alignment goes to the
+ * anti-diagonal wavefront path (default 512).  They belong to an index (they depend
+ * on its occurrence lists). */
 typedef struct {
     uint32_t tile_hits;
     uint32_t fill_threads;
     uint32_t bucket_target;
+    uint32_t sw_lanes;
+    uint32_t sw_wave_rows;
     uint32_t reserved;
 } gn_tuning;
 GN_API gn_status gn_index_set_tuning(gn_index *index, const gn_tuning *tuning);
@@ -171,8 +177,10 @@ GN_API gn_status gn_index_get_tuning(const gn_index *index, gn_tuning *tuning);
  * wider bands recover alignments whose indels drift off the seed diagonal, at a
  * cost that grows with the band.  w changes results, so the caller passes the
  * chosen params to every later search (and to any reference it compares with).  With GN_TUNE_KERNELS it times
- * the search of the sample with several gn_tuning candidates and installs the
- * fastest on the index (and copies it to *tuning if not NULL).  Not to be run
+ * the search of the sample with several gn_tuning candidates, one group of settings
+ * after the other (fill threads and tile size; raw hits per bucket; lanes per HSP
+ * and wavefront rows of the alignment kernel), and installs the fastest on the
+ * index (and copies it to *tuning if not NULL).  Not to be run
  * concurrently with other searches on the same index.  Errors as gn_search. */
 #define GN_TUNE_BAND 1u
 #define GN_TUNE_KERNELS 2u

@@ -60,7 +60,8 @@ class gn_params(ctypes.Structure):
 
 
 class gn_tuning(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint32) for n in ("tile_hits", "fill_threads", "bucket_target", "reserved")]
+    _fields_ = [(n, ctypes.c_uint32) for n in ("tile_hits", "fill_threads", "bucket_target", "sw_lanes",
+                                                "sw_wave_rows", "reserved")]
 
 
 class gn_serve_stats(ctypes.Structure):
@@ -510,9 +511,10 @@ class Server:
             pass
 
 
-def set_tuning(index: Index, tile_hits=0, fill_threads=0, bucket_target=0):
+def set_tuning(index: Index, tile_hits=0, fill_threads=0, bucket_target=0, sw_lanes=0, sw_wave_rows=0):
     _check(load().gn_index_set_tuning(ctypes.c_void_p(index.handle),
-                                      ctypes.byref(gn_tuning(tile_hits, fill_threads, bucket_target, 0))))
+                                      ctypes.byref(gn_tuning(tile_hits, fill_threads, bucket_target, sw_lanes,
+                                                             sw_wave_rows, 0))))
 
 
 def get_tuning(index: Index) -> dict:

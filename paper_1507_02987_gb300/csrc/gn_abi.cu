@@ -365,6 +365,10 @@ gn_status gn_index_set_tuning(gn_index *ix, const gn_tuning *t) {
         g_last_error = "fill_threads is 0, 256 or 512";
         return GN_EINVAL;
     }
+    if (t->sw_lanes != 0 && t->sw_lanes != 8 && t->sw_lanes != 16 && t->sw_lanes != 32) {
+        g_last_error = "sw_lanes is 0, 8, 16 or 32";
+        return GN_EINVAL;
+    }
     ix->tuning = *t;
     return GN_OK;
 }
@@ -430,21 +434,44 @@ gn_status gn_autotune(gn_index *ix, const gn_queries *q, const gn_scoring *sc, g
             cudaEvent_t e0, e1;
             GN_CUDA(cudaEventCreate(&e0));
             GN_CUDA(cudaEventCreate(&e1));
-            for (uint32_t th : {512u, 256u}) {
-                for (uint32_t hits : {25000u, 50000u, 100000u}) {
-                    gn_tuning cand{hits, th, 0, 0};
-                    ix->tuning = cand;
-                    float ms = 0.f;
-                    for (int rep = 0; rep < 2; ++rep) {  // the first run warms pools and caches
-                        gn_results r;
-                        GN_CUDA(cudaEventRecord(e0, s));
-                        run(*p, r);
-                        GN_CUDA(cudaEventRecord(e1, s));
-                        GN_CUDA(cudaEventSynchronize(e1));
-                        GN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                    }
-                    if (!have || ms < best_ms) { best = cand; best_ms = ms; have = true; }
+            auto time_of = [&](const gn_tuning &cand) {
+                ix->tuning = cand;
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {  // the first run warms pools and caches
+                    gn_results r;
+                    GN_CUDA(cudaEventRecord(e0, s));
+                    run(*p, r);
+                    GN_CUDA(cudaEventRecord(e1, s));
+                    GN_CUDA(cudaEventSynchronize(e1));
+                    GN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
                 }
+                if (!have || ms < best_ms) { best = cand; best_ms = ms; have = true; }
+            };
+            // one group of settings after the other, each from the best so far
+            for (uint32_t th : {512u, 256u})
+                for (uint32_t hits : {25000u, 50000u, 100000u}) {
+                    gn_tuning cand = best;
+                    cand.fill_threads = th;
+                    cand.tile_hits = hits;
+                    time_of(cand);
+                }
+            {
+                const gn_tuning base = best;
+                for (uint32_t bt : {2048u, 4096u, 8192u}) {
+                    gn_tuning cand = base;
+                    cand.bucket_target = bt;
+                    time_of(cand);
+                }
+            }
+            {
+                const gn_tuning base = best;
+                for (uint32_t lanes : {8u, 16u, 32u})
+                    for (uint32_t rows : {256u, 512u, 1024u}) {
+                        gn_tuning cand = base;
+                        cand.sw_lanes = lanes;
+                        cand.sw_wave_rows = rows;
+                        time_of(cand);
+                    }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);

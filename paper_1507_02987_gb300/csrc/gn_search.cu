@@ -1620,7 +1620,7 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
             const uint32_t SD = Hd > 0 ? pSH[k] : rowbase | (uint32_t)(b0 + k);
             uint32_t d;
             if (SEG) d = ((dbad >> k) & 1u) ? 4u : (uint32_t)(dcodes >> (62 - 2 * k)) & 3u;
-            else d = lane_on ? wd.at(jb + k) : 4u;
+            else d = ((amask >> k) & 1u) ? wd.at(jb + k) : 4u;  // the window covers the active cells only
             const int32_t Dg = Hd + ((qc < 4u && d == qc) ? match : mismatch);
             // diagonal over E on ties
             bool pd;
@@ -1830,7 +1830,9 @@ __device__ __forceinline__ void sw_wave(const DevHsp &h, const uint32_t *__restr
 // Warps take 32 / SWG_G selected HSPs at a time; each segment of SWG_G lanes aligns one
 // whose band fits SWG_G x SWG_K offsets, and the whole warp then aligns the others one by
 // one (pair or strip path).
-constexpr int SWG_G = 8, SWG_K = 5;
+// SWG_G lanes per HSP (32 / SWG_G HSPs per warp), SWG_K band offsets per lane: <8, 5>
+// (bands of up to 40 diagonals, the default), <16, 3> (48) or <32, 2> (64).
+template <int SWG_G, int SWG_K>
 __global__ void __launch_bounds__(128, 1) k_banded_sw(const DevHsp *__restrict__ sel, uint32_t n,
                                                    const uint64_t *__restrict__ strip_off, SwCell *__restrict__ strips,
                                                    const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
@@ -2472,8 +2474,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 if (const char *e = getenv("GN_TILE_POS")) tpos = std::max(32, std::min(4096, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS")) fbits = std::max(12, std::min(19, atoi(e)));
                 if (const char *e = getenv("GN_TILE_FBITS2")) fbits2 = std::max(12, std::min(19, atoi(e)));
-                // the filter keeps about a fifth of the hits; capacity has ~2x slack over the expected fill
-                uint32_t target = filter ? (ix->tuning.bucket_target ? ix->tuning.bucket_target : 2048) : 512, bcap = 1024;
+                // the filter keeps about 2 % of the hits: buckets of about 4,096 raw hits hold about 80 kept
+                // hits, most of them within the grouping warps' 256 candidates; capacity 1,024
+                uint32_t target = filter ? (ix->tuning.bucket_target ? ix->tuning.bucket_target : 4096) : 512, bcap = 1024;
                 if (const char *e = getenv("GN_BUCKET_TARGET")) target = std::max(64, std::min(65536, atoi(e)));
                 if (const char *e = getenv("GN_BUCKET_CAP")) {  // small buckets (exercises the spill path)
                     bcap = (uint32_t)std::max(8ul, std::min(65536ul, strtoul(e, nullptr, 10)));
@@ -2824,7 +2827,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         uint64_t *okeys = arena.alloc_n<uint64_t>(n_sel), *okeys_alt = arena.alloc_n<uint64_t>(n_sel);
         // alignments of at least sw_long rows go to the wavefront path (their rows would
         // bound the kernel's time on the grouped path)
-        uint32_t sw_long = 512;
+        uint32_t sw_long = ix->tuning.sw_wave_rows ? ix->tuning.sw_wave_rows : 512;
         if (const char *e = getenv("GN_SW_LONG_ROWS")) sw_long = (uint32_t)std::max(1l, strtol(e, nullptr, 10));
         uint32_t *n_long = arena.alloc_n<uint32_t>(2);
         GN_CUDA(cudaMemsetAsync(n_long, 0, 8, s));
@@ -2836,13 +2839,19 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                     ? okeys_alt : okeys;
         GN_CUDA(cudaMemsetAsync(counter, 0, 12, s));
         uint32_t *wide = arena.alloc_n<uint32_t>(n_sel);
-        unsigned warps = (unsigned)std::min<uint64_t>((n_sel + 3) / 4, (uint64_t)num_sms() * 32);
+        // lanes per HSP of the grouped path (the index's tuning; GN_SW_LANES overrides)
+        uint32_t sw_lanes = ix->tuning.sw_lanes ? ix->tuning.sw_lanes : 8;
+        if (const char *e = getenv("GN_SW_LANES")) sw_lanes = (uint32_t)atoi(e);
+        if (sw_lanes != 16 && sw_lanes != 32) sw_lanes = 8;
+        auto sw_kernel = sw_lanes == 32 ? k_banded_sw<32, 2> : sw_lanes == 16 ? k_banded_sw<16, 3> : k_banded_sw<8, 5>;
+        const uint32_t per_warp = 32 / sw_lanes;
+        unsigned warps = (unsigned)std::min<uint64_t>((n_sel + per_warp - 1) / per_warp, (uint64_t)num_sms() * 32);
         GN_LAUNCH("k_banded_sw", area[0], s,
-                  k_banded_sw<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
-                                                            ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
-                                                            sc.mismatch, sc.gap_open, sc.gap_extend,
-                                                            (int32_t)p.band_w, counter, order, wide, counter + 1,
-                                                            n_long, n_long + 1, aln, status));
+                  sw_kernel<<<(warps * 32 + 127) / 128, 128, 0, s>>>(sel, n_sel, soff, strips, qp.pk, qp.nb, qstart_d,
+                                                          ix->bank.pk, ix->bank.nb, ix->seq_start_d, sc.match,
+                                                          sc.mismatch, sc.gap_open, sc.gap_extend,
+                                                          (int32_t)p.band_w, counter, order, wide, counter + 1,
+                                                          n_long, n_long + 1, aln, status));
         GN_LAUNCH("k_banded_sw_wide", area[1], s,
                   k_banded_sw_wide<<<num_sms() * 4, 128, 0, s>>>(sel, wide, counter + 1, counter + 2, soff, strips, qp.pk,
                                                                 qp.nb, qstart_d, ix->bank.pk, ix->bank.nb,

@@ -239,7 +239,8 @@ def test_chunked_equals_unchunked(gn, mid_small, monkeypatch):
                                  {"GN_RANK_PATH": "sort"}, {"GN_TILE_POS": "64"}, {"GN_SELECT_PATH": "sort"},
                                  {"GN_BUCKET_CAP": "64", "GN_MAX_CHUNK_HITS": "30000"},
                                  {"GN_BUCKET_CAP": "64", "GN_SPILL_ROOM": "16"}, {"GN_SW_LONG_ROWS": "1"},
-                                 {"GN_SW_LONG_ROWS": "100"}])
+                                 {"GN_SW_LONG_ROWS": "100"}, {"GN_SW_LANES": "16"}, {"GN_SW_LANES": "32"},
+                                 {"GN_BUCKET_TARGET": "2048"}, {"GN_BUCKET_TARGET": "16384"}])
 def test_hit_grouping_paths_agree_with_oracle(gn, mid_small, monkeypatch, env):
     """The global sort path, the bucketed path and its overflow fallback give the oracle's HSPs."""
     bank, qs, ix, ox = mid_small
@@ -310,6 +311,8 @@ def test_autotune(gn, mid_small):
     p, tuning = gn.autotune(ix, sub.start, sub.bases)
     assert p.band_w in (16, 32, 64, 128)
     assert tuning["fill_threads"] in (256, 512) and tuning["tile_hits"] in (25000, 50000, 100000)
+    assert tuning["bucket_target"] in (2048, 4096, 8192)
+    assert tuning["sw_lanes"] in (8, 16, 32) and tuning["sw_wave_rows"] in (256, 512, 1024)
     assert gn.get_tuning(ix) == tuning
     after = gn.search(ix, sub.start, sub.bases).all()
     for a, b in zip(before, after):
@@ -325,7 +328,8 @@ def test_autotune(gn, mid_small):
         b = sum(int(x["score"].sum()) for x in wide)
         assert b - a <= 0.005 * max(a, 1)
     gn.set_tuning(ix)
-    assert gn.get_tuning(ix) == {"tile_hits": 0, "fill_threads": 0, "bucket_target": 0}
+    assert gn.get_tuning(ix) == {"tile_hits": 0, "fill_threads": 0, "bucket_target": 0, "sw_lanes": 0,
+                                 "sw_wave_rows": 0}
     ix.close()
 
 
