@@ -96,10 +96,12 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB):
-            raise ImportError(f"{_build.LIB} is missing: build it with paper_1507_02987_gb300._build.build() "
+        # GN_LIBRARY=checks selects the checked build (device-side bounds checks) of the same library
+        path = _build.CHECKS_LIB if os.environ.get("GN_LIBRARY") == "checks" else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_1507_02987_gb300._build.build() "
                               "(the search runs only in the CUDA library; there is no CPU fallback)")
-        lib = ctypes.CDLL(_build.LIB)
+        lib = ctypes.CDLL(path)
         vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32
         st = ctypes.c_int
         sig = {

@@ -428,7 +428,12 @@ gn_status gn_autotune(gn_index *ix, const gn_queries *q, const gn_scoring *sc, g
         if (what & GN_TUNE_KERNELS) {
             // fastest of a few result-invariant settings, by CUDA-event time on the caller's stream
             const gn_tuning saved = ix->tuning;
-            gn_tuning best = saved;
+            gn_tuning best = saved;  // the library's defaults where unset, so that the result is explicit
+            if (!best.tile_hits) best.tile_hits = 50000;
+            if (!best.fill_threads) best.fill_threads = 512;
+            if (!best.bucket_target) best.bucket_target = 4096;
+            if (!best.sw_lanes) best.sw_lanes = 8;
+            if (!best.sw_wave_rows) best.sw_wave_rows = 512;
             float best_ms = 0.f;
             bool have = false;
             cudaEvent_t e0, e1;

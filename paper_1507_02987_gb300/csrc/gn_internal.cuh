@@ -261,8 +261,21 @@ struct SeqMap {
     const uint32_t *lut;
     uint32_t n_seqs;
 };
+// ------------------------------------------------------ device-side checks --
+// Built with -DGN_CHECKS (paper_1507_02987_gb300._build.build(checks=True)), the search
+// kernels check indices they compute from data before using them; a failed check records
+// DEV_ERR_BOUNDS in g_check_bits and skips the access, and the search then returns
+// GN_EINTERNAL.  Without it the checks compile to nothing.
+#ifdef GN_CHECKS
+static __device__ uint32_t g_check_bits;
+#define GN_CHECK(cond) ((cond) || (atomicOr(&::gn::g_check_bits, (uint32_t)DEV_ERR_BOUNDS), false))
+#else
+#define GN_CHECK(cond) true
+#endif
+
 // sequence holding bank position x (x < bank length); empty sequences are skipped
 __device__ __forceinline__ uint32_t dev_seq_of(const SeqMap &m, uint64_t x) {
+    if (!GN_CHECK(x < m.start[m.n_seqs])) return m.n_seqs ? m.n_seqs - 1 : 0u;
     uint32_t s = m.lut[x >> SEQ_LUT_SHIFT];
     while (m.start[s + 1] <= x) ++s;
     return s;

@@ -279,6 +279,7 @@ struct TileTable {
     uint32_t *qp, *beg, *end, *qq, *bb, *cs;
     uint8_t *bs;
     uint32_t span, nchunks;
+    uint64_t nquads;  // quads of the occurrence array (checked builds)
 };
 
 // Last table index i in [i_lo, i_hi] with qp[i] <= e: the offset whose list holds quad e.
@@ -325,6 +326,7 @@ __device__ __forceinline__ void tile_quad_load(const TileTable &t, uint32_t c, u
         L.ok[v] = e >= r0 && e < r1;
         const uint32_t q = (t.beg[i] >> 2) + (e - t.qp[i]);
         L.occ[v] = q << 2;
+        if (L.ok[v] && !GN_CHECK(q < t.nquads)) L.ok[v] = false;
         L.ent[v] = L.ok[v] ? __ldg(&post4[q]) : make_uint4(0u, 0u, 0u, 0u);
     }
 }
@@ -395,7 +397,8 @@ __device__ __forceinline__ uint32_t bf_block_scan(uint32_t v, uint32_t *wtot, ui
 __device__ __forceinline__ void bucket_place(uint32_t b, uint64_t key, uint32_t ql, uint32_t *__restrict__ bcount,
                                              uint64_t *__restrict__ bkeys, uint32_t bcap, uint64_t *__restrict__ spill,
                                              unsigned long long *__restrict__ spill_count,
-                                             unsigned long long spill_cap, int qbits) {
+                                             unsigned long long spill_cap, int qbits, uint32_t NB) {
+    if (!GN_CHECK(b < NB)) return;
     const uint32_t slot = atomicAdd(&bcount[b], 1u);
     if (slot < bcap) {
         bkeys[(uint64_t)b * bcap + slot] = key;
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     const uint32_t *__restrict__ bshift, uint32_t *__restrict__ bcount, uint64_t *__restrict__ bkeys, uint32_t bcap,
     uint64_t *__restrict__ spill, unsigned long long *__restrict__ spill_count, unsigned long long spill_cap,
     int qbits, int filter, uint32_t D, int tpos, int fbits, int fbits2, unsigned long long *__restrict__ kept_total,
-    uint32_t tile_step, int count_only, uint32_t stage_cap) {
+    uint32_t tile_step, int count_only, uint32_t stage_cap, uint32_t NB, uint64_t post_quads) {
     extern __shared__ __align__(16) unsigned char bf_smem[];
     const uint32_t halo = filter ? D : 0u;
     const uint32_t span_max = (uint32_t)tpos + 2u * halo;
@@ -429,6 +432,7 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     uint32_t *seen = reinterpret_cast<uint32_t *>(stage_key + stage_cap);
     uint32_t *seen2 = seen + nwords;
     TileTable t;
+    t.nquads = post_quads;
     t.qp = seen2 + nwords2;
     t.beg = t.qp + span_max + 1;
     t.end = t.beg + span_max;
@@ -544,7 +548,8 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
                         stage_b[at] = b;
                         stage_q[at] = (uint16_t)(qq >> 16);
                     } else {
-                        bucket_place(b, key, qq >> 16, bcount, bkeys, bcap, spill, spill_count, spill_cap, qbits);
+                        bucket_place(b, key, qq >> 16, bcount, bkeys, bcap, spill, spill_count, spill_cap, qbits,
+                                     NB);
                     }
                 }
             }
@@ -554,7 +559,7 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
             const uint32_t ns = min(nstage, stage_cap);
             for (uint32_t j = threadIdx.x; j < ns; j += blockDim.x)
                 bucket_place(stage_b[j], stage_key[j], stage_q[j], bcount, bkeys, bcap, spill, spill_count, spill_cap,
-                             qbits);
+                             qbits, NB);
         }
         __syncthreads();  // the table and filters are rebuilt for the next tile
     }
@@ -944,11 +949,13 @@ __device__ __forceinline__ uint32_t xdrop_walk_warp(const uint32_t *__restrict__
 __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__restrict__ qpk,
                         const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
                         const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
-                        const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch, int32_t X) {
+                        const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch, int32_t X,
+                        uint32_t nq, uint32_t n_seqs) {
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
         DevHsp r = h[i];
+        if (!GN_CHECK(r.qi < nq && r.seq < n_seqs)) continue;
         const uint64_t qb = qstart[r.qi], sb = seq_start[r.seq];
         const uint32_t m = (uint32_t)(qstart[r.qi + 1] - qb), L = (uint32_t)(seq_start[r.seq + 1] - sb);
         const uint32_t el = xdrop_walk_warp<-1>(qpk, qnb, bpk, bnb, qb + r.qs, sb + r.ds, min(r.qs, r.ds), match,
@@ -2267,6 +2274,11 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     uint32_t *wait_status = arena.alloc_n<uint32_t>(1);
     GN_CUDA(cudaMemsetAsync(wait_status, 0, 4, s));
     WaitStatusScope wscope(wait_status);
+#ifdef GN_CHECKS
+    uint32_t *check_bits = nullptr;  // the failed device-side checks of this search
+    GN_CUDA(cudaGetSymbolAddress(reinterpret_cast<void **>(&check_bits), g_check_bits));
+    GN_CUDA(cudaMemsetAsync(check_bits, 0, 4, s));
+#endif
 
     // a5: pack queries, code every offset, list lengths
     Packed qp;
@@ -2571,7 +2583,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                             bf_smem, s>>>(
                                   qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, nullptr, nullptr, bcap,
                                   nullptr, nullptr, 0ull, qbits, filter, p.max_hit_distance, tpos, fbits, fbits2,
-                                  kept_total, tile_step, 1, stage_cap));
+                                  kept_total, tile_step, 1, stage_cap, NB, post_alloc_entries(ix->n_postings) / 4));
                     GN_CUDA(cudaMemcpyAsync(got, kept_total, 16, cudaMemcpyDeviceToHost, s));
                     GN_CUDA(cudaStreamSynchronize(s));
                     if (got[1]) {
@@ -2597,7 +2609,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                   fill_kernel<<<fgrid, fthreads, bf_smem, s>>>(
                                       qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
                                       spill, spill_count, (unsigned long long)spill_room, qbits, filter,
-                                      p.max_hit_distance, tpos, fbits, fbits2, kept_total, 1u, 0, stage_cap));
+                                      p.max_hit_distance, tpos, fbits, fbits2, kept_total, 1u, 0, stage_cap, NB,
+                                      post_alloc_entries(ix->n_postings) / 4));
                         GN_CUDA(cudaMemcpyAsync(&n_spill, spill_count, 8, cudaMemcpyDeviceToHost, s));
                         GN_CUDA(cudaMemcpyAsync(&n_kept, kept_total, 8, cudaMemcpyDeviceToHost, s));
                         GN_CUDA(cudaStreamSynchronize(s));
@@ -2725,7 +2738,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         GN_LAUNCH("k_xdrop", n_hsp, s,
                   k_xdrop<<<blocks_for(xwarps * 32, 256), 256, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d,
                                                                       ix->bank.pk, ix->bank.nb, ix->seq_start_d,
-                                                                      sc.match, sc.mismatch, p.xdrop));
+                                                                      sc.match, sc.mismatch, p.xdrop, nq, ix->n_seqs));
     }
     timer.mark("xdrop_extend");
     if (keep) {
@@ -2936,6 +2949,12 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     GN_CUDA(cudaMemcpyAsync(&wst, wait_status, 4, cudaMemcpyDeviceToHost, s));
     res->hits = to_host(fin, n_out, s);
     GN_REQUIRE((wst & DEV_ERR_TIMEOUT) == 0, GN_ETIMEOUT, "a device-side wait ran out (scan look-back)");
+#ifdef GN_CHECKS
+    uint32_t cbits = 0;
+    GN_CUDA(cudaMemcpyAsync(&cbits, check_bits, 4, cudaMemcpyDeviceToHost, s));
+    GN_CUDA(cudaStreamSynchronize(s));
+    GN_REQUIRE((cbits & DEV_ERR_BOUNDS) == 0, GN_EINTERNAL, "a device-side bounds check failed (checked build)");
+#endif
     GN_REQUIRE((st & DEV_ERR_BOUNDS) == 0, GN_EINTERNAL, "a device-side bounds check failed");
     GN_REQUIRE((st & DEV_ERR_BAND_TOO_WIDE) == 0, GN_ETOOBIG,
                "an alignment band exceeded 65,535 diagonals or its window 2^32 cells");
