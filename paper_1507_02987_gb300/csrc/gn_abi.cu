@@ -119,21 +119,28 @@ static uint64_t footprint_of(const gn_server *sv, uint64_t hits, uint64_t len) {
 constexpr size_t COUNT_MAX_REQUESTS = 4096;
 constexpr uint64_t COUNT_MAX_BASES = 16ull << 20;
 
-// Device buffer that only grows (one per worker and purpose).
+// Device buffer that only grows (one per worker and purpose), stream-ordered on the worker's
+// stream: growing it waits for nothing the other workers run (a plain free would wait for the
+// whole device).
 struct GrowBuf {
+    cudaStream_t s = nullptr;
     void *p = nullptr;
     size_t cap = 0;
     void *get(size_t bytes) {
         if (bytes > cap) {
-            if (p) cudaFree(p);
+            if (p) GN_CUDA(cudaFreeAsync(p, s));
             p = nullptr;
-            cap = std::max<size_t>(bytes, 1 << 20);
-            GN_CUDA(cudaMalloc(&p, cap));
+            cap = 0;
+            const size_t want = std::max<size_t>(bytes, 1 << 20);
+            GN_CUDA(cudaMallocAsync(&p, want, s));
+            cap = want;
         }
         return p;
     }
-    ~GrowBuf() {
-        if (p) cudaFree(p);
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        cap = 0;
     }
 };
 
@@ -141,7 +148,7 @@ static void serve_worker(gn_server *sv) {
     cudaSetDevice(sv->device);
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
-    GrowBuf dbases, dstart, dhits;
+    GrowBuf dbases{s}, dstart{s}, dhits{s};
     auto first_uncounted = [&]() -> size_t {  // position of the first request not yet claimed for counting
         auto it = std::lower_bound(sv->queue.begin(), sv->queue.end(), sv->count_from,
                                    [](const Request &r, uint64_t t) { return r.ticket < t; });
@@ -296,6 +303,10 @@ static void serve_worker(gn_server *sv) {
         sv->cv_done.notify_all();
         sv->cv_work.notify_all();
     }
+    dbases.release();
+    dstart.release();
+    dhits.release();
+    cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
 }
 }  // namespace gn
