@@ -34,14 +34,19 @@ METRIC = "query kbp/s vs 4 Gbp bank (batched/served vs plain, same GPU); p50/p99
 UNIT = "kbp/s"
 
 # Algorithmic bytes per work item of each kernel (HBM-bound kernels), see the design notes:
-#   sort downsweep: read + write one 8-byte key; upsweep: read the key
+#   sort pass (or downsweep): read + write one 8-byte key (and a 4-byte value); histogram (or
+#   upsweep): read the key
 #   seed gather: read one 4-byte occurrence, write one 8-byte hit key
 #   hit merge: read one 8-byte hit key
 BYTES_PER_UNIT = {
+    "hit_sort_pass": 16.0,
+    "hit_sort_hist": 8.0,
     "hit_sort_downsweep": 16.0,
     "hit_sort_upsweep": 8.0,
     "k_seed_gather": 12.0,
     "k_hit_merge": 8.0,
+    "record_sort_pass": 24.0,
+    "record_sort_hist": 8.0,
     "record_sort_downsweep": 24.0,
     "record_sort_upsweep": 8.0,
     "k_query_codes": 17.0,

@@ -391,6 +391,18 @@ GN_API void gn_debug_fail_alloc(uint64_t nth);
  * GN_ETIMEOUT if a wait ran out (out is then wrong), after the stream has finished. */
 GN_API gn_status gn_debug_scan(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t wait_cycles, int drop_first,
                                void *cuda_stream);
+/* The library's LSD radix sort, for tests: sorts keys (n uint64, device memory) in place,
+ * stably, by bits [bit_lo, bit_hi) (8 bits per pass), with vals (n uint32, device memory,
+ * or NULL) moved along.  Sorts of up to 2^27 keys take the single-pass form (one
+ * histogram launch, then one launch per pass whose blocks wait, with decoupled look-back,
+ * for the blocks before them to publish their digit counts); three_kernel = 1 forces the
+ * three-kernel passes (upsweep, scan, downsweep) that larger sorts take.  wait_cycles and
+ * drop_first (the first tile of 4,096 keys publishes nothing) as in gn_debug_scan.
+ * Errors: GN_EINVAL (keys NULL with n > 0, bits outside 0 <= bit_lo <= bit_hi <= 64),
+ * GN_ETOOBIG (n >= 2^32), GN_ENOMEM, GN_ETIMEOUT if a wait ran out (the keys are then
+ * wrong), GN_ECUDA.  Returns after the stream has finished. */
+GN_API gn_status gn_debug_sort(uint64_t *keys, uint32_t *vals, uint64_t n, int bit_lo, int bit_hi,
+                               uint64_t wait_cycles, int drop_first, int three_kernel, void *cuda_stream);
 GN_API uint64_t gn_debug_alloc_count(void);
 GN_API int64_t gn_debug_live_allocs(void);
 

@@ -141,6 +141,7 @@ def load():
             "gn_measure_int_peaks": (st, [ctypes.POINTER(gn_int_peaks), vp]),
             "gn_debug_fail_alloc": (None, [u64]),
             "gn_debug_scan": (st, [vp, vp, u64, u64, ctypes.c_int, vp]),
+            "gn_debug_sort": (st, [vp, vp, u64, ctypes.c_int, ctypes.c_int, u64, ctypes.c_int, ctypes.c_int, vp]),
             "gn_debug_alloc_count": (u64, []),
             "gn_debug_live_allocs": (ctypes.c_int64, []),
             "gn_last_error": (ctypes.c_char_p, []),
@@ -176,6 +177,15 @@ def gn_debug_scan(in_ptr: int, out_ptr: int, n: int, wait_cycles: int = 0, drop_
     """The library's single-pass scan on device buffers (tests of its bounded wait)."""
     _check(load().gn_debug_scan(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), n, wait_cycles,
                                 1 if drop_first else 0, ctypes.c_void_p(stream)))
+
+
+def gn_debug_sort(keys_ptr: int, vals_ptr: int | None, n: int, bit_lo: int, bit_hi: int, wait_cycles: int = 0,
+                  drop_first: bool = False, three_kernel: bool = False, stream: int = 0):
+    """The library's radix sort on device buffers, in place (tests of both forms and of the
+    single-pass form's bounded wait)."""
+    _check(load().gn_debug_sort(ctypes.c_void_p(keys_ptr), ctypes.c_void_p(vals_ptr or 0), n, bit_lo, bit_hi,
+                                wait_cycles, 1 if drop_first else 0, 1 if three_kernel else 0,
+                                ctypes.c_void_p(stream)))
 
 
 def gn_debug_alloc_count() -> int:

@@ -783,6 +783,18 @@ gn_status gn_debug_scan(const uint32_t *in, uint64_t *out, uint64_t n, uint64_t 
         GN_REQUIRE(!ran_out, GN_ETIMEOUT, "a device-side wait ran out (scan look-back)");
     });
 }
+gn_status gn_debug_sort(uint64_t *keys, uint32_t *vals, uint64_t n, int bit_lo, int bit_hi, uint64_t wait_cycles,
+                        int drop_first, int three_kernel, void *cuda_stream) {
+    return guarded([&] {
+        GN_REQUIRE(n == 0 || keys, GN_EINVAL, "keys are required");
+        GN_REQUIRE(bit_lo >= 0 && bit_hi <= 64 && bit_lo <= bit_hi, GN_EINVAL, "bits must satisfy 0 <= bit_lo <= bit_hi <= 64");
+        GN_REQUIRE(n < (1ull << 32), GN_ETOOBIG, "at most 2^32 - 1 keys");
+        const long long budget = wait_cycles ? (long long)std::min<uint64_t>(wait_cycles, 1ull << 40) : (1ll << 31);
+        const bool ran_out = debug_sort(keys, vals, n, bit_lo, bit_hi, budget, drop_first ? 1 : 0, three_kernel != 0,
+                                        (cudaStream_t)cuda_stream);
+        GN_REQUIRE(!ran_out, GN_ETIMEOUT, "a device-side wait ran out (sort look-back)");
+    });
+}
 uint64_t gn_debug_alloc_count(void) { return debug_alloc_count(); }
 int64_t gn_debug_live_allocs(void) { return debug_live_allocs(); }
 

@@ -153,11 +153,14 @@ struct WaitStatusScope {
 // when the sorted data ended in the *_alt buffers.
 size_t radix_scratch_bytes(uint64_t n);
 struct RadixTag {
-    const char *up, *down;  // kernel-timer names of the two passes
+    const char *up, *down;     // kernel-timer names: histogram and pass kernels of the single-pass sort
+    const char *up3, *down3;   // upsweep and downsweep of the three-kernel passes (large sorts)
 };
 extern const RadixTag TAG_HIT_SORT, TAG_INDEX_SORT, TAG_RECORD_SORT;
 bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
                 int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag);
+bool debug_sort(uint64_t *keys, uint32_t *vals, uint64_t n, int bit_lo, int bit_hi, long long budget,
+                int drop_first, bool three_kernel, cudaStream_t s);
 unsigned long long launch_count();
 
 // Sort of fixed-size records made of uint32 words by a list of fields (first =

@@ -357,6 +357,68 @@ struct RsSmem {
     uint32_t tot;
 };
 
+// Ranks one tile of keys (tn <= RS_TILE, starting at tb) by digit and writes them (and
+// their values) to sk / sv in digit order, stably: S.tcnt[d] keys of digit d start at
+// S.tbase[d].  Keys are read warp-striped (warp w holds tile positions w * 512 to
+// w * 512 + 511), ranked per warp with __match_any_sync, and the per-warp counts are
+// scanned over the warps, then over the digits.  Ends with the block synchronised.
+template <bool VALS>
+__device__ __forceinline__ void rs_rank_tile(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                             uint64_t tb, uint32_t tn, int shift, uint32_t mask, RsSmem &S,
+                                             uint64_t *sk, uint32_t *sv) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&S.wcnt[0][0])[i] = 0;
+    __syncthreads();
+    uint64_t k[RS_ITEMS];
+    uint32_t v[RS_ITEMS];
+    uint32_t dg[RS_ITEMS];
+    uint32_t rk[RS_ITEMS];
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        uint32_t li = warp * (RS_ITEMS * 32) + it * 32 + lane;
+        bool ok = li < tn;
+        k[it] = ok ? kin[tb + li] : 0ull;
+        if (VALS) v[it] = ok ? vin[tb + li] : 0u;
+        dg[it] = ok ? ((uint32_t)(k[it] >> shift) & mask) : 256u;
+    }
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        uint32_t d = dg[it];
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = (d < 256u) ? S.wcnt[warp][d] : 0u;
+        __syncwarp();
+        rk[it] = before + __popc(peers & lt_mask);
+        if (d < 256u && (peers & lt_mask) == 0u) S.wcnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = tid;  // RS_THREADS == 256 digits
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            uint32_t c = S.wcnt[w][d];
+            S.wcnt[w][d] = s;
+            s += c;
+        }
+        S.tcnt[d] = s;
+        uint32_t b = block_excl_scan<uint32_t, RS_THREADS>(s, S.ws, &S.tot);
+        S.tbase[d] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < RS_ITEMS; ++it) {
+        uint32_t d = dg[it];
+        if (d < 256u) {
+            uint32_t pos = S.tbase[d] + S.wcnt[warp][d] + rk[it];
+            sk[pos] = k[it];
+            if (VALS) sv[pos] = v[it];
+        }
+    }
+    __syncthreads();
+}
+
 template <bool VALS>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t *__restrict__ kin,
                                                              const uint32_t *__restrict__ vin,
@@ -368,63 +430,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t *__r
     RsSmem &S = *reinterpret_cast<RsSmem *>(smem_raw);
     uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw + ((sizeof(RsSmem) + 15) / 16) * 16);
     uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_TILE);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int tid = threadIdx.x;
     if (tid < 256) S.run[tid] = offs[(uint64_t)tid * gridDim.x + blockIdx.x];
     uint64_t beg = (uint64_t)blockIdx.x * chunk, end = min(n, beg + chunk);
-
     for (uint64_t tb = beg; tb < end; tb += RS_TILE) {
         const uint32_t tn = (uint32_t)min((uint64_t)RS_TILE, end - tb);
-        for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&S.wcnt[0][0])[i] = 0;
-        __syncthreads();
-        uint64_t k[RS_ITEMS];
-        uint32_t v[RS_ITEMS];
-        uint32_t dg[RS_ITEMS];
-        uint32_t rk[RS_ITEMS];
-#pragma unroll
-        for (int it = 0; it < RS_ITEMS; ++it) {
-            uint32_t li = warp * (RS_ITEMS * 32) + it * 32 + lane;
-            bool ok = li < tn;
-            k[it] = ok ? kin[tb + li] : 0ull;
-            if (VALS) v[it] = ok ? vin[tb + li] : 0u;
-            dg[it] = ok ? ((uint32_t)(k[it] >> shift) & mask) : 256u;
-        }
-#pragma unroll
-        for (int it = 0; it < RS_ITEMS; ++it) {
-            uint32_t d = dg[it];
-            uint32_t peers = __match_any_sync(0xffffffffu, d);
-            uint32_t before = (d < 256u) ? S.wcnt[warp][d] : 0u;
-            __syncwarp();
-            rk[it] = before + __popc(peers & lt_mask);
-            if (d < 256u && (peers & lt_mask) == 0u) S.wcnt[warp][d] += __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        {
-            const int d = tid;  // RS_THREADS == 256 digits
-            uint32_t s = 0;
-#pragma unroll
-            for (int w = 0; w < RS_WARPS; ++w) {
-                uint32_t c = S.wcnt[w][d];
-                S.wcnt[w][d] = s;
-                s += c;
-            }
-            S.tcnt[d] = s;
-            uint32_t b = block_excl_scan<uint32_t, RS_THREADS>(s, S.ws, &S.tot);
-            S.tbase[d] = b;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int it = 0; it < RS_ITEMS; ++it) {
-            uint32_t d = dg[it];
-            if (d < 256u) {
-                uint32_t pos = S.tbase[d] + S.wcnt[warp][d] + rk[it];
-                sk[pos] = k[it];
-                if (VALS) sv[pos] = v[it];
-            }
-        }
-        __syncthreads();
+        rs_rank_tile<VALS>(kin, vin, tb, tn, shift, mask, S, sk, sv);
         for (uint32_t i = tid; i < tn; i += RS_THREADS) {
             uint64_t key = sk[i];
             uint32_t d = (uint32_t)(key >> shift) & mask;
@@ -435,6 +446,128 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint64_t *__r
         __syncthreads();
         S.run[tid] += S.tcnt[tid];
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------- single-pass radix sort --
+// For sorts of up to OS_MAX_TILES tiles: a histogram kernel counts the first pass's digits,
+// then one kernel per 8-bit pass.  A block of a pass takes the next tile from the pass's
+// ticket counter (so every tile it waits on belongs to a block that is already running),
+// turns the pass's digit counts into the digits' starts, ranks the tile's keys by digit,
+// counts the next pass's digits of its keys, publishes the tile's count of each digit, and
+// each thread (one per digit) adds the counts of the preceding tiles, reading OS_LOOK
+// state words at a time, until it meets a tile whose inclusive prefix is published
+// (decoupled look-back, as in the scan above); the block then publishes its inclusive
+// prefixes and writes its keys to their places.  A state word: flag in bits 63-62 (0
+// nothing, 1 the tile's count, 2 its inclusive prefix), the pass (plus one) in bits 61-56,
+// the value below; the words of all passes share one array, a word of an earlier pass
+// counting as not yet published.  Waits are bounded as in the scan (DEV_ERR_TIMEOUT).
+constexpr int OS_MAX_PASSES = 8;
+constexpr int OS_LOOK = 16;
+constexpr uint64_t OS_MAX_TILES = 1u << 15;
+constexpr uint64_t OS_AGG = 1ull << 62, OS_PRE = 2ull << 62, OS_EPOCH = 0x3Full << 56, OS_VAL = (1ull << 56) - 1;
+
+// Digit counts of the first pass (per-warp shared-memory counts, then one global atomic per
+// digit and block); each pass counts the next pass's digits of its own keys.
+__global__ void __launch_bounds__(RS_THREADS) k_os_hist(const uint64_t *__restrict__ keys, uint64_t n, int shift,
+                                                        uint32_t mask, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[RS_WARPS][256];
+    const int tid = threadIdx.x, w = tid >> 5;
+    for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * RS_THREADS + tid; i < n; i += (uint64_t)gridDim.x * RS_THREADS)
+        atomicAdd(&h[w][(uint32_t)(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ++ww) c += h[ww][tid];
+    if (c) atomicAdd(&hist[tid], c);
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(const uint64_t *__restrict__ kin,
+                                                        const uint32_t *__restrict__ vin,
+                                                        uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                        uint64_t n, int shift, uint32_t mask, uint64_t epoch,
+                                                        const uint32_t *__restrict__ hist,
+                                                        uint32_t *__restrict__ next_hist, int next_shift,
+                                                        uint32_t next_mask, unsigned long long *state,
+                                                        uint32_t *ticket, uint32_t *status, long long budget,
+                                                        int drop_first) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RsSmem &S = *reinterpret_cast<RsSmem *>(smem_raw);
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw + ((sizeof(RsSmem) + 15) / 16) * 16);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_TILE);
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t tb = (uint64_t)tile * RS_TILE;
+    const uint32_t tn = (uint32_t)min((uint64_t)RS_TILE, n - tb);
+    // the digits' starts: exclusive scan of the pass's digit counts (complete: the previous
+    // launch, or the histogram kernel, counted them)
+    const uint32_t dstart = block_excl_scan<uint32_t, RS_THREADS>(hist[tid], S.ws, &S.tot);
+    rs_rank_tile<VALS>(kin, vin, tb, tn, shift, mask, S, sk, sv);
+    if (next_hist) {  // the next pass's digit counts of this tile's keys
+        for (int i = tid; i < 256; i += RS_THREADS) S.wcnt[0][i] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < tn; i += RS_THREADS) atomicAdd(&S.wcnt[0][(uint32_t)(sk[i] >> next_shift) & next_mask], 1u);
+        __syncthreads();
+        const uint32_t c = S.wcnt[0][tid];
+        if (c) atomicAdd(&next_hist[tid], c);
+    }
+    {
+        const uint32_t d = tid;
+        const uint64_t cnt = S.tcnt[d];
+        unsigned long long *mine = state + (uint64_t)tile * 256 + d;
+        uint64_t excl = 0;
+        if (tile == 0) {
+            if (!drop_first) atomicExch(mine, OS_PRE | epoch | cnt);
+        } else {
+            atomicExch(mine, OS_AGG | epoch | cnt);
+            int64_t j = (int64_t)tile - 1;
+            const long long t0 = clock64();
+            for (;;) {
+                uint64_t w[OS_LOOK];
+#pragma unroll
+                for (int k = 0; k < OS_LOOK; ++k) {
+                    const int64_t q = j - k;
+                    w[k] = q >= 0 ? *(volatile unsigned long long *)&state[(uint64_t)q * 256 + d] : (OS_PRE | epoch);
+                }
+                int used = OS_LOOK;
+                bool pre = false;
+#pragma unroll
+                for (int k = 0; k < OS_LOOK; ++k) {
+                    if (used == OS_LOOK && !pre) {
+                        const uint64_t x = w[k];
+                        if ((x >> 62) == 0ull || (x & OS_EPOCH) != epoch) {
+                            used = k;
+                        } else {
+                            excl += x & OS_VAL;
+                            pre = (x >> 62) == 2ull;
+                        }
+                    }
+                }
+                if (pre) break;
+                j -= used;
+                if (used < OS_LOOK && clock64() - t0 > budget) {
+                    atomicOr(status, DEV_ERR_TIMEOUT);
+                    break;
+                }
+            }
+            atomicExch(mine, OS_PRE | epoch | (excl + cnt));
+        }
+        S.run[d] = dstart + excl;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < tn; i += RS_THREADS) {
+        const uint64_t key = sk[i];
+        const uint32_t d = (uint32_t)(key >> shift) & mask;
+        const uint64_t dst = S.run[d] + (i - S.tbase[d]);
+        if (!GN_CHECK(dst < n)) continue;
+        kout[dst] = key;
+        if (VALS) vout[dst] = sv[i];
     }
 }
 
@@ -467,25 +600,87 @@ static RsGeom rs_geometry(uint64_t n) {
     return geo;
 }
 
+// Scratch of the single-pass sort: digit counts (u32) of every pass, the passes' ticket
+// counters and a status word, then the tile states.
+constexpr size_t OS_HIST_OFF = 0, OS_CTR_OFF = OS_MAX_PASSES * 256 * 4, OS_STATE_OFF = OS_CTR_OFF + 64;
+
+static size_t os_scratch_bytes(uint64_t tiles) { return OS_STATE_OFF + (size_t)tiles * 256 * 8; }
+
 size_t radix_scratch_bytes(uint64_t n) {
-    (void)n;
     size_t g = (size_t)num_sms() * RS_MAX_GRID_PER_SM;
     size_t cnt = 256 * g;
-    return cnt * sizeof(uint32_t) + (cnt + 1) * sizeof(uint64_t) + scan_scratch_bytes(cnt) + 256;
+    const size_t three = cnt * sizeof(uint32_t) + (cnt + 1) * sizeof(uint64_t) + scan_scratch_bytes(cnt) + 256;
+    const uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    return tiles <= OS_MAX_TILES ? std::max(three, os_scratch_bytes(tiles)) : three;
 }
 
-const RadixTag TAG_HIT_SORT{"hit_sort_upsweep", "hit_sort_downsweep"};
-const RadixTag TAG_INDEX_SORT{"index_sort_upsweep", "index_sort_downsweep"};
-const RadixTag TAG_RECORD_SORT{"record_sort_upsweep", "record_sort_downsweep"};
+const RadixTag TAG_HIT_SORT{"hit_sort_hist", "hit_sort_pass", "hit_sort_upsweep", "hit_sort_downsweep"};
+const RadixTag TAG_INDEX_SORT{"index_sort_hist", "index_sort_pass", "index_sort_upsweep", "index_sort_downsweep"};
+const RadixTag TAG_RECORD_SORT{"record_sort_hist", "record_sort_pass", "record_sort_upsweep",
+                               "record_sort_downsweep"};
 
 thread_local KernelTimer *g_ktimer = nullptr;
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
-                int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag) {
+// Single-pass sort (tiles <= OS_MAX_TILES): one histogram launch (first pass), then one
+// launch per pass.  drop_first keeps the first tile from publishing its counts (tests of
+// the bounded wait).
+static bool radix_sort_onepass(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n,
+                               int bit_lo, int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag,
+                               uint32_t *status_word, long long budget, int drop_first) {
+    const uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    unsigned char *base = static_cast<unsigned char *>(scratch);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(base + OS_HIST_OFF);  // [p * 256 + digit]
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(base + OS_CTR_OFF);    // [p] tickets, [15] status
+    unsigned long long *state = reinterpret_cast<unsigned long long *>(base + OS_STATE_OFF);
+    uint32_t *status = status_word ? status_word : ctr + 15;
+    GN_CUDA(cudaMemsetAsync(base, 0, OS_CTR_OFF + 64, s));
+    GN_CUDA(cudaMemsetAsync(state, 0, (size_t)tiles * 256 * 8, s));
+    const size_t smem = rs_smem_bytes();
+    static std::once_flag attr_once;  // the pass kernels' shared memory exceeds the default 48 KB
+    std::call_once(attr_once, [smem] {
+        cudaFuncSetAttribute(k_os_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_os_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    auto digit_mask = [&](int shift) { return (1u << std::min(8, bit_hi - shift)) - 1u; };
+    const unsigned hgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * 4));
+    GN_LAUNCH(tag.up, n, s, k_os_hist<<<hgrid, RS_THREADS, 0, s>>>(keys, n, bit_lo, digit_mask(bit_lo), hist));
+    bool flip = false;
+    int p = 0;
+    for (int shift = bit_lo; shift < bit_hi; shift += 8, ++p) {
+        const uint32_t mask = digit_mask(shift);
+        const int nshift = shift + 8;
+        uint32_t *next = nshift < bit_hi ? hist + (p + 1) * 256 : nullptr;
+        const uint32_t nmask = next ? digit_mask(nshift) : 0u;
+        const uint64_t *kin = flip ? keys_alt : keys;
+        uint64_t *kout = flip ? keys : keys_alt;
+        const uint32_t *vin = flip ? vals_alt : vals;
+        uint32_t *vout = flip ? vals : vals_alt;
+        const uint64_t epoch = (uint64_t)(p + 1) << 56;
+        if (vals)
+            GN_LAUNCH(tag.down, n, s,
+                      k_os_pass<true><<<(unsigned)tiles, RS_THREADS, smem, s>>>(
+                          kin, vin, kout, vout, n, shift, mask, epoch, hist + p * 256, next, nshift, nmask, state,
+                          ctr + p, status, budget, drop_first));
+        else
+            GN_LAUNCH(tag.down, n, s,
+                      k_os_pass<false><<<(unsigned)tiles, RS_THREADS, smem, s>>>(
+                          kin, nullptr, kout, nullptr, n, shift, mask, epoch, hist + p * 256, next, nshift, nmask,
+                          state, ctr + p, status, budget, drop_first));
+        flip = !flip;
+    }
+    return flip;
+}
+
+static bool radix_sort_impl(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n,
+                            int bit_lo, int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag,
+                            uint32_t *status_word, long long budget, int drop_first, bool three_kernel) {
     if (n <= 1 || bit_hi <= bit_lo) return false;
+    if (!three_kernel && (n + RS_TILE - 1) / RS_TILE <= OS_MAX_TILES && bit_hi - bit_lo <= 8 * OS_MAX_PASSES)
+        return radix_sort_onepass(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, scratch, s, tag, status_word,
+                                  budget, drop_first);
     RsGeom geo = rs_geometry(n);
     size_t cnt = (size_t)256 * geo.grid;
     uint32_t *counts = static_cast<uint32_t *>(scratch);
@@ -502,21 +697,51 @@ bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *va
         uint64_t *kout = flip ? keys : keys_alt;
         const uint32_t *vin = flip ? vals_alt : vals;
         uint32_t *vout = flip ? vals : vals_alt;
-        GN_LAUNCH(tag.up, n, s,
+        GN_LAUNCH(tag.up3, n, s,
                   k_rs_upsweep<<<geo.grid, RS_THREADS, 0, s>>>(kin, n, geo.chunk, shift, mask, counts));
         exclusive_scan_u32(counts, offs, cnt, scan_scratch, s);
         if (vals) {
-            GN_LAUNCH(tag.down, n, s,
+            GN_LAUNCH(tag.down3, n, s,
                       k_rs_downsweep<true><<<geo.grid, RS_THREADS, smem, s>>>(kin, vin, kout, vout, n, geo.chunk,
                                                                               shift, mask, offs));
         } else {
-            GN_LAUNCH(tag.down, n, s,
+            GN_LAUNCH(tag.down3, n, s,
                       k_rs_downsweep<false><<<geo.grid, RS_THREADS, smem, s>>>(kin, nullptr, kout, nullptr, n,
                                                                                geo.chunk, shift, mask, offs));
         }
         flip = !flip;
     }
     return flip;
+}
+
+bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
+                int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag) {
+    static const bool three = getenv("GN_SORT_THREE_KERNEL") != nullptr;
+    return radix_sort_impl(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, scratch, s, tag, g_wait_status,
+                           SCAN_WAIT_BUDGET, 0, three);
+}
+
+// Sort of caller buffers in place (keys, and vals if given) by bits [bit_lo, bit_hi) with a
+// given wait budget; drop_first as in radix_sort_onepass, three_kernel forces the
+// three-kernel passes.  Returns whether a wait ran out.
+bool debug_sort(uint64_t *keys, uint32_t *vals, uint64_t n, int bit_lo, int bit_hi, long long budget,
+                int drop_first, bool three_kernel, cudaStream_t s) {
+    DeviceArena arena(s);
+    uint64_t *keys_alt = arena.alloc_n<uint64_t>(std::max<uint64_t>(n, 1));
+    uint32_t *vals_alt = vals ? arena.alloc_n<uint32_t>(std::max<uint64_t>(n, 1)) : nullptr;
+    void *scr = arena.alloc(radix_scratch_bytes(n));
+    uint32_t *st = arena.alloc_n<uint32_t>(1);
+    GN_CUDA(cudaMemsetAsync(st, 0, 4, s));
+    const bool flip = radix_sort_impl(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, scr, s, TAG_RECORD_SORT, st,
+                                      budget, drop_first, three_kernel);
+    if (flip) {
+        GN_CUDA(cudaMemcpyAsync(keys, keys_alt, 8 * n, cudaMemcpyDeviceToDevice, s));
+        if (vals) GN_CUDA(cudaMemcpyAsync(vals, vals_alt, 4 * n, cudaMemcpyDeviceToDevice, s));
+    }
+    uint32_t h = 0;
+    GN_CUDA(cudaMemcpyAsync(&h, st, 4, cudaMemcpyDeviceToHost, s));
+    GN_CUDA(cudaStreamSynchronize(s));
+    return (h & DEV_ERR_TIMEOUT) != 0;
 }
 
 // --------------------------------------------------------- record sort --

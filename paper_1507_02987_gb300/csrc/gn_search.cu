@@ -1025,38 +1025,74 @@ __global__ void k_stitch_sweep(const DevHsp *__restrict__ in, uint32_t n, uint32
 }
 
 // -------------------------------------------------- a10: overlap merging --
-// Records sorted by (qi, seq, qs, ds, qe, de).  The first record of each
-// (qi, seq) run sweeps the run: each record joins the current box when both its
-// query and bank ranges intersect the box, otherwise it starts a new box.  Box
-// i is written at the index of its first record; flag marks box heads.
+// Records sorted by (qi, seq, qs).  The first record of each (qi, seq) run sweeps
+// the run in (qs, ds, qe) order (records of one qs, rarely more than one, are taken
+// by increasing (ds, qe); de = ds + qe - qs for these ungapped HSPs, so records
+// equal in (ds, qe) are equal): each record joins the current box when both its
+// query and bank ranges intersect the box, otherwise it starts a new box.  The
+// run's boxes are written, in that order, at its first indices, flagged 1; its
+// other indices are flagged 0.
+__device__ __forceinline__ uint64_t ov_key(const DevHsp &h) { return ((uint64_t)h.ds << 32) | h.qe; }
+
 __global__ void k_overlap_sweep(const DevHsp *__restrict__ in, uint32_t n, DevHsp *__restrict__ out,
                                 uint32_t *__restrict__ flag) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    // only the head of a (qi, seq) run writes, for every record of the run
-    if (i > 0 && in[i - 1].qi == in[i].qi && in[i - 1].seq == in[i].seq) return;
-    uint32_t j = i;
-    while (j < n) {
-        DevHsp box = in[j];
-        uint32_t head = j;
-        ++j;
-        while (j < n && in[j].qi == box.qi && in[j].seq == box.seq) {
-            DevHsp h = in[j];
-            bool q_meet = h.qs < box.qe && box.qs < h.qe;
-            bool d_meet = h.ds < box.de && box.ds < h.de;
-            if (!(q_meet && d_meet)) break;
+    const uint32_t qi = in[i].qi, seq = in[i].seq;
+    if (i > 0 && in[i - 1].qi == qi && in[i - 1].seq == seq) return;  // not the head of a run
+    uint32_t o = i;  // next box slot
+    bool open = false;
+    DevHsp box;
+    auto visit = [&](const DevHsp &h) {
+        if (open && h.qs < box.qe && box.qs < h.qe && h.ds < box.de && box.ds < h.de) {
             box.qs = min(box.qs, h.qs);
             box.qe = max(box.qe, h.qe);
             box.ds = min(box.ds, h.ds);
             box.de = max(box.de, h.de);
-            flag[j] = 0;
-            ++j;
+            return;
         }
-        box.len = min(box.qe - box.qs, box.de - box.ds);
-        out[head] = box;
-        flag[head] = 1;
-        if (j >= n || in[j].qi != in[i].qi || in[j].seq != in[i].seq) break;
+        if (open) {
+            box.len = min(box.qe - box.qs, box.de - box.ds);
+            out[o] = box;
+            flag[o++] = 1;
+        }
+        box = h;
+        open = true;
+    };
+    uint32_t g0 = i;
+    while (g0 < n && in[g0].qi == qi && in[g0].seq == seq) {
+        const uint32_t qs = in[g0].qs;
+        uint32_t g1 = g0 + 1;
+        while (g1 < n && in[g1].qi == qi && in[g1].seq == seq && in[g1].qs == qs) ++g1;
+        if (g1 - g0 == 1) {
+            visit(in[g0]);
+        } else {
+            // the group's records by increasing (ds, qe), then index: each step takes the
+            // smallest (key, index) above the last one taken
+            uint64_t last_k = 0;
+            uint32_t last_j = 0;
+            for (uint32_t t = g0; t < g1; ++t) {
+                uint64_t best_k = ~0ull;
+                uint32_t best_j = g1;
+                for (uint32_t j = g0; j < g1; ++j) {
+                    const uint64_t kj = ov_key(in[j]);
+                    const bool after = t == g0 || kj > last_k || (kj == last_k && j > last_j);
+                    if (after && (kj < best_k || (kj == best_k && j < best_j))) {
+                        best_k = kj;
+                        best_j = j;
+                    }
+                }
+                visit(in[best_j]);
+                last_k = best_k;
+                last_j = best_j;
+            }
+        }
+        g0 = g1;
     }
+    box.len = min(box.qe - box.qs, box.de - box.ds);
+    out[o] = box;
+    flag[o++] = 1;
+    for (uint32_t j = o; j < g0; ++j) flag[j] = 0;
 }
 
 // ----------------------------------------------------- a11: selection --
@@ -2752,11 +2788,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     DevHsp *merged = arena.alloc_n<DevHsp>(n_hsp);
     if (n_hsp) {
         uint32_t *perm = arena.alloc_n<uint32_t>(n_hsp);
-        // (qi, seq, qs, ds, qe, de) order: de = ds + qe - qs for the ungapped HSPs, so it is not keyed
+        // (qi, seq, qs) order; the sweep takes the records of one qs by (ds, qe)
         sort_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, n_hsp,
-                     {{W_QI, qib, false}, {W_SEQ, seqb, false}, {W_QS, qposb, false}, {W_DS, posb, false},
-                      {W_QE, qposb, false}},
-                     perm, arena, s);
+                     {{W_QI, qib, false}, {W_SEQ, seqb, false}, {W_QS, qposb, false}}, perm, arena, s);
         DevHsp *srt = arena.alloc_n<DevHsp>(n_hsp);
         gather_records(reinterpret_cast<const uint32_t *>(hsp), HSP_WORDS, perm, n_hsp,
                        reinterpret_cast<uint32_t *>(srt), s);
