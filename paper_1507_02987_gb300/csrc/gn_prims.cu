@@ -716,7 +716,7 @@ static bool radix_sort_impl(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, 
 
 bool radix_sort(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint64_t n, int bit_lo,
                 int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag) {
-    static const bool three = getenv("GN_SORT_THREE_KERNEL") != nullptr;
+    const bool three = getenv("GN_SORT_THREE_KERNEL") != nullptr;
     return radix_sort_impl(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, scratch, s, tag, g_wait_status,
                            SCAN_WAIT_BUDGET, 0, three);
 }

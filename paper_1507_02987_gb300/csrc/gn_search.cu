@@ -899,14 +899,17 @@ struct BaseCursor {
 // (score += s; if score > best: best = score, ext = e; else if best - score > X:
 // stop) stops at the first e where max(best so far, score_e) - score_e > X, and
 // ext is the first step that reached the final best.  Returns ext.
+// The walk continues a lane's walk: steps e_first.. with the score, best and ext that the
+// steps before e_first left (0, 0, 0 and e_first = 1 for a fresh walk).
 template <int DIR>
 __device__ __forceinline__ uint32_t xdrop_walk_warp(const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
                                                     const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
                                                     uint64_t qg0, uint64_t dg0, uint32_t emax, int32_t match,
-                                                    int32_t mismatch, int32_t X, int lane) {
-    int32_t carry_score = 0, carry_best = 0;
-    uint32_t carry_ext = 0;
-    for (uint32_t e0 = 1; e0 <= emax; e0 += 32) {
+                                                    int32_t mismatch, int32_t X, int lane, uint32_t e_first,
+                                                    int32_t score0, int32_t best0, uint32_t ext0) {
+    int32_t carry_score = score0, carry_best = best0;
+    uint32_t carry_ext = ext0;
+    for (uint32_t e0 = e_first; e0 <= emax; e0 += 32) {
         const uint32_t e = e0 + lane;
         const bool in = e <= emax;
         int32_t sc = 0;
@@ -945,27 +948,132 @@ __device__ __forceinline__ uint32_t xdrop_walk_warp(const uint32_t *__restrict__
     return carry_ext;
 }
 
-// One warp per HSP: left end, then right end.
+// 16 bases from position p (p >= -16; bases before 0 read as code 0, non-base): 2-bit
+// codes with base p in bits 31-30, and a mask with bit i set when base p + i is a non-base.
+// The packed arrays carry two words past the last base, so p + 15 may pass the end.
+__device__ __forceinline__ void base_window16(const uint32_t *__restrict__ pk, const uint32_t *__restrict__ nb,
+                                             int64_t p, uint32_t &codes, uint32_t &bad) {
+    const int64_t a = p >> 4, b = p >> 5;  // floor division
+    const uint32_t w0 = a >= 0 ? pk[a] : 0u, w1 = pk[a + 1];
+    const uint32_t off = (uint32_t)(p & 15);
+    codes = (uint32_t)((((uint64_t)w0 << 32) | w1) >> (32 - 2 * off));
+    const uint32_t n0 = b >= 0 ? nb[b] : 0xFFFFFFFFu, n1 = nb[b + 1];
+    bad = (uint32_t)(((((uint64_t)n1) << 32) | n0) >> (uint32_t)(p & 31)) & 0xFFFFu;
+}
+
+// One direction of the walk on one lane, by the sequential rule, for at most lim steps,
+// 16 steps per window of bases: returns whether the walk ended (the drop passed X, or the
+// sequence ended); score, best, ext and the steps taken are left for a continuation.
+template <int DIR>
+__device__ __forceinline__ bool xdrop_walk_lane(const uint32_t *__restrict__ qpk, const uint32_t *__restrict__ qnb,
+                                                const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
+                                                uint64_t qg0, uint64_t dg0, uint32_t emax, int32_t match,
+                                                int32_t mismatch, int32_t X, uint32_t lim, int32_t &score,
+                                                int32_t &best, uint32_t &ext, uint32_t &steps) {
+    score = 0;
+    best = 0;
+    ext = 0;
+    const uint32_t until = min(emax, lim);
+    for (uint32_t e0 = 0; e0 < until; e0 += 16) {
+        // steps e0 + 1 .. e0 + 16: positions qg0 + e0 .. + 15 (right), qg0 - e0 - 16 .. - 1 (left)
+        const int64_t qp = DIR > 0 ? (int64_t)(qg0 + e0) : (int64_t)qg0 - (int64_t)e0 - 16;
+        const int64_t dp = DIR > 0 ? (int64_t)(dg0 + e0) : (int64_t)dg0 - (int64_t)e0 - 16;
+        uint32_t wq, bq, wd, bd;
+        base_window16(qpk, qnb, qp, wq, bq);
+        base_window16(bpk, bnb, dp, wd, bd);
+        const uint32_t x = ~(wq ^ wd), eq = x & (x >> 1);  // bit 30 - 2k: codes equal at window base k
+        const uint32_t bad = bq | bd;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const uint32_t e = e0 + (uint32_t)t + 1;
+            if (e > until) {
+                steps = until;
+                return until == emax;
+            }
+            const int k = DIR > 0 ? t : 15 - t;
+            const bool same = ((eq >> (30 - 2 * k)) & 1u) && !((bad >> k) & 1u);
+            score += same ? match : mismatch;
+            if (score > best) {
+                best = score;
+                ext = e;
+            } else if (best - score > X) {
+                steps = e;
+                return true;
+            }
+        }
+    }
+    steps = until;
+    return until == emax;
+}
+
+// X-drop extension of both ends of every HSP.  Each lane walks one HSP's ends on its own
+// (most walks end within a few dozen steps) for at most lim steps each; the warp then
+// continues the walks that did not end, one after the other, 32 steps per round.
 __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__restrict__ qpk,
                         const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
                         const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
                         const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch, int32_t X,
-                        uint32_t nq, uint32_t n_seqs) {
+                        uint32_t nq, uint32_t n_seqs, uint32_t lim) {
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
-        DevHsp r = h[i];
-        if (!GN_CHECK(r.qi < nq && r.seq < n_seqs)) continue;
-        const uint64_t qb = qstart[r.qi], sb = seq_start[r.seq];
-        const uint32_t m = (uint32_t)(qstart[r.qi + 1] - qb), L = (uint32_t)(seq_start[r.seq + 1] - sb);
-        const uint32_t el = xdrop_walk_warp<-1>(qpk, qnb, bpk, bnb, qb + r.qs, sb + r.ds, min(r.qs, r.ds), match,
-                                               mismatch, X, lane);
-        const uint32_t er = xdrop_walk_warp<1>(qpk, qnb, bpk, bnb, qb + r.qe, sb + r.de, min(m - r.qe, L - r.de),
-                                              match, mismatch, X, lane);
-        r.qs -= el; r.ds -= el;
-        r.qe += er; r.de += er;
-        r.len = min(r.qe - r.qs, r.de - r.ds);
-        if (lane == 0) h[i] = r;
+    for (uint32_t b0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; b0 < n; b0 += nwarps * 32u) {
+        const uint32_t i = b0 + lane;
+        bool valid = i < n;
+        DevHsp r;
+        uint64_t qb = 0, sb = 0;
+        uint32_t emax_l = 0, emax_r = 0;
+        if (valid) {
+            r = h[i];
+            valid = GN_CHECK(r.qi < nq && r.seq < n_seqs);
+        }
+        if (valid) {
+            qb = qstart[r.qi];
+            sb = seq_start[r.seq];
+            const uint32_t m = (uint32_t)(qstart[r.qi + 1] - qb), L = (uint32_t)(seq_start[r.seq + 1] - sb);
+            emax_l = min(r.qs, r.ds);
+            emax_r = min(m - r.qe, L - r.de);
+        }
+        int32_t sl = 0, bl = 0, sr = 0, br = 0;
+        uint32_t el = 0, er = 0, nl = 0, nr = 0;
+        bool done_l = true, done_r = true;
+        if (valid) {
+            done_l = xdrop_walk_lane<-1>(qpk, qnb, bpk, bnb, qb + r.qs, sb + r.ds, emax_l, match, mismatch, X, lim, sl,
+                                         bl, el, nl);
+            done_r = xdrop_walk_lane<1>(qpk, qnb, bpk, bnb, qb + r.qe, sb + r.de, emax_r, match, mismatch, X, lim, sr,
+                                        br, er, nr);
+        }
+        // walks that did not end: the whole warp continues them
+        uint32_t todo = __ballot_sync(0xffffffffu, !done_l || !done_r);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint64_t q0 = __shfl_sync(0xffffffffu, qb, src), s0 = __shfl_sync(0xffffffffu, sb, src);
+            const bool cl = __shfl_sync(0xffffffffu, !done_l, src), cr = __shfl_sync(0xffffffffu, !done_r, src);
+            if (cl) {
+                const uint32_t qs = __shfl_sync(0xffffffffu, valid ? r.qs : 0u, src);
+                const uint32_t ds = __shfl_sync(0xffffffffu, valid ? r.ds : 0u, src);
+                const uint32_t x = xdrop_walk_warp<-1>(
+                    qpk, qnb, bpk, bnb, q0 + qs, s0 + ds, __shfl_sync(0xffffffffu, emax_l, src), match, mismatch, X,
+                    lane, __shfl_sync(0xffffffffu, nl, src) + 1, __shfl_sync(0xffffffffu, sl, src),
+                    __shfl_sync(0xffffffffu, bl, src), __shfl_sync(0xffffffffu, el, src));
+                if (lane == src) el = x;
+            }
+            if (cr) {
+                const uint32_t qe = __shfl_sync(0xffffffffu, valid ? r.qe : 0u, src);
+                const uint32_t de = __shfl_sync(0xffffffffu, valid ? r.de : 0u, src);
+                const uint32_t x = xdrop_walk_warp<1>(
+                    qpk, qnb, bpk, bnb, q0 + qe, s0 + de, __shfl_sync(0xffffffffu, emax_r, src), match, mismatch, X,
+                    lane, __shfl_sync(0xffffffffu, nr, src) + 1, __shfl_sync(0xffffffffu, sr, src),
+                    __shfl_sync(0xffffffffu, br, src), __shfl_sync(0xffffffffu, er, src));
+                if (lane == src) er = x;
+            }
+        }
+        if (valid) {
+            r.qs -= el; r.ds -= el;
+            r.qe += er; r.de += er;
+            r.len = min(r.qe - r.qs, r.de - r.ds);
+            h[i] = r;
+        }
     }
 }
 
@@ -2766,15 +2874,20 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
 
     // a9: extension
     if (n_hsp) {
-        // resident warps only: each walks a fixed stride of the HSPs, so warps that would wait
-        // for a second wave would finish late
+        // resident warps only: each takes a fixed stride of 32-HSP groups, so warps that would
+        // wait for a second wave would finish late
         int xocc = 0;
         GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xocc, k_xdrop, 256, 0));
-        const uint64_t xwarps = std::min<uint64_t>(n_hsp, (uint64_t)num_sms() * std::max(xocc, 1) * 8);
+        const uint64_t xwarps =
+            std::min<uint64_t>((n_hsp + 31) / 32, (uint64_t)num_sms() * std::max(xocc, 1) * 8);
+        // steps a lane walks alone before the warp takes the walk over (GN_XDROP_LANE_STEPS overrides)
+        uint32_t lim = 64;
+        if (const char *e = getenv("GN_XDROP_LANE_STEPS")) lim = (uint32_t)std::max(0l, strtol(e, nullptr, 10));
         GN_LAUNCH("k_xdrop", n_hsp, s,
                   k_xdrop<<<blocks_for(xwarps * 32, 256), 256, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d,
                                                                       ix->bank.pk, ix->bank.nb, ix->seq_start_d,
-                                                                      sc.match, sc.mismatch, p.xdrop, nq, ix->n_seqs));
+                                                                      sc.match, sc.mismatch, p.xdrop, nq, ix->n_seqs,
+                                                                      lim));
     }
     timer.mark("xdrop_extend");
     if (keep) {

@@ -240,7 +240,9 @@ def test_chunked_equals_unchunked(gn, mid_small, monkeypatch):
                                  {"GN_BUCKET_CAP": "64", "GN_MAX_CHUNK_HITS": "30000"},
                                  {"GN_BUCKET_CAP": "64", "GN_SPILL_ROOM": "16"}, {"GN_SW_LONG_ROWS": "1"},
                                  {"GN_SW_LONG_ROWS": "100"}, {"GN_SW_LANES": "16"}, {"GN_SW_LANES": "32"},
-                                 {"GN_BUCKET_TARGET": "2048"}, {"GN_BUCKET_TARGET": "16384"}])
+                                 {"GN_BUCKET_TARGET": "2048"}, {"GN_BUCKET_TARGET": "16384"},
+                                 {"GN_XDROP_LANE_STEPS": "0"}, {"GN_XDROP_LANE_STEPS": "5"},
+                                 {"GN_XDROP_LANE_STEPS": "100000"}, {"GN_SORT_THREE_KERNEL": "1"}])
 def test_hit_grouping_paths_agree_with_oracle(gn, mid_small, monkeypatch, env):
     """The global sort path, the bucketed path and its overflow fallback give the oracle's HSPs."""
     bank, qs, ix, ox = mid_small
