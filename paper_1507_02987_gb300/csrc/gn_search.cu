@@ -2825,9 +2825,14 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     GN_CUDA(cudaMemsetAsync(status, 0, 4, s));
                 }
                 // buckets with more candidates than a warp holds: a block each
+                int bocc = 0;
+                if (n_big)
+                    GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bocc, k_bucket_group_block, 256, 0));
+                const unsigned bgrid =
+                    (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(n_big, (uint64_t)num_sms() * std::max(bocc, 1)));
                 if (n_big) emit([&](DevHsp *o, uint32_t room) {
                     GN_LAUNCH("k_bucket_group_block", n_big, s,
-                              k_bucket_group_block<<<num_sms() * 4, 256, 0, s>>>(
+                              k_bucket_group_block<<<bgrid, 256, 0, s>>>(
                                   bkeys, bcount, bcap, bq, big, big_count, qa, k, p.max_hit_distance, hit_min_len,
                                   singles, seq_map(ix), o, counter, room, status));
                 });
