@@ -1755,6 +1755,14 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
             dcodes = segwin_codes(sd, o0);
             dbad = segwin_bad(sd, o0);
         }
+        // bit k: offset b0 + k pairs two equal bases (the row's query base against the K codes)
+        uint32_t dm = 0;
+        if (SEG && lane_on && qc < 4u) {
+            const uint32_t x = ~((uint32_t)(dcodes >> 32) ^ (qc * 0x55555555u)), eq = x & (x >> 1);
+#pragma unroll
+            for (int k = 0; k < K; ++k) dm |= ((eq >> (30 - 2 * k)) & 1u) << k;
+            dm &= ~dbad;
+        }
         const uint32_t rowbase = (uint32_t)r << 16;
         int32_t H0[K], E[K], X[K];
         uint32_t C[K], SE[K];
@@ -1769,10 +1777,14 @@ __device__ __forceinline__ void sw_group(bool valid, const DevHsp &h, const uint
             // diagonal: from the previous row's H, or a start here
             const int32_t Hd = pH[k];
             const uint32_t SD = Hd > 0 ? pSH[k] : rowbase | (uint32_t)(b0 + k);
-            uint32_t d;
-            if (SEG) d = ((dbad >> k) & 1u) ? 4u : (uint32_t)(dcodes >> (62 - 2 * k)) & 3u;
-            else d = ((amask >> k) & 1u) ? wd.at(jb + k) : 4u;  // the window covers the active cells only
-            const int32_t Dg = Hd + ((qc < 4u && d == qc) ? match : mismatch);
+            bool same;
+            if (SEG) {
+                same = (dm >> k) & 1u;
+            } else {
+                const uint32_t d = ((amask >> k) & 1u) ? wd.at(jb + k) : 4u;  // the window covers the active cells only
+                same = qc < 4u && d == qc;
+            }
+            const int32_t Dg = Hd + (same ? match : mismatch);
             // diagonal over E on ties
             bool pd;
             const int32_t cv = __vibmax_s32(Dg, E[k], &pd);
