@@ -1210,7 +1210,7 @@ __global__ void k_overlap_sweep(const DevHsp *__restrict__ in, uint32_t n, DevHs
 // length T comes from two 256-bin histograms (high and low byte of the length); the
 // selected records are those longer than T and the first ones of length T.
 constexpr int SQ_CAP = 1024;  // largest N this kernel handles
-constexpr int SQ_THREADS = 256;
+constexpr int SQ_THREADS = 512;
 
 __global__ void __launch_bounds__(SQ_THREADS) k_select_query(const DevHsp *__restrict__ rec,
                                                              const uint32_t *__restrict__ qfirst,
@@ -1231,10 +1231,19 @@ __global__ void __launch_bounds__(SQ_THREADS) k_select_query(const DevHsp *__res
         for (int level = 0; level < 2; ++level) {
             for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
             __syncthreads();
-            for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x) {
-                const uint32_t len = min(rec[i].len, 65535u);
-                if (level == 0) atomicAdd(&hist[len >> 8], 1u);
-                else if ((len >> 8) == hb) atomicAdd(&hist[len & 0xFFu], 1u);
+            // one shared-memory atomic per distinct bin of a warp's 32 records (lengths are
+            // concentrated in few bins)
+            for (uint32_t i0 = a + (threadIdx.x & ~31u); i0 < b; i0 += blockDim.x) {
+                const uint32_t i = i0 + (threadIdx.x & 31u);
+                uint32_t bin = 256u;
+                if (i < b) {
+                    const uint32_t len = min(rec[i].len, 65535u);
+                    if (level == 0) bin = len >> 8;
+                    else if ((len >> 8) == hb) bin = len & 0xFFu;
+                }
+                const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+                if (bin < 256u && (threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1))
+                    atomicAdd(&hist[bin], (uint32_t)__popc(peers));
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -1251,24 +1260,30 @@ __global__ void __launch_bounds__(SQ_THREADS) k_select_query(const DevHsp *__res
         }
         r_eq = N - above;  // records of length T to take, in array order
     }
-    // ordered compaction of the selected records (array order), keyed by (length desc, position)
-    uint32_t base = 0, eq_seen = 0;
-    for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
-        const uint32_t i = i0 + threadIdx.x;
-        uint32_t len = 0;
-        bool eq = false, gt = false;
-        if (i < n) {
-            len = min(rec[a + i].len, 65535u);
-            gt = n <= N || len > T;
-            eq = !gt && len == T;
-        }
-        uint32_t eq_tot = 0, take_tot = 0;
-        const uint32_t eq_rank = eq_seen + block_excl_scan(eq ? 1u : 0u, warp_tot, eq_tot);
+    // ordered compaction of the selected records (array order), keyed by (length desc, position):
+    // each thread takes a contiguous run of records, counts its records longer than T and of
+    // length T, and two block scans give its first output slot and its first rank among the
+    // records of length T
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+    uint32_t n_gt = 0, n_eq = 0;
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint32_t len = min(rec[a + i].len, 65535u);
+        const bool gt = n <= N || len > T;
+        n_gt += gt ? 1u : 0u;
+        n_eq += (!gt && len == T) ? 1u : 0u;
+    }
+    uint32_t tot = 0;
+    uint32_t eq_rank = block_excl_scan(n_eq, warp_tot, tot);
+    const uint32_t n_take = n_gt + min(n_eq, r_eq > eq_rank ? r_eq - eq_rank : 0u);
+    uint32_t pos = block_excl_scan(n_take, warp_tot, tot);
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint32_t len = min(rec[a + i].len, 65535u);
+        const bool gt = n <= N || len > T;
+        const bool eq = !gt && len == T;
         const bool take = gt || (eq && eq_rank < r_eq);
-        const uint32_t pos = base + block_excl_scan(take ? 1u : 0u, warp_tot, take_tot);
-        if (take) keys[pos] = ((uint64_t)(65535u - len) << 32) | i;
-        base += take_tot;
-        eq_seen += eq_tot;
+        eq_rank += eq ? 1u : 0u;
+        if (take) keys[pos++] = ((uint64_t)(65535u - len) << 32) | i;
     }
     __syncthreads();
     // bitonic sort of the nsel keys (unique: they carry the position)
