@@ -414,7 +414,8 @@ __device__ __forceinline__ void bucket_place(uint32_t b, uint64_t key, uint32_t 
 // Buckets have a fixed capacity bcap; hits past it go to the spill list in global
 // hit-key format, which the global sort path handles.  count_only: no placement,
 // kept_total[0] counts the kept core hits and kept_total[1] all core hits of the
-// tiles visited (tiles 0, tile_step, 2 tile_step, ...).
+// tiles visited (tiles 0, tile_step, 2 tile_step, ...).  kept_total[2] hands out the
+// tiles (zero at launch).
 __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     const uint32_t *__restrict__ qinfo, const uint32_t *__restrict__ src, const uint64_t *__restrict__ hoff,
     uint64_t xa, uint64_t xb, const uint32_t *__restrict__ post, uint32_t qa, const uint32_t *__restrict__ bbase,
@@ -446,8 +447,13 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     __shared__ uint32_t wtot[32];
     uint32_t my_kept = 0;
     unsigned long long my_core = 0;  // core hits of the visited tiles (count-only runs)
-    for (uint64_t t0 = xa + (uint64_t)blockIdx.x * tile_step * tpos; t0 < xb;
-         t0 += (uint64_t)gridDim.x * tile_step * tpos) {
+    // tiles from a counter (kept_total[2]): blocks that drew small tiles take more
+    __shared__ uint64_t s_t0;
+    for (;;) {
+        if (threadIdx.x == 0) s_t0 = xa + atomicAdd(kept_total + 2, 1ull) * tile_step * (uint64_t)tpos;
+        __syncthreads();
+        const uint64_t t0 = s_t0;
+        if (t0 >= xb) break;
         const uint64_t t1 = min(xb, t0 + (uint64_t)tpos);
         const uint64_t lo = t0 - xa > halo ? t0 - halo : xa, hi = min(xb, t1 + halo);
         const uint32_t span = (uint32_t)(hi - lo);
@@ -2728,7 +2734,8 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const unsigned fgrid = (unsigned)std::max<uint64_t>(
                     1, std::min<uint64_t>(tiles, (uint64_t)num_sms() * std::max(focc, 1) * 4));
                 unsigned long long n_spill = 0, n_kept = 0;
-                unsigned long long *kept_total = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(2));
+                // kept hits, core hits (sampling), tile counter
+                unsigned long long *kept_total = reinterpret_cast<unsigned long long *>(carena.alloc_n<uint64_t>(3));
                 // Keep rate of the repeat filter, measured on a sample of tiles (no placement): the plan
                 // above assumes the stride-11 rate; where far more hits are kept (small strides, where
                 // overlapping k-mers put most hits next to another on their diagonal) the buckets are
@@ -2748,7 +2755,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     const uint32_t tile_step = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(256, tiles / 256));
                     const uint64_t stiles = (tiles + tile_step - 1) / tile_step;
                     unsigned long long got[2] = {0, 0};
-                    GN_CUDA(cudaMemsetAsync(kept_total, 0, 16, s));
+                    GN_CUDA(cudaMemsetAsync(kept_total, 0, 24, s));
                     GN_LAUNCH("k_bucket_fill_sample", Hc / tile_step, s,
                               fill_kernel<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(stiles, fgrid)), fthreads,
                                             bf_smem, s>>>(
@@ -2775,7 +2782,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                     for (int attempt = 0;; ++attempt) {
                         GN_CUDA(cudaMemsetAsync(bcount, 0, 4ull * NB, s));
                         GN_CUDA(cudaMemsetAsync(spill_count, 0, 8, s));
-                        GN_CUDA(cudaMemsetAsync(kept_total, 0, 8, s));
+                        GN_CUDA(cudaMemsetAsync(kept_total, 0, 24, s));
                         GN_LAUNCH("k_bucket_fill", Hc, s,
                                   fill_kernel<<<fgrid, fthreads, bf_smem, s>>>(
                                       qinfo, src, hoff, xa, xb, ix->post_d, qa, d_bbase, d_bshift, bcount, bkeys, bcap,
