@@ -1019,10 +1019,14 @@ __global__ void k_xdrop(DevHsp *__restrict__ h, uint32_t n, const uint32_t *__re
                         const uint32_t *__restrict__ qnb, const uint64_t *__restrict__ qstart,
                         const uint32_t *__restrict__ bpk, const uint32_t *__restrict__ bnb,
                         const uint64_t *__restrict__ seq_start, int32_t match, int32_t mismatch, int32_t X,
-                        uint32_t nq, uint32_t n_seqs, uint32_t lim) {
+                        uint32_t nq, uint32_t n_seqs, uint32_t lim, uint32_t *__restrict__ next_group) {
     const int lane = threadIdx.x & 31;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t b0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; b0 < n; b0 += nwarps * 32u) {
+    for (;;) {
+        // groups of 32 HSPs from a counter: a warp whose group held long walks takes fewer
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(next_group, 1u);
+        const uint32_t b0 = __shfl_sync(0xffffffffu, g, 0) * 32u;
+        if (b0 >= n) break;
         const uint32_t i = b0 + lane;
         bool valid = i < n;
         DevHsp r;
@@ -2913,8 +2917,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
 
     // a9: extension
     if (n_hsp) {
-        // resident warps only: each takes a fixed stride of 32-HSP groups, so warps that would
-        // wait for a second wave would finish late
+        // resident warps only, taking 32-HSP groups from a counter
+        uint32_t *next_group = arena.alloc_n<uint32_t>(1);
+        GN_CUDA(cudaMemsetAsync(next_group, 0, 4, s));
         int xocc = 0;
         GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xocc, k_xdrop, 256, 0));
         const uint64_t xwarps =
@@ -2926,7 +2931,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                   k_xdrop<<<blocks_for(xwarps * 32, 256), 256, 0, s>>>(hsp, n_hsp, qp.pk, qp.nb, qstart_d,
                                                                       ix->bank.pk, ix->bank.nb, ix->seq_start_d,
                                                                       sc.match, sc.mismatch, p.xdrop, nq, ix->n_seqs,
-                                                                      lim));
+                                                                      lim, next_group));
     }
     timer.mark("xdrop_extend");
     if (keep) {
