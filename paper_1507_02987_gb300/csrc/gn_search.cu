@@ -2848,10 +2848,10 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                       singles, seq_map(ix), o, counter, room, gsp + spilled_fill,
                                       (unsigned long long)group_room, ovf_count, status, counter + 1, big,
                                       big_count));
+                        // read back with the HSP count, in emit's one synchronisation
+                        GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
+                        GN_CUDA(cudaMemcpyAsync(&n_big, big_count, 4, cudaMemcpyDeviceToHost, s));
                     });
-                    GN_CUDA(cudaMemcpyAsync(&n_ovf, ovf_count, 8, cudaMemcpyDeviceToHost, s));
-                    GN_CUDA(cudaMemcpyAsync(&n_big, big_count, 4, cudaMemcpyDeviceToHost, s));
-                    GN_CUDA(cudaStreamSynchronize(s));
                     if (n_ovf <= group_room) break;
                     GN_REQUIRE(attempt < 3, GN_EINTERNAL, "hit-bucket overflow sizing did not converge");
                     n_hsp = hsp_before;  // the rerun emits this chunk's bucket HSPs again
