@@ -416,6 +416,8 @@ __device__ __forceinline__ void bucket_place(uint32_t b, uint64_t key, uint32_t 
 // kept_total[0] counts the kept core hits and kept_total[1] all core hits of the
 // tiles visited (tiles 0, tile_step, 2 tile_step, ...).  kept_total[2] hands out the
 // tiles (zero at launch).
+// FB, FB2: the filters' sizes in bits as constants (0: the run-time fbits, fbits2).
+template <int FB, int FB2>
 __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     const uint32_t *__restrict__ qinfo, const uint32_t *__restrict__ src, const uint64_t *__restrict__ hoff,
     uint64_t xa, uint64_t xb, const uint32_t *__restrict__ post, uint32_t qa, const uint32_t *__restrict__ bbase,
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(512, 2) k_bucket_fill(
     extern __shared__ __align__(16) unsigned char bf_smem[];
     const uint32_t halo = filter ? D : 0u;
     const uint32_t span_max = (uint32_t)tpos + 2u * halo;
-    const int wbits = fbits - 5, wbits2 = fbits2 - 5;
+    const int wbits = (FB ? FB : fbits) - 5, wbits2 = (FB2 ? FB2 : fbits2) - 5;
     const uint32_t nwords = filter ? 1u << wbits : 0u, nwords2 = filter ? 1u << wbits2 : 0u;
     const uint4 *__restrict__ post4 = reinterpret_cast<const uint4 *>(post);
     uint64_t *stage_key = reinterpret_cast<uint64_t *>(bf_smem);  // G' << 16 | query offset
@@ -2384,7 +2386,8 @@ void allow_max_smem(int device) {
         GN_CUDA(cudaFuncGetAttributes(&fa, fn));
         GN_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
     };
-    allow(reinterpret_cast<const void *>(k_bucket_fill));
+    allow(reinterpret_cast<const void *>(k_bucket_fill<0, 0>));
+    allow(reinterpret_cast<const void *>(k_bucket_fill<19, 17>));
     allow(reinterpret_cast<const void *>(k_bucket_group_warp));
     done[device] = true;
 }
@@ -2731,7 +2734,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 }
                 const size_t bf_smem = bucket_fill_smem(tpos, filter ? p.max_hit_distance : 0u, filter, fbits, fbits2,
                                                         stage_cap);
-                auto fill_kernel = k_bucket_fill;
+                auto fill_kernel = (fbits == 19 && fbits2 == 17) ? k_bucket_fill<19, 17> : k_bucket_fill<0, 0>;
                 allow_max_smem(ix->device);
                 int focc = 0;
                 GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, fill_kernel, fthreads, bf_smem));
