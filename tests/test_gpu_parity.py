@@ -356,3 +356,43 @@ def test_wavefront_alignment_path(gn, mid_small, band_w, monkeypatch):
     ref = ox.search(sub, oracle.Params(band_w=band_w), threads=os.cpu_count() or 1)
     for i in range(sub.n):
         assert_ranked_equal(res.query(i), ref[i].ranked, f"band {band_w} query {i}")
+
+
+@pytest.mark.parametrize("stride", [11, 1])
+def test_tandem_repeats_equal_qs_groups(gn, stride):
+    """Tandem repeats of a unit whose length is a multiple of the stride: one query stretch
+    hits every copy with the same window phase, so the extended HSPs of many diagonals start
+    at the same query position.  The overlap merge takes such records by (ds, qe); every
+    phase, and the merged order, equals the oracle's."""
+    rng = np.random.default_rng(17)
+    alphabet = np.frombuffer(b"ACGT", dtype=np.uint8)
+    rand = lambda n: alphabet[rng.integers(0, 4, n)].tobytes()
+    unit = rand(66)
+    seqs, queries = [], []
+    for i in range(40):
+        copies = int(rng.integers(3, 9))
+        body = bytearray(unit * copies)
+        for _ in range(int(rng.integers(0, 4))):  # a few point changes between copies
+            body[int(rng.integers(len(body)))] = int(alphabet[rng.integers(0, 4)])
+        seqs.append(rand(int(rng.integers(0, 200))) + bytes(body) + rand(int(rng.integers(0, 200))))
+    seqs += [rand(int(rng.integers(100, 900))) for _ in range(200)]
+    bank = synth.bank_from_strings(seqs)
+    for j in range(12):
+        n_units = int(rng.integers(1, 4))
+        q = bytearray(rand(int(rng.integers(0, 40))) + unit * n_units + rand(int(rng.integers(0, 40))))
+        if j % 3 == 0:
+            q[int(rng.integers(len(q)))] = ord("T")
+        queries.append(bytes(q))
+    qs = synth.queries_from_strings(queries)
+    ix = gn.Index.from_bank(bank, stride=stride)
+    ox = oracle.Index(bank, stride=stride)
+    res = gn.search(ix, qs.start, qs.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
+    ref = ox.search(qs, oracle.Params(stride=stride), threads=os.cpu_count() or 1)
+    check_stages(gn, res, ref, qs.n, f"tandem repeats, stride {stride}")
+    ext = res.stage(gn.GN_STAGE_EXT)
+    keys = {}
+    for r in ext:
+        keys[(int(r["query"]), int(r["seq"]), int(r["q_start"]))] = keys.get(
+            (int(r["query"]), int(r["seq"]), int(r["q_start"])), 0) + 1
+    assert max(keys.values()) >= 3  # groups of equal (query, sequence, qs) did occur
+    ix.close()
