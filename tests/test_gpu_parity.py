@@ -396,3 +396,30 @@ def test_tandem_repeats_equal_qs_groups(gn, stride):
             (int(r["query"]), int(r["seq"]), int(r["q_start"])), 0) + 1
     assert max(keys.values()) >= 3  # groups of equal (query, sequence, qs) did occur
     ix.close()
+
+
+def test_extension_reaches_both_array_starts(gn):
+    """A left extension that runs to position 0 of the packed query array and of the packed
+    bank at once (its last 16-base window starts before both arrays), and a right extension
+    that runs to the end of both: every phase equals the oracle's."""
+    rng = np.random.default_rng(23)
+    alphabet = np.frombuffer(b"ACGT", dtype=np.uint8)
+    rand = lambda n: alphabet[rng.integers(0, 4, n)].tobytes()
+    q = bytearray(rand(700))
+    head = bytearray(q)
+    head[10] = ord("A") if head[10] != ord("A") else ord("C")  # the bank window at 0 misses; the HSP starts at 11
+    tail = bytearray(q[-300:])
+    tail[-5] = ord("G") if tail[-5] != ord("G") else ord("T")
+    seqs = [bytes(head)] + [rand(int(rng.integers(200, 900))) for _ in range(150)] + [bytes(tail)]
+    bank = synth.bank_from_strings(seqs)
+    qs = synth.queries_from_strings([bytes(q), bytes(q[-300:])])
+    for stride in (11, 4):
+        ix = gn.Index.from_bank(bank, stride=stride)
+        ox = oracle.Index(bank, stride=stride)
+        res = gn.search(ix, qs.start, qs.bases, params=gn.make_params(flags=gn.GN_FLAG_KEEP_STAGES))
+        ref = ox.search(qs, oracle.Params(stride=stride), threads=os.cpu_count() or 1)
+        check_stages(gn, res, ref, qs.n, f"array starts, stride {stride}")
+        ext = res.stage(gn.GN_STAGE_EXT)
+        first = ext[(ext["query"] == 0) & (ext["seq"] == 0)]
+        assert len(first) and int(first["q_start"].min()) == 0 and int(first["db_start"].min()) == 0
+        ix.close()
