@@ -3079,6 +3079,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     // a13: duplicates (same query, sequence and ranges: keep the best score), rank by score, statistics
     uint32_t n_out = 0;
     gn_hit *fin = arena.alloc_n<gn_hit>(n_sel);
+    const uint64_t *qoff_dev = nullptr;  // per-query offsets of fin, when a phase computed them
     const char *renv = getenv("GN_RANK_PATH");
     const bool per_query_rank = p.max_alignments != 0 && p.max_alignments <= (uint32_t)RQ_CAP &&
                                 !(renv && strcmp(renv, "sort") == 0);
@@ -3095,6 +3096,7 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         uint64_t *qoff = arena.alloc_n<uint64_t>(nq + 1);
         void *scr = arena.alloc(scan_scratch_bytes(nq));
         exclusive_scan_u32(qcount, qoff, nq, scr, s);
+        qoff_dev = qoff;  // the results' per-query offsets
         uint64_t tot = 0;
         GN_CUDA(cudaMemcpyAsync(&tot, qoff + nq, 8, cudaMemcpyDeviceToHost, s));
         GN_CUDA(cudaStreamSynchronize(s));
@@ -3152,9 +3154,13 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
     GN_REQUIRE((st & DEV_ERR_BOUNDS) == 0, GN_EINTERNAL, "a device-side bounds check failed");
     GN_REQUIRE((st & DEV_ERR_BAND_TOO_WIDE) == 0, GN_ETOOBIG,
                "an alignment band exceeded 65,535 diagonals or its window 2^32 cells");
-    res->qoff.assign(nq + 1, 0);
-    for (uint32_t i = 0; i < n_out; ++i) res->qoff[res->hits[i].query + 1]++;
-    for (uint32_t i = 0; i < nq; ++i) res->qoff[i + 1] += res->qoff[i];
+    if (qoff_dev) {
+        res->qoff = to_host(qoff_dev, nq + 1, s);
+    } else {
+        res->qoff.assign(nq + 1, 0);
+        for (uint32_t i = 0; i < n_out; ++i) res->qoff[res->hits[i].query + 1]++;
+        for (uint32_t i = 0; i < nq; ++i) res->qoff[i + 1] += res->qoff[i];
+    }
     timer.mark("output");
     GN_CUDA(cudaStreamSynchronize(s));
     {
