@@ -263,11 +263,13 @@ __device__ __forceinline__ uint32_t bf_key(uint32_t ent, uint32_t kadd, uint32_t
 // words; the bits inside the word from 5-bit fields of the key itself, which differ
 // between nearby diagonals.
 __device__ __forceinline__ uint32_t bf_hash(uint32_t key) { return key * 0x9E3779B1u; }
+// 1 << (x mod 32) in one funnel shift (the shift amount wraps modulo 32)
+__device__ __forceinline__ uint32_t bit_of(uint32_t x) { return __funnelshift_l(0u, 1u, x); }
 __device__ __forceinline__ uint32_t bf_mask(uint32_t key) {  // "seen": three bits
-    return (1u << (key & 31u)) | (1u << ((key >> 5) & 31u)) | (1u << ((key >> 10) & 31u));
+    return bit_of(key) | bit_of(key >> 5) | bit_of(key >> 10);
 }
 __device__ __forceinline__ uint32_t bf2_mask(uint32_t key) {  // "seen twice": two bits
-    return (1u << ((key >> 15) & 31u)) | (1u << ((key >> 20) & 31u));
+    return bit_of(key >> 15) | bit_of(key >> 20);
 }
 
 // Shared-memory table of a tile's query offsets lo + i, i in [0, span): quad prefix
