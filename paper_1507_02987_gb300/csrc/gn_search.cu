@@ -2665,6 +2665,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                 const double tile_hits = ix->tuning.tile_hits ? (double)ix->tuning.tile_hits : 50000.0;
                 int tpos = 32;
                 while (tpos < 1024 && tpos * 2 * per_offset <= tile_hits * 1.5) tpos *= 2;
+                // a small search (one query, a few) gets smaller tiles, so that its hits are spread
+                // over the SMs instead of filling one or two tiles one after the other
+                while (tpos > 32 && (xb - xa + tpos - 1) / tpos < 4ull * (uint64_t)num_sms()) tpos /= 2;
                 int fthreads = ix->tuning.fill_threads == 256 ? 256 : 512;
                 if (const char *e = getenv("GN_FILL_THREADS")) fthreads = atoi(e) >= 512 ? 512 : 256;
                 // two 512-thread tiles or four 256-thread tiles per SM
