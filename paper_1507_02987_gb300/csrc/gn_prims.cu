@@ -571,6 +571,40 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_os_pass(const uint64_t *__res
     }
 }
 
+// Sorts of at most one tile (n <= RS_TILE) in one launch of one block: each pass ranks the
+// keys by digit in shared memory (the tile's digit order is the sorted order); the next pass
+// ranks a copy of that order, and the last writes it to keys_alt / vals_alt.
+template <bool VALS>
+__global__ void __launch_bounds__(RS_THREADS) k_sort_tile(const uint64_t *__restrict__ keys,
+                                                          uint64_t *__restrict__ keys_alt,
+                                                          const uint32_t *__restrict__ vals,
+                                                          uint32_t *__restrict__ vals_alt, uint32_t n, int bit_lo,
+                                                          int bit_hi) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RsSmem &S = *reinterpret_cast<RsSmem *>(smem_raw);
+    uint64_t *sk = reinterpret_cast<uint64_t *>(smem_raw + ((sizeof(RsSmem) + 15) / 16) * 16);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + RS_TILE);
+    uint64_t *ck = reinterpret_cast<uint64_t *>(sv + RS_TILE);  // copy of the last pass's order
+    uint32_t *cv = reinterpret_cast<uint32_t *>(ck + RS_TILE);
+    for (int shift = bit_lo; shift < bit_hi; shift += 8) {
+        const uint32_t mask = (1u << min(8, bit_hi - shift)) - 1u;
+        if (shift == bit_lo) {
+            rs_rank_tile<VALS>(keys, vals, 0, n, shift, mask, S, sk, sv);
+        } else {
+            for (uint32_t i = threadIdx.x; i < n; i += RS_THREADS) {
+                ck[i] = sk[i];
+                if (VALS) cv[i] = sv[i];
+            }
+            __syncthreads();
+            rs_rank_tile<VALS>(ck, cv, 0, n, shift, mask, S, sk, sv);
+        }
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += RS_THREADS) {
+        keys_alt[i] = sk[i];
+        if (VALS) vals_alt[i] = sv[i];
+    }
+}
+
 static size_t rs_smem_bytes() {
     return ((sizeof(RsSmem) + 15) / 16) * 16 + (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t));
 }
@@ -678,6 +712,23 @@ static bool radix_sort_impl(uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, 
                             int bit_lo, int bit_hi, void *scratch, cudaStream_t s, const RadixTag &tag,
                             uint32_t *status_word, long long budget, int drop_first, bool three_kernel) {
     if (n <= 1 || bit_hi <= bit_lo) return false;
+    if (!three_kernel && n <= RS_TILE) {  // one tile: every pass in one launch of one block
+        const size_t smem = rs_smem_bytes() + (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(uint32_t));
+        static std::once_flag attr_once;
+        std::call_once(attr_once, [smem] {
+            cudaFuncSetAttribute(k_sort_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_sort_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (vals)
+            GN_LAUNCH(tag.down, n, s,
+                      k_sort_tile<true><<<1, RS_THREADS, smem, s>>>(keys, keys_alt, vals, vals_alt, (uint32_t)n, bit_lo,
+                                                                     bit_hi));
+        else
+            GN_LAUNCH(tag.down, n, s,
+                      k_sort_tile<false><<<1, RS_THREADS, smem, s>>>(keys, keys_alt, nullptr, nullptr, (uint32_t)n,
+                                                                      bit_lo, bit_hi));
+        return true;  // the sorted keys are in keys_alt
+    }
     if (!three_kernel && (n + RS_TILE - 1) / RS_TILE <= OS_MAX_TILES && bit_hi - bit_lo <= 8 * OS_MAX_PASSES)
         return radix_sort_onepass(keys, keys_alt, vals, vals_alt, n, bit_lo, bit_hi, scratch, s, tag, status_word,
                                   budget, drop_first);
