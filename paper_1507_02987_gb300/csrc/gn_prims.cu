@@ -809,11 +809,16 @@ __global__ void k_iota(uint32_t *p, uint32_t n) {
     if (i < n) p[i] = i;
 }
 
-__global__ void k_make_keys(const uint32_t *__restrict__ recs, int rec_words, const uint32_t *__restrict__ perm,
-                            uint32_t n, KeyFields f, uint64_t *__restrict__ keys) {
+// keys[i] from the fields of record perm[i]; with first set, perm is the identity and is
+// written here (perm[i] = i).
+__global__ void k_make_keys(const uint32_t *__restrict__ recs, int rec_words, uint32_t *__restrict__ perm,
+                            uint32_t n, KeyFields f, uint64_t *__restrict__ keys, int first) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t *r = recs + (uint64_t)perm[i] * rec_words;
+    uint32_t pi = i;
+    if (first) perm[i] = i;
+    else pi = perm[i];
+    const uint32_t *r = recs + (uint64_t)pi * rec_words;
     uint64_t k = 0;
     for (int j = 0; j < f.n; ++j) {
         uint32_t v = r[f.word[j]];
@@ -832,8 +837,9 @@ void sort_records(const uint32_t *recs, int rec_words, uint32_t n, const std::ve
     uint64_t *keys = arena.alloc_n<uint64_t>(n);
     uint64_t *keys_alt = arena.alloc_n<uint64_t>(n);
     void *scratch = arena.alloc(radix_scratch_bytes(n));
-    GN_LAUNCH("k_iota", n, s, k_iota<<<grid, 256, 0, s>>>(perm, n));
-    // group fields into <= 64-bit keys, least significant group first
+    // group fields into <= 64-bit keys, least significant group first (the first group's key
+    // launch also writes the identity permutation)
+    bool first = true;
     int fi = (int)fields.size() - 1;
     while (fi >= 0) {
         KeyFields kf;
@@ -852,10 +858,12 @@ void sort_records(const uint32_t *recs, int rec_words, uint32_t n, const std::ve
         if (kf.n == 0) throw Error{GN_EINTERNAL, "sort field wider than 64 bits"};
         if (used == 0) continue;
         GN_LAUNCH("k_make_keys", n, s,
-                  k_make_keys<<<grid, 256, 0, s>>>(recs, rec_words, perm, n, kf, keys));
+                  k_make_keys<<<grid, 256, 0, s>>>(recs, rec_words, perm, n, kf, keys, first ? 1 : 0));
+        first = false;
         bool flipped = radix_sort(keys, keys_alt, perm, perm_alt, n, 0, used, scratch, s, TAG_RECORD_SORT);
         if (flipped) std::swap(perm, perm_alt);
     }
+    if (first) GN_LAUNCH("k_iota", n, s, k_iota<<<grid, 256, 0, s>>>(perm, n));  // no field has bits
     if (perm != perm_out) GN_CUDA(cudaMemcpyAsync(perm_out, perm, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
 }
 

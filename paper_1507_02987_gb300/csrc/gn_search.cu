@@ -1164,7 +1164,7 @@ __global__ void k_overlap_sweep(const DevHsp *__restrict__ in, uint32_t n, DevHs
     if (i > 0 && in[i - 1].qi == qi && in[i - 1].seq == seq) return;  // not the head of a run
     uint32_t o = i;  // next box slot
     bool open = false;
-    DevHsp box;
+    DevHsp box{};  // set by the run's first record
     auto visit = [&](const DevHsp &h) {
         if (open && h.qs < box.qe && box.qs < h.qe && h.ds < box.de && box.ds < h.de) {
             box.qs = min(box.qs, h.qs);
@@ -1320,23 +1320,25 @@ __global__ void __launch_bounds__(SQ_THREADS) k_select_query(const DevHsp *__res
     for (uint32_t k = threadIdx.x; k < nsel; k += blockDim.x) sel[out0 + k] = rec[a + (uint32_t)(keys[k] & 0xFFFFFFFFu)];
 }
 
-// first[q] = first record of query q in records sorted by query (first[nq] = n)
-__global__ void k_query_bounds(const DevHsp *__restrict__ rec, uint32_t n, uint32_t nq, uint32_t *__restrict__ first) {
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q > nq) return;
+// first[q] = first record of query q in records sorted by query (first[nq] = n), and, when
+// cnt is given, cnt[q] = min(N, records of query q): the counts of the selected records
+__device__ __forceinline__ uint32_t first_of_query(const DevHsp *__restrict__ rec, uint32_t n, uint32_t q) {
     uint32_t lo = 0, hi = n;  // first index with qi >= q
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         if (rec[mid].qi < q) lo = mid + 1;
         else hi = mid;
     }
-    first[q] = lo;
+    return lo;
 }
 
-// counts of the selected records per query: min(N, records of the query)
-__global__ void k_select_counts(const uint32_t *__restrict__ first, uint32_t nq, uint32_t N, uint32_t *__restrict__ cnt) {
+__global__ void k_query_bounds(const DevHsp *__restrict__ rec, uint32_t n, uint32_t nq, uint32_t *__restrict__ first,
+                               uint32_t N, uint32_t *__restrict__ cnt) {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < nq) cnt[q] = min(N, first[q + 1] - first[q]);
+    if (q > nq) return;
+    const uint32_t f = first_of_query(rec, n, q);
+    first[q] = f;
+    if (cnt && q < nq) cnt[q] = min(N, first_of_query(rec, n, q + 1) - f);
 }
 
 __global__ void k_first_of_query(const uint32_t *__restrict__ recs, int W, uint32_t n, uint32_t *__restrict__ first) {
@@ -2123,39 +2125,33 @@ __global__ void __launch_bounds__(128) k_banded_sw_wide(const DevHsp *__restrict
     }
 }
 
-// Alignment order: key = (65535 - DP-window rows) << 32 | task, so that an ascending
-// sort on bits 32..47 hands out the longest alignments first (they bound the kernel's
-// time) and groups alignments of similar length.
-// Alignments of at least long_rows rows are counted in *n_long (they sort first).
-__global__ void k_sw_order_keys(const DevHsp *__restrict__ h, uint32_t n, int32_t w,
-                                const uint64_t *__restrict__ qstart, uint32_t long_rows, uint64_t *__restrict__ keys,
-                                uint32_t *__restrict__ n_long) {
+// Preparation of the alignment phase, per selected HSP:
+// - the strip length of its band (B + 1), and the band area (DP-window rows x B, the cells
+//   the alignment kernels evaluate) summed into cells[0] (bands of at most 64 diagonals) or
+//   cells[1] (wider bands);
+// - its alignment-order key (65535 - DP-window rows) << 32 | task, so that an ascending sort
+//   on bits 32..47 hands out the longest alignments first (they bound the kernel's time) and
+//   groups alignments of similar length; alignments of at least long_rows rows are counted
+//   in *n_long (they sort first).
+__global__ void k_sw_prepare(const DevHsp *__restrict__ h, uint32_t n, int32_t w, const uint64_t *__restrict__ qstart,
+                             uint32_t *__restrict__ B, unsigned long long *__restrict__ cells, uint32_t long_rows,
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ n_long) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = i < n;
     int64_t rows = 0;
     if (in) {
-        const int64_t m = (int64_t)(qstart[h[i].qi + 1] - qstart[h[i].qi]);
-        rows = min(m, (int64_t)h[i].qe + w) - max((int64_t)0, (int64_t)h[i].qs - w);
+        const DevHsp x = h[i];
+        const int64_t d_s = (int64_t)x.ds - x.qs, d_e = (int64_t)x.de - x.qe;
+        const int64_t b = (max(d_s, d_e) + w) - (min(d_s, d_e) - w) + 1;
+        B[i] = (uint32_t)min(b + 1, (int64_t)65537);  // +1: the strip is read at b + 1
+        const int64_t m = (int64_t)(qstart[x.qi + 1] - qstart[x.qi]);
+        rows = min(m, (int64_t)x.qe + w) - max((int64_t)0, (int64_t)x.qs - w);
+        if (rows > 0) atomicAdd(cells + (b > 64 ? 1 : 0), (unsigned long long)(rows * b));
         const int64_t r = rows < 0 ? 0 : (rows > 65535 ? 65535 : rows);
         keys[i] = ((uint64_t)(65535 - (uint32_t)r) << 32) | i;
     }
     const uint32_t lng = __ballot_sync(0xffffffffu, in && rows >= (int64_t)min(long_rows, 65535u));
     if ((threadIdx.x & 31) == 0 && lng) atomicAdd(n_long, (uint32_t)__popc(lng));
-}
-
-// Strip length of each HSP's band (B + 1), and the band area (DP-window rows x B, the
-// cells the alignment kernels evaluate) summed into cells[0] (bands of at most 64
-// diagonals) or cells[1] (wider bands).
-__global__ void k_band_width(const DevHsp *__restrict__ h, uint32_t n, int32_t w, const uint64_t *__restrict__ qstart,
-                             uint32_t *__restrict__ B, unsigned long long *__restrict__ cells) {
-    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t d_s = (int64_t)h[i].ds - h[i].qs, d_e = (int64_t)h[i].de - h[i].qe;
-    int64_t b = (max(d_s, d_e) + w) - (min(d_s, d_e) - w) + 1;
-    B[i] = (uint32_t)min(b + 1, (int64_t)65537);  // +1: the strip is read at b + 1
-    const int64_t m = (int64_t)(qstart[h[i].qi + 1] - qstart[h[i].qi]);
-    const int64_t rows = min(m, (int64_t)h[i].qe + w) - max((int64_t)0, (int64_t)h[i].qs - w);
-    if (rows > 0) atomicAdd(cells + (b > 64 ? 1 : 0), (unsigned long long)(rows * b));
 }
 
 // ------------------------------------------------------ a13: ranking --
@@ -2982,10 +2978,9 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
                                   max_qlen <= 65535 && !(senv && strcmp(senv, "sort") == 0);
     if (n_mg && per_query_select) {
         uint32_t *qb = arena.alloc_n<uint32_t>(nq + 1);
-        GN_LAUNCH("k_query_bounds", nq + 1, s, k_query_bounds<<<blocks_for(nq + 1), 256, 0, s>>>(merged, n_mg, nq, qb));
         uint32_t *cnt = arena.alloc_n<uint32_t>(nq);
-        GN_LAUNCH("k_select_counts", nq, s,
-                  k_select_counts<<<blocks_for(nq), 256, 0, s>>>(qb, nq, p.max_alignments, cnt));
+        GN_LAUNCH("k_query_bounds", nq + 1, s,
+                  k_query_bounds<<<blocks_for(nq + 1), 256, 0, s>>>(merged, n_mg, nq, qb, p.max_alignments, cnt));
         uint64_t *qo = arena.alloc_n<uint64_t>(nq + 1);
         void *scr = arena.alloc(scan_scratch_bytes(nq));
         exclusive_scan_u32(cnt, qo, nq, scr, s);
@@ -3026,16 +3021,6 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         uint64_t *soff = arena.alloc_n<uint64_t>(n_sel + 1);
         unsigned long long *dp_cells = reinterpret_cast<unsigned long long *>(arena.alloc_n<uint64_t>(2));
         GN_CUDA(cudaMemsetAsync(dp_cells, 0, 16, s));
-        GN_LAUNCH("k_band_width", n_sel, s,
-                  k_band_width<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, B,
-                                                                  dp_cells));
-        void *scr = arena.alloc(scan_scratch_bytes(n_sel));
-        exclusive_scan_u32(B, soff, n_sel, scr, s);
-        uint64_t cells = 0, area[2] = {0, 0};
-        GN_CUDA(cudaMemcpyAsync(&cells, soff + n_sel, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        GN_CUDA(cudaMemcpyAsync(area, dp_cells, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        GN_CUDA(cudaStreamSynchronize(s));
-        SwCell *strips = arena.alloc_n<SwCell>(cells);
         uint64_t *okeys = arena.alloc_n<uint64_t>(n_sel), *okeys_alt = arena.alloc_n<uint64_t>(n_sel);
         // alignments of at least sw_long rows go to the wavefront path (their rows would
         // bound the kernel's time on the grouped path)
@@ -3043,9 +3028,16 @@ void search(gn_index *ix, const uint8_t *qbases_dev, const std::vector<uint64_t>
         if (const char *e = getenv("GN_SW_LONG_ROWS")) sw_long = (uint32_t)std::max(1l, strtol(e, nullptr, 10));
         uint32_t *n_long = arena.alloc_n<uint32_t>(2);
         GN_CUDA(cudaMemsetAsync(n_long, 0, 8, s));
-        GN_LAUNCH("k_sw_order_keys", n_sel, s,
-                  k_sw_order_keys<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, sw_long,
-                                                                    okeys, n_long));
+        GN_LAUNCH("k_sw_prepare", n_sel, s,
+                  k_sw_prepare<<<blocks_for(n_sel), 256, 0, s>>>(sel, n_sel, (int32_t)p.band_w, qstart_d, B, dp_cells,
+                                                                  sw_long, okeys, n_long));
+        void *scr = arena.alloc(scan_scratch_bytes(n_sel));
+        exclusive_scan_u32(B, soff, n_sel, scr, s);
+        uint64_t cells = 0, area[2] = {0, 0};
+        GN_CUDA(cudaMemcpyAsync(&cells, soff + n_sel, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        GN_CUDA(cudaMemcpyAsync(area, dp_cells, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        GN_CUDA(cudaStreamSynchronize(s));
+        SwCell *strips = arena.alloc_n<SwCell>(cells);
         void *rs = arena.alloc(radix_scratch_bytes(n_sel));
         const uint64_t *order = radix_sort(okeys, okeys_alt, nullptr, nullptr, n_sel, 32, 48, rs, s, TAG_RECORD_SORT)
                                     ? okeys_alt : okeys;
