@@ -393,10 +393,11 @@ GN_API gn_status gn_debug_scan(const uint32_t *in, uint64_t *out, uint64_t n, ui
                                void *cuda_stream);
 /* The library's LSD radix sort, for tests: sorts keys (n uint64, device memory) in place,
  * stably, by bits [bit_lo, bit_hi) (8 bits per pass), with vals (n uint32, device memory,
- * or NULL) moved along.  Sorts of up to 2^27 keys take the single-pass form (one
- * histogram launch, then one launch per pass whose blocks wait, with decoupled look-back,
- * for the blocks before them to publish their digit counts); three_kernel = 1 forces the
- * three-kernel passes (upsweep, scan, downsweep) that larger sorts take.  wait_cycles and
+ * or NULL) moved along.  Sorts of at most 4,096 keys run every pass in one launch of one
+ * block; sorts of up to 2^27 keys take the single-pass form (one histogram launch, then
+ * one launch per pass whose blocks wait, with decoupled look-back, for the blocks before
+ * them to publish their digit counts); three_kernel = 1 forces the three-kernel passes
+ * (upsweep, scan, downsweep) that larger sorts take.  wait_cycles and
  * drop_first (the first tile of 4,096 keys publishes nothing) as in gn_debug_scan.
  * Errors: GN_EINVAL (keys NULL with n > 0, bits outside 0 <= bit_lo <= bit_hi <= 64),
  * GN_ETOOBIG (n >= 2^32), GN_ENOMEM, GN_ETIMEOUT if a wait ran out (the keys are then
